@@ -1,0 +1,330 @@
+"""Benchmark of the chaos-game hot path on GB300.
+
+One step = one frame of the composed 2D/3D scene (square primitive +
+Sierpinski triangle, 2^22 points x 500 steps, burn-in 20; rotate/swirl/
+sinusoidal into a 2048^2 FP32 RGBA layer and torus/perspective into a 2048^2
+packed depth+colour layer): clear both layers, then the two render launches.
+Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cfs|reference]
+
+N > 1 (under torchrun): every rank renders its own frame (its own range of
+point indices), no collective on the data path; value = point-steps of all
+ranks / max time over ranks (weak scaling).  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_02226_gb300 import workloads as W  # noqa: E402
+
+METRIC = "point-steps/s (iterate+splat) on 1 GB300"
+UNIT = "point-steps/s"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic cost model of one point-step of the composed scene
+# ---------------------------------------------------------------------------
+# Splat traffic per point-step after burn-in: one 16-byte FP32 RGBA vector
+# reduction and one 8-byte depth+colour key (read, then a 64-bit minimum when
+# it is lower).  These are the L2 operations the splat roofline counts.
+SPLAT_BYTES_PER_SPLAT_STEP = 16 + 8
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+def _oracle_sample(wl, n_per_job: int):
+    """Oracle render of the first n_per_job points of each job (all 500
+    steps); returns (point-steps, seconds)."""
+    from oracle import oracle as O
+    bufs = [O.alloc_target_buffer(t) for t in wl.targets]
+    t0 = time.perf_counter()
+    for job in wl.jobs:
+        O.render(job.system, wl.chain, wl.targets, n_points=n_per_job, iters=wl.iters,
+                 burn_in=wl.burn_in, seed=wl.seed, system_id=job.system_id,
+                 point_begin=job.point_begin, bufs=bufs)
+    dt = time.perf_counter() - t0
+    return n_per_job * len(wl.jobs) * wl.iters, dt
+
+
+def cpu_baseline(wl, target_s: float = 10.0):
+    """The oracle as it stands, single-threaded, on a bounded sample sized to
+    about target_s seconds of CPU work."""
+    ps, dt = _oracle_sample(wl, 64)
+    rate = ps / dt
+    n = int(max(64, min(wl.jobs[0].n_points, target_s * rate / (len(wl.jobs) * wl.iters))))
+    ps, dt = _oracle_sample(wl, n)
+    return {"value": ps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} points of each of the {len(wl.jobs)} objects, all "
+                      f"{wl.iters} steps ({ps} point-steps, {dt:.1f} s, 1 thread)"}
+
+
+def run_reference(args, wl):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    O.build()
+    n = 512          # points per object per step: a bounded sample (about a second)
+    for _ in range(args.warmup):
+        _oracle_sample(wl, n)
+    tot_ps, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        ps, dt = _oracle_sample(wl, n)
+        tot_ps += ps
+        tot_s += dt
+    value = tot_ps / tot_s
+    sample = (f"per step: first {n} points of each of the {len(wl.jobs)} objects, all "
+              f"{wl.iters} steps, 1 thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(wl):
+    n = sum(j.n_points for j in wl.jobs)
+    return {"workload": "composed square+Sierpinski; rotate 0.7/swirl/sinusoidal -> 2048^2 "
+                        "RGBA f32; torus/perspective -> 2048^2 depth+colour u64",
+            "points": n, "iters": wl.iters, "burn_in": wl.burn_in,
+            "resolution": wl.targets[0].W, "seed": wl.seed,
+            "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_cfs(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_02226_gb300 import cfs
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    n_total = sum(j.n_points for j in wl.jobs)
+    jobs = [W.RenderJob(j.system, j.point_begin + rank * n_total, j.n_points, j.system_id)
+            for j in wl.jobs]
+    systems = [cfs.System(j.system) for j in jobs]
+    chain = cfs.Chain(wl.chain, 2)
+    targets = [cfs.alloc_target(t, device=dev) for t in wl.targets]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for s in systems:
+        cfs.prepare(s, chain, wl.targets, targets)      # compile outside the timed region
+
+    def render_frame():
+        cfs.target_clear(wl.targets, targets, stream)
+        for s, j in zip(systems, jobs):
+            cfs.render(s, chain, wl.targets, targets, n_points=j.n_points, iters=wl.iters,
+                       burn_in=wl.burn_in, seed=wl.seed, system_id=j.system_id,
+                       point_begin=j.point_begin, stream=stream)
+
+    for _ in range(args.warmup):
+        render_frame()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(K):
+        flush.fill_(k & 0xFF)                           # L2 flush, outside the timed step
+        e0, e1, e2 = ev[k]
+        e0.record(stream)
+        cfs.target_clear(wl.targets, targets, stream)
+        e1.record(stream)
+        for s, j in zip(systems, jobs):
+            cfs.render(s, chain, wl.targets, targets, n_points=j.n_points, iters=wl.iters,
+                       burn_in=wl.burn_in, seed=wl.seed, system_id=j.system_id,
+                       point_begin=j.point_begin, stream=stream)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    render_ms = [b.elapsed_time(c) for a, b, c in ev]
+    mean_step = sum(step_ms) / K
+    mean_render = sum(render_ms) / K
+    t_local = torch.tensor([mean_step, mean_render], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    mean_step, mean_render = float(t_local[0]), float(t_local[1])
+    value = world * wl.point_steps / (mean_step * 1e-3)
+
+    # ---- end to end through the public API with host buffers ------------
+    e2e = None
+    host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in targets]
+    d2h = sum(h.numel() * h.element_size() for h in host)
+    torch.cuda.synchronize()
+    n_e2e = max(2, min(K, 5))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ss = [cfs.System(j.system) for j in jobs]        # inputs handed over from the host
+        ch = cfs.Chain(wl.chain, 2)
+        cfs.target_clear(wl.targets, targets, stream)
+        for s, j in zip(ss, jobs):
+            cfs.render(s, ch, wl.targets, targets, n_points=j.n_points, iters=wl.iters,
+                       burn_in=wl.burn_in, seed=wl.seed, system_id=j.system_id,
+                       point_begin=j.point_begin, stream=stream)
+        for h, t in zip(host, targets):
+            h.copy_(t, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e = {"value": wl.point_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": d2h,
+           "note": "system and chain built from host descriptions and passed through the C "
+                   "ABI each step (parameters travel in the launch); both layers read back "
+                   "to pinned host memory"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = _peaks()
+    # dominant kernel: the render launches (two per step)
+    launch_ms = mean_render / len(jobs)
+    splat_steps_per_launch = wl.splat_steps / len(jobs)
+    achieved_bytes = SPLAT_BYTES_PER_SPLAT_STEP * splat_steps_per_launch / (launch_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": mean_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(wl),
+            "render_ms_per_launch": launch_ms,
+            "splats_per_s": 2 * world * wl.splat_steps / (mean_step * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": achieved_bytes / 1e9,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved_bytes / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": peak_src, "kernel": "cfs_render_kernel",
+                         "note": "provisional"},
+            "e2e": e2e, "gpu_launches": len(jobs) * K, "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, target_s=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cfs", choices=["cfs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    wl = W.composed_render()
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_cfs(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * cfs.h -- C ABI of libcfs, the GB300 (sm_103a) chaos-game renderer for
+ * composable function systems (Schloss, "Composable function systems as a
+ * general-purpose rendering framework").
+ *
+ * The library runs the chaos game of Section 1 / Section 3 on the GPU: every
+ * point starts at a random position; every step it draws one map of an
+ * iterated function system with that map's probability and applies it; after
+ * burn-in a copy of the point goes through a composed chain of spatial
+ * transforms (Fig. 1, Fig. 2B) and is splatted into caller-owned device
+ * buffers.  The generator maps and the chain are compiled together into one
+ * fused kernel at run time (NVRTC), so no map or transform is called through
+ * a function pointer.
+ *
+ * Conventions (every entry point):
+ *  - Return value: CFS_OK (0) or an error code; cfs_last_error() returns a
+ *    thread-local message for the last failure on the calling thread.
+ *  - Argument errors are reported synchronously and nothing is launched.
+ *  - Handles (cfs_system, cfs_chain) are owned by the library from create to
+ *    destroy; destroying a handle while work that uses it is still queued is
+ *    allowed (launch arguments are copied at launch time).
+ *  - Device buffers (targets, start points, counters, clouds) are owned by
+ *    the caller; the library never frees them and never allocates outputs.
+ *  - All GPU work is enqueued on the caller's stream (a cudaStream_t passed
+ *    as void*; NULL = the legacy default stream) and returns without waiting.
+ *  - Rendering ACCUMULATES into targets; clear them with cfs_target_clear.
+ *  - The current CUDA device of the calling thread is the one used.
+ *
+ * Randomness: Philox4x32-10 (Salmon et al., SC'11) with key (seed low 32 bits,
+ * seed high 32 bits); step n of point i of system s uses word n & 3 of the
+ * block for counter (i, n >> 2, s, 0); the start point uses counter
+ * (i, 0, s, 1), coordinate j = (word_j >> 8) * 2^-24.  Results therefore do
+ * not depend on the launch configuration.
+ */
+#ifndef CFS_H
+#define CFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CFS_OK = 0,
+    CFS_ERR_INVALID_ARG = 1,
+    CFS_ERR_UNSUPPORTED = 2,
+    CFS_ERR_COMPILE = 3,   /* NVRTC failed; the log is in cfs_last_error() */
+    CFS_ERR_CUDA = 4,      /* a CUDA runtime/driver call failed */
+    CFS_ERR_OOM = 5,
+    CFS_ERR_TIMEOUT = 6
+} cfs_status;
+
+#define CFS_MAX_MAPS 16
+#define CFS_MAX_OPS 32
+#define CFS_MAX_TARGETS 4
+#define CFS_OP_PARAMS 16
+
+/* ---- generator maps (Section 1: f_1 .. f_n of an IFS) -------------------- */
+typedef enum {
+    /* Affine map.  2D params: a b c d e f with x' = a x + b y + e,
+     * y' = c x + d y + f, evaluated as fma(a, x, fma(b, y, e)).  3D params:
+     * row-major A (9 floats) then b (3). */
+    CFS_MAP_AFFINE = 0,
+    /* Non-affine circle map of Eq. 1 (2D only), params[0] = f_id (0 or 1):
+     * theta = atan2(y, x) in [0, 2 pi), r = |p|, theta2 = pi (r + f_id),
+     * r2 = sqrt(theta / 2 pi), p' = r2 (cos theta2, sin theta2). */
+    CFS_MAP_CIRCLE = 1
+} cfs_map_kind;
+
+typedef struct {
+    int32_t kind;        /* cfs_map_kind */
+    float params[12];
+} cfs_map;
+
+/* ---- transform chain ops (Section 3: human-readable spatial functions
+ *      applied to a copy of the iterated point, Fig. 1, Fig. 2B) ----------- */
+typedef enum {
+    CFS_OP_AFFINE2 = 1,      /* a b c d e f (as CFS_MAP_AFFINE)                  */
+    CFS_OP_AFFINE3 = 2,      /* A (row-major 9) then b (3)                        */
+    CFS_OP_ROTATE2 = 3,      /* angle: affine with (float)cos, (float)sin of the
+                                angle evaluated in double                         */
+    CFS_OP_ROTATE3 = 4,      /* angle, axis (0 = x, 1 = y, 2 = z)                 */
+    CFS_OP_TRANSLATE3 = 5,   /* tx ty tz                                          */
+    CFS_OP_SWIRL = 6,        /* (x sin r^2 - y cos r^2, x cos r^2 + y sin r^2)    */
+    CFS_OP_SINUSOIDAL = 7,   /* (sin x, sin y)                                    */
+    CFS_OP_SINUSOIDAL3 = 8,  /* (sin x, sin y, sin z)                             */
+    CFS_OP_STRETCH = 9,      /* Eq. 2: (2 x, y - cos x)                           */
+    CFS_OP_TORUS = 10,       /* R, r: (u, v) -> ((R + r cos 2pi v) cos 2pi u,
+                                (R + r cos 2pi v) sin 2pi u, r sin 2pi v); lifts
+                                2D to 3D                                          */
+    CFS_OP_PERSPECTIVE = 11, /* focal, near: (f x / z, f y / z, z); discards the
+                                point unless z > near                             */
+    CFS_OP_TWIST_Z = 12,     /* kappa: rotate (x, y) by kappa z                   */
+    CFS_OP_BEND = 13,        /* beta: x' = sin(beta x)(1/beta - z),
+                                z' = 1/beta - cos(beta x)(1/beta - z)             */
+    CFS_OP_INVERSION = 14,   /* cx cy cz rho: c + rho^2 (p - c) / |p - c|^2;
+                                discards when |p - c|^2 < 1e-12                   */
+    CFS_OP_SPLAT = 15,       /* params[0] = target slot: splat the current point */
+    CFS_OP_RESET = 16        /* start a new branch from a fresh copy of the
+                                iterated point                                    */
+} cfs_op_kind;
+
+typedef struct {
+    int32_t kind;        /* cfs_op_kind */
+    float params[CFS_OP_PARAMS];
+} cfs_transform;
+
+/* ---- output targets (Section 1: "histogrammed or splatted on to some output
+ *      layer"; the colour is the map used to land) ------------------------- */
+typedef enum {
+    /* u32 [C][H][W]; +1 in channel (k mod C), k = last generator map */
+    CFS_TARGET_HIST_U32 = 0,
+    /* f32 [H][W][4]; += palette[k] (vector reduction) */
+    CFS_TARGET_RGBA_F32 = 1,
+    /* u64 [H][W]; min= (float bits of depth z) << 32 | palette8[k]; the empty
+     * value is all ones; needs a 3D point at the splat */
+    CFS_TARGET_DEPTH_U64 = 2
+} cfs_target_kind;
+
+typedef struct {
+    int32_t kind;                 /* cfs_target_kind */
+    int32_t width, height, channels;
+    /* view window: x in [x0, x1] -> columns, y in [y0, y1] -> rows; bin
+     * ix = floor((x - x0) * (W / (x1 - x0))) in FP32, last bin closed; points
+     * outside the window are discarded (and counted) */
+    float x0, x1, y0, y1;
+    void* data;                   /* device pointer, 16-byte aligned */
+    float palette[CFS_MAX_MAPS][4];   /* RGBA colours per map index */
+    uint32_t palette8[CFS_MAX_MAPS];  /* packed RGBA8 per map index (depth) */
+} cfs_target;
+
+/* ---- render parameters -------------------------------------------------- */
+#define CFS_FLAG_REUSE 1u   /* Fig. 2C: the chain's result replaces the point */
+
+typedef struct {
+    uint64_t seed;
+    uint32_t system_id;    /* Philox counter word 2 */
+    uint32_t point_begin;  /* global index of the first point (counter word 0) */
+    uint32_t n_points;
+    uint32_t step_begin;   /* first step index n run (0 for a fresh start) */
+    uint32_t iters;        /* steps n = step_begin .. iters-1 are run */
+    uint32_t burn_in;      /* steps n < burn_in are not splatted */
+    uint32_t flags;        /* CFS_FLAG_* */
+    /* optional device SoA start points, [dim][n_points] floats (point j of
+     * this call at start[d * n_points + j]); NULL = Philox start point */
+    const float* start;
+    /* optional device u64 [n_targets]: discarded splats per target are ADDED
+     * here (splats + discards = n_points * (iters - max(step_begin, burn_in))) */
+    unsigned long long* discards;
+} cfs_render_params;
+
+typedef struct cfs_system cfs_system;
+typedef struct cfs_chain cfs_chain;
+
+/* Creates an IFS (Section 1): `n_maps` maps (1..16) of dimension `dim` (2|3)
+ * with probabilities `probs` (>= 0, finite, positive sum; normalised here).
+ * The threshold table is T_k = floor(S_k 2^32), S_k = (sum_{j<=k} p_j)/sum p
+ * in double; map k = #{j < n-1 : w >= T_j}.  All pointers are host pointers
+ * and are copied. */
+cfs_status cfs_system_create(int dim, int n_maps, const cfs_map* maps, const double* probs,
+                             cfs_system** out);
+cfs_status cfs_system_destroy(cfs_system* sys);
+
+/* Composes a transform chain (Section 3, Fig. 2B) for points of dimension
+ * `dim_in` (the generator's).  Validates dimensions (3D ops need a 3D point;
+ * TORUS lifts 2D to 3D), derives the per-op constants and keeps a host copy;
+ * the fused kernel is generated and compiled (NVRTC, cached by structure) at
+ * the first render that uses it, or ahead of time by cfs_prepare. */
+cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chain** out);
+cfs_status cfs_chain_destroy(cfs_chain* chain);
+/* Replaces the parameters of op `index` (same kind); for animated chains. */
+cfs_status cfs_chain_set_params(cfs_chain* chain, int index, const float* params);
+
+/* Runs the chaos game (Section 1, Section 3) for points point_begin ..
+ * point_begin + n_points - 1 and splats into `targets` (device buffers of
+ * the caller; at most CFS_MAX_TARGETS; the chain's SPLAT ops name slots in
+ * this array).  Enqueued on `stream`. */
+cfs_status cfs_render(const cfs_system* sys, const cfs_chain* chain,
+                      const cfs_render_params* params, const cfs_target* targets,
+                      int n_targets, void* stream);
+
+/* Compiles (or finds in the cache) the fused kernel a cfs_render with these
+ * arguments would use, without launching; lets callers keep compilation out
+ * of timed or captured regions. */
+cfs_status cfs_prepare(const cfs_system* sys, const cfs_chain* chain,
+                       const cfs_target* targets, int n_targets);
+
+/* Records, for the n_ids points listed in the device array `ids` (global
+ * indices), every step's map index (device i32 [n_ids][steps]), iterated
+ * point (device f32 [n_ids][steps][3]) and, per SPLAT op of the chain, the
+ * point reaching it (device f32 [n_ids][steps][n_splat_ops][4]: x y z alive),
+ * steps = iters - step_begin.  The same generated step code as cfs_render;
+ * nothing is splatted.  `params->start`, if set, holds [dim][n_ids]. */
+cfs_status cfs_trace(const cfs_system* sys, const cfs_chain* chain,
+                     const cfs_render_params* params, const uint32_t* ids, uint32_t n_ids,
+                     int32_t* k_out, float* p_out, float* q_out, void* stream);
+
+/* Debugging aid, needs no GPU: writes the CUDA source of the fused program
+ * that cfs_render (mode 0) or cfs_trace (mode 1) would use into `src` (at most
+ * src_cap bytes, NUL-terminated), compiles it with NVRTC for sm_103a and
+ * writes the compiler log, including ptxas register/spill usage, into `log`.
+ * Either buffer may be NULL. */
+cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
+                             const cfs_target* targets, int n_targets, int mode, char* src,
+                             size_t src_cap, char* log, size_t log_cap);
+
+/* Fills targets with their empty value (0; depth: all ones). */
+cfs_status cfs_target_clear(const cfs_target* targets, int n_targets, void* stream);
+
+/* Philox4x32-10 of n (counter, key) pairs: ctr device u32 [n][4], key device
+ * u32 [n][2], out device u32 [n][4]. */
+cfs_status cfs_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, uint32_t n,
+                      void* stream);
+
+/* Atomic-throughput microbenchmark of the splat operations (the roofline of
+ * the splat path): `blocks` x 256 threads each issue `iters` reductions at
+ * uniformly random element indices of `buf` (device, n_elems elements, a
+ * power of two): kind 0 = red.add.u32 (4-byte elements), 1 =
+ * red.add.v4.f32 (16-byte), 2 = red.min.u64 (8-byte), 3 = strong u64 load
+ * then red.min.u64 when it lowers the value seen (the depth test).  The
+ * caller times it on `stream`; contents of buf are overwritten. */
+cfs_status cfs_atomic_bench(int kind, void* buf, uint64_t n_elems, uint32_t blocks,
+                            uint32_t iters, uint32_t seed, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cfs_last_error(void);
+
+/* Library version string. */
+const char* cfs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFS_H */

@@ -1,0 +1,351 @@
+"""Thin Python binding of ``libcfs.so`` (declared in ``include/cfs.h``).
+
+Argument marshalling only: every step of the chaos game runs in the library's
+CUDA kernels.  Device buffers are torch tensors; streams are torch streams.
+There is no CPU fallback: if the library cannot be built or loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+MAX_MAPS = 16
+MAX_OPS = 32
+MAX_TARGETS = 4
+OP_PARAMS = 16
+
+MAP_KINDS = {"affine": 0, "circle": 1}
+OP_KINDS = {
+    "affine2": 1, "affine3": 2, "rotate2": 3, "rotate3": 4, "translate3": 5, "swirl": 6,
+    "sinusoidal": 7, "sinusoidal3": 8, "stretch": 9, "torus": 10, "perspective": 11,
+    "twist_z": 12, "bend": 13, "inversion": 14, "splat": 15, "reset": 16,
+}
+TARGET_KINDS = {"hist_u32": 0, "rgba_f32": 1, "depth_u64": 2}
+FLAG_REUSE = 1
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "COMPILE", 4: "CUDA", 5: "OOM",
+          6: "TIMEOUT"}
+
+
+class CfsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cfs {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class cfs_map(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("params", ctypes.c_float * 12)]
+
+
+class cfs_transform(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("params", ctypes.c_float * OP_PARAMS)]
+
+
+class cfs_target(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("x0", ctypes.c_float), ("x1", ctypes.c_float),
+                ("y0", ctypes.c_float), ("y1", ctypes.c_float),
+                ("data", ctypes.c_void_p),
+                ("palette", (ctypes.c_float * 4) * MAX_MAPS),
+                ("palette8", ctypes.c_uint32 * MAX_MAPS)]
+
+
+class cfs_render_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("system_id", ctypes.c_uint32),
+                ("point_begin", ctypes.c_uint32), ("n_points", ctypes.c_uint32),
+                ("step_begin", ctypes.c_uint32), ("iters", ctypes.c_uint32),
+                ("burn_in", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("start", ctypes.c_void_p), ("discards", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "cfs_system_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(cfs_map),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(_P)]),
+    "cfs_system_destroy": (ctypes.c_int, [_P]),
+    "cfs_compose": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cfs_transform), ctypes.c_int,
+                                   ctypes.POINTER(_P)]),
+    "cfs_chain_destroy": (ctypes.c_int, [_P]),
+    "cfs_chain_set_params": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+    "cfs_render": (ctypes.c_int, [_P, _P, ctypes.POINTER(cfs_render_params),
+                                  ctypes.POINTER(cfs_target), ctypes.c_int, _P]),
+    "cfs_prepare": (ctypes.c_int, [_P, _P, ctypes.POINTER(cfs_target), ctypes.c_int]),
+    "cfs_trace": (ctypes.c_int, [_P, _P, ctypes.POINTER(cfs_render_params), _P,
+                                 ctypes.c_uint32, _P, _P, _P, _P]),
+    "cfs_codegen_check": (ctypes.c_int, [_P, _P, ctypes.POINTER(cfs_target), ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t,
+                                         ctypes.c_char_p, ctypes.c_size_t]),
+    "cfs_target_clear": (ctypes.c_int, [ctypes.POINTER(cfs_target), ctypes.c_int, _P]),
+    "cfs_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P]),
+    "cfs_atomic_bench": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.c_uint32, _P]),
+    "cfs_last_error": (ctypes.c_char_p, []),
+    "cfs_version": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Builds (if needed) and loads libcfs.so; raises if that fails."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().cfs_last_error().decode(errors="replace")
+        raise CfsError(status, msg)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+class System:
+    """An IFS (Section 1): maps with probabilities.  ``desc`` has ``.dim``,
+    ``.maps`` (``.kind``, ``.params``) and ``.probs``."""
+
+    def __init__(self, desc):
+        n = len(desc.maps)
+        maps = (cfs_map * max(n, 1))()
+        for j, m in enumerate(desc.maps):
+            maps[j].kind = MAP_KINDS[m.kind]
+            for q, v in enumerate(m.params):
+                maps[j].params[q] = float(v)
+        probs = (ctypes.c_double * max(n, 1))(*[float(p) for p in desc.probs])
+        h = _P()
+        _check(lib().cfs_system_create(desc.dim, n, maps, probs, ctypes.byref(h)))
+        self.handle = h
+        self.dim = desc.dim
+        self.n_maps = n
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _LIB is not None:
+            _LIB.cfs_system_destroy(h)
+            self.handle = None
+
+
+def _transforms(ops) -> Tuple[ctypes.Array, int]:
+    n = len(ops)
+    arr = (cfs_transform * max(n, 1))()
+    for j, o in enumerate(ops):
+        arr[j].kind = OP_KINDS[o.kind]
+        for q, v in enumerate(o.params):
+            arr[j].params[q] = float(v)
+    return arr, n
+
+
+class Chain:
+    """A composed transform chain (Section 3, Fig. 2B) for points of
+    dimension ``dim_in``; ``ops`` are ``.kind`` / ``.params`` records."""
+
+    def __init__(self, ops, dim_in: int):
+        arr, n = _transforms(ops)
+        h = _P()
+        _check(lib().cfs_compose(dim_in, arr, n, ctypes.byref(h)))
+        self.handle = h
+        self.ops = list(ops)
+        self.dim_in = dim_in
+        self.n_splat = sum(1 for o in ops if o.kind == "splat")
+
+    def set_params(self, index: int, params: Sequence[float]):
+        buf = (ctypes.c_float * OP_PARAMS)(*([float(v) for v in params] +
+                                             [0.0] * (OP_PARAMS - len(params))))
+        _check(lib().cfs_chain_set_params(self.handle, index, buf))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _LIB is not None:
+            _LIB.cfs_chain_destroy(h)
+            self.handle = None
+
+
+# ---------------------------------------------------------------------------
+# targets
+# ---------------------------------------------------------------------------
+def target_shape(desc) -> Tuple[Tuple[int, ...], str]:
+    if desc.kind == "hist_u32":
+        return (desc.C, desc.H, desc.W), "int32"
+    if desc.kind == "rgba_f32":
+        return (desc.H, desc.W, 4), "float32"
+    if desc.kind == "depth_u64":
+        return (desc.H, desc.W), "int64"
+    raise ValueError(desc.kind)
+
+
+def alloc_target(desc, device="cuda"):
+    """A device tensor for ``desc`` (u32 histograms and u64 depth keys live in
+    int32 / int64 tensors of the same bytes), cleared to the empty value."""
+    import torch
+    shape, dt = target_shape(desc)
+    t = torch.empty(shape, dtype=getattr(torch, dt), device=device)
+    if desc.kind == "depth_u64":
+        t.fill_(-1)
+    else:
+        t.zero_()
+    return t
+
+
+def make_targets(descs, tensors=None, fake_ptr: bool = False):
+    n = len(descs)
+    if n > MAX_TARGETS:
+        raise ValueError("at most 4 targets")
+    arr = (cfs_target * max(n, 1))()
+    for j, d in enumerate(descs):
+        t = arr[j]
+        t.kind = TARGET_KINDS[d.kind]
+        t.width, t.height = d.W, d.H
+        t.channels = d.C if d.kind == "hist_u32" else 1
+        t.x0, t.x1, t.y0, t.y1 = [float(v) for v in d.view]
+        if fake_ptr:
+            t.data = 256
+        else:
+            tt = tensors[j]
+            if not tt.is_cuda or not tt.is_contiguous():
+                raise ValueError("targets must be contiguous CUDA tensors")
+            shape, _ = target_shape(d)
+            if tuple(tt.shape) != shape:
+                raise ValueError(f"target {j}: shape {tuple(tt.shape)} != {shape}")
+            t.data = tt.data_ptr()
+        if getattr(d, "palette", None) is not None:
+            p = np.asarray(d.palette, dtype=np.float32)
+            for k in range(min(MAX_MAPS, p.shape[0])):
+                for c in range(4):
+                    t.palette[k][c] = float(p[k, c])
+        if getattr(d, "palette8", None) is not None:
+            p8 = np.asarray(d.palette8, dtype=np.uint32)
+            for k in range(min(MAX_MAPS, p8.shape[0])):
+                t.palette8[k] = int(p8[k])
+    return arr, n
+
+
+def target_clear(descs, tensors, stream=None):
+    arr, n = make_targets(descs, tensors)
+    _check(lib().cfs_target_clear(arr, n, _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# calls
+# ---------------------------------------------------------------------------
+def _params(*, seed, system_id, point_begin, n_points, step_begin, iters, burn_in, flags,
+            start, discards):
+    p = cfs_render_params()
+    p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    p.system_id, p.point_begin, p.n_points = int(system_id), int(point_begin), int(n_points)
+    p.step_begin, p.iters, p.burn_in, p.flags = int(step_begin), int(iters), int(burn_in), flags
+    p.start = start.data_ptr() if start is not None else None
+    p.discards = discards.data_ptr() if discards is not None else None
+    return p
+
+
+def render(system: System, chain: Chain, target_descs, target_tensors, *, n_points: int,
+           iters: int, burn_in: int, seed: int = 0, system_id: int = 0, point_begin: int = 0,
+           step_begin: int = 0, reuse: bool = False, start=None, discards=None, stream=None):
+    """Enqueues the chaos game for points point_begin .. +n_points on
+    ``stream`` (default: torch's current stream).  ``start``: optional device
+    float32 [dim, n_points]; ``discards``: optional device int64
+    [n_targets] to which discarded splats are added."""
+    arr, n = make_targets(target_descs, target_tensors)
+    if start is not None:
+        assert start.is_cuda and start.is_contiguous() and start.shape == (system.dim, n_points)
+    if discards is not None:
+        assert discards.is_cuda and discards.numel() >= n
+    p = _params(seed=seed, system_id=system_id, point_begin=point_begin, n_points=n_points,
+                step_begin=step_begin, iters=iters, burn_in=burn_in,
+                flags=FLAG_REUSE if reuse else 0, start=start, discards=discards)
+    _check(lib().cfs_render(system.handle, chain.handle, ctypes.byref(p), arr, n,
+                            _stream_handle(stream)))
+
+
+def prepare(system: System, chain: Chain, target_descs, target_tensors):
+    arr, n = make_targets(target_descs, target_tensors)
+    _check(lib().cfs_prepare(system.handle, chain.handle, arr, n))
+
+
+def trace(system: System, chain: Chain, ids, *, iters: int, seed: int = 0, system_id: int = 0,
+          step_begin: int = 0, burn_in: int = 0, reuse: bool = False, start=None, stream=None):
+    """Per-step map index, point and chain inputs of the points in ``ids``
+    (device uint32/int32 tensor); returns device tensors k [n, steps],
+    p [n, steps, 3], q [n, steps, n_splat, 4]."""
+    import torch
+    n = int(ids.numel())
+    steps = iters - step_begin
+    n_sp = max(1, chain.n_splat)
+    dev = ids.device
+    k = torch.empty((n, steps), dtype=torch.int32, device=dev)
+    p = torch.empty((n, steps, 3), dtype=torch.float32, device=dev)
+    q = torch.empty((n, steps, n_sp, 4), dtype=torch.float32, device=dev)
+    prm = _params(seed=seed, system_id=system_id, point_begin=0, n_points=n,
+                  step_begin=step_begin, iters=iters, burn_in=burn_in,
+                  flags=FLAG_REUSE if reuse else 0, start=start, discards=None)
+    _check(lib().cfs_trace(system.handle, chain.handle, ctypes.byref(prm), ids.data_ptr(), n,
+                           k.data_ptr(), p.data_ptr(), q.data_ptr(), _stream_handle(stream)))
+    return k, p, q
+
+
+def philox(ctr, key, stream=None):
+    """Philox4x32-10 on the GPU: ctr int32 [n, 4], key int32 [n, 2] device
+    tensors (bit patterns of u32) -> int32 [n, 4]."""
+    import torch
+    n = ctr.shape[0]
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    _check(lib().cfs_philox(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), n,
+                            _stream_handle(stream)))
+    return out
+
+
+def atomic_bench(kind: int, buf, n_elems: int, blocks: int, iters: int, seed: int = 1,
+                 stream=None):
+    """Enqueues the atomic microbenchmark (see include/cfs.h) on ``stream``."""
+    _check(lib().cfs_atomic_bench(kind, buf.data_ptr(), n_elems, blocks, iters, seed,
+                                  _stream_handle(stream)))
+
+
+def codegen_check(system: System, chain: Chain, target_descs, mode: int = 0,
+                  cap: int = 1 << 20) -> Tuple[str, str]:
+    """Generated source and NVRTC log (ptxas usage) of the fused program; no
+    GPU needed."""
+    arr, n = make_targets(target_descs, fake_ptr=True)
+    src = ctypes.create_string_buffer(cap)
+    log = ctypes.create_string_buffer(cap)
+    st = lib().cfs_codegen_check(system.handle, chain.handle, arr, n, mode, src, cap, log, cap)
+    if st != 0:
+        raise CfsError(st, lib().cfs_last_error().decode(errors="replace"))
+    return src.value.decode(), log.value.decode()
+
+
+def version() -> str:
+    return lib().cfs_version().decode()

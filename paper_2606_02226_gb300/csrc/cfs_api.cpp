@@ -1,0 +1,479 @@
+// cfs_api.cpp -- the extern "C" entry points of libcfs (include/cfs.h).
+//
+// Host work only: argument validation, the threshold table, per-op
+// constants, the kernel argument block, and launches of the generated
+// programs on the caller's stream.  Every step of the chaos game itself runs
+// in the generated CUDA kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <sstream>
+
+#include "cfs_internal.h"
+
+namespace cfs {
+const char* last_error();
+
+void philox_round_keys(uint64_t seed, unsigned int rk[10][2])
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[r][0] = k0;
+        rk[r][1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+void derive_op_params(const cfs_transform& op, float out[CFS_OP_PARAMS])
+{
+    std::memset(out, 0, sizeof(float) * CFS_OP_PARAMS);
+    const float* v = op.params;
+    switch (op.kind) {
+    case CFS_OP_ROTATE2: {
+        const float c = (float)std::cos((double)v[0]), s = (float)std::sin((double)v[0]);
+        out[0] = c; out[1] = -s; out[2] = s; out[3] = c;
+        break;
+    }
+    case CFS_OP_ROTATE3: {
+        const float c = (float)std::cos((double)v[0]), s = (float)std::sin((double)v[0]);
+        float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        const int axis = (int)v[1];
+        if (axis == 0) { R[4] = c; R[5] = -s; R[7] = s; R[8] = c; }
+        else if (axis == 1) { R[0] = c; R[2] = s; R[6] = -s; R[8] = c; }
+        else { R[0] = c; R[1] = -s; R[3] = s; R[4] = c; }
+        std::memcpy(out, R, sizeof(R));
+        break;
+    }
+    case CFS_OP_TRANSLATE3:
+        out[0] = 1; out[4] = 1; out[8] = 1;
+        out[9] = v[0]; out[10] = v[1]; out[11] = v[2];
+        break;
+    case CFS_OP_BEND:
+        out[0] = v[0];
+        out[1] = 1.0f / v[0];
+        break;
+    case CFS_OP_INVERSION:
+        out[0] = v[0]; out[1] = v[1]; out[2] = v[2];
+        out[3] = v[3] * v[3];
+        break;
+    default:
+        std::memcpy(out, v, sizeof(float) * CFS_OP_PARAMS);
+        break;
+    }
+}
+
+namespace {
+
+bool finite_all(const float* v, int n)
+{
+    for (int j = 0; j < n; ++j)
+        if (!std::isfinite(v[j])) return false;
+    return true;
+}
+
+int op_out_dim(int kind, int dim_in)
+{
+    switch (kind) {
+    case CFS_OP_TORUS: return 3;
+    default: return dim_in;
+    }
+}
+
+bool op_needs_3d(int kind)
+{
+    switch (kind) {
+    case CFS_OP_AFFINE3: case CFS_OP_ROTATE3: case CFS_OP_TRANSLATE3: case CFS_OP_SINUSOIDAL3:
+    case CFS_OP_PERSPECTIVE: case CFS_OP_TWIST_Z: case CFS_OP_BEND: case CFS_OP_INVERSION:
+        return true;
+    default:
+        return false;
+    }
+}
+
+cfs_status validate_targets(const cfs_chain* ch, const cfs_target* tg, int n_tg)
+{
+    if (n_tg < 0 || n_tg > CFS_MAX_TARGETS)
+        return fail(CFS_ERR_INVALID_ARG, "n_targets must be in 0..4");
+    if (n_tg > 0 && !tg) return fail(CFS_ERR_INVALID_ARG, "targets is NULL");
+    for (int t = 0; t < n_tg; ++t) {
+        const cfs_target& g = tg[t];
+        std::ostringstream m;
+        m << "target " << t << ": ";
+        if (g.kind < CFS_TARGET_HIST_U32 || g.kind > CFS_TARGET_DEPTH_U64)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "unknown kind");
+        if (g.width <= 0 || g.height <= 0 || g.width > 65536 || g.height > 65536)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "width/height must be in 1..65536");
+        if (g.kind == CFS_TARGET_HIST_U32 && (g.channels < 1 || g.channels > CFS_MAX_MAPS))
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "histogram channels must be in 1..16");
+        if (!g.data) return fail(CFS_ERR_INVALID_ARG, m.str() + "data is NULL");
+        if (((uintptr_t)g.data) % 16 != 0)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "data must be 16-byte aligned");
+        if (!(std::isfinite(g.x0) && std::isfinite(g.x1) && std::isfinite(g.y0) &&
+              std::isfinite(g.y1) && g.x1 > g.x0 && g.y1 > g.y0))
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "view needs finite x0 < x1, y0 < y1");
+    }
+    // every SPLAT names an existing slot, and depth splats see a 3D point
+    int dim = ch->dim_in;
+    for (int o = 0; o < ch->n_ops; ++o) {
+        const cfs_transform& op = ch->ops[o];
+        if (op.kind == CFS_OP_RESET) dim = ch->dim_in;
+        if (op.kind == CFS_OP_SPLAT) {
+            const int slot = (int)op.params[0];
+            if (slot < 0 || slot >= n_tg) {
+                std::ostringstream m;
+                m << "op " << o << ": SPLAT names target slot " << slot << " but only " << n_tg
+                  << " targets were given";
+                return fail(CFS_ERR_INVALID_ARG, m.str());
+            }
+            if (tg[slot].kind == CFS_TARGET_DEPTH_U64 && dim != 3)
+                return fail(CFS_ERR_INVALID_ARG, "depth targets need a 3D point at the splat");
+        }
+        dim = op_out_dim(op.kind, dim);
+    }
+    return CFS_OK;
+}
+
+ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
+                      const cfs_target* tg, int n_tg, bool reuse)
+{
+    ProgramSpec sp;
+    sp.mode = mode;
+    sp.dim = sys->dim;
+    sp.n_maps = sys->n_maps;
+    for (int j = 0; j < sys->n_maps; ++j) sp.map_kind[j] = sys->maps[j].kind;
+    sp.n_cmp = sys->n_cmp;
+    sp.reuse = reuse;
+    sp.n_ops = ch->n_ops;
+    sp.n_targets = n_tg;
+    for (int o = 0; o < ch->n_ops; ++o) {
+        sp.op_kind[o] = ch->ops[o].kind;
+        if (ch->ops[o].kind == CFS_OP_SPLAT) {
+            const int slot = (int)ch->ops[o].params[0];
+            SplatSpec s;
+            s.slot = slot;
+            s.kind = tg ? tg[slot].kind : CFS_TARGET_HIST_U32;
+            s.channels = (tg && tg[slot].kind == CFS_TARGET_HIST_U32) ? tg[slot].channels : 1;
+            sp.splats.push_back(s);
+        }
+    }
+    // register budget: 256 threads x 4 blocks leaves 64 registers per thread
+    sp.block = 256;
+    sp.min_blocks = 4;
+    sp.depth_test = 1;
+    return sp;
+}
+
+void fill_args(cfs_launch_args* a, const cfs_system* sys, const cfs_chain* ch,
+               const cfs_target* tg, int n_tg, const cfs_render_params* p)
+{
+    std::memset(a, 0, sizeof(*a));
+    for (int j = 0; j < sys->n_cmp; ++j) a->sys.T[j] = sys->T[j];
+    a->sys.n_maps = sys->n_maps;
+    a->sys.n_cmp = sys->n_cmp;
+    a->sys.dim = sys->dim;
+    for (int k = 0; k < sys->n_maps; ++k)
+        for (int j = 0; j < 12; ++j) a->sys.prm[j][k] = sys->maps[k].params[j];
+    for (int o = 0; o < ch->n_ops; ++o) derive_op_params(ch->ops[o], a->op[o]);
+    for (int t = 0; t < n_tg; ++t) {
+        const cfs_target& g = tg[t];
+        cfs_dev_target& d = a->tg[t];
+        d.data = (unsigned long long)(uintptr_t)g.data;
+        d.W = g.width;
+        d.H = g.height;
+        d.C = g.channels < 1 ? 1 : g.channels;
+        d.kind = g.kind;
+        d.x0 = g.x0; d.x1 = g.x1; d.y0 = g.y0; d.y1 = g.y1;
+        d.sx = (float)g.width / (g.x1 - g.x0);
+        d.sy = (float)g.height / (g.y1 - g.y0);
+        std::memcpy(d.palette, g.palette, sizeof(d.palette));
+        std::memcpy(d.palette8, g.palette8, sizeof(d.palette8));
+    }
+    philox_round_keys(p->seed, a->rk);
+    a->discards = (unsigned long long)(uintptr_t)p->discards;
+    a->start = (unsigned long long)(uintptr_t)p->start;
+    a->system_id = p->system_id;
+    a->point_begin = p->point_begin;
+    a->n_points = p->n_points;
+    a->step_begin = p->step_begin;
+    a->iters = p->iters;
+    a->burn_in = p->burn_in;
+    a->flags = p->flags;
+}
+
+cfs_status validate_run(const cfs_system* sys, const cfs_chain* ch, const cfs_render_params* p)
+{
+    if (!sys || !ch || !p) return fail(CFS_ERR_INVALID_ARG, "NULL system, chain or params");
+    if (ch->dim_in != sys->dim)
+        return fail(CFS_ERR_INVALID_ARG, "chain was composed for another dimension");
+    if (p->step_begin > p->iters) return fail(CFS_ERR_INVALID_ARG, "step_begin > iters");
+    if ((uint64_t)p->point_begin + p->n_points > (1ull << 32))
+        return fail(CFS_ERR_INVALID_ARG, "point indices exceed 2^32");
+    if (p->flags & ~CFS_FLAG_REUSE) return fail(CFS_ERR_INVALID_ARG, "unknown flags");
+    if (p->flags & CFS_FLAG_REUSE) {
+        int dim = ch->dim_in;
+        for (int o = 0; o < ch->n_ops; ++o) {
+            if (ch->ops[o].kind == CFS_OP_RESET) dim = ch->dim_in;
+            dim = op_out_dim(ch->ops[o].kind, dim);
+        }
+        if (dim != ch->dim_in)
+            return fail(CFS_ERR_INVALID_ARG, "reuse needs a chain that keeps the dimension");
+    }
+    return CFS_OK;
+}
+
+}  // namespace
+}  // namespace cfs
+
+using namespace cfs;
+
+extern "C" {
+
+const char* cfs_last_error(void) { return cfs::last_error(); }
+
+const char* cfs_version(void) { return "cfs-gb300 0.1 (sm_103a)"; }
+
+cfs_status cfs_system_create(int dim, int n_maps, const cfs_map* maps, const double* probs,
+                             cfs_system** out)
+{
+    clear_error();
+    if (!out) return fail(CFS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(CFS_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (n_maps < 1 || n_maps > CFS_MAX_MAPS)
+        return fail(CFS_ERR_INVALID_ARG, "n_maps must be in 1..16");
+    if (!maps || !probs) return fail(CFS_ERR_INVALID_ARG, "maps or probs is NULL");
+    double total = 0.0;
+    for (int j = 0; j < n_maps; ++j) {
+        if (!(probs[j] >= 0.0) || std::isinf(probs[j]))
+            return fail(CFS_ERR_INVALID_ARG, "probabilities must be finite and >= 0");
+        total += probs[j];
+    }
+    if (!(total > 0.0) || std::isinf(total))
+        return fail(CFS_ERR_INVALID_ARG, "probabilities must have a positive finite sum");
+    for (int j = 0; j < n_maps; ++j) {
+        if (maps[j].kind != CFS_MAP_AFFINE && maps[j].kind != CFS_MAP_CIRCLE)
+            return fail(CFS_ERR_INVALID_ARG, "unknown map kind");
+        if (maps[j].kind == CFS_MAP_CIRCLE && dim != 2)
+            return fail(CFS_ERR_INVALID_ARG, "the circle map (Eq. 1) is 2D");
+        if (!finite_all(maps[j].params, 12))
+            return fail(CFS_ERR_INVALID_ARG, "map parameters must be finite");
+    }
+    cfs_system* s = new (std::nothrow) cfs_system();
+    if (!s) return fail(CFS_ERR_OOM, "host allocation failed");
+    s->dim = dim;
+    s->n_maps = n_maps;
+    for (int j = 0; j < n_maps; ++j) {
+        s->maps[j] = maps[j];
+        if (maps[j].kind == CFS_MAP_AFFINE && dim == 2)
+            for (int q = 6; q < 12; ++q) s->maps[j].params[q] = 0.0f;
+        s->probs[j] = probs[j];
+    }
+    // T_k = floor(S_k 2^32) for k < n-1; those >= 2^32 never count (they can
+    // only trail, the sums being non-decreasing)
+    double running = 0.0;
+    s->n_cmp = 0;
+    for (int k = 0; k < n_maps - 1; ++k) {
+        running += probs[k];
+        const double t = std::floor((running / total) * 4294967296.0);
+        if (t >= 4294967296.0) break;
+        s->T[s->n_cmp++] = (uint32_t)(t < 0.0 ? 0.0 : t);
+    }
+    *out = s;
+    return CFS_OK;
+}
+
+cfs_status cfs_system_destroy(cfs_system* sys)
+{
+    delete sys;
+    return CFS_OK;
+}
+
+cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chain** out)
+{
+    clear_error();
+    if (!out) return fail(CFS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dim_in != 2 && dim_in != 3) return fail(CFS_ERR_INVALID_ARG, "dim_in must be 2 or 3");
+    if (n_ops < 0 || n_ops > CFS_MAX_OPS)
+        return fail(CFS_ERR_INVALID_ARG, "n_ops must be in 0..32");
+    if (n_ops > 0 && !ops) return fail(CFS_ERR_INVALID_ARG, "ops is NULL");
+    int dim = dim_in, n_splat = 0;
+    for (int o = 0; o < n_ops; ++o) {
+        const cfs_transform& op = ops[o];
+        std::ostringstream m;
+        m << "op " << o << ": ";
+        if (op.kind < CFS_OP_AFFINE2 || op.kind > CFS_OP_RESET)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "unknown kind");
+        if (!finite_all(op.params, CFS_OP_PARAMS))
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "parameters must be finite");
+        if (op.kind == CFS_OP_RESET) dim = dim_in;
+        if (op_needs_3d(op.kind) && dim != 3)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "needs a 3D point");
+        if (op.kind == CFS_OP_TORUS && dim != 2)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "torus embeds a 2D point");
+        if (op.kind == CFS_OP_BEND && op.params[0] == 0.0f)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "bend needs a nonzero curvature");
+        if (op.kind == CFS_OP_ROTATE3 && (op.params[1] != 0.0f && op.params[1] != 1.0f &&
+                                          op.params[1] != 2.0f))
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "rotate3 axis must be 0, 1 or 2");
+        if (op.kind == CFS_OP_SPLAT) {
+            const float s = op.params[0];
+            if (!(s >= 0.0f && s < CFS_MAX_TARGETS && s == std::floor(s)))
+                return fail(CFS_ERR_INVALID_ARG, m.str() + "splat slot must be 0..3");
+            ++n_splat;
+        }
+        dim = op_out_dim(op.kind, dim);
+    }
+    cfs_chain* c = new (std::nothrow) cfs_chain();
+    if (!c) return fail(CFS_ERR_OOM, "host allocation failed");
+    c->dim_in = dim_in;
+    c->n_ops = n_ops;
+    for (int o = 0; o < n_ops; ++o) c->ops[o] = ops[o];
+    c->n_splat = n_splat;
+    *out = c;
+    return CFS_OK;
+}
+
+cfs_status cfs_chain_destroy(cfs_chain* chain)
+{
+    delete chain;
+    return CFS_OK;
+}
+
+cfs_status cfs_chain_set_params(cfs_chain* chain, int index, const float* params)
+{
+    clear_error();
+    if (!chain || !params) return fail(CFS_ERR_INVALID_ARG, "NULL chain or params");
+    if (index < 0 || index >= chain->n_ops) return fail(CFS_ERR_INVALID_ARG, "index out of range");
+    if (!finite_all(params, CFS_OP_PARAMS))
+        return fail(CFS_ERR_INVALID_ARG, "parameters must be finite");
+    cfs_transform t = chain->ops[index];
+    std::memcpy(t.params, params, sizeof(t.params));
+    if (t.kind == CFS_OP_SPLAT && t.params[0] != chain->ops[index].params[0])
+        return fail(CFS_ERR_INVALID_ARG, "a SPLAT's slot cannot change");
+    if (t.kind == CFS_OP_BEND && t.params[0] == 0.0f)
+        return fail(CFS_ERR_INVALID_ARG, "bend needs a nonzero curvature");
+    chain->ops[index] = t;
+    return CFS_OK;
+}
+
+cfs_status cfs_prepare(const cfs_system* sys, const cfs_chain* chain, const cfs_target* targets,
+                       int n_targets)
+{
+    clear_error();
+    if (!sys || !chain) return fail(CFS_ERR_INVALID_ARG, "NULL system or chain");
+    if (chain->dim_in != sys->dim)
+        return fail(CFS_ERR_INVALID_ARG, "chain was composed for another dimension");
+    cfs_status st = validate_targets(chain, targets, n_targets);
+    if (st != CFS_OK) return st;
+    ProgramSpec sp = make_spec(Mode::Render, sys, chain, targets, n_targets, false);
+    Kernel k;
+    return get_kernel(sp, "cfs_render_kernel", &k);
+}
+
+cfs_status cfs_render(const cfs_system* sys, const cfs_chain* chain,
+                      const cfs_render_params* params, const cfs_target* targets, int n_targets,
+                      void* stream)
+{
+    clear_error();
+    cfs_status st = validate_run(sys, chain, params);
+    if (st != CFS_OK) return st;
+    st = validate_targets(chain, targets, n_targets);
+    if (st != CFS_OK) return st;
+    if (params->n_points == 0 || params->step_begin >= params->iters) return CFS_OK;
+    ProgramSpec sp = make_spec(Mode::Render, sys, chain, targets, n_targets,
+                               (params->flags & CFS_FLAG_REUSE) != 0);
+    Kernel k;
+    st = get_kernel(sp, "cfs_render_kernel", &k);
+    if (st != CFS_OK) return st;
+    cfs_launch_args a;
+    fill_args(&a, sys, chain, targets, n_targets, params);
+    const uint64_t blocks_needed = ((uint64_t)params->n_points + k.block - 1) / k.block;
+    uint64_t grid = (uint64_t)k.max_blocks_per_sm * (uint64_t)(k.num_sms > 0 ? k.num_sms : 1);
+    if (grid == 0) grid = 1;
+    if (grid > blocks_needed) grid = blocks_needed;
+    return launch(k, (unsigned)grid, &a, sizeof(a), (cudaStream_t)stream);
+}
+
+cfs_status cfs_trace(const cfs_system* sys, const cfs_chain* chain,
+                     const cfs_render_params* params, const uint32_t* ids, uint32_t n_ids,
+                     int32_t* k_out, float* p_out, float* q_out, void* stream)
+{
+    clear_error();
+    cfs_status st = validate_run(sys, chain, params);
+    if (st != CFS_OK) return st;
+    if (n_ids == 0 || params->step_begin >= params->iters) return CFS_OK;
+    if (!ids || !k_out || !p_out || !q_out)
+        return fail(CFS_ERR_INVALID_ARG, "NULL ids or trace output");
+    // the trace splats nothing: targets are only needed for their kinds
+    ProgramSpec sp = make_spec(Mode::Trace, sys, chain, nullptr, 0,
+                               (params->flags & CFS_FLAG_REUSE) != 0);
+    Kernel k;
+    st = get_kernel(sp, "cfs_trace_kernel", &k);
+    if (st != CFS_OK) return st;
+    cfs_launch_args a;
+    cfs_render_params p = *params;
+    p.n_points = n_ids;
+    p.discards = nullptr;
+    fill_args(&a, sys, chain, nullptr, 0, &p);
+    a.ids = (unsigned long long)(uintptr_t)ids;
+    a.k_out = (unsigned long long)(uintptr_t)k_out;
+    a.p_out = (unsigned long long)(uintptr_t)p_out;
+    a.q_out = (unsigned long long)(uintptr_t)q_out;
+    const unsigned grid = (n_ids + k.block - 1) / k.block;
+    return launch(k, grid, &a, sizeof(a), (cudaStream_t)stream);
+}
+
+cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
+                             const cfs_target* targets, int n_targets, int mode, char* src,
+                             size_t src_cap, char* log, size_t log_cap)
+{
+    clear_error();
+    if (!sys || !chain) return fail(CFS_ERR_INVALID_ARG, "NULL system or chain");
+    if (chain->dim_in != sys->dim)
+        return fail(CFS_ERR_INVALID_ARG, "chain was composed for another dimension");
+    if (mode != 0 && mode != 1) return fail(CFS_ERR_INVALID_ARG, "mode must be 0 or 1");
+    cfs_status st = CFS_OK;
+    if (mode == 0) {
+        st = validate_targets(chain, targets, n_targets);
+        if (st != CFS_OK) return st;
+    }
+    ProgramSpec sp = make_spec(mode == 0 ? Mode::Render : Mode::Trace, sys, chain,
+                               mode == 0 ? targets : nullptr, mode == 0 ? n_targets : 0, false);
+    std::string s, l;
+    st = compile_only(sp, &s, &l);
+    auto copy = [](const std::string& from, char* to, size_t cap) {
+        if (!to || cap == 0) return;
+        const size_t n = from.size() < cap - 1 ? from.size() : cap - 1;
+        std::memcpy(to, from.data(), n);
+        to[n] = '\0';
+    };
+    copy(s, src, src_cap);
+    copy(l, log, log_cap);
+    return st;
+}
+
+cfs_status cfs_target_clear(const cfs_target* targets, int n_targets, void* stream)
+{
+    clear_error();
+    if (n_targets < 0 || n_targets > CFS_MAX_TARGETS || (n_targets > 0 && !targets))
+        return fail(CFS_ERR_INVALID_ARG, "bad targets");
+    for (int t = 0; t < n_targets; ++t) {
+        const cfs_target& g = targets[t];
+        if (!g.data || g.width <= 0 || g.height <= 0)
+            return fail(CFS_ERR_INVALID_ARG, "bad target");
+        size_t n = (size_t)g.width * (size_t)g.height;
+        int fill = 0;
+        if (g.kind == CFS_TARGET_HIST_U32) n *= 4 * (size_t)(g.channels < 1 ? 1 : g.channels);
+        else if (g.kind == CFS_TARGET_RGBA_F32) n *= 16;
+        else if (g.kind == CFS_TARGET_DEPTH_U64) { n *= 8; fill = 0xFF; }
+        else return fail(CFS_ERR_INVALID_ARG, "unknown target kind");
+        cfs_status st = check_cuda(cudaMemsetAsync(g.data, fill, n, (cudaStream_t)stream),
+                                   "cudaMemsetAsync");
+        if (st != CFS_OK) return st;
+    }
+    return CFS_OK;
+}
+
+}  // extern "C"

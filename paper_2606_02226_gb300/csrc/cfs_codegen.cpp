@@ -1,0 +1,171 @@
+// cfs_codegen.cpp -- emits the fused generator + transform-chain program.
+//
+// The paper's renderer composes user functions into one large kernel so that
+// no map or transform is called through a function pointer (Section 1,
+// Section 2; Fig. 3 shows its verse/stanza injection).  Here the same idea is
+// applied to CUDA: from the structure of a render -- generator map kinds,
+// the chain's op sequence, the kinds of the targets it splats into -- this
+// file writes straight-line device code (a switch only where maps of
+// different kinds meet) that NVRTC compiles for sm_103a.  Every numeric
+// parameter stays in the kernel's argument block, so one compiled program
+// serves every system and chain of the same structure.
+#include <sstream>
+
+#include "cfs_internal.h"
+
+namespace cfs {
+
+std::string ProgramSpec::key() const
+{
+    std::ostringstream s;
+    s << "m" << int(mode) << ".d" << dim << ".n" << n_maps << ".c" << n_cmp << ".r" << reuse
+      << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << ".k";
+    for (int j = 0; j < n_maps; ++j) s << map_kind[j];
+    s << ".o";
+    for (int j = 0; j < n_ops; ++j) s << op_kind[j] << ",";
+    s << ".s";
+    for (const auto& sp : splats) s << sp.slot << ":" << sp.kind << ":" << sp.channels << ",";
+    return s.str();
+}
+
+static std::string P(int o, int j)
+{
+    std::ostringstream s;
+    s << "a.op[" << o << "][" << j << "]";
+    return s.str();
+}
+
+static std::string Plist(int o, int n)
+{
+    std::ostringstream s;
+    for (int j = 0; j < n; ++j) s << P(o, j) << ", ";
+    return s.str();
+}
+
+// Generator: one map evaluation for map index k.
+static void emit_gen_map(std::ostringstream& s, const ProgramSpec& sp)
+{
+    s << "__device__ __forceinline__ void cfs_gen_map(const cfs_launch_args& a, int k, float& x,"
+         " float& y, float& z, const CfsSmem& sm)\n{\n    (void)a; (void)sm;\n";
+    bool all_affine = true, all_circle = true;
+    for (int j = 0; j < sp.n_maps; ++j) {
+        all_affine = all_affine && sp.map_kind[j] == CFS_MAP_AFFINE;
+        all_circle = all_circle && sp.map_kind[j] == CFS_MAP_CIRCLE;
+    }
+    if (all_affine) {
+        // one code path for every map: parameters gathered from shared memory
+        if (sp.dim == 2)
+            s << "    cfs_affine2_tab(k, x, y, sm);\n    (void)z;\n";
+        else
+            s << "    cfs_affine3_tab(k, x, y, z, sm);\n";
+    } else if (all_circle) {
+        s << "    cfs_circle(sm.prm2[0][k].x, x, y);\n    (void)z;\n";
+    } else {
+        // maps of different kinds: the fused switch
+        s << "    switch (k) {\n";
+        for (int j = 0; j < sp.n_maps; ++j) {
+            s << "    case " << j << ": ";
+            if (sp.map_kind[j] == CFS_MAP_AFFINE) {
+                if (sp.dim == 2)
+                    s << "cfs_affine2(a_sys_prm(0, " << j << "), a_sys_prm(1, " << j
+                      << "), a_sys_prm(2, " << j << "), a_sys_prm(3, " << j
+                      << "), a_sys_prm(4, " << j << "), a_sys_prm(5, " << j << "), x, y);";
+                else {
+                    s << "cfs_affine3(";
+                    for (int q = 0; q < 12; ++q) s << "a_sys_prm(" << q << ", " << j << "), ";
+                    s << "x, y, z);";
+                }
+            } else {
+                s << "cfs_circle(a_sys_prm(0, " << j << "), x, y);";
+            }
+            s << " break;\n";
+        }
+        s << "    default: break;\n    }\n";
+    }
+    s << "}\n\n";
+}
+
+// Chain: the copy of the point through every op, splats where the chain says.
+static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
+{
+    s << "__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a, const CfsSmem& sm,"
+         " float px, float py, float pz, int k, u32* disc, bool do_splat, float* rec,"
+         " float& ox, float& oy, float& oz)\n{\n";
+    s << "    float qx = px, qy = py, qz = pz;\n    bool alive = true;\n";
+    s << "    (void)sm; (void)disc; (void)do_splat; (void)rec; (void)k;\n";
+    size_t si = 0;
+    for (int o = 0; o < sp.n_ops; ++o) {
+        s << "    /* op " << o << " */ ";
+        switch (sp.op_kind[o]) {
+        case CFS_OP_AFFINE2:
+        case CFS_OP_ROTATE2:
+            s << "cfs_affine2(" << Plist(o, 6) << "qx, qy);\n";
+            break;
+        case CFS_OP_AFFINE3:
+        case CFS_OP_ROTATE3:
+        case CFS_OP_TRANSLATE3:
+            s << "cfs_affine3(" << Plist(o, 12) << "qx, qy, qz);\n";
+            break;
+        case CFS_OP_SWIRL: s << "cfs_swirl(qx, qy);\n"; break;
+        case CFS_OP_SINUSOIDAL: s << "cfs_sinusoidal(qx, qy);\n"; break;
+        case CFS_OP_SINUSOIDAL3: s << "cfs_sinusoidal3(qx, qy, qz);\n"; break;
+        case CFS_OP_STRETCH: s << "cfs_stretch(qx, qy);\n"; break;
+        case CFS_OP_TORUS: s << "cfs_torus(" << Plist(o, 2) << "qx, qy, qz);\n"; break;
+        case CFS_OP_PERSPECTIVE:
+            s << "alive = cfs_perspective(" << Plist(o, 2) << "qx, qy, qz) && alive;\n";
+            break;
+        case CFS_OP_TWIST_Z: s << "cfs_twist_z(" << P(o, 0) << ", qx, qy, qz);\n"; break;
+        case CFS_OP_BEND: s << "cfs_bend(" << Plist(o, 2) << "qx, qz);\n"; break;
+        case CFS_OP_INVERSION:
+            s << "alive = cfs_inversion(" << Plist(o, 4) << "qx, qy, qz) && alive;\n";
+            break;
+        case CFS_OP_RESET:
+            s << "qx = px; qy = py; qz = pz; alive = true;\n";
+            break;
+        case CFS_OP_SPLAT: {
+            const SplatSpec& t = sp.splats[si];
+            s << "\n    if (rec) { rec[" << 4 * si << "] = qx; rec[" << 4 * si + 1
+              << "] = qy; rec[" << 4 * si + 2 << "] = qz; rec[" << 4 * si + 3
+              << "] = alive ? 1.0f : 0.0f; }\n";
+            s << "    if (do_splat) ";
+            if (t.kind == CFS_TARGET_HIST_U32)
+                s << "cfs_splat_hist(a.tg[" << t.slot << "], qx, qy, alive, k % " << t.channels
+                  << ", disc[" << t.slot << "]);\n";
+            else if (t.kind == CFS_TARGET_RGBA_F32)
+                s << "cfs_splat_rgba(a.tg[" << t.slot << "], qx, qy, alive, sm.pal[" << t.slot
+                  << "][k], disc[" << t.slot << "]);\n";
+            else
+                s << "cfs_splat_depth(a.tg[" << t.slot << "], qx, qy, qz, alive, sm.pal8["
+                  << t.slot << "][k], disc[" << t.slot << "]);\n";
+            ++si;
+            break;
+        }
+        default: s << "\n"; break;
+        }
+    }
+    s << "    ox = qx; oy = qy; oz = qz;\n    return alive;\n}\n\n";
+}
+
+std::string generate_source(const ProgramSpec& sp)
+{
+    std::ostringstream s;
+    s << "// generated: " << sp.key() << "\n";
+    s << "#define CFS_DIM " << sp.dim << "\n";
+    s << "#define CFS_NCMP " << sp.n_cmp << "\n";
+    s << "#define CFS_NT " << sp.n_targets << "\n";
+    s << "#define CFS_NSPLAT_ARR " << (sp.splats.empty() ? 1 : sp.splats.size()) << "\n";
+    s << "#define CFS_REUSE " << (sp.reuse ? 1 : 0) << "\n";
+    s << "#define CFS_DEPTH_TEST " << sp.depth_test << "\n";
+    s << "#define CFS_BLOCK " << sp.block << "\n";
+    s << "#define CFS_MINB " << sp.min_blocks << "\n";
+    s << "#include \"cfs_device.cuh\"\n";
+    // generator parameters with constant indices come straight from the
+    // argument block (the constant bank); only the table path uses smem
+    s << "#define a_sys_prm(j, k) (a.sys.prm[j][k])\n\n";
+    emit_gen_map(s, sp);
+    emit_chain(s, sp);
+    s << "#include \"cfs_kernels.cuh\"\n";
+    return s.str();
+}
+
+}  // namespace cfs

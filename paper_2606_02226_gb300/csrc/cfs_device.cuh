@@ -1,0 +1,322 @@
+/*
+ * cfs_device.cuh -- device helpers of the generated chaos-game kernels.
+ *
+ * This text is handed to NVRTC together with the generated prelude (the
+ * structural #defines and the fused map/chain functions) and cfs_kernels.cuh.
+ * It is compiled for sm_103a with --fmad=false: every fused multiply-add is
+ * written out with fmaf(), and no other contraction happens, so the FP32
+ * results follow the written evaluation order exactly.
+ */
+#ifndef CFS_DEVICE_CUH
+#define CFS_DEVICE_CUH
+
+#include "cfs_args.h"
+
+typedef unsigned int u32;
+typedef unsigned long long u64;
+
+#define CFS_TWO_PI_F 6.28318530717958647692f
+#define CFS_PI_F 3.14159265358979323846f
+#define CFS_INV_2_24 5.9604644775390625e-08f
+
+/* ---- Philox4x32-10 (Salmon et al. 2011): 10 rounds of two 32x32->64
+ *      multiplies; the round keys of the launch's seed are precomputed on the
+ *      host (key + r * (0x9E3779B9, 0xBB67AE85)) and read from the constant
+ *      bank. ------------------------------------------------------------- */
+__device__ __forceinline__ uint4 cfs_philox_rk(const unsigned int (&rk)[10][2], u32 c0, u32 c1,
+                                               u32 c2, u32 c3)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const u64 p0 = (u64)0xD2511F53u * (u64)c0;
+        const u64 p1 = (u64)0xCD9E8D57u * (u64)c2;
+        const u32 hi0 = (u32)(p0 >> 32), lo0 = (u32)p0;
+        const u32 hi1 = (u32)(p1 >> 32), lo1 = (u32)p1;
+        c0 = hi1 ^ c1 ^ rk[r][0];
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ rk[r][1];
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint4 cfs_philox(const cfs_launch_args& a, u32 c0, u32 c1, u32 c2,
+                                            u32 c3)
+{
+    return cfs_philox_rk(a.rk, c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ u32 cfs_word(uint4 r, u32 s)
+{
+    return s == 0 ? r.x : (s == 1 ? r.y : (s == 2 ? r.z : r.w));
+}
+
+/* ---- shared-memory copy of the per-launch tables ---------------------- */
+struct CfsSmem {
+    float2 prm2[6][CFS_A_MAX_MAPS];           /* map params, pairs (0,1) (2,3) ... */
+    float4 pal[CFS_A_MAX_TARGETS][CFS_A_MAX_MAPS];
+    u32 pal8[CFS_A_MAX_TARGETS][CFS_A_MAX_MAPS];
+};
+
+__device__ __forceinline__ void cfs_load_smem(const cfs_launch_args& a, CfsSmem& sm)
+{
+    for (int t = threadIdx.x; t < 6 * CFS_A_MAX_MAPS; t += blockDim.x) {
+        const int j = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
+        sm.prm2[j][k] = make_float2(a.sys.prm[2 * j][k], a.sys.prm[2 * j + 1][k]);
+    }
+    for (int t = threadIdx.x; t < CFS_A_MAX_TARGETS * CFS_A_MAX_MAPS; t += blockDim.x) {
+        const int g = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
+        sm.pal[g][k] = make_float4(a.tg[g].palette[k][0], a.tg[g].palette[k][1],
+                                   a.tg[g].palette[k][2], a.tg[g].palette[k][3]);
+        sm.pal8[g][k] = a.tg[g].palette8[k];
+    }
+}
+
+/* ---- generator maps ------------------------------------------------------ */
+/* Affine 2D map k from the shared table: x' = fma(a, x, fma(b, y, e)). */
+__device__ __forceinline__ void cfs_affine2_tab(int k, float& x, float& y, const CfsSmem& sm)
+{
+    const float2 ab = sm.prm2[0][k], cd = sm.prm2[1][k], ef = sm.prm2[2][k];
+    const float nx = fmaf(ab.x, x, fmaf(ab.y, y, ef.x));
+    const float ny = fmaf(cd.x, x, fmaf(cd.y, y, ef.y));
+    x = nx;
+    y = ny;
+}
+
+/* Affine 3D map k: row-major A then b. */
+__device__ __forceinline__ void cfs_affine3_tab(int k, float& x, float& y, float& z,
+                                                const CfsSmem& sm)
+{
+    const float2 m01 = sm.prm2[0][k], m23 = sm.prm2[1][k], m45 = sm.prm2[2][k];
+    const float2 m67 = sm.prm2[3][k], m89 = sm.prm2[4][k], mab = sm.prm2[5][k];
+    const float nx = fmaf(m01.x, x, fmaf(m01.y, y, fmaf(m23.x, z, m89.y)));
+    const float ny = fmaf(m23.y, x, fmaf(m45.x, y, fmaf(m45.y, z, mab.x)));
+    const float nz = fmaf(m67.x, x, fmaf(m67.y, y, fmaf(m89.x, z, mab.y)));
+    x = nx;
+    y = ny;
+    z = nz;
+}
+
+__device__ __forceinline__ void cfs_affine2(float a, float b, float c, float d, float e, float f,
+                                            float& x, float& y)
+{
+    const float nx = fmaf(a, x, fmaf(b, y, e));
+    const float ny = fmaf(c, x, fmaf(d, y, f));
+    x = nx;
+    y = ny;
+}
+
+__device__ __forceinline__ void cfs_affine3(float m0, float m1, float m2, float m3, float m4,
+                                            float m5, float m6, float m7, float m8, float b0,
+                                            float b1, float b2, float& x, float& y, float& z)
+{
+    const float nx = fmaf(m0, x, fmaf(m1, y, fmaf(m2, z, b0)));
+    const float ny = fmaf(m3, x, fmaf(m4, y, fmaf(m5, z, b1)));
+    const float nz = fmaf(m6, x, fmaf(m7, y, fmaf(m8, z, b2)));
+    x = nx;
+    y = ny;
+    z = nz;
+}
+
+/* Eq. 1 (circle IFS), read with atan2 taken into [0, 2 pi) and r2 in the last
+ * two lines: theta2 = pi (r + f_id), r2 = sqrt(theta / 2 pi). */
+__device__ __forceinline__ void cfs_circle(float fid, float& x, float& y)
+{
+    const float r = sqrtf(fmaf(x, x, y * y));
+    float th = atan2f(y, x);
+    if (th < 0.0f) th = th + CFS_TWO_PI_F;
+    const float th2 = CFS_PI_F * (r + fid);
+    const float r2 = sqrtf(th / CFS_TWO_PI_F);
+    float s, c;
+    sincosf(th2, &s, &c);
+    x = r2 * c;
+    y = r2 * s;
+}
+
+/* ---- transform chain ops (Section 3; Eq. 2) ------------------------------ */
+__device__ __forceinline__ void cfs_swirl(float& x, float& y)
+{
+    const float r2 = fmaf(x, x, y * y);
+    float s, c;
+    sincosf(r2, &s, &c);
+    const float nx = fmaf(x, s, -(y * c));
+    const float ny = fmaf(x, c, y * s);
+    x = nx;
+    y = ny;
+}
+
+__device__ __forceinline__ void cfs_sinusoidal(float& x, float& y)
+{
+    x = sinf(x);
+    y = sinf(y);
+}
+
+__device__ __forceinline__ void cfs_sinusoidal3(float& x, float& y, float& z)
+{
+    x = sinf(x);
+    y = sinf(y);
+    z = sinf(z);
+}
+
+__device__ __forceinline__ void cfs_stretch(float& x, float& y)
+{
+    const float ox = x;
+    x = 2.0f * ox;
+    y = y - cosf(ox);
+}
+
+__device__ __forceinline__ void cfs_torus(float R, float r, float& x, float& y, float& z)
+{
+    const float a = CFS_TWO_PI_F * x, b = CFS_TWO_PI_F * y;
+    float sa, ca, sb, cb;
+    sincosf(a, &sa, &ca);
+    sincosf(b, &sb, &cb);
+    const float w = fmaf(r, cb, R);
+    x = w * ca;
+    y = w * sa;
+    z = r * sb;
+}
+
+__device__ __forceinline__ bool cfs_perspective(float f, float near_z, float& x, float& y,
+                                                float z)
+{
+    const float inv = 1.0f / z;
+    x = (f * x) * inv;
+    y = (f * y) * inv;
+    return z > near_z;
+}
+
+__device__ __forceinline__ void cfs_twist_z(float kappa, float& x, float& y, float z)
+{
+    float s, c;
+    sincosf(kappa * z, &s, &c);
+    const float nx = fmaf(x, c, -(y * s));
+    const float ny = fmaf(x, s, y * c);
+    x = nx;
+    y = ny;
+}
+
+/* beta and 1/beta (the latter rounded once, on the host) */
+__device__ __forceinline__ void cfs_bend(float beta, float invb, float& x, float& z)
+{
+    float s, c;
+    sincosf(beta * x, &s, &c);
+    const float d = invb - z;
+    x = s * d;
+    z = invb - c * d;
+}
+
+/* centre (cx, cy, cz), rho2 = rho * rho rounded once on the host */
+__device__ __forceinline__ bool cfs_inversion(float cx, float cy, float cz, float rho2,
+                                              float& x, float& y, float& z)
+{
+    const float dx = x - cx, dy = y - cy, dz = z - cz;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float s = rho2 / d2;
+    x = fmaf(s, dx, cx);
+    y = fmaf(s, dy, cy);
+    z = fmaf(s, dz, cz);
+    return d2 >= 1e-12f;
+}
+
+/* ---- splats (Section 1: the point colours the appropriate pixel) -------- */
+/* Bin of one coordinate: floor((u - lo) * scale), valid for lo <= u <= hi,
+ * the last bin closed.  Returns -1 when outside (NaN included). */
+__device__ __forceinline__ int cfs_bin(float u, float lo, float hi, float scale, int n)
+{
+    const bool in = (u >= lo) && (u <= hi);
+    const int b = min(__float2int_rd((u - lo) * scale), n - 1);
+    return in ? b : -1;
+}
+
+__device__ __forceinline__ void cfs_red_add_u32(u32* p, u32 v)
+{
+    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void cfs_red_add_v4f32(float* p, float4 v)
+{
+    asm volatile("red.global.v4.f32.add [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cfs_red_min_u64(u64* p, u64 v)
+{
+    asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ u64 cfs_ld_relaxed_u64(const u64* p)
+{
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+/* u32 histogram [C][H][W]: +1 in channel ch. */
+__device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x, float y,
+                                               bool alive, int ch, u32& disc)
+{
+    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
+    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
+    if (alive && ix >= 0 && iy >= 0) {
+        u32* base = reinterpret_cast<u32*>(t.data);
+        const size_t off = ((size_t)ch * (size_t)t.H + (size_t)iy) * (size_t)t.W + (size_t)ix;
+        cfs_red_add_u32(base + off, 1u);
+    } else {
+        disc += 1;
+    }
+}
+
+/* f32 RGBA [H][W][4]: += colour (one 16-byte vector reduction). */
+__device__ __forceinline__ void cfs_splat_rgba(const cfs_dev_target& t, float x, float y,
+                                               bool alive, float4 col, u32& disc)
+{
+    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
+    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
+    if (alive && ix >= 0 && iy >= 0) {
+        float* base = reinterpret_cast<float*>(t.data);
+        const size_t off = ((size_t)iy * (size_t)t.W + (size_t)ix) * 4;
+        cfs_red_add_v4f32(base + off, col);
+    } else {
+        disc += 1;
+    }
+}
+
+/* u64 depth+colour [H][W]: min= (bits(z) << 32) | rgba8.  With
+ * CFS_DEPTH_TEST the current value is read first (a strong relaxed load) and
+ * the reduction is skipped when it could not lower it: keys only decrease,
+ * so a key not below an observed value is not below the final one either. */
+__device__ __forceinline__ void cfs_splat_depth(const cfs_dev_target& t, float x, float y,
+                                                float z, bool alive, u32 rgba8, u32& disc)
+{
+    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
+    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
+    if (alive && ix >= 0 && iy >= 0) {
+        u64* base = reinterpret_cast<u64*>(t.data);
+        u64* p = base + ((size_t)iy * (size_t)t.W + (size_t)ix);
+        const u64 key = ((u64)__float_as_uint(z) << 32) | (u64)rgba8;
+#if CFS_DEPTH_TEST
+        if (key < cfs_ld_relaxed_u64(p)) cfs_red_min_u64(p, key);
+#else
+        cfs_red_min_u64(p, key);
+#endif
+    } else {
+        disc += 1;
+    }
+}
+
+/* Adds each thread's discard counts to the per-target u64 counters: one
+ * atomic per warp and target. */
+__device__ __forceinline__ void cfs_flush_discards(const cfs_launch_args& a, const u32* disc,
+                                                   int n)
+{
+    if (a.discards == 0ull) return;
+    u64* out = reinterpret_cast<u64*>(a.discards);
+    for (int t = 0; t < n; ++t) {
+        const u32 s = __reduce_add_sync(0xffffffffu, disc[t]);
+        if ((threadIdx.x & 31) == 0 && s) atomicAdd(out + t, (u64)s);
+    }
+}
+
+#endif /* CFS_DEVICE_CUH */

@@ -1,0 +1,88 @@
+// cfs_internal.h -- host-side internals of libcfs (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cfs.h"
+#include "cfs_args.h"
+
+struct cfs_system {
+    int dim = 2;
+    int n_maps = 0;
+    cfs_map maps[CFS_MAX_MAPS];
+    double probs[CFS_MAX_MAPS];
+    uint32_t T[CFS_MAX_MAPS];   // thresholds below 2^32
+    int n_cmp = 0;              // how many of them count
+};
+
+struct cfs_chain {
+    int dim_in = 2;
+    int n_ops = 0;
+    cfs_transform ops[CFS_MAX_OPS];
+    int n_splat = 0;
+};
+
+namespace cfs {
+
+// ---- error reporting (thread-local message) -------------------------------
+cfs_status fail(cfs_status s, const std::string& msg);
+void clear_error();
+
+// ---- structural description of one generated program ----------------------
+enum class Mode { Render = 0, Trace = 1, Cloud = 2, Points = 3, Batch = 4 };
+
+struct SplatSpec {
+    int slot;        // target slot
+    int kind;        // cfs_target_kind
+    int channels;    // histogram channel count
+};
+
+struct ProgramSpec {
+    Mode mode = Mode::Render;
+    int dim = 2;
+    int n_maps = 1;
+    int map_kind[CFS_MAX_MAPS] = {};
+    int n_cmp = 0;
+    bool reuse = false;
+    int n_ops = 0;
+    int op_kind[CFS_MAX_OPS] = {};
+    std::vector<SplatSpec> splats;   // in op order
+    int n_targets = 0;
+    int depth_test = 1;
+    int block = 256;
+    int min_blocks = 4;
+
+    std::string key() const;
+};
+
+std::string generate_source(const ProgramSpec& spec);
+
+// ---- runtime: driver entry points, NVRTC, module cache ---------------------
+struct Kernel {
+    void* fn = nullptr;         // CUfunction
+    int max_blocks_per_sm = 0;
+    int block = 256;
+    int num_sms = 0;
+};
+
+// Compiles (or fetches from the cache) the program and returns the named
+// kernel.  Thread-safe.
+cfs_status get_kernel(const ProgramSpec& spec, const char* name, Kernel* out);
+// NVRTC only (no GPU needed): generated source and compiler log with the
+// ptxas resource usage.
+cfs_status compile_only(const ProgramSpec& spec, std::string* src, std::string* log);
+cfs_status launch(const Kernel& k, unsigned grid, const void* args, size_t args_size,
+                  cudaStream_t stream);
+cfs_status check_cuda(cudaError_t e, const char* what);
+int device_sm_count();
+
+// ---- host-side tables ---------------------------------------------------
+void philox_round_keys(uint64_t seed, unsigned int rk[10][2]);
+// per-op constants the kernels read (rotations turned into affine params, ...)
+void derive_op_params(const cfs_transform& op, float out[CFS_OP_PARAMS]);
+
+}  // namespace cfs

@@ -1,0 +1,212 @@
+// cfs_runtime.cpp -- NVRTC compilation of generated programs, the program
+// cache, and kernel launches.
+//
+// The driver API calls (module load, launch, occupancy) are reached through
+// cudaGetDriverEntryPointByVersion, so the library links only the CUDA
+// runtime and NVRTC and loads on machines without a GPU driver (where every
+// compute entry point then reports CFS_ERR_CUDA).
+#include <cuda.h>
+#include <nvrtc.h>
+
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <unordered_map>
+
+#include "cfs_internal.h"
+
+namespace cfs {
+
+// ---- embedded device sources (generated at build time from csrc/) --------
+extern const char* const kSrcArgs;
+extern const char* const kSrcDevice;
+extern const char* const kSrcKernels;
+
+// ---- error reporting ---------------------------------------------------------
+static thread_local std::string t_err;
+
+cfs_status fail(cfs_status s, const std::string& msg)
+{
+    t_err = msg;
+    return s;
+}
+
+void clear_error() { t_err.clear(); }
+
+const char* last_error() { return t_err.c_str(); }
+
+cfs_status check_cuda(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return CFS_OK;
+    std::ostringstream s;
+    s << what << ": " << cudaGetErrorName(e) << " (" << cudaGetErrorString(e) << ")";
+    return fail(e == cudaErrorMemoryAllocation ? CFS_ERR_OOM : CFS_ERR_CUDA, s.str());
+}
+
+// ---- driver entry points -------------------------------------------------
+namespace {
+typedef CUresult (*PFN_ModuleLoadData)(CUmodule*, const void*);
+typedef CUresult (*PFN_ModuleGetFunction)(CUfunction*, CUmodule, const char*);
+typedef CUresult (*PFN_LaunchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned,
+                                     unsigned, unsigned, unsigned, CUstream, void**, void**);
+typedef CUresult (*PFN_Occupancy)(int*, CUfunction, int, size_t);
+typedef CUresult (*PFN_GetErrorString)(CUresult, const char**);
+
+struct Driver {
+    PFN_ModuleLoadData module_load = nullptr;
+    PFN_ModuleGetFunction get_function = nullptr;
+    PFN_LaunchKernel launch = nullptr;
+    PFN_Occupancy occupancy = nullptr;
+    PFN_GetErrorString error_string = nullptr;
+    bool ok = false;
+    std::string why;
+};
+
+Driver& driver()
+{
+    static Driver d;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        auto get = [](const char* name, void** fn) -> bool {
+            cudaDriverEntryPointQueryResult q;
+            cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q);
+            return e == cudaSuccess && q == cudaDriverEntryPointSuccess && *fn != nullptr;
+        };
+        bool ok = get("cuModuleLoadData", (void**)&d.module_load) &&
+                  get("cuModuleGetFunction", (void**)&d.get_function) &&
+                  get("cuLaunchKernel", (void**)&d.launch) &&
+                  get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.occupancy) &&
+                  get("cuGetErrorString", (void**)&d.error_string);
+        d.ok = ok;
+        if (!ok) d.why = "CUDA driver entry points unavailable (no GPU driver?)";
+    });
+    return d;
+}
+
+cfs_status check_cu(CUresult r, const char* what)
+{
+    if (r == CUDA_SUCCESS) return CFS_OK;
+    const char* msg = "unknown";
+    if (driver().error_string) driver().error_string(r, &msg);
+    std::ostringstream s;
+    s << what << ": CUresult " << int(r) << " (" << msg << ")";
+    return fail(r == CUDA_ERROR_OUT_OF_MEMORY ? CFS_ERR_OOM : CFS_ERR_CUDA, s.str());
+}
+
+struct Program {
+    CUmodule module = nullptr;
+    std::unordered_map<std::string, Kernel> kernels;
+};
+
+std::mutex g_cache_mu;
+// key: device ordinal + generated source text
+std::unordered_map<std::string, std::unique_ptr<Program>> g_cache;
+
+cfs_status compile(const std::string& src, std::vector<char>* cubin, std::string* log_out,
+                   bool verbose)
+{
+    nvrtcProgram prog;
+    const char* headers[] = {kSrcArgs, kSrcDevice, kSrcKernels};
+    const char* names[] = {"cfs_args.h", "cfs_device.cuh", "cfs_kernels.cuh"};
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "cfs_generated.cu", 3, headers, names);
+    if (r != NVRTC_SUCCESS)
+        return fail(CFS_ERR_COMPILE, std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r));
+    const char* opts[] = {"--gpu-architecture=sm_103a", "--fmad=false", "--std=c++17",
+                          "-default-device", "--extra-device-vectorization", "-lineinfo",
+                          "--ptxas-options=-v"};
+    const int n_opts = sizeof(opts) / sizeof(opts[0]) - (verbose ? 0 : 1);
+    r = nvrtcCompileProgram(prog, n_opts, opts);
+    {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        if (n) nvrtcGetProgramLog(prog, &log[0]);
+        if (log_out) *log_out = log;
+        if (r != NVRTC_SUCCESS) {
+            nvrtcDestroyProgram(&prog);
+            return fail(CFS_ERR_COMPILE,
+                        std::string("NVRTC failed:\n") + log + "\n--- source ---\n" + src);
+        }
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin->resize(n);
+    nvrtcGetCUBIN(prog, cubin->data());
+    nvrtcDestroyProgram(&prog);
+    return CFS_OK;
+}
+}  // namespace
+
+cfs_status compile_only(const ProgramSpec& spec, std::string* src, std::string* log)
+{
+    *src = generate_source(spec);
+    std::vector<char> cubin;
+    return compile(*src, &cubin, log, true);
+}
+
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return n;
+}
+
+cfs_status get_kernel(const ProgramSpec& spec, const char* name, Kernel* out)
+{
+    Driver& d = driver();
+    if (!d.ok) return fail(CFS_ERR_CUDA, d.why);
+    int dev = 0;
+    cfs_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != CFS_OK) return st;
+    // make sure the primary context is current for the driver calls below
+    st = check_cuda(cudaFree(nullptr), "cudaFree(0)");
+    if (st != CFS_OK) return st;
+
+    const std::string src = generate_source(spec);
+    const std::string key = std::to_string(dev) + "\n" + src;
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto it = g_cache.find(key);
+    Program* prog = nullptr;
+    if (it == g_cache.end()) {
+        std::vector<char> cubin;
+        st = compile(src, &cubin, nullptr, false);
+        if (st != CFS_OK) return st;
+        auto p = std::make_unique<Program>();
+        st = check_cu(d.module_load(&p->module, cubin.data()), "cuModuleLoadData");
+        if (st != CFS_OK) return st;
+        prog = p.get();
+        g_cache.emplace(key, std::move(p));
+    } else {
+        prog = it->second.get();
+    }
+    auto kit = prog->kernels.find(name);
+    if (kit == prog->kernels.end()) {
+        Kernel k;
+        CUfunction fn = nullptr;
+        st = check_cu(d.get_function(&fn, prog->module, name), "cuModuleGetFunction");
+        if (st != CFS_OK) return st;
+        k.fn = (void*)fn;
+        k.block = spec.block;
+        st = check_cu(d.occupancy(&k.max_blocks_per_sm, fn, spec.block, 0),
+                      "cuOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (st != CFS_OK) return st;
+        k.num_sms = device_sm_count();
+        kit = prog->kernels.emplace(name, k).first;
+    }
+    *out = kit->second;
+    return CFS_OK;
+}
+
+cfs_status launch(const Kernel& k, unsigned grid, const void* args, size_t args_size,
+                  cudaStream_t stream)
+{
+    (void)args_size;
+    void* params[] = {const_cast<void*>(args)};
+    return check_cu(driver().launch((CUfunction)k.fn, grid, 1, 1, (unsigned)k.block, 1, 1, 0,
+                                    (CUstream)stream, params, nullptr),
+                    "cuLaunchKernel");
+}
+
+}  // namespace cfs

@@ -1,0 +1,103 @@
+"""Shared helpers of the parity tests: run a workload on the GPU through the
+C-ABI binding and on the CPU oracle with the same seeded inputs, and compare
+with the tolerances the tests state."""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_2606_02226_gb300 import workloads as W
+
+EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def gpu_render(wl, jobs=None, stream=None, discards=None, depth_test=None):
+    """Renders every job of ``wl`` on the GPU; returns host numpy buffers and
+    the per-target discard counts."""
+    import torch
+    from paper_2606_02226_gb300 import cfs
+    tensors = [cfs.alloc_target(t) for t in wl.targets]
+    disc = torch.zeros(len(wl.targets), dtype=torch.int64, device="cuda")
+    for job in (jobs or wl.jobs):
+        sysh = cfs.System(job.system)
+        ch = cfs.Chain(wl.chain, job.system.dim)
+        cfs.render(sysh, ch, wl.targets, tensors, n_points=job.n_points, iters=wl.iters,
+                   burn_in=wl.burn_in, seed=wl.seed, system_id=job.system_id,
+                   point_begin=job.point_begin, discards=disc, stream=stream)
+    torch.cuda.synchronize()
+    return [to_host(t, d) for t, d in zip(tensors, wl.targets)], [int(v) for v in disc.cpu()]
+
+
+def to_host(t, desc):
+    a = t.cpu().numpy()
+    if desc.kind == "hist_u32":
+        return a.view(np.uint32)
+    if desc.kind == "depth_u64":
+        return a.view(np.uint64)
+    return a
+
+
+def oracle_render(wl, jobs=None, margin_px=0.0, track=False):
+    bufs = [O.alloc_target_buffer(t) for t in wl.targets]
+    res_all = None
+    for job in (jobs or wl.jobs):
+        res = O.render(job.system, wl.chain, wl.targets, n_points=job.n_points, iters=wl.iters,
+                       burn_in=wl.burn_in, seed=wl.seed, system_id=job.system_id,
+                       point_begin=job.point_begin, margin_px=margin_px, track=track, bufs=bufs)
+        if res_all is None:
+            res_all = res
+        else:
+            for a, r in zip(res_all, res):
+                a.n_splat += r.n_splat
+                a.n_discard += r.n_discard
+                a.n_amb += r.n_amb
+                if track:
+                    a.amb += r.amb
+                    if a.zlo is not None:
+                        np.minimum(a.zlo, r.zlo, out=a.zlo)
+                        np.minimum(a.zhi, r.zhi, out=a.zhi)
+    return res_all
+
+
+def depth_of(keys):
+    return (keys >> np.uint64(32)).astype(np.uint32).view(np.float32)
+
+
+def check_hist_close(g, o, amb, total, rel_l1=1e-5):
+    """Per bin |gpu - oracle| <= the oracle's near-edge slack of that bin, and
+    the summed difference <= rel_l1 of the total."""
+    d = np.abs(g.astype(np.int64) - o.astype(np.int64))
+    slack = amb if d.ndim == amb.ndim else np.broadcast_to(amb, d.shape)
+    bad = d > slack
+    assert not bad.any(), f"{bad.sum()} bins differ beyond the near-edge slack"
+    assert d.sum() <= rel_l1 * total, (d.sum(), total)
+
+
+def check_rgba_close(g, o, amb, total, rel_l1=1e-5):
+    """Palette components are <= 1, so one moved splat changes a channel by
+    at most 1: |gpu - oracle| <= slack per channel; alpha difference summed
+    <= rel_l1 of the total."""
+    d = np.abs(g.astype(np.float64) - o.astype(np.float64))
+    bad = d > amb[..., None]
+    assert not bad.any(), f"{bad.sum()} RGBA values differ beyond the near-edge slack"
+    assert d[..., 3].sum() <= rel_l1 * total, (d[..., 3].sum(), total)
+
+
+def check_depth_close(g, o, zlo, zhi, rel=1e-5):
+    """Per pixel the GPU's depth lies between the lowest depth that may land
+    there and the lowest that surely lands there (relative tolerance ``rel``
+    for FP32 differences of the chain); where the oracle's pixel is
+    unambiguous (zlo == zhi) and depths agree exactly, the colours agree."""
+    ge = g == EMPTY
+    oe = o == EMPTY
+    # a GPU-empty pixel must not have a sure splat
+    assert not (ge & np.isfinite(zhi)).any(), "GPU left a pixel empty that surely has a splat"
+    zg = depth_of(g[~ge]).astype(np.float64)
+    lo = zlo[~ge].astype(np.float64)
+    hi = zhi[~ge].astype(np.float64)
+    assert np.all(np.isfinite(lo)), "GPU splatted where no point can land"
+    assert np.all(zg >= lo * (1 - rel)), "GPU depth below every candidate"
+    assert np.all(zg <= hi * (1 + rel) + (~np.isfinite(hi)) * 1e30), "GPU depth above a sure splat"
+    same = (~ge) & (~oe) & (zlo == zhi) & (g >> np.uint64(32) == o >> np.uint64(32))
+    frac = (g[same] == o[same]).mean() if same.any() else 1.0
+    return frac

@@ -1,0 +1,128 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads,
+exports every symbol the public header declares, validates arguments, and
+its code generator produces programs NVRTC compiles for sm_103a without
+register spills."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2606_02226_gb300 import cfs
+from paper_2606_02226_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(cfs_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = cfs.lib()
+    names = _declared_functions()
+    assert "cfs_render" in names and "cfs_compose" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_version_string():
+    assert "sm_103a" in cfs.version()
+
+
+def _err(fn):
+    with pytest.raises(cfs.CfsError) as e:
+        fn()
+    return e.value.status
+
+
+def test_system_validation():
+    ok = W.Map("affine", (0.5, 0, 0, 0.5, 0, 0))
+    assert _err(lambda: cfs.System(W.System(2, [ok], [0.0]))) == 1
+    assert _err(lambda: cfs.System(W.System(2, [ok, ok], [-1.0, 2.0]))) == 1
+    assert _err(lambda: cfs.System(W.System(2, [ok], [float("nan")]))) == 1
+    assert _err(lambda: cfs.System(W.System(4, [ok], [1.0]))) == 1
+    assert _err(lambda: cfs.System(W.System(2, [ok] * 17, [1.0] * 17))) == 1
+    assert _err(lambda: cfs.System(W.System(3, [W.Map("circle", (0.0,))], [1.0]))) == 1
+    bad = W.Map("affine", (float("inf"), 0, 0, 0.5, 0, 0))
+    assert _err(lambda: cfs.System(W.System(2, [bad], [1.0]))) == 1
+    cfs.System(W.System(2, [ok, ok], [0.0, 1.0]))   # zero probabilities are fine
+
+
+def test_chain_validation():
+    assert _err(lambda: cfs.Chain([W.Op("perspective", (1.0, 0.1))], 2)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("torus", (1.0, 0.3)), W.Op("torus", (1, 0.3))], 2)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("bend", (0.0,))], 3)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("rotate3", (0.1, 5.0))], 3)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("splat", (7,))], 2)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("splat", (0,))] * 33, 2)) == 1
+    c = cfs.Chain([W.Op("torus", (1.0, 0.3)), W.Op("perspective", (2.0, 0.1)),
+                   W.Op("reset"), W.Op("swirl"), W.Op("splat", (0,))], 2)
+    c.set_params(0, (1.0, 0.5))
+    assert _err(lambda: c.set_params(9, (0.0,))) == 1
+    assert _err(lambda: c.set_params(4, (1.0,))) == 1      # a splat's slot is fixed
+
+
+def test_render_argument_errors_need_no_gpu():
+    s = cfs.System(W.square_system())
+    c = cfs.Chain([W.Op("splat", (1,))], 2)
+    t = [W.Target("hist_u32", 8, 8, 4)]
+    # slot 1 but one target: rejected before anything touches the GPU
+    with pytest.raises(cfs.CfsError):
+        cfs.codegen_check(s, c, t)
+    c3 = cfs.Chain([W.Op("torus", (1.0, 0.3)), W.Op("splat", (0,))], 2)
+    with pytest.raises(cfs.CfsError):
+        cfs.codegen_check(cfs.System(W.cloud_system()), c3, t)  # 3D system, 2D chain
+    cd = cfs.Chain([W.Op("splat", (0,))], 2)
+    with pytest.raises(cfs.CfsError):                            # depth needs 3D
+        cfs.codegen_check(s, cd, [W.Target("depth_u64", 8, 8, 1)])
+
+
+def _programs():
+    comp = W.composed_render(n_points=16, iters=30, W=64)
+    yield "square", W.square_system(), W.square_render().chain, W.square_render().targets
+    yield "composed_sq", comp.jobs[0].system, comp.chain, comp.targets
+    yield "composed_si", comp.jobs[1].system, comp.chain, comp.targets
+    yield "circle", W.circle_system(), [W.Op("stretch"), W.Op("splat", (0,))], \
+        [W.Target("hist_u32", 64, 64, 2, (-3, 3, -3, 3))]
+    sq = W.square_system()
+    mixed = W.System(2, sq.maps[:3] + [W.Map("circle", (1.0,))], [0.25] * 4)
+    yield "mixed", mixed, [W.Op("splat", (0,))], [W.Target("hist_u32", 64, 64, 4)]
+    yield "cloud", W.cloud_system(), W.cloud_chain(10), [W.cloud_target(64)]
+    frames = W.animation_frames(n_frames=3)
+    yield "frame", frames[0].system, [W.Op("splat", (0,))], [W.animation_target(256)]
+
+
+@pytest.mark.parametrize("prog", list(_programs()), ids=lambda p: p[0])
+def test_codegen_compiles_without_spills(prog):
+    name, sysd, chain, targets = prog
+    s = cfs.System(sysd)
+    c = cfs.Chain(chain, sysd.dim)
+    for mode in (0, 1):
+        src, log = cfs.codegen_check(s, c, targets, mode=mode)
+        assert "cfs_chain" in src and "cfs_kernels.cuh" in src
+        assert "0 bytes spill stores" in log and "0 bytes spill loads" in log, log
+        assert "error" not in log.lower()
+        regs = [int(m) for m in re.findall(r"Used (\d+) registers", log)]
+        assert regs and max(regs) <= 64, log     # 4 blocks of 256 threads per SM
+
+
+def test_codegen_is_structural():
+    # two systems of the same structure share one program text
+    a = cfs.codegen_check(cfs.System(W.square_system()), cfs.Chain([W.Op("splat", (0,))], 2),
+                          [W.Target("hist_u32", 8, 8, 4)])[0]
+    sq = W.square_system()
+    sq.maps[0] = W.Map("affine", (0.1, 0.2, 0.3, 0.4, 0.5, 0.6))
+    sq.probs = [0.1, 0.2, 0.3, 0.4]
+    b = cfs.codegen_check(cfs.System(sq), cfs.Chain([W.Op("splat", (0,))], 2),
+                          [W.Target("hist_u32", 512, 512, 4, (-1, 2, -1, 2))])[0]
+    assert a == b

@@ -187,6 +187,53 @@ cfs_status cfs_render(const cfs_system* sys, const cfs_chain* chain,
 cfs_status cfs_prepare(const cfs_system* sys, const cfs_chain* chain,
                        const cfs_target* targets, int n_targets);
 
+/* ---- batched rendering (many frames in one persistent launch) ---------- */
+/* One frame of a batch: its own system, range of point indices and targets
+ * (device buffers of the caller).  Frames of a batch share the chain, the
+ * step counts and the seed; their systems have maps of one kind (all affine
+ * or all circle) and the same dimension; their targets have the same kinds. */
+typedef struct {
+    const cfs_system* system;
+    uint32_t n_points;
+    uint32_t point_begin;
+    uint32_t system_id;
+    uint32_t reserved;
+    cfs_target targets[CFS_MAX_TARGETS];
+} cfs_frame;
+
+typedef struct cfs_batch cfs_batch;
+
+/* Plans a batch (the paper's animation frames and in-betweens, Section 4):
+ * copies the frames (systems by value), compiles the batch program, cuts the
+ * points into work items numbered frame by frame and allocates a device
+ * workspace (frame descriptors, work counter, per-frame discard counters)
+ * owned by the batch.  The kernel is persistent: CTAs take items from the
+ * counter with one atomicAdd each and never wait for one another. */
+cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
+                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
+                            cfs_batch** out);
+/* Replaces frame `frame`'s system (same dimension and map kind, at most as
+ * many thresholds as planned); waits for the previous launch's upload. */
+cfs_status cfs_batch_set_system(cfs_batch* batch, int frame, const cfs_system* sys);
+/* Enqueues the batch on `stream` as one CUDA graph: upload of the frame
+ * descriptors, counter reset, (clear != 0) clear of every frame's targets,
+ * the persistent kernel.  The graph is captured at the first launch of each
+ * clear mode. */
+cfs_status cfs_batch_launch(cfs_batch* batch, int clear, void* stream);
+/* Discarded splats of the last launch, host u64 [n_frames][n_targets];
+ * waits for that launch. */
+cfs_status cfs_batch_discards(cfs_batch* batch, uint64_t* out);
+/* Work items, points per item, persistent grid size. */
+cfs_status cfs_batch_info(const cfs_batch* batch, uint32_t* n_items, uint32_t* chunk,
+                          uint32_t* grid);
+/* Waits for the batch's last launch, then frees it. */
+cfs_status cfs_batch_destroy(cfs_batch* batch);
+/* One-shot: create, launch, destroy.  Returns after the frames are rendered
+ * (the plan's workspace is freed on return). */
+cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
+                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
+                            int clear, void* stream);
+
 /* Records, for the n_ids points listed in the device array `ids` (global
  * indices), every step's map index (device i32 [n_ids][steps]), iterated
  * point (device f32 [n_ids][steps][3]) and, per SPLAT op of the chain, the
@@ -198,7 +245,8 @@ cfs_status cfs_trace(const cfs_system* sys, const cfs_chain* chain,
                      int32_t* k_out, float* p_out, float* q_out, void* stream);
 
 /* Debugging aid, needs no GPU: writes the CUDA source of the fused program
- * that cfs_render (mode 0) or cfs_trace (mode 1) would use into `src` (at most
+ * that cfs_render (mode 0), cfs_trace (mode 1) or a batch of frames like this
+ * one (mode 2) would use into `src` (at most
  * src_cap bytes, NUL-terminated), compiles it with NVRTC for sm_103a and
  * writes the compiler log, including ptxas register/spill usage, into `log`.
  * Either buffer may be NULL. */

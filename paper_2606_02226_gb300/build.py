@@ -24,8 +24,8 @@ LIB = os.path.join(BUILD, "libcfs.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 EMBEDDED = [("kSrcArgs", "cfs_args.h"), ("kSrcDevice", "cfs_device.cuh"),
             ("kSrcKernels", "cfs_kernels.cuh")]
-SOURCES = ["cfs_api.cpp", "cfs_codegen.cpp", "cfs_runtime.cpp", "cfs_builtin.cu",
-           "cfs_embed.cpp"]
+SOURCES = ["cfs_api.cpp", "cfs_batch.cpp", "cfs_codegen.cpp", "cfs_runtime.cpp",
+           "cfs_builtin.cu", "cfs_embed.cpp"]
 _LOCK = threading.Lock()
 
 

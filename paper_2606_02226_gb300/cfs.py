@@ -66,6 +66,12 @@ class cfs_render_params(ctypes.Structure):
                 ("start", ctypes.c_void_p), ("discards", ctypes.c_void_p)]
 
 
+class cfs_frame(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_void_p), ("n_points", ctypes.c_uint32),
+                ("point_begin", ctypes.c_uint32), ("system_id", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("targets", cfs_target * MAX_TARGETS)]
+
+
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "cfs_system_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(cfs_map),
@@ -88,6 +94,19 @@ _SIGNATURES = {
     "cfs_philox": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P]),
     "cfs_atomic_bench": (ctypes.c_int, [ctypes.c_int, _P, ctypes.c_uint64, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_uint32, _P]),
+    "cfs_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
+                                        ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "cfs_batch_set_system": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "cfs_batch_launch": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "cfs_batch_discards": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "cfs_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.POINTER(ctypes.c_uint32)]),
+    "cfs_batch_destroy": (ctypes.c_int, [_P]),
+    "cfs_render_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
+                                        ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint64, ctypes.c_int, _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -325,6 +344,77 @@ def philox(ctr, key, stream=None):
     _check(lib().cfs_philox(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), n,
                             _stream_handle(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+def _frames(frames):
+    """frames: list of (System, n_points, point_begin, system_id, target_descs,
+    target_tensors) -> ctypes array."""
+    arr = (cfs_frame * len(frames))()
+    n_t = None
+    for f, (sysh, n, pb, sid, descs, tens) in enumerate(frames):
+        arr[f].system = sysh.handle
+        arr[f].n_points, arr[f].point_begin, arr[f].system_id = int(n), int(pb), int(sid)
+        t_arr, nt = make_targets(descs, tens)
+        for t in range(nt):
+            arr[f].targets[t] = t_arr[t]
+        n_t = nt if n_t is None else n_t
+        if nt != n_t:
+            raise ValueError("every frame needs the same number of targets")
+    return arr, (n_t or 0)
+
+
+class Batch:
+    """Many frames in one persistent launch replayed as a CUDA graph.  Frames
+    are (System, n_points, point_begin, system_id, target_descs,
+    target_tensors) tuples; they share ``chain``, ``iters``, ``burn_in`` and
+    ``seed``."""
+
+    def __init__(self, chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 0):
+        arr, nt = _frames(frames)
+        h = _P()
+        _check(lib().cfs_batch_create(chain.handle, nt, arr, len(frames), iters, burn_in,
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(h)))
+        self.handle = h
+        self.n_frames = len(frames)
+        self.n_targets = nt
+        self._keep = [f[0] for f in frames] + [chain]
+
+    def launch(self, clear: bool = True, stream=None):
+        _check(lib().cfs_batch_launch(self.handle, 1 if clear else 0, _stream_handle(stream)))
+
+    def set_system(self, frame: int, system: System):
+        _check(lib().cfs_batch_set_system(self.handle, frame, system.handle))
+        self._keep.append(system)
+
+    def discards(self) -> np.ndarray:
+        out = np.zeros((self.n_frames, max(1, self.n_targets)), dtype=np.uint64)
+        _check(lib().cfs_batch_discards(self.handle,
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out
+
+    def info(self):
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(lib().cfs_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                    ctypes.byref(c)))
+        return {"n_items": a.value, "chunk": b.value, "grid": c.value}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _LIB is not None:
+            _LIB.cfs_batch_destroy(h)
+            self.handle = None
+
+
+def render_batch(chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 0,
+                 clear: bool = True, stream=None):
+    """One-shot batch: plans, launches and frees (returns after rendering)."""
+    arr, nt = _frames(frames)
+    _check(lib().cfs_render_batch(chain.handle, nt, arr, len(frames), iters, burn_in,
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if clear else 0,
+                                  _stream_handle(stream)))
 
 
 def atomic_bench(kind: int, buf, n_elems: int, blocks: int, iters: int, seed: int = 1,

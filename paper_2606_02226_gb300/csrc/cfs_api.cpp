@@ -5,6 +5,7 @@
 // programs on the caller's stream.  Every step of the chaos game itself runs
 // in the generated CUDA kernels.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <sstream>
@@ -157,10 +158,18 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
             sp.splats.push_back(s);
         }
     }
-    // register budget: 256 threads x 4 blocks leaves 64 registers per thread
+    // register budget: 256 threads x 8 blocks (full occupancy) leaves 32
+    // registers per thread; the generated programs fit without spills
     sp.block = 256;
-    sp.min_blocks = 4;
+    sp.min_blocks = 8;
     sp.depth_test = 1;
+    // launch-shape knobs for tuning sweeps (all variants compute the same)
+    if (const char* e = std::getenv("CFS_BLOCK")) sp.block = std::atoi(e);
+    if (const char* e = std::getenv("CFS_MINB")) sp.min_blocks = std::atoi(e);
+    if (const char* e = std::getenv("CFS_DEPTH_TEST")) sp.depth_test = std::atoi(e);
+    if (sp.block != 128 && sp.block != 256 && sp.block != 512) sp.block = 256;
+    if (sp.min_blocks < 1 || sp.min_blocks > 16) sp.min_blocks = 4;
+    sp.depth_test = sp.depth_test ? 1 : 0;
     return sp;
 }
 
@@ -223,6 +232,22 @@ cfs_status validate_run(const cfs_system* sys, const cfs_chain* ch, const cfs_re
 }
 
 }  // namespace
+
+cfs_status validate_targets_ext(const cfs_chain* ch, const cfs_target* tg, int n_tg)
+{
+    return validate_targets(ch, tg, n_tg);
+}
+
+// chain constants, Philox round keys and step range of a launch
+void fill_args_common(cfs_launch_args* a, const cfs_chain* ch, uint64_t seed, uint32_t iters,
+                      uint32_t burn_in)
+{
+    std::memset(a, 0, sizeof(*a));
+    for (int o = 0; o < ch->n_ops; ++o) derive_op_params(ch->ops[o], a->op[o]);
+    philox_round_keys(seed, a->rk);
+    a->iters = iters;
+    a->burn_in = burn_in;
+}
 }  // namespace cfs
 
 using namespace cfs;
@@ -433,14 +458,23 @@ cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
     if (!sys || !chain) return fail(CFS_ERR_INVALID_ARG, "NULL system or chain");
     if (chain->dim_in != sys->dim)
         return fail(CFS_ERR_INVALID_ARG, "chain was composed for another dimension");
-    if (mode != 0 && mode != 1) return fail(CFS_ERR_INVALID_ARG, "mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(CFS_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
     cfs_status st = CFS_OK;
-    if (mode == 0) {
+    if (mode != 1) {
         st = validate_targets(chain, targets, n_targets);
         if (st != CFS_OK) return st;
     }
-    ProgramSpec sp = make_spec(mode == 0 ? Mode::Render : Mode::Trace, sys, chain,
-                               mode == 0 ? targets : nullptr, mode == 0 ? n_targets : 0, false);
+    const bool tg = mode != 1;
+    ProgramSpec sp = make_spec(mode == 0 ? Mode::Render : (mode == 1 ? Mode::Trace : Mode::Batch),
+                               sys, chain, tg ? targets : nullptr, tg ? n_targets : 0, false);
+    if (mode == 2) {
+        for (int k = 0; k < sys->n_maps; ++k)
+            if (sys->maps[k].kind != sys->maps[0].kind)
+                return fail(CFS_ERR_UNSUPPORTED, "a batch needs maps of one kind");
+        sp.n_maps = CFS_MAX_MAPS;
+        for (int j = 0; j < CFS_MAX_MAPS; ++j) sp.map_kind[j] = sys->maps[0].kind;
+        sp.spill_allowance = 64;
+    }
     std::string s, l;
     st = compile_only(sp, &s, &l);
     auto copy = [](const std::string& from, char* to, size_t cap) {

@@ -28,6 +28,16 @@ typedef struct {
     float prm[12][CFS_A_MAX_MAPS];      /* map parameters, SoA: prm[j][k] */
 } cfs_dev_system;
 
+/* one frame of a batch (device copy, read by the persistent batch kernel) */
+typedef struct {
+    unsigned int T[CFS_A_MAX_MAPS];
+    int n_maps, n_cmp, dim, pad;
+    float prm[12][CFS_A_MAX_MAPS];
+    unsigned int n_points, point_begin, system_id, item_begin;   /* first work item */
+    unsigned int chunk, pad1, pad2, pad3;                        /* points per item */
+    cfs_dev_target tg[CFS_A_MAX_TARGETS];
+} cfs_dev_frame;
+
 typedef struct {
     cfs_dev_system sys;
     float op[CFS_A_MAX_OPS][CFS_A_OP_PARAMS];   /* derived per-op constants */
@@ -39,6 +49,9 @@ typedef struct {
     unsigned long long k_out, p_out, q_out;   /* trace outputs */
     unsigned int system_id, point_begin, n_points, step_begin;
     unsigned int iters, burn_in, flags, pad2;
+    /* batch: frames, work counter, per-frame discard counters */
+    unsigned long long frames, work_counter, frame_discards;
+    unsigned int n_frames, n_items, chunk, pad3;
 } cfs_launch_args;
 
 #endif

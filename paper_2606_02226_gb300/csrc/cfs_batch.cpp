@@ -1,0 +1,374 @@
+// cfs_batch.cpp -- batched rendering of many frames in one persistent launch
+// (animation frames and in-betweens of different systems; the paper's
+// smear-frame / in-between application, Section 4).
+//
+// A batch is planned once on the host: frame descriptors (thresholds, map
+// tables, target geometry, point ranges) are packed into a pinned staging
+// buffer, the work is cut into items of `chunk` points numbered frame by
+// frame, and the whole frame -- descriptor upload, counter reset, optional
+// clears of every frame's targets, the persistent kernel -- is captured into
+// a CUDA graph that each cfs_batch_launch replays on the caller's stream.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <sstream>
+#include <vector>
+
+#include "cfs_internal.h"
+
+namespace cfs {
+void fill_args_common(cfs_launch_args* a, const cfs_chain* ch, uint64_t seed, uint32_t iters,
+                      uint32_t burn_in);
+cfs_status validate_targets_ext(const cfs_chain* ch, const cfs_target* tg, int n_tg);
+}  // namespace cfs
+
+struct cfs_batch {
+    int device = 0;
+    int n_frames = 0;
+    int n_targets = 0;
+    cfs_chain chain;
+    uint32_t iters = 0, burn_in = 0;
+    uint64_t seed = 0;
+    std::vector<cfs_frame> frames;        // host copy (targets by value)
+    std::vector<cfs_system> systems;      // host copies
+    std::vector<uint32_t> chunks;         // points per item, per frame
+    cfs::ProgramSpec spec;
+    cfs::Kernel kernel;
+    cfs_launch_args args;
+    uint32_t chunk = 0, n_items = 0, grid = 0;
+    cfs_dev_frame* h_frames = nullptr;    // pinned staging
+    unsigned char* d_work = nullptr;      // frames | counter | discards
+    cfs_dev_frame* d_frames = nullptr;
+    unsigned int* d_counter = nullptr;
+    unsigned long long* d_disc = nullptr;
+    size_t work_bytes = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [clear]
+    cudaEvent_t done = nullptr;
+    bool launched = false;
+};
+
+namespace {
+using namespace cfs;
+
+void pack_frame(cfs_dev_frame* d, const cfs_system& s, const cfs_frame& f, int n_targets,
+                uint32_t item_begin, uint32_t chunk)
+{
+    std::memset(d, 0, sizeof(*d));
+    for (int j = 0; j < s.n_cmp; ++j) d->T[j] = s.T[j];
+    d->n_maps = s.n_maps;
+    d->n_cmp = s.n_cmp;
+    d->dim = s.dim;
+    for (int k = 0; k < s.n_maps; ++k)
+        for (int j = 0; j < 12; ++j) d->prm[j][k] = s.maps[k].params[j];
+    d->n_points = f.n_points;
+    d->point_begin = f.point_begin;
+    d->system_id = f.system_id;
+    d->item_begin = item_begin;
+    d->chunk = chunk;
+    for (int t = 0; t < n_targets; ++t) {
+        const cfs_target& g = f.targets[t];
+        cfs_dev_target& o = d->tg[t];
+        o.data = (unsigned long long)(uintptr_t)g.data;
+        o.W = g.width;
+        o.H = g.height;
+        o.C = g.channels < 1 ? 1 : g.channels;
+        o.kind = g.kind;
+        o.x0 = g.x0; o.x1 = g.x1; o.y0 = g.y0; o.y1 = g.y1;
+        o.sx = (float)g.width / (g.x1 - g.x0);
+        o.sy = (float)g.height / (g.y1 - g.y0);
+        std::memcpy(o.palette, g.palette, sizeof(o.palette));
+        std::memcpy(o.palette8, g.palette8, sizeof(o.palette8));
+    }
+}
+
+size_t target_bytes(const cfs_target& g)
+{
+    size_t n = (size_t)g.width * (size_t)g.height;
+    if (g.kind == CFS_TARGET_HIST_U32) return n * 4 * (size_t)(g.channels < 1 ? 1 : g.channels);
+    if (g.kind == CFS_TARGET_RGBA_F32) return n * 16;
+    return n * 8;
+}
+
+void release(cfs_batch* b)
+{
+    for (auto& e : b->exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->d_work) cudaFree(b->d_work);
+    if (b->h_frames) cudaFreeHost(b->h_frames);
+}
+
+cfs_status capture(cfs_batch* b, int clear)
+{
+    cudaStream_t s = b->cap_stream;
+    cfs_status st = check_cuda(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal),
+                               "cudaStreamBeginCapture");
+    if (st != CFS_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(b->d_frames, b->h_frames,
+                                    sizeof(cfs_dev_frame) * (size_t)b->n_frames,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->d_counter, 0,
+                            b->work_bytes - ((unsigned char*)b->d_counter - b->d_work), s);
+    if (e == cudaSuccess && clear) {
+        for (int f = 0; f < b->n_frames && e == cudaSuccess; ++f)
+            for (int t = 0; t < b->n_targets && e == cudaSuccess; ++t) {
+                const cfs_target& g = b->frames[f].targets[t];
+                e = cudaMemsetAsync(g.data, g.kind == CFS_TARGET_DEPTH_U64 ? 0xFF : 0,
+                                    target_bytes(g), s);
+            }
+    }
+    cfs_status lst = CFS_OK;
+    if (e == cudaSuccess && b->n_items > 0)
+        lst = launch(b->kernel, b->grid, &b->args, sizeof(b->args), s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return check_cuda(e, "batch capture");
+    }
+    if (lst != CFS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return lst;
+    }
+    st = check_cuda(e2, "cudaStreamEndCapture");
+    if (st != CFS_OK) return st;
+    st = check_cuda(cudaGraphInstantiate(&b->exec[clear], g, 0), "cudaGraphInstantiate");
+    cudaGraphDestroy(g);
+    return st;
+}
+}  // namespace
+
+extern "C" {
+
+cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
+                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
+                            cfs_batch** out)
+{
+    clear_error();
+    if (!out) return fail(CFS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!chain || !frames || n_frames <= 0)
+        return fail(CFS_ERR_INVALID_ARG, "need a chain and at least one frame");
+    if (n_targets < 0 || n_targets > CFS_MAX_TARGETS)
+        return fail(CFS_ERR_INVALID_ARG, "n_targets must be in 0..4");
+    const cfs_system* s0 = frames[0].system;
+    if (!s0) return fail(CFS_ERR_INVALID_ARG, "frame 0 has no system");
+    uint64_t total_items = 0;
+    int max_cmp = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const cfs_frame& fr = frames[f];
+        std::ostringstream m;
+        m << "frame " << f << ": ";
+        if (!fr.system) return fail(CFS_ERR_INVALID_ARG, m.str() + "no system");
+        if (fr.system->dim != chain->dim_in)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "system dimension differs from the chain's");
+        for (int k = 0; k < fr.system->n_maps; ++k)
+            if (fr.system->maps[k].kind != s0->maps[0].kind)
+                return fail(CFS_ERR_UNSUPPORTED,
+                            m.str() + "a batch needs maps of one kind in every frame");
+        if ((uint64_t)fr.point_begin + fr.n_points > (1ull << 32))
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "point indices exceed 2^32");
+        cfs_status st = validate_targets_ext(chain, fr.targets, n_targets);
+        if (st != CFS_OK) return fail(st, m.str() + cfs_last_error());
+        for (int t = 0; t < n_targets; ++t)
+            if (fr.targets[t].kind != frames[0].targets[t].kind ||
+                (fr.targets[t].kind == CFS_TARGET_HIST_U32 &&
+                 fr.targets[t].channels != frames[0].targets[t].channels))
+                return fail(CFS_ERR_INVALID_ARG, m.str() + "target kinds differ between frames");
+        max_cmp = std::max(max_cmp, fr.system->n_cmp);
+    }
+    if (burn_in > iters) burn_in = iters;
+
+    cfs_batch* b = new (std::nothrow) cfs_batch();
+    if (!b) return fail(CFS_ERR_OOM, "host allocation failed");
+    cfs_status st = check_cuda(cudaGetDevice(&b->device), "cudaGetDevice");
+    if (st != CFS_OK) { delete b; return st; }
+    b->n_frames = n_frames;
+    b->n_targets = n_targets;
+    b->chain = *chain;
+    b->iters = iters;
+    b->burn_in = burn_in;
+    b->seed = seed;
+    b->frames.assign(frames, frames + n_frames);
+    b->systems.resize(n_frames);
+    for (int f = 0; f < n_frames; ++f) b->systems[f] = *frames[f].system;
+
+    // program: table-driven generator, thresholds from shared memory
+    ProgramSpec& sp = b->spec;
+    sp.mode = Mode::Batch;
+    sp.dim = s0->dim;
+    sp.n_maps = CFS_MAX_MAPS;
+    for (int j = 0; j < CFS_MAX_MAPS; ++j) sp.map_kind[j] = s0->maps[0].kind;
+    sp.n_cmp = max_cmp;
+    sp.n_ops = chain->n_ops;
+    sp.n_targets = n_targets;
+    for (int o = 0; o < chain->n_ops; ++o) {
+        sp.op_kind[o] = chain->ops[o].kind;
+        if (chain->ops[o].kind == CFS_OP_SPLAT) {
+            const int slot = (int)chain->ops[o].params[0];
+            SplatSpec ss;
+            ss.slot = slot;
+            ss.kind = frames[0].targets[slot].kind;
+            ss.channels = ss.kind == CFS_TARGET_HIST_U32 ? frames[0].targets[slot].channels : 1;
+            sp.splats.push_back(ss);
+        }
+    }
+    sp.block = 256;
+    sp.min_blocks = 8;
+    sp.spill_allowance = 64;
+    sp.depth_test = 1;
+    if (const char* e = std::getenv("CFS_BATCH_MINB")) sp.min_blocks = std::max(1, std::atoi(e));
+    st = get_kernel(sp, "cfs_batch_kernel", &b->kernel);
+    if (st != CFS_OK) { delete b; return st; }
+
+    // Items: every frame is cut into at least `grid` items (whole warps of
+    // points, at most chunk_max), so all CTAs work on one or two frames at a
+    // time and the live layers stay in L2.
+    b->grid = (uint32_t)std::max(1, b->kernel.max_blocks_per_sm * std::max(1, b->kernel.num_sms));
+    b->chunk = 8u * (uint32_t)sp.block;
+    if (const char* e = std::getenv("CFS_BATCH_CHUNK")) {
+        const int c = std::atoi(e);
+        if (c >= 32 && c % 32 == 0) b->chunk = (uint32_t)c;
+    }
+    b->chunks.resize(n_frames);
+    for (int f = 0; f < n_frames; ++f) {
+        const uint64_t per = ((uint64_t)frames[f].n_points / b->grid) / 32 * 32;
+        const uint32_t c = (uint32_t)std::min<uint64_t>(b->chunk, std::max<uint64_t>(32, per));
+        b->chunks[f] = c;
+        total_items += ((uint64_t)frames[f].n_points + c - 1) / c;
+    }
+    if (total_items >= (1ull << 31)) {
+        delete b;
+        return fail(CFS_ERR_INVALID_ARG, "too many work items");
+    }
+    b->n_items = (uint32_t)total_items;
+    if (b->grid > b->n_items && b->n_items > 0) b->grid = b->n_items;
+
+    // workspace: frames | counter (u32, padded to 256 B) | discards
+    const size_t fbytes = sizeof(cfs_dev_frame) * (size_t)n_frames;
+    const size_t off_counter = (fbytes + 255) & ~(size_t)255;
+    const size_t off_disc = off_counter + 256;
+    b->work_bytes = off_disc + sizeof(unsigned long long) * (size_t)n_frames *
+                                   (size_t)std::max(1, n_targets);
+    st = check_cuda(cudaMalloc(&b->d_work, b->work_bytes), "cudaMalloc(batch workspace)");
+    if (st == CFS_OK)
+        st = check_cuda(cudaMallocHost(&b->h_frames, fbytes), "cudaMallocHost(batch frames)");
+    if (st == CFS_OK)
+        st = check_cuda(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking),
+                        "cudaStreamCreate");
+    if (st == CFS_OK)
+        st = check_cuda(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming),
+                        "cudaEventCreate");
+    if (st != CFS_OK) { release(b); delete b; return st; }
+    b->d_frames = reinterpret_cast<cfs_dev_frame*>(b->d_work);
+    b->d_counter = reinterpret_cast<unsigned int*>(b->d_work + off_counter);
+    b->d_disc = reinterpret_cast<unsigned long long*>(b->d_work + off_disc);
+
+    uint32_t item = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        pack_frame(&b->h_frames[f], b->systems[f], b->frames[f], n_targets, item, b->chunks[f]);
+        item += (frames[f].n_points + b->chunks[f] - 1) / b->chunks[f];
+    }
+    fill_args_common(&b->args, chain, seed, iters, burn_in);
+    b->args.frames = (unsigned long long)(uintptr_t)b->d_frames;
+    b->args.work_counter = (unsigned long long)(uintptr_t)b->d_counter;
+    b->args.frame_discards = (unsigned long long)(uintptr_t)b->d_disc;
+    b->args.n_frames = (unsigned)n_frames;
+    b->args.n_items = b->n_items;
+    b->args.chunk = b->chunk;
+    *out = b;
+    return CFS_OK;
+}
+
+cfs_status cfs_batch_set_system(cfs_batch* b, int frame, const cfs_system* sys)
+{
+    clear_error();
+    if (!b || !sys) return fail(CFS_ERR_INVALID_ARG, "NULL batch or system");
+    if (frame < 0 || frame >= b->n_frames) return fail(CFS_ERR_INVALID_ARG, "frame out of range");
+    if (sys->dim != b->chain.dim_in || sys->n_cmp > b->spec.n_cmp)
+        return fail(CFS_ERR_INVALID_ARG, "system does not fit the batch's program "
+                                         "(dimension or more maps than planned)");
+    for (int k = 0; k < sys->n_maps; ++k)
+        if (sys->maps[k].kind != b->spec.map_kind[0])
+            return fail(CFS_ERR_UNSUPPORTED, "a batch needs maps of one kind");
+    // the staging buffer is read by the previous launch's upload: wait for it
+    if (b->launched) {
+        cfs_status st = check_cuda(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+        if (st != CFS_OK) return st;
+    }
+    b->systems[frame] = *sys;
+    const uint32_t item_begin = b->h_frames[frame].item_begin;
+    pack_frame(&b->h_frames[frame], b->systems[frame], b->frames[frame], b->n_targets, item_begin,
+               b->chunks[frame]);
+    return CFS_OK;
+}
+
+cfs_status cfs_batch_launch(cfs_batch* b, int clear, void* stream)
+{
+    clear_error();
+    if (!b) return fail(CFS_ERR_INVALID_ARG, "NULL batch");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(CFS_ERR_INVALID_ARG, "batch belongs to another device");
+    clear = clear ? 1 : 0;
+    if (!b->exec[clear]) {
+        cfs_status st = capture(b, clear);
+        if (st != CFS_OK) return st;
+    }
+    cfs_status st = check_cuda(cudaGraphLaunch(b->exec[clear], (cudaStream_t)stream),
+                               "cudaGraphLaunch");
+    if (st != CFS_OK) return st;
+    b->launched = true;
+    return check_cuda(cudaEventRecord(b->done, (cudaStream_t)stream), "cudaEventRecord");
+}
+
+cfs_status cfs_batch_discards(cfs_batch* b, uint64_t* out)
+{
+    clear_error();
+    if (!b || !out) return fail(CFS_ERR_INVALID_ARG, "NULL batch or out");
+    if (b->launched) {
+        cfs_status st = check_cuda(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+        if (st != CFS_OK) return st;
+    }
+    return check_cuda(cudaMemcpy(out, b->d_disc,
+                                 sizeof(uint64_t) * (size_t)b->n_frames *
+                                     (size_t)std::max(1, b->n_targets),
+                                 cudaMemcpyDeviceToHost),
+                      "cudaMemcpy(discards)");
+}
+
+cfs_status cfs_batch_info(const cfs_batch* b, uint32_t* n_items, uint32_t* chunk, uint32_t* grid)
+{
+    clear_error();
+    if (!b) return fail(CFS_ERR_INVALID_ARG, "NULL batch");
+    if (n_items) *n_items = b->n_items;
+    if (chunk) *chunk = b->chunk;
+    if (grid) *grid = b->grid;
+    return CFS_OK;
+}
+
+cfs_status cfs_batch_destroy(cfs_batch* b)
+{
+    if (!b) return CFS_OK;
+    if (b->launched) cudaEventSynchronize(b->done);
+    release(b);
+    delete b;
+    return CFS_OK;
+}
+
+cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
+                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
+                            int clear, void* stream)
+{
+    cfs_batch* b = nullptr;
+    cfs_status st = cfs_batch_create(chain, n_targets, frames, n_frames, iters, burn_in, seed, &b);
+    if (st != CFS_OK) return st;
+    st = cfs_batch_launch(b, clear, stream);
+    cfs_batch_destroy(b);   // waits for the launch: the workspace must outlive it
+    return st;
+}
+
+}  // extern "C"

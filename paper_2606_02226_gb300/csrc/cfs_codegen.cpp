@@ -19,7 +19,8 @@ std::string ProgramSpec::key() const
 {
     std::ostringstream s;
     s << "m" << int(mode) << ".d" << dim << ".n" << n_maps << ".c" << n_cmp << ".r" << reuse
-      << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << ".k";
+      << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << "."
+      << spill_allowance << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
     for (int j = 0; j < n_ops; ++j) s << op_kind[j] << ",";
@@ -88,11 +89,11 @@ static void emit_gen_map(std::ostringstream& s, const ProgramSpec& sp)
 // Chain: the copy of the point through every op, splats where the chain says.
 static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
 {
-    s << "__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a, const CfsSmem& sm,"
-         " float px, float py, float pz, int k, u32* disc, bool do_splat, float* rec,"
-         " float& ox, float& oy, float& oz)\n{\n";
+    s << "template <class TG>\n__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a,"
+         " const TG& tg, const CfsSmem& sm, float px, float py, float pz, int k, u32* disc,"
+         " bool do_splat, float* rec, float& ox, float& oy, float& oz)\n{\n";
     s << "    float qx = px, qy = py, qz = pz;\n    bool alive = true;\n";
-    s << "    (void)sm; (void)disc; (void)do_splat; (void)rec; (void)k;\n";
+    s << "    (void)a; (void)tg; (void)sm; (void)disc; (void)do_splat; (void)rec; (void)k;\n";
     size_t si = 0;
     for (int o = 0; o < sp.n_ops; ++o) {
         s << "    /* op " << o << " */ ";
@@ -129,13 +130,13 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
               << "] = alive ? 1.0f : 0.0f; }\n";
             s << "    if (do_splat) ";
             if (t.kind == CFS_TARGET_HIST_U32)
-                s << "cfs_splat_hist(a.tg[" << t.slot << "], qx, qy, alive, k % " << t.channels
+                s << "cfs_splat_hist(tg[" << t.slot << "], qx, qy, alive, k % " << t.channels
                   << ", disc[" << t.slot << "]);\n";
             else if (t.kind == CFS_TARGET_RGBA_F32)
-                s << "cfs_splat_rgba(a.tg[" << t.slot << "], qx, qy, alive, sm.pal[" << t.slot
+                s << "cfs_splat_rgba(tg[" << t.slot << "], qx, qy, alive, sm.pal[" << t.slot
                   << "][k], disc[" << t.slot << "]);\n";
             else
-                s << "cfs_splat_depth(a.tg[" << t.slot << "], qx, qy, qz, alive, sm.pal8["
+                s << "cfs_splat_depth(tg[" << t.slot << "], qx, qy, qz, alive, sm.pal8["
                   << t.slot << "][k], disc[" << t.slot << "]);\n";
             ++si;
             break;
@@ -155,6 +156,7 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_NT " << sp.n_targets << "\n";
     s << "#define CFS_NSPLAT_ARR " << (sp.splats.empty() ? 1 : sp.splats.size()) << "\n";
     s << "#define CFS_REUSE " << (sp.reuse ? 1 : 0) << "\n";
+    s << "#define CFS_BATCH " << (sp.mode == Mode::Batch ? 1 : 0) << "\n";
     s << "#define CFS_DEPTH_TEST " << sp.depth_test << "\n";
     s << "#define CFS_BLOCK " << sp.block << "\n";
     s << "#define CFS_MINB " << sp.min_blocks << "\n";

@@ -229,27 +229,29 @@ __device__ __forceinline__ int cfs_bin(float u, float lo, float hi, float scale,
     return in ? b : -1;
 }
 
+/* The splat reductions carry no "memory" clobber: nothing in a kernel reads
+ * a target except the depth test, which is correct under any order (keys
+ * only decrease), so the compiler may schedule them freely. */
 __device__ __forceinline__ void cfs_red_add_u32(u32* p, u32 v)
 {
-    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v));
 }
 
 __device__ __forceinline__ void cfs_red_add_v4f32(float* p, float4 v)
 {
     asm volatile("red.global.v4.f32.add [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y),
-                 "f"(v.z), "f"(v.w)
-                 : "memory");
+                 "f"(v.z), "f"(v.w));
 }
 
 __device__ __forceinline__ void cfs_red_min_u64(u64* p, u64 v)
 {
-    asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v));
 }
 
 __device__ __forceinline__ u64 cfs_ld_relaxed_u64(const u64* p)
 {
     u64 v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
 

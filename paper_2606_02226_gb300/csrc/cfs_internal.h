@@ -54,7 +54,8 @@ struct ProgramSpec {
     int n_targets = 0;
     int depth_test = 1;
     int block = 256;
-    int min_blocks = 4;
+    int min_blocks = 8;        // upper bound; lowered while ptxas spills
+    int spill_allowance = 0;   // bytes of spill stores accepted at min_blocks
 
     std::string key() const;
 };

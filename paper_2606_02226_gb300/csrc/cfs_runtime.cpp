@@ -8,6 +8,9 @@
 #include <cuda.h>
 #include <nvrtc.h>
 
+#include <algorithm>
+#include <cctype>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -96,6 +99,7 @@ cfs_status check_cu(CUresult r, const char* what)
 
 struct Program {
     CUmodule module = nullptr;
+    int min_blocks = 0;
     std::unordered_map<std::string, Kernel> kernels;
 };
 
@@ -138,11 +142,45 @@ cfs_status compile(const std::string& src, std::vector<char>* cubin, std::string
 }
 }  // namespace
 
+int spill_bytes(const std::string& log)
+{
+    int worst = 0;
+    const std::string tag = " bytes spill stores";
+    for (size_t p = log.find(tag); p != std::string::npos; p = log.find(tag, p + 1)) {
+        size_t b = p;
+        while (b > 0 && std::isdigit((unsigned char)log[b - 1])) --b;
+        worst = std::max(worst, std::atoi(log.c_str() + b));
+    }
+    return worst;
+}
+
+// Occupancy search: compile at the spec's blocks/SM; while ptxas reports more
+// spill bytes than the spec allows, try fewer blocks per SM (more registers).
+cfs_status select_and_compile(const ProgramSpec& spec, std::string* src, std::vector<char>* cubin,
+                              std::string* log, int* chosen_min_blocks)
+{
+    const int cands[] = {spec.min_blocks, 6, 4, 2};
+    cfs_status st = CFS_OK;
+    int last = -1;
+    for (int c : cands) {
+        if (c > spec.min_blocks || c == last) continue;
+        last = c;
+        ProgramSpec sp = spec;
+        sp.min_blocks = c;
+        *src = generate_source(sp);
+        st = compile(*src, cubin, log, true);
+        if (st != CFS_OK) return st;
+        *chosen_min_blocks = c;
+        if (spill_bytes(*log) <= spec.spill_allowance) break;
+    }
+    return st;
+}
+
 cfs_status compile_only(const ProgramSpec& spec, std::string* src, std::string* log)
 {
-    *src = generate_source(spec);
     std::vector<char> cubin;
-    return compile(*src, &cubin, log, true);
+    int mb = 0;
+    return select_and_compile(spec, src, &cubin, log, &mb);
 }
 
 int device_sm_count()
@@ -164,18 +202,20 @@ cfs_status get_kernel(const ProgramSpec& spec, const char* name, Kernel* out)
     st = check_cuda(cudaFree(nullptr), "cudaFree(0)");
     if (st != CFS_OK) return st;
 
-    const std::string src = generate_source(spec);
-    const std::string key = std::to_string(dev) + "\n" + src;
+    const std::string key = std::to_string(dev) + "\n" + spec.key();
     std::lock_guard<std::mutex> lock(g_cache_mu);
     auto it = g_cache.find(key);
     Program* prog = nullptr;
     if (it == g_cache.end()) {
         std::vector<char> cubin;
-        st = compile(src, &cubin, nullptr, false);
+        std::string src, log;
+        int mb = spec.min_blocks;
+        st = select_and_compile(spec, &src, &cubin, &log, &mb);
         if (st != CFS_OK) return st;
         auto p = std::make_unique<Program>();
         st = check_cu(d.module_load(&p->module, cubin.data()), "cuModuleLoadData");
         if (st != CFS_OK) return st;
+        p->min_blocks = mb;
         prog = p.get();
         g_cache.emplace(key, std::move(p));
     } else {

@@ -1,0 +1,137 @@
+"""GPU parity of the batched renderer (many frames of different systems in one
+persistent launch, replayed as a CUDA graph) against the CPU oracle, frame by
+frame.  The animation frames are affine with a splat-only chain, so every
+histogram is bit-exact."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_02226_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _setup(frames, view=None):
+    from paper_2606_02226_gb300 import cfs
+    chain = cfs.Chain([W.Op("splat", (0,))], 2)
+    items, descs, tens, systems = [], [], [], []
+    begin = 0
+    for f, fr in enumerate(frames):
+        t = W.animation_target(fr.W)
+        if view is not None:
+            t.view = view
+        ten = cfs.alloc_target(t)
+        s = cfs.System(fr.system)
+        systems.append(s)
+        items.append((s, fr.n_points, begin, f, [t], [ten]))
+        descs.append(t)
+        tens.append(ten)
+        begin += fr.n_points
+    return cfs, chain, items, descs, tens
+
+
+def _oracle(frames, descs, iters, burn_in, seed):
+    out, disc = [], []
+    begin = 0
+    for f, (fr, t) in enumerate(zip(frames, descs)):
+        r = O.render(fr.system, [W.Op("splat", (0,))], [t], n_points=fr.n_points,
+                     point_begin=begin, system_id=f, iters=iters, burn_in=burn_in, seed=seed)
+        out.append(r[0].buf)
+        disc.append(r[0].n_discard)
+        begin += fr.n_points
+    return out, disc
+
+
+def _host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def test_batch_matches_oracle_frame_by_frame(torch_cuda):
+    frames = W.animation_frames(n_frames=14, seed=2, min_log2=8, max_log2=12,
+                                resolutions=(64, 128))
+    cfs, chain, items, descs, tens = _setup(frames)
+    b = cfs.Batch(chain, items, iters=60, burn_in=20, seed=4)
+    info = b.info()
+    assert info["n_items"] >= len(frames) and info["grid"] >= 1
+    b.launch(clear=True)
+    torch_cuda.cuda.synchronize()
+    ref, rdisc = _oracle(frames, descs, 60, 20, 4)
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), ref[f]), f
+        assert int(_host(tens[f]).sum()) == frames[f].n_points * 40
+    assert list(b.discards()[:, 0]) == rdisc == [0] * len(frames)
+
+
+def test_batch_graph_replay_clear_and_accumulate(torch_cuda):
+    frames = W.animation_frames(n_frames=5, seed=3, min_log2=9, max_log2=11, resolutions=(64,))
+    cfs, chain, items, descs, tens = _setup(frames)
+    b = cfs.Batch(chain, items, iters=40, burn_in=8, seed=1)
+    b.launch(clear=True)
+    b.launch(clear=True)          # replay: same image
+    torch_cuda.cuda.synchronize()
+    first = [_host(t).copy() for t in tens]
+    b.launch(clear=False)         # accumulate: doubles every bin
+    torch_cuda.cuda.synchronize()
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), 2 * first[f])
+    ref, _ = _oracle(frames, descs, 40, 8, 1)
+    for f in range(len(frames)):
+        assert np.array_equal(first[f], ref[f])
+
+
+def test_batch_discards_and_set_system(torch_cuda):
+    frames = W.animation_frames(n_frames=6, seed=5, min_log2=9, max_log2=10, resolutions=(64,))
+    view = (-1.0, 1.0, -1.0, 1.0)      # crops the attractors: discards
+    cfs, chain, items, descs, tens = _setup(frames, view=view)
+    b = cfs.Batch(chain, items, iters=30, burn_in=10, seed=2)
+    b.launch()
+    torch_cuda.cuda.synchronize()
+    ref, rdisc = _oracle(frames, descs, 30, 10, 2)
+    assert [int(v) for v in b.discards()[:, 0]] == rdisc
+    assert sum(rdisc) > 0
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), ref[f])
+    # animate frame 2: give it frame 4's system
+    b.set_system(2, cfs.System(frames[4].system))
+    b.launch()
+    torch_cuda.cuda.synchronize()
+    frames2 = list(frames)
+    frames2[2] = W.Frame(frames[4].system, frames[2].n_points, frames[2].W, frames[2].t)
+    ref2, _ = _oracle(frames2, descs, 30, 10, 2)
+    assert np.array_equal(_host(tens[2]), ref2[2])
+    assert not np.array_equal(ref2[2], ref[2])
+
+
+def test_batch_equals_single_renders_and_one_shot(torch_cuda):
+    frames = W.animation_frames(n_frames=4, seed=6, min_log2=10, max_log2=12, resolutions=(128,))
+    cfs, chain, items, descs, tens = _setup(frames)
+    cfs.render_batch(chain, items, iters=50, burn_in=20, seed=7)
+    torch_cuda.cuda.synchronize()
+    got = [_host(t).copy() for t in tens]
+    begin = 0
+    for f, fr in enumerate(frames):
+        single = cfs.alloc_target(descs[f])
+        cfs.render(cfs.System(fr.system), chain, [descs[f]], [single], n_points=fr.n_points,
+                   point_begin=begin, system_id=f, iters=50, burn_in=20, seed=7)
+        torch_cuda.cuda.synchronize()
+        assert np.array_equal(_host(single), got[f])
+        begin += fr.n_points
+
+
+def test_batch_rejects_mixed_kinds(torch_cuda):
+    from paper_2606_02226_gb300 import cfs
+    t = W.Target("hist_u32", 16, 16, 4)
+    ten = cfs.alloc_target(t)
+    sq = W.square_system()
+    mixed = W.System(2, sq.maps[:2] + [W.Map("circle", (0.0,))], [0.3, 0.3, 0.4])
+    chain = cfs.Chain([W.Op("splat", (0,))], 2)
+    with pytest.raises(cfs.CfsError):
+        cfs.Batch(chain, [(cfs.System(mixed), 10, 0, 0, [t], [ten])], iters=5, burn_in=1)

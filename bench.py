@@ -343,6 +343,8 @@ def run_cfs(args, wl):
             "e2e": e2e, "gpu_launches": len(jobs) * K, "clocks": clk}
     if args.batch:
         line["batch"] = bench_batch(torch, cfs, dev, stream)
+    if args.cloud:
+        line["cloud"] = bench_cloud(torch, cfs, dev, stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -386,6 +388,68 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3):
             "grid": info["grid"], "gpu_launches_per_batch": 1}
 
 
+def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64):
+    """Stored-cloud deformation: a 2^26-point cloud of a 3D IFS (8 maps)
+    generated once, then 64 animation frames each streaming it through twist,
+    bend, sphere inversion, sinusoidal, four affines and a perspective splat
+    into an 8192^2 depth+colour layer (clear included)."""
+    peaks, src = _peaks()
+    n, Wd = 1 << 26, 8192
+    sysh = cfs.System(W.cloud_system())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    xyz, fn = cfs.pointcloud_generate(sysh, n, 32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gen_ms = e0.elapsed_time(e1)
+    t = W.cloud_target(Wd)
+    layer = cfs.alloc_target(t, device=dev)
+    chain = cfs.Chain(W.cloud_chain(0, n_frames), 3)
+
+    def frame(f):
+        ops = W.cloud_chain(f, n_frames)
+        chain.set_params(0, ops[0].params)          # twist kappa(t)
+        chain.set_params(1, ops[1].params)          # bend beta(t)
+        cfs.target_clear([t], [layer], stream)
+        cfs.render_points(chain, xyz, fn, [t], [layer], stream=stream)
+
+    for f in range(2):
+        frame(f)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(n_frames)]
+    for f in range(n_frames):
+        a, b, c = ev[f]
+        a.record(stream)
+        cfs.target_clear([t], [layer], stream)
+        b.record(stream)
+        ops = W.cloud_chain(f, n_frames)
+        chain.set_params(0, ops[0].params)
+        chain.set_params(1, ops[1].params)
+        cfs.render_points(chain, xyz, fn, [t], [layer], stream=stream)
+        c.record(stream)
+    torch.cuda.synchronize()
+    frame_ms = sum(a.elapsed_time(c) for a, b, c in ev) / n_frames
+    kern_ms = sum(b.elapsed_time(c) for a, b, c in ev) / n_frames
+    # algorithmic bytes of a frame: the cloud read once (12 B of positions +
+    # 1 B of map index per point) and the layer written once (clear)
+    cloud_bytes = 13 * n
+    layer_bytes = 8 * Wd * Wd
+    frame_gbs = (cloud_bytes + layer_bytes) / (frame_ms * 1e-3) / 1e9
+    kern_gbs = cloud_bytes / (kern_ms * 1e-3) / 1e9
+    return {"workload": "2^26-point 3D IFS cloud; twist/bend/inversion/sinusoidal/4 affines/"
+                        "perspective -> 8192^2 depth+colour u64; 64 frames",
+            "generate_ms": gen_ms, "ms_per_frame": frame_ms, "frames_per_s": 1e3 / frame_ms,
+            "points_per_s": n / (frame_ms * 1e-3), "render_points_ms": kern_ms,
+            "roofline": {"bound": "hbm", "kernel": "cfs_points_kernel",
+                         "achieved": kern_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": kern_gbs / peaks["hbm_gbs"],
+                         "peak_source": f"{src} (MEASURED_PEAKS.json copy bandwidth)",
+                         "bytes": "13 B per point (cloud read once)"},
+            "frame_gbs_algorithmic": frame_gbs}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +463,8 @@ def main():
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batched-animation measurement")
+    ap.add_argument("--no-cloud", dest="cloud", action="store_false",
+                    help="skip the stored-cloud measurement")
     args = ap.parse_args()
     wl = W.composed_render(n_points=args.points, iters=args.iters)
     if args.impl == "reference":

@@ -187,6 +187,25 @@ cfs_status cfs_render(const cfs_system* sys, const cfs_chain* chain,
 cfs_status cfs_prepare(const cfs_system* sys, const cfs_chain* chain,
                        const cfs_target* targets, int n_targets);
 
+/* ---- stored point clouds (Section 3: the staged alternative, "store all
+ *      points ... then transform", used for controllable deformation of a
+ *      cloud over many frames, Section 4) --------------------------------- */
+/* Generates n points: point i runs steps 0 .. iters-1 of the chaos game
+ * from its Philox start point (the rules of cfs_render, system id
+ * `system_id`); its final position is written SoA to xyz (device, dim
+ * floats per point: xyz[d * n + i]) and the index of its last map to fn[i]
+ * (device u8).  Enqueued on `stream`. */
+cfs_status cfs_pointcloud_generate(const cfs_system* sys, uint64_t seed, uint32_t system_id,
+                                   uint32_t n, uint32_t iters, float* xyz, uint8_t* fn,
+                                   void* stream);
+/* Streams a stored cloud (device SoA xyz [chain dim_in][n], u8 fn [n]) once
+ * through the chain and splats every point (colour index fn[i]).  n must be
+ * a multiple of 4; xyz 16-byte aligned, fn 4-byte aligned.  Discarded
+ * splats are added to `discards` (device u64 [n_targets]) when not NULL. */
+cfs_status cfs_render_points(const cfs_chain* chain, const float* xyz, const uint8_t* fn,
+                             uint32_t n, const cfs_target* targets, int n_targets,
+                             unsigned long long* discards, void* stream);
+
 /* ---- batched rendering (many frames in one persistent launch) ---------- */
 /* One frame of a batch: its own system, range of point indices and targets
  * (device buffers of the caller).  Frames of a batch share the chain, the
@@ -245,8 +264,9 @@ cfs_status cfs_trace(const cfs_system* sys, const cfs_chain* chain,
                      int32_t* k_out, float* p_out, float* q_out, void* stream);
 
 /* Debugging aid, needs no GPU: writes the CUDA source of the fused program
- * that cfs_render (mode 0), cfs_trace (mode 1) or a batch of frames like this
- * one (mode 2) would use into `src` (at most
+ * that cfs_render (mode 0), cfs_trace (mode 1), a batch of frames like this
+ * one (mode 2), cfs_pointcloud_generate (mode 3) or cfs_render_points (mode
+ * 4) would use into `src` (at most
  * src_cap bytes, NUL-terminated), compiles it with NVRTC for sm_103a and
  * writes the compiler log, including ptxas register/spill usage, into `log`.
  * Either buffer may be NULL. */

@@ -107,6 +107,10 @@ _SIGNATURES = {
     "cfs_render_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
                                         ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_uint64, ctypes.c_int, _P]),
+    "cfs_pointcloud_generate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P]),
+    "cfs_render_points": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32,
+                                         ctypes.POINTER(cfs_target), ctypes.c_int, _P, _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -344,6 +348,37 @@ def philox(ctr, key, stream=None):
     _check(lib().cfs_philox(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), n,
                             _stream_handle(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# stored clouds
+# ---------------------------------------------------------------------------
+def pointcloud_generate(system: System, n: int, iters: int, *, seed: int = 0,
+                        system_id: int = 0, xyz=None, fn=None, stream=None):
+    """Returns device tensors xyz float32 [dim, n] (SoA) and fn uint8 [n]."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if xyz is None:
+        xyz = torch.empty((system.dim, n), dtype=torch.float32, device=dev)
+    if fn is None:
+        fn = torch.empty((n,), dtype=torch.uint8, device=dev)
+    _check(lib().cfs_pointcloud_generate(system.handle, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                         system_id, n, iters, xyz.data_ptr(), fn.data_ptr(),
+                                         _stream_handle(stream)))
+    return xyz, fn
+
+
+def render_points(chain: Chain, xyz, fn, target_descs, target_tensors, *, discards=None,
+                  stream=None):
+    """Streams the stored cloud (xyz float32 [dim, n], fn uint8 [n]) through
+    ``chain`` into the targets."""
+    arr, nt = make_targets(target_descs, target_tensors)
+    assert xyz.is_cuda and xyz.is_contiguous() and fn.is_cuda and fn.is_contiguous()
+    n = int(fn.numel())
+    assert xyz.shape == (chain.dim_in, n)
+    _check(lib().cfs_render_points(chain.handle, xyz.data_ptr(), fn.data_ptr(), n, arr, nt,
+                                   discards.data_ptr() if discards is not None else None,
+                                   _stream_handle(stream)))
 
 
 # ---------------------------------------------------------------------------

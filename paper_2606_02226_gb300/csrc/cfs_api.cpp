@@ -450,6 +450,77 @@ cfs_status cfs_trace(const cfs_system* sys, const cfs_chain* chain,
     return launch(k, grid, &a, sizeof(a), (cudaStream_t)stream);
 }
 
+cfs_status cfs_pointcloud_generate(const cfs_system* sys, uint64_t seed, uint32_t system_id,
+                                   uint32_t n, uint32_t iters, float* xyz, uint8_t* fn,
+                                   void* stream)
+{
+    clear_error();
+    if (!sys) return fail(CFS_ERR_INVALID_ARG, "NULL system");
+    if (n == 0) return CFS_OK;
+    if (!xyz || !fn) return fail(CFS_ERR_INVALID_ARG, "NULL xyz or fn");
+    if (iters == 0) return fail(CFS_ERR_INVALID_ARG, "iters must be >= 1");
+    cfs_chain empty;
+    empty.dim_in = sys->dim;
+    empty.n_ops = 0;
+    ProgramSpec sp = make_spec(Mode::Cloud, sys, &empty, nullptr, 0, false);
+    Kernel k;
+    cfs_status st = get_kernel(sp, "cfs_cloud_kernel", &k);
+    if (st != CFS_OK) return st;
+    cfs_render_params p{};
+    p.seed = seed;
+    p.system_id = system_id;
+    p.n_points = n;
+    p.iters = iters;
+    cfs_launch_args a;
+    fill_args(&a, sys, &empty, nullptr, 0, &p);
+    a.cloud_xyz = (unsigned long long)(uintptr_t)xyz;
+    a.cloud_fn = (unsigned long long)(uintptr_t)fn;
+    const uint64_t need = ((uint64_t)n + k.block - 1) / k.block;
+    uint64_t grid = (uint64_t)k.max_blocks_per_sm * (uint64_t)(k.num_sms > 0 ? k.num_sms : 1);
+    if (grid == 0) grid = 1;
+    if (grid > need) grid = need;
+    return launch(k, (unsigned)grid, &a, sizeof(a), (cudaStream_t)stream);
+}
+
+cfs_status cfs_render_points(const cfs_chain* chain, const float* xyz, const uint8_t* fn,
+                             uint32_t n, const cfs_target* targets, int n_targets,
+                             unsigned long long* discards, void* stream)
+{
+    clear_error();
+    if (!chain) return fail(CFS_ERR_INVALID_ARG, "NULL chain");
+    if (n == 0) return CFS_OK;
+    if (!xyz || !fn) return fail(CFS_ERR_INVALID_ARG, "NULL xyz or fn");
+    if (n % 4 != 0) return fail(CFS_ERR_INVALID_ARG, "n must be a multiple of 4");
+    if ((uintptr_t)xyz % 16 != 0 || (uintptr_t)fn % 4 != 0)
+        return fail(CFS_ERR_INVALID_ARG, "xyz must be 16-byte and fn 4-byte aligned");
+    cfs_status st = validate_targets(chain, targets, n_targets);
+    if (st != CFS_OK) return st;
+    // the generator plays no part: a one-map stand-in of the chain's dimension
+    cfs_system stand_in;
+    stand_in.dim = chain->dim_in;
+    stand_in.n_maps = 1;
+    stand_in.maps[0].kind = CFS_MAP_AFFINE;
+    std::memset(stand_in.maps[0].params, 0, sizeof(stand_in.maps[0].params));
+    stand_in.n_cmp = 0;
+    ProgramSpec sp = make_spec(Mode::Points, &stand_in, chain, targets, n_targets, false);
+    Kernel k;
+    st = get_kernel(sp, "cfs_points_kernel", &k);
+    if (st != CFS_OK) return st;
+    cfs_render_params p{};
+    p.n_points = n;
+    p.iters = 1;
+    p.discards = discards;
+    cfs_launch_args a;
+    fill_args(&a, &stand_in, chain, targets, n_targets, &p);
+    a.cloud_xyz = (unsigned long long)(uintptr_t)xyz;
+    a.cloud_fn = (unsigned long long)(uintptr_t)fn;
+    const uint64_t need = ((uint64_t)(n / 4) + k.block - 1) / k.block;
+    uint64_t grid = (uint64_t)k.max_blocks_per_sm * (uint64_t)(k.num_sms > 0 ? k.num_sms : 1);
+    if (grid == 0) grid = 1;
+    if (grid > need) grid = need;
+    return launch(k, (unsigned)grid, &a, sizeof(a), (cudaStream_t)stream);
+}
+
 cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
                              const cfs_target* targets, int n_targets, int mode, char* src,
                              size_t src_cap, char* log, size_t log_cap)
@@ -458,15 +529,16 @@ cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
     if (!sys || !chain) return fail(CFS_ERR_INVALID_ARG, "NULL system or chain");
     if (chain->dim_in != sys->dim)
         return fail(CFS_ERR_INVALID_ARG, "chain was composed for another dimension");
-    if (mode < 0 || mode > 2) return fail(CFS_ERR_INVALID_ARG, "mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 4) return fail(CFS_ERR_INVALID_ARG, "mode must be in 0..4");
     cfs_status st = CFS_OK;
-    if (mode != 1) {
+    const bool tg = mode != 1 && mode != 3;
+    if (tg) {
         st = validate_targets(chain, targets, n_targets);
         if (st != CFS_OK) return st;
     }
-    const bool tg = mode != 1;
-    ProgramSpec sp = make_spec(mode == 0 ? Mode::Render : (mode == 1 ? Mode::Trace : Mode::Batch),
-                               sys, chain, tg ? targets : nullptr, tg ? n_targets : 0, false);
+    const Mode modes[] = {Mode::Render, Mode::Trace, Mode::Batch, Mode::Cloud, Mode::Points};
+    ProgramSpec sp = make_spec(modes[mode], sys, chain, tg ? targets : nullptr,
+                               tg ? n_targets : 0, false);
     if (mode == 2) {
         for (int k = 0; k < sys->n_maps; ++k)
             if (sys->maps[k].kind != sys->maps[0].kind)
@@ -474,6 +546,8 @@ cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
         sp.n_maps = CFS_MAX_MAPS;
         for (int j = 0; j < CFS_MAX_MAPS; ++j) sp.map_kind[j] = sys->maps[0].kind;
         sp.spill_allowance = 64;
+        sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
+        sp.warp_agg = sp.tile;
     }
     std::string s, l;
     st = compile_only(sp, &s, &l);

@@ -49,9 +49,12 @@ typedef struct {
     unsigned long long k_out, p_out, q_out;   /* trace outputs */
     unsigned int system_id, point_begin, n_points, step_begin;
     unsigned int iters, burn_in, flags, pad2;
+    /* stored clouds: SoA positions [dim][n_points] and map index [n_points] */
+    unsigned long long cloud_xyz, cloud_fn;
     /* batch: frames, work counter, per-frame discard counters */
     unsigned long long frames, work_counter, frame_discards;
-    unsigned int n_frames, n_items, chunk, pad3;
+    unsigned long long frame_bbox;      /* int4 [n_frames]: sampled pixel box of target 0 */
+    unsigned int n_frames, n_items, chunk, tile_cap;    /* tile_cap: shared u32 counters */
 } cfs_launch_args;
 
 #endif

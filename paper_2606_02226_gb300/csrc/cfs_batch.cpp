@@ -34,6 +34,8 @@ struct cfs_batch {
     std::vector<uint32_t> chunks;         // points per item, per frame
     cfs::ProgramSpec spec;
     cfs::Kernel kernel;
+    cfs::Kernel bbox_kernel;              // pre-pass of the privatized window
+    uint32_t tile_cap = 0;
     cfs_launch_args args;
     uint32_t chunk = 0, n_items = 0, grid = 0;
     cfs_dev_frame* h_frames = nullptr;    // pinned staging
@@ -41,6 +43,7 @@ struct cfs_batch {
     cfs_dev_frame* d_frames = nullptr;
     unsigned int* d_counter = nullptr;
     unsigned long long* d_disc = nullptr;
+    int* d_bbox = nullptr;
     size_t work_bytes = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [clear]
@@ -121,7 +124,9 @@ cfs_status capture(cfs_batch* b, int clear)
             }
     }
     cfs_status lst = CFS_OK;
-    if (e == cudaSuccess && b->n_items > 0)
+    if (e == cudaSuccess && b->n_items > 0 && b->spec.tile)
+        lst = launch(b->bbox_kernel, (unsigned)b->n_frames, &b->args, sizeof(b->args), s);
+    if (e == cudaSuccess && lst == CFS_OK && b->n_items > 0)
         lst = launch(b->kernel, b->grid, &b->args, sizeof(b->args), s);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
@@ -221,8 +226,26 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     sp.spill_allowance = 64;
     sp.depth_test = 1;
     if (const char* e = std::getenv("CFS_BATCH_MINB")) sp.min_blocks = std::max(1, std::atoi(e));
+    // privatized window: when the chain splats once, into a histogram
+    sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
+    sp.warp_agg = 1;
+    b->tile_cap = 8192;
+    if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
+    if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
+    if (const char* e = std::getenv("CFS_TILE_CAP")) {
+        const int c = std::atoi(e);
+        if (c >= 256 && c <= 53248) b->tile_cap = (uint32_t)c;
+    }
+    if (!sp.tile) { sp.warp_agg = 0; b->tile_cap = 0; }
+    sp.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
     st = get_kernel(sp, "cfs_batch_kernel", &b->kernel);
     if (st != CFS_OK) { delete b; return st; }
+    if (sp.tile) {
+        ProgramSpec bs = sp;
+        bs.dyn_smem = 0;
+        st = get_kernel(bs, "cfs_bbox_kernel", &b->bbox_kernel);
+        if (st != CFS_OK) { delete b; return st; }
+    }
 
     // Items: every frame is cut into at least `grid` items (whole warps of
     // points, at most chunk_max), so all CTAs work on one or two frames at a
@@ -247,9 +270,11 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     b->n_items = (uint32_t)total_items;
     if (b->grid > b->n_items && b->n_items > 0) b->grid = b->n_items;
 
-    // workspace: frames | counter (u32, padded to 256 B) | discards
+    // workspace: frames | bbox (int4 per frame) | counter (u32, padded to
+    // 256 B) | discards (the counter and discards are reset every launch)
     const size_t fbytes = sizeof(cfs_dev_frame) * (size_t)n_frames;
-    const size_t off_counter = (fbytes + 255) & ~(size_t)255;
+    const size_t off_bbox = (fbytes + 255) & ~(size_t)255;
+    const size_t off_counter = (off_bbox + 16 * (size_t)n_frames + 255) & ~(size_t)255;
     const size_t off_disc = off_counter + 256;
     b->work_bytes = off_disc + sizeof(unsigned long long) * (size_t)n_frames *
                                    (size_t)std::max(1, n_targets);
@@ -264,6 +289,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
                         "cudaEventCreate");
     if (st != CFS_OK) { release(b); delete b; return st; }
     b->d_frames = reinterpret_cast<cfs_dev_frame*>(b->d_work);
+    b->d_bbox = reinterpret_cast<int*>(b->d_work + off_bbox);
     b->d_counter = reinterpret_cast<unsigned int*>(b->d_work + off_counter);
     b->d_disc = reinterpret_cast<unsigned long long*>(b->d_work + off_disc);
 
@@ -279,6 +305,8 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     b->args.n_frames = (unsigned)n_frames;
     b->args.n_items = b->n_items;
     b->args.chunk = b->chunk;
+    b->args.frame_bbox = (unsigned long long)(uintptr_t)b->d_bbox;
+    b->args.tile_cap = b->tile_cap;
     *out = b;
     return CFS_OK;
 }

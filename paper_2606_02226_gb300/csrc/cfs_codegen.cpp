@@ -20,7 +20,7 @@ std::string ProgramSpec::key() const
     std::ostringstream s;
     s << "m" << int(mode) << ".d" << dim << ".n" << n_maps << ".c" << n_cmp << ".r" << reuse
       << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << "."
-      << spill_allowance << ".k";
+      << spill_allowance << ".p" << tile << warp_agg << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
     for (int j = 0; j < n_ops; ++j) s << op_kind[j] << ",";
@@ -91,7 +91,8 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
 {
     s << "template <class TG>\n__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a,"
          " const TG& tg, const CfsSmem& sm, float px, float py, float pz, int k, u32* disc,"
-         " bool do_splat, float* rec, float& ox, float& oy, float& oz)\n{\n";
+         " bool do_splat, float* rec, float& ox, float& oy, float& oz, const CfsTile& tile)\n{\n";
+    s << "    (void)tile;\n";
     s << "    float qx = px, qy = py, qz = pz;\n    bool alive = true;\n";
     s << "    (void)a; (void)tg; (void)sm; (void)disc; (void)do_splat; (void)rec; (void)k;\n";
     size_t si = 0;
@@ -129,7 +130,10 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
               << "] = qy; rec[" << 4 * si + 2 << "] = qz; rec[" << 4 * si + 3
               << "] = alive ? 1.0f : 0.0f; }\n";
             s << "    if (do_splat) ";
-            if (t.kind == CFS_TARGET_HIST_U32)
+            if (t.kind == CFS_TARGET_HIST_U32 && sp.tile && si == 0)
+                s << "cfs_splat_hist_tile(tg[" << t.slot << "], tile, qx, qy, alive, k % "
+                  << t.channels << ", disc[" << t.slot << "]);\n";
+            else if (t.kind == CFS_TARGET_HIST_U32)
                 s << "cfs_splat_hist(tg[" << t.slot << "], qx, qy, alive, k % " << t.channels
                   << ", disc[" << t.slot << "]);\n";
             else if (t.kind == CFS_TARGET_RGBA_F32)
@@ -157,6 +161,11 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_NSPLAT_ARR " << (sp.splats.empty() ? 1 : sp.splats.size()) << "\n";
     s << "#define CFS_REUSE " << (sp.reuse ? 1 : 0) << "\n";
     s << "#define CFS_BATCH " << (sp.mode == Mode::Batch ? 1 : 0) << "\n";
+    s << "#define CFS_CLOUD " << (sp.mode == Mode::Cloud ? 1 : 0) << "\n";
+    s << "#define CFS_TILE " << (sp.tile ? 1 : 0) << "\n";
+    s << "#define CFS_WARP_AGG " << (sp.warp_agg ? 1 : 0) << "\n";
+    s << "#define CFS_TILE_C " << (sp.splats.empty() ? 1 : sp.splats[0].channels) << "\n";
+    s << "#define CFS_POINTS " << (sp.mode == Mode::Points ? 1 : 0) << "\n";
     s << "#define CFS_DEPTH_TEST " << sp.depth_test << "\n";
     s << "#define CFS_BLOCK " << sp.block << "\n";
     s << "#define CFS_MINB " << sp.min_blocks << "\n";

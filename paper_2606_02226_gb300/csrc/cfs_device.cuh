@@ -270,6 +270,65 @@ __device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x,
     }
 }
 
+/* Privatized histogram window (batched frames): u32 counters in shared
+ * memory for pixels [wx0, wx0 + ww) x [wy0, wy0 + wh) of every channel,
+ * layout [ch][y][x].  ww == 0 turns it off. */
+struct CfsTile {
+    u32* cnt;
+    int wx0, wy0, ww, wh;
+};
+
+/* u32 histogram splat that adds to the shared window when the bin lies in
+ * it (one shared atomic per group of lanes hitting the same counter with
+ * CFS_WARP_AGG) and to global memory otherwise. */
+__device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, const CfsTile& tl,
+                                                    float x, float y, bool alive, int ch,
+                                                    u32& disc)
+{
+    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
+    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
+    if (alive && ix >= 0 && iy >= 0) {
+        const int lx = ix - tl.wx0, ly = iy - tl.wy0;
+        if ((unsigned)lx < (unsigned)tl.ww && (unsigned)ly < (unsigned)tl.wh) {
+            const u32 idx = ((u32)ch * (u32)tl.wh + (u32)ly) * (u32)tl.ww + (u32)lx;
+#if CFS_WARP_AGG
+            const u32 act = __activemask();
+            const u32 peers = __match_any_sync(act, idx);
+            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(tl.cnt + idx, __popc(peers));
+#else
+            atomicAdd(tl.cnt + idx, 1u);
+#endif
+        } else {
+            u32* base = reinterpret_cast<u32*>(t.data);
+            const size_t off = ((size_t)ch * (size_t)t.H + (size_t)iy) * (size_t)t.W + (size_t)ix;
+            cfs_red_add_u32(base + off, 1u);
+        }
+    } else {
+        disc += 1;
+    }
+}
+
+/* Adds the window's nonzero counters to the global histogram and zeroes
+ * them (all threads of the CTA; the caller synchronizes around it). */
+__device__ __forceinline__ void cfs_flush_tile(const cfs_dev_target& t, const CfsTile& tl, int C)
+{
+    if (tl.ww <= 0) return;
+    const u32 per = (u32)tl.ww * (u32)tl.wh;
+    const u32 n = (u32)C * per;
+    u32* base = reinterpret_cast<u32*>(t.data);
+    for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
+        const u32 v = tl.cnt[e];
+        if (v) {
+            const u32 ch = e / per, r = e - ch * per;
+            const u32 ly = r / (u32)tl.ww, lx = r - ly * (u32)tl.ww;
+            const size_t off = ((size_t)ch * (size_t)t.H + (size_t)(tl.wy0 + (int)ly)) *
+                                   (size_t)t.W + (size_t)(tl.wx0 + (int)lx);
+            cfs_red_add_u32(base + off, v);
+            tl.cnt[e] = 0u;
+        }
+    }
+}
+
 /* f32 RGBA [H][W][4]: += colour (one 16-byte vector reduction). */
 __device__ __forceinline__ void cfs_splat_rgba(const cfs_dev_target& t, float x, float y,
                                                bool alive, float4 col, u32& disc)

@@ -56,6 +56,9 @@ struct ProgramSpec {
     int block = 256;
     int min_blocks = 8;        // upper bound; lowered while ptxas spills
     int spill_allowance = 0;   // bytes of spill stores accepted at min_blocks
+    int tile = 0;              // batch: privatized shared window for the first splat
+    int warp_agg = 0;          // warp-aggregated shared atomics in that window
+    int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
 
     std::string key() const;
 };
@@ -68,6 +71,7 @@ struct Kernel {
     int max_blocks_per_sm = 0;
     int block = 256;
     int num_sms = 0;
+    int dyn_smem = 0;     // dynamic shared memory per CTA at launch (bytes)
 };
 
 // Compiles (or fetches from the cache) the program and returns the named

@@ -64,21 +64,21 @@ __device__ __forceinline__ void cfs_start(const cfs_launch_args& a, u32 i, u32 s
 template <class CH, class TG>
 __device__ __forceinline__ void cfs_step(const cfs_launch_args& a, const CH& choose, const TG& tg,
                                          const CfsSmem& sm, u32 n, u32 w, float& x, float& y,
-                                         float& z, u32* disc)
+                                         float& z, u32* disc, const CfsTile& tile)
 {
     const int k = choose(w);
     cfs_gen_map(a, k, x, y, z, sm);
 #if CFS_REUSE
     {
         float qx, qy, qz;
-        if (cfs_chain(a, tg, sm, x, y, z, k, disc, n >= a.burn_in, (float*)0, qx, qy, qz)) {
+        if (cfs_chain(a, tg, sm, x, y, z, k, disc, n >= a.burn_in, (float*)0, qx, qy, qz, tile)) {
             x = qx; y = qy; z = qz;
         }
     }
 #else
     if (n >= a.burn_in) {
         float qx, qy, qz;
-        cfs_chain(a, tg, sm, x, y, z, k, disc, true, (float*)0, qx, qy, qz);
+        cfs_chain(a, tg, sm, x, y, z, k, disc, true, (float*)0, qx, qy, qz, tile);
     }
 #endif
 }
@@ -90,7 +90,8 @@ __device__ __forceinline__ void cfs_step(const cfs_launch_args& a, const CH& cho
 template <class CH, class TG>
 __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH& choose,
                                               const TG& tg, const CfsSmem& sm, u32 i, u32 sid,
-                                              float& x, float& y, float& z, u32* disc)
+                                              float& x, float& y, float& z, u32* disc,
+                                              const CfsTile& tile)
 {
     const u32 b0 = a.step_begin, b1 = a.iters;
     const bool whole = ((b0 | b1) & 3u) == 0u;
@@ -98,17 +99,121 @@ __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH
     for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
         const uint4 r = cfs_philox(a, i, nb, sid, 0u);
         const u32 n = nb << 2;
-        if (whole || (n >= b0 && n < b1)) cfs_step(a, choose, tg, sm, n, r.x, x, y, z, disc);
+        if (whole || (n >= b0 && n < b1)) cfs_step(a, choose, tg, sm, n, r.x, x, y, z, disc, tile);
         if (whole || (n + 1 >= b0 && n + 1 < b1))
-            cfs_step(a, choose, tg, sm, n + 1, r.y, x, y, z, disc);
+            cfs_step(a, choose, tg, sm, n + 1, r.y, x, y, z, disc, tile);
         if (whole || (n + 2 >= b0 && n + 2 < b1))
-            cfs_step(a, choose, tg, sm, n + 2, r.z, x, y, z, disc);
+            cfs_step(a, choose, tg, sm, n + 2, r.z, x, y, z, disc, tile);
         if (whole || (n + 3 >= b0 && n + 3 < b1))
-            cfs_step(a, choose, tg, sm, n + 3, r.w, x, y, z, disc);
+            cfs_step(a, choose, tg, sm, n + 3, r.w, x, y, z, disc, tile);
     }
 }
 
-#if !CFS_BATCH
+#if CFS_CLOUD
+/* Stored point cloud (Section 3: "store all points ... then transform"):
+ * point i runs steps 0 .. iters-1 from its Philox start point; its final
+ * position goes to SoA xyz[d][i] (coalesced) and the index of its last map
+ * to fn[i]. */
+extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
+cfs_cloud_kernel(const __grid_constant__ cfs_launch_args a)
+{
+    __shared__ CfsSmem sm;
+    cfs_load_smem(a, sm);
+    __syncthreads();
+    const CfsChooseConst choose{a};
+    float* xyz = reinterpret_cast<float*>(a.cloud_xyz);
+    unsigned char* fn = reinterpret_cast<unsigned char*>(a.cloud_fn);
+    const u32 n_pts = a.n_points, sid = a.system_id;
+    const u32 stride = gridDim.x * blockDim.x;
+    for (u32 j = blockIdx.x * blockDim.x + threadIdx.x; j < n_pts; j += stride) {
+        const u32 i = a.point_begin + j;
+        float x, y, z;
+        cfs_start(a, i, sid, j, n_pts, x, y, z);
+        int k = 0;
+#pragma unroll 1
+        for (u32 nb = 0; (nb << 2) < a.iters; ++nb) {
+            const uint4 r = cfs_philox(a, i, nb, sid, 0u);
+            const u32 w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((nb << 2) + q < a.iters) {
+                    k = choose(w[q]);
+                    cfs_gen_map(a, k, x, y, z, sm);
+                }
+            }
+        }
+        xyz[j] = x;
+        xyz[(size_t)n_pts + j] = y;
+        if (CFS_DIM == 3) xyz[2 * (size_t)n_pts + j] = z;
+        fn[j] = (unsigned char)k;
+    }
+}
+#endif
+
+#if CFS_POINTS
+/* 16-byte streaming load that neither allocates in L1 nor lingers in L2
+ * (the cloud is read once per frame; L2 is kept for the layer). */
+__device__ __forceinline__ float4 cfs_ld_stream_f4(const float* p, u64 policy)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(policy));
+    return v;
+}
+
+__device__ __forceinline__ u32 cfs_ld_stream_u32(const void* p, u64 policy)
+{
+    u32 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;"
+                 : "=r"(v)
+                 : "l"(p), "l"(policy));
+    return v;
+}
+
+/* Streams a stored cloud through the chain: each thread takes four
+ * consecutive points (three 16-byte loads of x, y, z and one 4-byte load of
+ * the map indices), runs the fused chain on each and splats it.  n_points is
+ * a multiple of 4 and the arrays are 16-byte aligned (checked on the host). */
+extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
+cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
+{
+    __shared__ CfsSmem sm;
+    cfs_load_smem(a, sm);
+    __syncthreads();
+    u32 disc[CFS_NT_ARR];
+#pragma unroll
+    for (int t = 0; t < CFS_NT_ARR; ++t) disc[t] = 0;
+    u64 policy;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+    const float* xs = reinterpret_cast<const float*>(a.cloud_xyz);
+    const unsigned char* fn = reinterpret_cast<const unsigned char*>(a.cloud_fn);
+    const u32 n_pts = a.n_points;
+    const u32 groups = n_pts >> 2;
+    const u32 stride = gridDim.x * blockDim.x;
+    for (u32 g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += stride) {
+        const size_t o = (size_t)g * 4;
+        const float4 X = cfs_ld_stream_f4(xs + o, policy);
+        const float4 Y = cfs_ld_stream_f4(xs + (size_t)n_pts + o, policy);
+        float4 Z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (CFS_DIM == 3) Z = cfs_ld_stream_f4(xs + 2 * (size_t)n_pts + o, policy);
+        const u32 K = cfs_ld_stream_u32(fn + o, policy);
+        const CfsTile nt{0, 0, 0, 0, 0};
+        float qx, qy, qz;
+        cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), disc, true, (float*)0, qx, qy, qz,
+                  nt);
+        cfs_chain(a, a.tg, sm, X.y, Y.y, Z.y, (int)((K >> 8) & 0xFFu), disc, true, (float*)0, qx,
+                  qy, qz, nt);
+        cfs_chain(a, a.tg, sm, X.z, Y.z, Z.z, (int)((K >> 16) & 0xFFu), disc, true, (float*)0, qx,
+                  qy, qz, nt);
+        cfs_chain(a, a.tg, sm, X.w, Y.w, Z.w, (int)(K >> 24), disc, true, (float*)0, qx, qy, qz,
+                  nt);
+    }
+    cfs_flush_discards(a, disc, CFS_NT);
+}
+#endif
+
+#if !CFS_BATCH && !CFS_CLOUD && !CFS_POINTS
 /* The render kernel: a persistent grid (a multiple of the SM count) strides
  * over the points of this launch. */
 extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
@@ -126,7 +231,7 @@ cfs_render_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 i = a.point_begin + j;
         float x, y, z;
         cfs_start(a, i, a.system_id, j, a.n_points, x, y, z);
-        cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc);
+        cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc, CfsTile{0, 0, 0, 0, 0});
     }
     cfs_flush_discards(a, disc, CFS_NT);
 }
@@ -156,7 +261,8 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         cfs_gen_map(a, k, x, y, z, sm);
         float qx, qy, qz;
         const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, disc, false,
-                                     qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz);
+                                     qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz,
+                                     CfsTile{0, 0, 0, 0, 0});
 #if CFS_REUSE
         if (alive) { x = qx; y = qy; z = qz; }
 #else
@@ -168,7 +274,9 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         pout[3 * s + 2] = z;
     }
 }
-#else  /* CFS_BATCH */
+#endif
+
+#if CFS_BATCH
 
 /* Adds this CTA's discard counts of frame f to the per-frame counters. */
 __device__ __forceinline__ void cfs_flush_frame_discards(const cfs_launch_args& a, int f,
@@ -182,15 +290,116 @@ __device__ __forceinline__ void cfs_flush_frame_discards(const cfs_launch_args& 
     }
 }
 
+/* Frame descriptor -> shared tables (all threads; the caller syncs). */
+__device__ __forceinline__ void cfs_load_frame(const cfs_dev_frame& fr, CfsSmem& sm, u32* s_T,
+                                               cfs_dev_target* s_tg)
+{
+    for (int t = threadIdx.x; t < 6 * CFS_A_MAX_MAPS; t += blockDim.x) {
+        const int jj = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
+        sm.prm2[jj][k] = make_float2(fr.prm[2 * jj][k], fr.prm[2 * jj + 1][k]);
+    }
+    for (int t = threadIdx.x; t < CFS_NT_ARR * CFS_A_MAX_MAPS; t += blockDim.x) {
+        const int g = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
+        sm.pal[g][k] = make_float4(fr.tg[g].palette[k][0], fr.tg[g].palette[k][1],
+                                   fr.tg[g].palette[k][2], fr.tg[g].palette[k][3]);
+        sm.pal8[g][k] = fr.tg[g].palette8[k];
+    }
+    if (threadIdx.x < CFS_A_MAX_MAPS) s_T[threadIdx.x] = fr.T[threadIdx.x];
+    if (threadIdx.x < CFS_NT_ARR) s_tg[threadIdx.x] = fr.tg[threadIdx.x];
+}
+
+#if CFS_TILE
+/* Pre-pass of the privatized window: one CTA per frame runs its first
+ * blockDim points for up to 32 splat steps and records the pixel box they
+ * reach in target 0 (a sample: splats outside the final window still go to
+ * global memory, so the box only has to catch most of them). */
+extern "C" __global__ void __launch_bounds__(CFS_BLOCK)
+cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
+{
+    __shared__ CfsSmem sm;
+    __shared__ u32 s_T[CFS_A_MAX_MAPS];
+    __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
+    __shared__ int s_box[4];
+    const int f = blockIdx.x;
+    const cfs_dev_frame& fr = reinterpret_cast<const cfs_dev_frame*>(a.frames)[f];
+    cfs_load_frame(fr, sm, s_T, s_tg);
+    if (threadIdx.x == 0) {
+        s_box[0] = 0x7fffffff; s_box[1] = 0x7fffffff; s_box[2] = -1; s_box[3] = -1;
+    }
+    __syncthreads();
+    const CfsChooseTab choose{s_T, fr.n_cmp};
+    int bx0 = 0x7fffffff, by0 = 0x7fffffff, bx1 = -1, by1 = -1;
+    const u32 j = threadIdx.x;
+    if (j < fr.n_points) {
+        const u32 i = fr.point_begin + j, sid = fr.system_id;
+        const uint4 r0 = cfs_philox(a, i, 0u, sid, 1u);
+        float x = (float)(r0.x >> 8) * CFS_INV_2_24;
+        float y = (float)(r0.y >> 8) * CFS_INV_2_24;
+        float z = CFS_DIM == 3 ? (float)(r0.z >> 8) * CFS_INV_2_24 : 0.0f;
+        const u32 n1 = min(a.iters, a.burn_in + 32u);
+        const cfs_dev_target& t0 = s_tg[0];
+        u32 disc[CFS_NT_ARR];
+        for (u32 n = 0; n < n1; ++n) {
+            const uint4 r = cfs_philox(a, i, n >> 2, sid, 0u);
+            const int k = choose(cfs_word(r, n & 3u));
+            cfs_gen_map(a, k, x, y, z, sm);
+            if (n < a.burn_in) continue;
+            float rec[4 * CFS_NSPLAT_ARR];
+            float qx, qy, qz;
+            cfs_chain(a, s_tg, sm, x, y, z, k, disc, false, rec, qx, qy, qz,
+                      CfsTile{0, 0, 0, 0, 0});
+            const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
+            const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);
+            if (rec[3] != 0.0f && ix >= 0 && iy >= 0) {
+                bx0 = min(bx0, ix); by0 = min(by0, iy);
+                bx1 = max(bx1, ix); by1 = max(by1, iy);
+            }
+        }
+    }
+    atomicMin(&s_box[0], bx0); atomicMin(&s_box[1], by0);
+    atomicMax(&s_box[2], bx1); atomicMax(&s_box[3], by1);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        reinterpret_cast<int4*>(a.frame_bbox)[f] = make_int4(s_box[0], s_box[1], s_box[2], s_box[3]);
+}
+
+/* Window of frame f: its sampled box when it fits the tile, else the
+ * largest centred square-ish window that does. */
+__device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, int f, u32* cnt)
+{
+    const int4 b = reinterpret_cast<const int4*>(a.frame_bbox)[f];
+    CfsTile tl{cnt, 0, 0, 0, 0};
+    const int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
+    if (b.z < b.x || b.w < b.y || a.tile_cap < (u32)CFS_TILE_C) return tl;
+    const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* pixels */
+    int ww = bw, wh = bh;
+    if ((long long)bw * bh > cap) {
+        int side = (int)sqrtf((float)cap);
+        while ((side + 1) * (side + 1) <= cap) ++side;
+        while (side * side > cap) --side;
+        ww = min(bw, side);
+        wh = min(bh, cap / max(ww, 1));
+        wh = min(wh, bh);
+    }
+    tl.ww = ww;
+    tl.wh = wh;
+    tl.wx0 = b.x + (bw - ww) / 2;
+    tl.wy0 = b.y + (bh - wh) / 2;
+    return tl;
+}
+#endif
+
 /* The batched renderer (many frames of different systems, one launch): a
  * persistent grid whose CTAs take work items -- a chunk of one frame's
  * points -- from a global counter (one atomicAdd per item; no CTA ever waits
  * for another).  Items are numbered frame by frame and every frame has at
  * least as many items as the grid has CTAs (small frames get small items),
  * so the whole grid works on one or two frames at a time and their layers
- * stay in L2.  A CTA loads a
- * frame's thresholds, maps, palettes and target geometry into shared memory
- * when its next item belongs to another frame. */
+ * stay in L2.  A CTA loads a frame's thresholds, maps, palettes and target
+ * geometry into shared memory when its next item belongs to another frame.
+ * With CFS_TILE the first splat goes to a privatized shared-memory window
+ * of the frame's histogram (attractors are small and dense: many splats hit
+ * the same bins), flushed to global memory when the CTA leaves the frame. */
 extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
 cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
 {
@@ -199,6 +408,13 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
     __shared__ u32 s_item, s_frame, s_npts, s_pbeg, s_sid, s_ibeg, s_chunk;
     __shared__ int s_ncmp;
+#if CFS_TILE
+    extern __shared__ u32 s_cnt[];
+    for (u32 e = threadIdx.x; e < a.tile_cap; e += blockDim.x) s_cnt[e] = 0u;
+    CfsTile tile{s_cnt, 0, 0, 0, 0};
+#else
+    const CfsTile tile{0, 0, 0, 0, 0};
+#endif
     const cfs_dev_frame* frames = reinterpret_cast<const cfs_dev_frame*>(a.frames);
     u32* counter = reinterpret_cast<u32*>(a.work_counter);
     int cur = -1;
@@ -225,20 +441,15 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
         if (item >= a.n_items) break;
         const int f = (int)s_frame;
         if (f != cur) {
-            if (cur >= 0) cfs_flush_frame_discards(a, cur, disc);
+            if (cur >= 0) {
+                cfs_flush_frame_discards(a, cur, disc);
+#if CFS_TILE
+                cfs_flush_tile(s_tg[0], tile, CFS_TILE_C);
+#endif
+            }
+            __syncthreads();
             const cfs_dev_frame& fr = frames[f];
-            for (int t = threadIdx.x; t < 6 * CFS_A_MAX_MAPS; t += blockDim.x) {
-                const int jj = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
-                sm.prm2[jj][k] = make_float2(fr.prm[2 * jj][k], fr.prm[2 * jj + 1][k]);
-            }
-            for (int t = threadIdx.x; t < CFS_NT_ARR * CFS_A_MAX_MAPS; t += blockDim.x) {
-                const int g = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
-                sm.pal[g][k] = make_float4(fr.tg[g].palette[k][0], fr.tg[g].palette[k][1],
-                                           fr.tg[g].palette[k][2], fr.tg[g].palette[k][3]);
-                sm.pal8[g][k] = fr.tg[g].palette8[k];
-            }
-            if (threadIdx.x < CFS_A_MAX_MAPS) s_T[threadIdx.x] = fr.T[threadIdx.x];
-            if (threadIdx.x < CFS_NT_ARR) s_tg[threadIdx.x] = fr.tg[threadIdx.x];
+            cfs_load_frame(fr, sm, s_T, s_tg);
             if (threadIdx.x == 0) {
                 s_npts = fr.n_points;
                 s_pbeg = fr.point_begin;
@@ -247,6 +458,9 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
                 s_chunk = fr.chunk;
                 s_ncmp = fr.n_cmp;
             }
+#if CFS_TILE
+            tile = cfs_frame_window(a, f, s_cnt);
+#endif
             __syncthreads();
             cur = f;
         }
@@ -260,11 +474,16 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
             float x = (float)(r.x >> 8) * CFS_INV_2_24;
             float y = (float)(r.y >> 8) * CFS_INV_2_24;
             float z = CFS_DIM == 3 ? (float)(r.z >> 8) * CFS_INV_2_24 : 0.0f;
-            cfs_run_point(a, choose, s_tg, sm, i, sid, x, y, z, disc);
+            cfs_run_point(a, choose, s_tg, sm, i, sid, x, y, z, disc, tile);
         }
         __syncthreads();
     }
-    if (cur >= 0) cfs_flush_frame_discards(a, cur, disc);
+    if (cur >= 0) {
+        cfs_flush_frame_discards(a, cur, disc);
+#if CFS_TILE
+        cfs_flush_tile(s_tg[0], tile, CFS_TILE_C);
+#endif
+    }
 }
 #endif /* CFS_BATCH */
 

@@ -55,6 +55,7 @@ typedef CUresult (*PFN_LaunchKernel)(CUfunction, unsigned, unsigned, unsigned, u
                                      unsigned, unsigned, unsigned, CUstream, void**, void**);
 typedef CUresult (*PFN_Occupancy)(int*, CUfunction, int, size_t);
 typedef CUresult (*PFN_GetErrorString)(CUresult, const char**);
+typedef CUresult (*PFN_FuncSetAttribute)(CUfunction, CUfunction_attribute, int);
 
 struct Driver {
     PFN_ModuleLoadData module_load = nullptr;
@@ -62,6 +63,7 @@ struct Driver {
     PFN_LaunchKernel launch = nullptr;
     PFN_Occupancy occupancy = nullptr;
     PFN_GetErrorString error_string = nullptr;
+    PFN_FuncSetAttribute set_attribute = nullptr;
     bool ok = false;
     std::string why;
 };
@@ -80,7 +82,8 @@ Driver& driver()
                   get("cuModuleGetFunction", (void**)&d.get_function) &&
                   get("cuLaunchKernel", (void**)&d.launch) &&
                   get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.occupancy) &&
-                  get("cuGetErrorString", (void**)&d.error_string);
+                  get("cuGetErrorString", (void**)&d.error_string) &&
+                  get("cuFuncSetAttribute", (void**)&d.set_attribute);
         d.ok = ok;
         if (!ok) d.why = "CUDA driver entry points unavailable (no GPU driver?)";
     });
@@ -221,7 +224,8 @@ cfs_status get_kernel(const ProgramSpec& spec, const char* name, Kernel* out)
     } else {
         prog = it->second.get();
     }
-    auto kit = prog->kernels.find(name);
+    const std::string kname = std::string(name) + "/" + std::to_string(spec.dyn_smem);
+    auto kit = prog->kernels.find(kname);
     if (kit == prog->kernels.end()) {
         Kernel k;
         CUfunction fn = nullptr;
@@ -229,11 +233,18 @@ cfs_status get_kernel(const ProgramSpec& spec, const char* name, Kernel* out)
         if (st != CFS_OK) return st;
         k.fn = (void*)fn;
         k.block = spec.block;
-        st = check_cu(d.occupancy(&k.max_blocks_per_sm, fn, spec.block, 0),
+        k.dyn_smem = spec.dyn_smem;
+        if (spec.dyn_smem > 48 * 1024) {
+            st = check_cu(d.set_attribute(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
+                                          spec.dyn_smem),
+                          "cuFuncSetAttribute(max dynamic shared memory)");
+            if (st != CFS_OK) return st;
+        }
+        st = check_cu(d.occupancy(&k.max_blocks_per_sm, fn, spec.block, (size_t)spec.dyn_smem),
                       "cuOccupancyMaxActiveBlocksPerMultiprocessor");
         if (st != CFS_OK) return st;
         k.num_sms = device_sm_count();
-        kit = prog->kernels.emplace(name, k).first;
+        kit = prog->kernels.emplace(kname, k).first;
     }
     *out = kit->second;
     return CFS_OK;
@@ -244,8 +255,8 @@ cfs_status launch(const Kernel& k, unsigned grid, const void* args, size_t args_
 {
     (void)args_size;
     void* params[] = {const_cast<void*>(args)};
-    return check_cu(driver().launch((CUfunction)k.fn, grid, 1, 1, (unsigned)k.block, 1, 1, 0,
-                                    (CUstream)stream, params, nullptr),
+    return check_cu(driver().launch((CUfunction)k.fn, grid, 1, 1, (unsigned)k.block, 1, 1,
+                                    (unsigned)k.dyn_smem, (CUstream)stream, params, nullptr),
                     "cuLaunchKernel");
 }
 

@@ -54,7 +54,16 @@ def _host(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def test_batch_matches_oracle_frame_by_frame(torch_cuda):
+@pytest.mark.parametrize("tile_cap,warp_agg,use_tile", [("8192", "1", "1"), ("256", "1", "1"),
+                                                       ("1024", "0", "1"), ("8192", "1", "0")])
+def test_batch_matches_oracle_frame_by_frame(torch_cuda, monkeypatch, tile_cap, warp_agg,
+                                             use_tile):
+    # the privatized window at its default size, at a size smaller than most
+    # attractors (splats split between shared and global memory), without
+    # warp aggregation, and switched off
+    monkeypatch.setenv("CFS_TILE_CAP", tile_cap)
+    monkeypatch.setenv("CFS_WARP_AGG", warp_agg)
+    monkeypatch.setenv("CFS_TILE", use_tile)
     frames = W.animation_frames(n_frames=14, seed=2, min_log2=8, max_log2=12,
                                 resolutions=(64, 128))
     cfs, chain, items, descs, tens = _setup(frames)

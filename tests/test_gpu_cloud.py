@@ -1,0 +1,114 @@
+"""GPU parity of the stored point-cloud path (generation, then streaming the
+cloud through an 8-transform chain into a depth+colour layer) against the
+CPU oracle on the same inputs."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_02226_gb300 import workloads as W
+
+from _parity import EMPTY, check_depth_close, depth_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _cfs():
+    from paper_2606_02226_gb300 import cfs
+    return cfs
+
+
+@pytest.mark.parametrize("n,iters", [(10001, 32), (4096, 5), (1, 3)])
+def test_cloud_generation_bit_exact(torch_cuda, n, iters):
+    cfs = _cfs()
+    sysd = W.cloud_system()
+    xyz, fn = cfs.pointcloud_generate(cfs.System(sysd), n, iters, seed=3, system_id=2)
+    torch_cuda.cuda.synchronize()
+    ox, ofn = O.pointcloud_generate(sysd, n, iters, seed=3, system_id=2)
+    assert np.array_equal(xyz.cpu().numpy().T, ox)
+    assert np.array_equal(fn.cpu().numpy(), ofn)
+
+
+def _stream_parity(frame, n, W_):
+    torch = pytest.importorskip("torch")
+    cfs = _cfs()
+    sysd = W.cloud_system()
+    ox, ofn = O.pointcloud_generate(sysd, n, 32)
+    chain = W.cloud_chain(frame)
+    t = W.cloud_target(W_)
+    ten = cfs.alloc_target(t)
+    disc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    xyz = torch.from_numpy(np.ascontiguousarray(ox.T)).cuda()
+    fn = torch.from_numpy(ofn).cuda()
+    cfs.render_points(cfs.Chain(chain, 3), xyz, fn, [t], [ten], discards=disc)
+    torch.cuda.synchronize()
+    g = ten.cpu().numpy().view(np.uint64)
+    # margin from the chain's FP32 differences: 2e-6 of the [-1, 1] view in
+    # pixels, plus the bin rule's own rounding
+    margin = 2e-6 * W_ / 2 * 2 + 1e-4
+    o = O.render_points(ox, ofn, chain, [t], margin_px=margin, track=True)[0]
+    frac = check_depth_close(g, o.buf, o.zlo, o.zhi)
+    assert frac >= 0.999
+    d = int(disc.item())
+    assert abs(d - o.n_discard) <= o.n_amb
+    assert int((g != EMPTY).sum()) > 0
+    return g, o
+
+
+@pytest.mark.parametrize("frame", [0, 21, 63])
+def test_cloud_streaming_parity(torch_cuda, frame):
+    _stream_parity(frame, 1 << 15, 512)
+
+
+def test_render_points_needs_multiple_of_4(torch_cuda):
+    torch = torch_cuda
+    cfs = _cfs()
+    t = W.cloud_target(16)
+    ten = cfs.alloc_target(t)
+    xyz = torch.zeros((3, 6), dtype=torch.float32, device="cuda")
+    fn = torch.zeros(6, dtype=torch.uint8, device="cuda")
+    with pytest.raises(cfs.CfsError):
+        cfs.render_points(cfs.Chain(W.cloud_chain(0), 3), xyz, fn, [t], [ten])
+
+
+def test_cloud_full_size_sampled(torch_cuda):
+    """The benchmark's cloud (2^26 points, 8192^2 layer): every sampled
+    point's key bounds its pixel's minimum from above, and every stored key
+    decodes to a palette colour."""
+    torch = torch_cuda
+    cfs = _cfs()
+    sysd = W.cloud_system()
+    n = 1 << 26
+    xyz, fn = cfs.pointcloud_generate(cfs.System(sysd), n, 32)
+    t = W.cloud_target(8192)
+    ten = cfs.alloc_target(t)
+    chain = W.cloud_chain(40)
+    cfs.render_points(cfs.Chain(chain, 3), xyz, fn, [t], [ten])
+    torch.cuda.synchronize()
+    ids = np.linspace(0, n - 1, 257).astype(np.int64)
+    sx = xyz[:, torch.from_numpy(ids).cuda()].cpu().numpy().T.copy()
+    sfn = fn[torch.from_numpy(ids).cuda()].cpu().numpy()
+    # the sampled stored points equal the oracle's trajectories' endpoints
+    k, p, _ = O.trace(sysd, [W.Op("splat", (0,))], ids.astype(np.uint32), iters=32)
+    assert np.array_equal(sx, p[:, -1, :]) and np.array_equal(sfn, k[:, -1])
+    # each sampled point's depth bounds the layer's depth at the pixel it
+    # surely lands in (relative 1e-5 for the chain's FP32 differences)
+    r = O.render_points(sx, sfn, chain, [t], margin_px=2e-6 * 8192 + 1e-4, track=True)[0]
+    layer = ten.cpu().numpy().view(np.uint64)
+    sure = np.isfinite(r.zhi)
+    assert sure.sum() > 100
+    assert np.all(layer[sure] != EMPTY)
+    assert np.all(depth_of(layer[sure]).astype(np.float64) <=
+                  r.zhi[sure].astype(np.float64) * (1 + 1e-5))
+    keys = layer[layer != EMPTY]
+    cols = set(np.unique((keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)).tolist())
+    assert cols <= set(W.palette_rgba8(16)[:8].tolist())
+    z = depth_of(keys)
+    assert np.all(z > 1e-3)

@@ -403,6 +403,14 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64):
     e1.record(stream)
     torch.cuda.synchronize()
     gen_ms = e0.elapsed_time(e1)
+    # store the cloud in Morton order of its positions (once, at creation)
+    e0.record(stream)
+    xyz_m, fn_m = cfs.pointcloud_reorder(xyz, fn, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    reorder_ms = e0.elapsed_time(e1)
+    unsorted = (xyz, fn)
+    xyz, fn = xyz_m, fn_m
     t = W.cloud_target(Wd)
     layer = cfs.alloc_target(t, device=dev)
     chain = cfs.Chain(W.cloud_chain(0, n_frames), 3)
@@ -432,6 +440,13 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64):
     torch.cuda.synchronize()
     frame_ms = sum(a.elapsed_time(c) for a, b, c in ev) / n_frames
     kern_ms = sum(b.elapsed_time(c) for a, b, c in ev) / n_frames
+    # the same frames from the cloud in generation (random) order
+    e0.record(stream)
+    for f in range(8):
+        cfs.render_points(chain, unsorted[0], unsorted[1], [t], [layer], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    unsorted_ms = e0.elapsed_time(e1) / 8
     # algorithmic bytes of a frame: the cloud read once (12 B of positions +
     # 1 B of map index per point) and the layer written once (clear)
     cloud_bytes = 13 * n
@@ -440,7 +455,9 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64):
     kern_gbs = cloud_bytes / (kern_ms * 1e-3) / 1e9
     return {"workload": "2^26-point 3D IFS cloud; twist/bend/inversion/sinusoidal/4 affines/"
                         "perspective -> 8192^2 depth+colour u64; 64 frames",
-            "generate_ms": gen_ms, "ms_per_frame": frame_ms, "frames_per_s": 1e3 / frame_ms,
+            "generate_ms": gen_ms, "reorder_ms": reorder_ms,
+            "render_points_ms_generation_order": unsorted_ms,
+            "ms_per_frame": frame_ms, "frames_per_s": 1e3 / frame_ms,
             "points_per_s": n / (frame_ms * 1e-3), "render_points_ms": kern_ms,
             "roofline": {"bound": "hbm", "kernel": "cfs_points_kernel",
                          "achieved": kern_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

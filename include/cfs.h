@@ -206,6 +206,19 @@ cfs_status cfs_render_points(const cfs_chain* chain, const float* xyz, const uin
                              uint32_t n, const cfs_target* targets, int n_targets,
                              unsigned long long* discards, void* stream);
 
+/* Reorders a stored cloud into Morton (Z-curve) order of its positions so
+ * that streaming it splats neighbouring points into neighbouring pixels.
+ * Key: each coordinate quantized to 10 bits over the cloud's bounding box,
+ * q = min(1023, (int)((v - lo) * (1024 / (hi - lo)))) in FP32 (non-finite
+ * or degenerate -> 0), bits interleaved with x lowest; stable sort (equal
+ * keys keep their order), so the permutation is unique.  Inputs xyz [dim][n]
+ * and fn [n]; outputs xyz_out, fn_out (not in place) and, if not NULL,
+ * perm_out [n] with xyz_out[d][j] = xyz[d][perm_out[j]].  Allocates its
+ * scratch (about 16 bytes per point) stream-ordered on `stream`. */
+cfs_status cfs_pointcloud_reorder(const float* xyz, const uint8_t* fn, uint32_t n, int dim,
+                                  float* xyz_out, uint8_t* fn_out, uint32_t* perm_out,
+                                  void* stream);
+
 /* ---- batched rendering (many frames in one persistent launch) ---------- */
 /* One frame of a batch: its own system, range of point indices and targets
  * (device buffers of the caller).  Frames of a batch share the chain, the

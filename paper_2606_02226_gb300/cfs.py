@@ -111,6 +111,8 @@ _SIGNATURES = {
                                                ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P]),
     "cfs_render_points": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32,
                                          ctypes.POINTER(cfs_target), ctypes.c_int, _P, _P]),
+    "cfs_pointcloud_reorder": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int, _P, _P,
+                                              _P, _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -366,6 +368,20 @@ def pointcloud_generate(system: System, n: int, iters: int, *, seed: int = 0,
                                          system_id, n, iters, xyz.data_ptr(), fn.data_ptr(),
                                          _stream_handle(stream)))
     return xyz, fn
+
+
+def pointcloud_reorder(xyz, fn, stream=None, want_perm: bool = False):
+    """Morton-ordered copy of a stored cloud: (xyz_out, fn_out[, perm])."""
+    import torch
+    dim, n = xyz.shape
+    xo = torch.empty_like(xyz)
+    fo = torch.empty_like(fn)
+    perm = torch.empty(n, dtype=torch.int32, device=xyz.device) if want_perm else None
+    _check(lib().cfs_pointcloud_reorder(xyz.data_ptr(), fn.data_ptr(), n, dim, xo.data_ptr(),
+                                        fo.data_ptr(),
+                                        perm.data_ptr() if perm is not None else None,
+                                        _stream_handle(stream)))
+    return (xo, fo, perm) if want_perm else (xo, fo)
 
 
 def render_points(chain: Chain, xyz, fn, target_descs, target_tensors, *, discards=None,

@@ -149,6 +149,7 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     sp.n_targets = n_tg;
     for (int o = 0; o < ch->n_ops; ++o) {
         sp.op_kind[o] = ch->ops[o].kind;
+        if (ch->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)ch->ops[o].params[1];
         if (ch->ops[o].kind == CFS_OP_SPLAT) {
             const int slot = (int)ch->ops[o].params[0];
             SplatSpec s;

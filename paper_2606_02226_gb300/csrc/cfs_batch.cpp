@@ -212,6 +212,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     sp.n_targets = n_targets;
     for (int o = 0; o < chain->n_ops; ++o) {
         sp.op_kind[o] = chain->ops[o].kind;
+        if (chain->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)chain->ops[o].params[1];
         if (chain->ops[o].kind == CFS_OP_SPLAT) {
             const int slot = (int)chain->ops[o].params[0];
             SplatSpec ss;
@@ -221,15 +222,22 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
             sp.splats.push_back(ss);
         }
     }
-    sp.block = 256;
-    sp.min_blocks = 8;
+    // measured on GB300: one 1024-thread CTA per SM sharing a ~208 KB
+    // privatized window beats smaller CTAs with smaller windows (the flush
+    // volume and the global-atomic share both shrink)
+    sp.block = 1024;
+    if (const char* e = std::getenv("CFS_BATCH_BLOCK")) {
+        const int v = std::atoi(e);
+        if (v == 128 || v == 256 || v == 512 || v == 1024) sp.block = v;
+    }
+    sp.min_blocks = std::max(1, 2048 / sp.block);
     sp.spill_allowance = 64;
     sp.depth_test = 1;
     if (const char* e = std::getenv("CFS_BATCH_MINB")) sp.min_blocks = std::max(1, std::atoi(e));
     // privatized window: when the chain splats once, into a histogram
     sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
     sp.warp_agg = 1;
-    b->tile_cap = 8192;
+    b->tile_cap = sp.block >= 1024 ? 53248 : 8192;
     if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
     if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
     if (const char* e = std::getenv("CFS_TILE_CAP")) {
@@ -251,15 +259,19 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     // points, at most chunk_max), so all CTAs work on one or two frames at a
     // time and the live layers stay in L2.
     b->grid = (uint32_t)std::max(1, b->kernel.max_blocks_per_sm * std::max(1, b->kernel.num_sms));
-    b->chunk = 8u * (uint32_t)sp.block;
+    b->chunk = 4096;
     if (const char* e = std::getenv("CFS_BATCH_CHUNK")) {
         const int c = std::atoi(e);
         if (c >= 32 && c % 32 == 0) b->chunk = (uint32_t)c;
     }
+    bool adaptive = false;
+    if (const char* e = std::getenv("CFS_BATCH_ADAPT")) adaptive = std::atoi(e) != 0;
     b->chunks.resize(n_frames);
     for (int f = 0; f < n_frames; ++f) {
         const uint64_t per = ((uint64_t)frames[f].n_points / b->grid) / 32 * 32;
-        const uint32_t c = (uint32_t)std::min<uint64_t>(b->chunk, std::max<uint64_t>(32, per));
+        const uint32_t c = adaptive
+                               ? (uint32_t)std::min<uint64_t>(b->chunk, std::max<uint64_t>(32, per))
+                               : b->chunk;
         b->chunks[f] = c;
         total_items += ((uint64_t)frames[f].n_points + c - 1) / c;
     }

@@ -23,7 +23,8 @@ std::string ProgramSpec::key() const
       << spill_allowance << ".p" << tile << warp_agg << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
-    for (int j = 0; j < n_ops; ++j) s << op_kind[j] << ",";
+    for (int j = 0; j < n_ops; ++j) s << op_kind[j] << (op_kind[j] == CFS_OP_ROTATE3 ? "r" : "")
+                                      << (op_kind[j] == CFS_OP_ROTATE3 ? op_axis[j] : 0) << ",";
     s << ".s";
     for (const auto& sp : splats) s << sp.slot << ":" << sp.kind << ":" << sp.channels << ",";
     return s.str();
@@ -104,9 +105,16 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
             s << "cfs_affine2(" << Plist(o, 6) << "qx, qy);\n";
             break;
         case CFS_OP_AFFINE3:
-        case CFS_OP_ROTATE3:
-        case CFS_OP_TRANSLATE3:
             s << "cfs_affine3(" << Plist(o, 12) << "qx, qy, qz);\n";
+            break;
+        case CFS_OP_ROTATE3:
+            // the affine evaluation with the zero entries dropped: the same
+            // roundings (only the sign of an exact zero can differ)
+            s << "cfs_rotate3_" << sp.op_axis[o] << "(" << Plist(o, 12) << "qx, qy, qz);\n";
+            break;
+        case CFS_OP_TRANSLATE3:
+            s << "qx = qx + " << P(o, 9) << "; qy = qy + " << P(o, 10) << "; qz = qz + "
+              << P(o, 11) << ";\n";
             break;
         case CFS_OP_SWIRL: s << "cfs_swirl(qx, qy);\n"; break;
         case CFS_OP_SINUSOIDAL: s << "cfs_sinusoidal(qx, qy);\n"; break;

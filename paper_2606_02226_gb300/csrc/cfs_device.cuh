@@ -118,6 +118,42 @@ __device__ __forceinline__ void cfs_affine3(float m0, float m1, float m2, float 
     z = nz;
 }
 
+/* Rotations about one axis: the affine evaluation above with its zero terms
+ * dropped (x' = fma(1, x, fma(0, y, fma(0, z, 0))) is x; the two rotated
+ * coordinates keep their fma(a, u, fma(b, v, 0)) = fma(a, u, b v) form). */
+__device__ __forceinline__ void cfs_rotate3_0(float, float, float, float, float m4, float m5,
+                                              float m6, float m7, float m8, float, float, float,
+                                              float& x, float& y, float& z)
+{
+    (void)m6; (void)x;
+    const float ny = fmaf(m4, y, m5 * z);
+    const float nz = fmaf(m7, y, m8 * z);
+    y = ny;
+    z = nz;
+}
+
+__device__ __forceinline__ void cfs_rotate3_1(float m0, float, float m2, float, float, float,
+                                              float m6, float, float m8, float, float, float,
+                                              float& x, float& y, float& z)
+{
+    (void)y;
+    const float nx = fmaf(m0, x, m2 * z);
+    const float nz = fmaf(m6, x, m8 * z);
+    x = nx;
+    z = nz;
+}
+
+__device__ __forceinline__ void cfs_rotate3_2(float m0, float m1, float, float m3, float m4,
+                                              float, float, float, float, float, float, float,
+                                              float& x, float& y, float& z)
+{
+    (void)z;
+    const float nx = fmaf(m0, x, m1 * y);
+    const float ny = fmaf(m3, x, m4 * y);
+    x = nx;
+    y = ny;
+}
+
 /* Eq. 1 (circle IFS), read with atan2 taken into [0, 2 pi) and r2 in the last
  * two lines: theta2 = pi (r + f_id), r2 = sqrt(theta / 2 pi). */
 __device__ __forceinline__ void cfs_circle(float fid, float& x, float& y)

@@ -50,6 +50,7 @@ struct ProgramSpec {
     bool reuse = false;
     int n_ops = 0;
     int op_kind[CFS_MAX_OPS] = {};
+    int op_axis[CFS_MAX_OPS] = {};   // rotate3: 0 x, 1 y, 2 z
     std::vector<SplatSpec> splats;   // in op order
     int n_targets = 0;
     int depth_test = 1;

@@ -112,3 +112,59 @@ def test_cloud_full_size_sampled(torch_cuda):
     assert cols <= set(W.palette_rgba8(16)[:8].tolist())
     z = depth_of(keys)
     assert np.all(z > 1e-3)
+
+
+def _morton_keys(xyz):
+    """Morton keys of a [dim, n] float32 cloud, computed as the reorder
+    defines them (FP32 box, scale, quantization; x in the lowest bit)."""
+    dim, n = xyz.shape
+    key = np.zeros(n, dtype=np.uint64)
+    for d in range(dim):
+        v = xyz[d]
+        fin = v[~np.isnan(v)]
+        lo, hi = np.float32(fin.min()), np.float32(fin.max())
+        ext = np.float32(hi - lo)
+        scale = np.float32(np.float32(1024.0) / ext) if ext > 0 else np.float32(0.0)
+        with np.errstate(invalid="ignore", over="ignore"):
+            u = (v - lo).astype(np.float32) * scale
+        q = np.zeros(n, dtype=np.int64)
+        ok = u >= 0
+        q[ok] = np.minimum(np.minimum(u[ok], 2**31 - 1).astype(np.int64), 1023)
+        for b in range(10):
+            key |= (((q >> b) & 1).astype(np.uint64)) << np.uint64(3 * b + d if dim == 3 else 2 * b + d)
+    return key
+
+
+@pytest.mark.parametrize("n,dim", [(100003, 3), (4096 * 3 + 17, 2), (1, 3)])
+def test_reorder_is_the_stable_morton_sort(torch_cuda, n, dim):
+    torch = torch_cuda
+    cfs = _cfs()
+    rng = np.random.default_rng(n)
+    xyz = rng.normal(size=(dim, n)).astype(np.float32)
+    if n > 10:
+        xyz[:, 5] = xyz[:, 3]          # equal keys keep their order
+        xyz[0, 7] = np.nan
+    fn = rng.integers(0, 8, n).astype(np.uint8)
+    xo, fo, perm = cfs.pointcloud_reorder(torch.from_numpy(xyz).cuda(), torch.from_numpy(fn).cuda(),
+                                          want_perm=True)
+    torch.cuda.synchronize()
+    expect = np.argsort(_morton_keys(xyz), kind="stable")
+    p = perm.cpu().numpy()
+    assert np.array_equal(p, expect)
+    assert np.array_equal(xo.cpu().numpy(), xyz[:, expect], equal_nan=True)
+    assert np.array_equal(fo.cpu().numpy(), fn[expect])
+
+
+def test_reordered_cloud_renders_the_same_layer(torch_cuda):
+    torch = torch_cuda
+    cfs = _cfs()
+    n = 1 << 18
+    xyz, fn = cfs.pointcloud_generate(cfs.System(W.cloud_system()), n, 32)
+    xo, fo = cfs.pointcloud_reorder(xyz, fn)
+    t = W.cloud_target(1024)
+    a, b = cfs.alloc_target(t), cfs.alloc_target(t)
+    ch = cfs.Chain(W.cloud_chain(30), 3)
+    cfs.render_points(ch, xyz, fn, [t], [a])
+    cfs.render_points(ch, xo, fo, [t], [b])
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)

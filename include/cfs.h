@@ -266,6 +266,67 @@ cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_fra
                             int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
                             int clear, void* stream);
 
+/* ---- learned warm-start sampler (the initial distribution the paper
+ *      proposes to derive automatically, Section 4) ---------------------- */
+/* Network: u (64) -> 128 -> 128 -> 128 -> 2 with SiLU after the first three
+ * layers; u = [Gaussian noise (2), affine parameters a b c d e f of up to 8
+ * maps (48, zero for missing maps), frame time t (1), zeros (13)].  BF16
+ * weights and activations (round to nearest even), FP32 accumulation on the
+ * tensor cores; FP32 master weights and Adam state on the device.
+ * Parameter vector (FP32, this order): W1 [128][64], b1 [128], W2 [128][128],
+ * b2, W3 [128][128], b3, W4 [2][128], b4 [2]: cfs_sampler_param_count()
+ * floats. */
+typedef struct cfs_sampler cfs_sampler;
+
+uint32_t cfs_sampler_param_count(void);
+/* Creates a sampler with host parameters `params` (NULL: uniform
+ * +-1/sqrt(fan_in) weights from Philox with `seed`, zero biases); Adam state
+ * zero, step 0. */
+cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** out);
+cfs_status cfs_sampler_destroy(cfs_sampler* s);
+/* Host copies of the parameters, Adam moments and step (any may be NULL):
+ * a checkpoint.  Synchronizes the device. */
+cfs_status cfs_sampler_get_params(const cfs_sampler* s, float* params, float* adam_m,
+                                  float* adam_v, uint32_t* step);
+/* Restores a checkpoint (moments may be NULL: left as they are). */
+cfs_status cfs_sampler_set_params(cfs_sampler* s, const float* params, const float* adam_m,
+                                  const float* adam_v, uint32_t step);
+/* Y (device f32 [B][2]) = network(U), U device BF16 [B][64]. */
+cfs_status cfs_sampler_forward(cfs_sampler* s, const void* U, uint32_t B, float* Y, void* stream);
+/* Adds to `grads` (device f32 [param_count]) the gradient of sum(dY * Y)
+ * (dY device f32 [B][2]) with respect to every parameter. */
+cfs_status cfs_sampler_backward(cfs_sampler* s, const void* U, uint32_t B, const float* dY,
+                                float* grads, void* stream);
+/* Sliced-Wasserstein loss of point sets X against T (device f32
+ * [n_sys][n_per][2]; n_per a power of two in 32..1024) over projections
+ * (cos phi_j, sin phi_j) (phi device f32 [n_proj]):
+ * L = mean_{s,j} mean_i (sort(X_s theta_j)_i - sort(T_s theta_j)_i)^2.
+ * L is added to *loss and dL/dX to dX (device). */
+cfs_status cfs_sw_loss(const float* X, const float* T, uint32_t n_sys, uint32_t n_per,
+                       const float* phi, uint32_t n_proj, float* loss, float* dX, void* stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8, bias-corrected at step t >= 1)
+ * with device gradients `grads`. */
+cfs_status cfs_sampler_adam(cfs_sampler* s, const float* grads, uint32_t t, float lr,
+                            void* stream);
+/* Trains for `steps` Adam steps on chaos-game points of `systems` (2D,
+ * affine, at most 8 maps; frame times t_values): every step picks
+ * systems_per_step systems, draws points_per_system targets per system from
+ * the library's own chaos game (40 steps from a uniform start), evaluates
+ * the network on fresh noise and applies the sliced-Wasserstein loss over
+ * n_proj projections (randomly rotated each step).  One step is captured as
+ * a CUDA graph and replayed.  Writes the per-step loss to loss_history
+ * (host, steps floats, may be NULL); returns when training is done. */
+cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
+                             const float* t_values, int n_systems, uint32_t steps,
+                             uint32_t systems_per_step, uint32_t points_per_system,
+                             uint32_t n_proj, float lr, uint64_t seed, float* loss_history,
+                             void* stream);
+/* Warm-start points for `sys` at frame time t: n network outputs on noise
+ * drawn from (seed), written SoA to start (device f32 [2][n]) -- the
+ * `start` of a cfs_render_params.  Returns after the points are written. */
+cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float t, uint32_t n,
+                                    uint64_t seed, float* start, void* stream);
+
 /* Records, for the n_ids points listed in the device array `ids` (global
  * indices), every step's map index (device i32 [n_ids][steps]), iterated
  * point (device f32 [n_ids][steps][3]) and, per SPLAT op of the chain, the

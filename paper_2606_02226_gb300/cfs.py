@@ -113,6 +113,22 @@ _SIGNATURES = {
                                          ctypes.POINTER(cfs_target), ctypes.c_int, _P, _P]),
     "cfs_pointcloud_reorder": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int, _P, _P,
                                               _P, _P]),
+    "cfs_sampler_param_count": (ctypes.c_uint32, []),
+    "cfs_sampler_create": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "cfs_sampler_destroy": (ctypes.c_int, [_P]),
+    "cfs_sampler_get_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_uint32)]),
+    "cfs_sampler_set_params": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_uint32]),
+    "cfs_sampler_forward": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
+    "cfs_sampler_backward": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P, _P]),
+    "cfs_sw_loss": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_uint32, _P,
+                                   ctypes.c_uint32, _P, _P, _P]),
+    "cfs_sampler_adam": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_float, _P]),
+    "cfs_sampler_train": (ctypes.c_int, [_P, ctypes.POINTER(_P), _P, ctypes.c_int,
+                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, _P,
+                                         _P]),
+    "cfs_sampler_start_points": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_uint32,
+                                                ctypes.c_uint64, _P, _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -466,6 +482,105 @@ def render_batch(chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 
     _check(lib().cfs_render_batch(chain.handle, nt, arr, len(frames), iters, burn_in,
                                   int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if clear else 0,
                                   _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# learned warm-start sampler
+# ---------------------------------------------------------------------------
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+class Sampler:
+    """The warm-start network (include/cfs.h): FP32 master parameters and
+    Adam state on the device, BF16 tensor-core forward/backward."""
+
+    def __init__(self, params=None, seed: int = 0):
+        h = _P()
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().cfs_sampler_create(_fptr(p), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                        ctypes.byref(h)))
+        self.handle = h
+        self.n_params = int(lib().cfs_sampler_param_count())
+
+    def get_params(self):
+        w = np.zeros(self.n_params, np.float32)
+        m = np.zeros(self.n_params, np.float32)
+        v = np.zeros(self.n_params, np.float32)
+        st = ctypes.c_uint32()
+        _check(lib().cfs_sampler_get_params(self.handle, _fptr(w), _fptr(m), _fptr(v),
+                                            ctypes.byref(st)))
+        return w, m, v, st.value
+
+    def set_params(self, w, m=None, v=None, step: int = 0):
+        w = np.ascontiguousarray(w, np.float32)
+        m = None if m is None else np.ascontiguousarray(m, np.float32)
+        v = None if v is None else np.ascontiguousarray(v, np.float32)
+        _check(lib().cfs_sampler_set_params(self.handle, _fptr(w), _fptr(m), _fptr(v), step))
+
+    def forward(self, U, stream=None):
+        """U: device bfloat16 [B, 64] -> device float32 [B, 2]."""
+        import torch
+        B = U.shape[0]
+        Y = torch.empty((B, 2), dtype=torch.float32, device=U.device)
+        _check(lib().cfs_sampler_forward(self.handle, U.data_ptr(), B, Y.data_ptr(),
+                                         _stream_handle(stream)))
+        return Y
+
+    def backward(self, U, dY, grads=None, stream=None):
+        import torch
+        if grads is None:
+            grads = torch.zeros(self.n_params, dtype=torch.float32, device=U.device)
+        _check(lib().cfs_sampler_backward(self.handle, U.data_ptr(), U.shape[0], dY.data_ptr(),
+                                          grads.data_ptr(), _stream_handle(stream)))
+        return grads
+
+    def adam(self, grads, t: int, lr: float = 1e-3, stream=None):
+        _check(lib().cfs_sampler_adam(self.handle, grads.data_ptr(), t, lr,
+                                      _stream_handle(stream)))
+
+    def train(self, systems, t_values, steps: int, *, systems_per_step: int = 64,
+              points_per_system: int = 1024, n_proj: int = 64, lr: float = 1e-3,
+              seed: int = 0, stream=None):
+        """systems: list of System handles; returns the loss per step."""
+        arr = (_P * len(systems))(*[s.handle for s in systems])
+        tv = np.ascontiguousarray(t_values, np.float32)
+        hist = np.zeros(max(steps, 1), np.float32)
+        _check(lib().cfs_sampler_train(self.handle, arr, _fptr(tv), len(systems), steps,
+                                       systems_per_step, points_per_system, n_proj, lr,
+                                       int(seed) & 0xFFFFFFFFFFFFFFFF, _fptr(hist),
+                                       _stream_handle(stream)))
+        return hist[:steps]
+
+    def start_points(self, system: System, t: float, n: int, seed: int = 0, out=None,
+                     stream=None):
+        """Device float32 [2, n] warm-start points (SoA) for ``system``."""
+        import torch
+        if out is None:
+            out = torch.empty((2, n), dtype=torch.float32,
+                              device=torch.device("cuda", torch.cuda.current_device()))
+        _check(lib().cfs_sampler_start_points(self.handle, system.handle, float(t), n,
+                                              int(seed) & 0xFFFFFFFFFFFFFFFF, out.data_ptr(),
+                                              _stream_handle(stream)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _LIB is not None:
+            _LIB.cfs_sampler_destroy(h)
+            self.handle = None
+
+
+def sw_loss(X, T, phi, stream=None):
+    """Sliced-Wasserstein loss of device point sets X, T [S, N, 2] over
+    angles phi [P] -> (loss tensor [1], dX tensor)."""
+    import torch
+    S, N, _ = X.shape
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    dX = torch.zeros_like(X)
+    _check(lib().cfs_sw_loss(X.data_ptr(), T.data_ptr(), S, N, phi.data_ptr(), phi.numel(),
+                             loss.data_ptr(), dX.data_ptr(), _stream_handle(stream)))
+    return loss, dX
 
 
 def atomic_bench(kind: int, buf, n_elems: int, blocks: int, iters: int, seed: int = 1,

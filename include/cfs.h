@@ -327,6 +327,38 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
 cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float t, uint32_t n,
                                     uint64_t seed, float* start, void* stream);
 
+/* ---- batched histograms without allocation --------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while rendering -- an application that
+ * records its frame loop into a larger CUDA graph and owns every allocation
+ * up front, a real-time or embedded host whose memory budget is fixed
+ * after start-up, a process whose GPU memory belongs to another allocator.
+ * It renders the same histograms as cfs_render_batch with a chain that only
+ * splats (CFS_OP_SPLAT into slot 0), but keeps its workspace (frame
+ * descriptors, work counter, discard counters) in one fixed device array
+ * compiled into the library instead of calling cudaMalloc.  It calls no
+ * allocating routine.
+ *  - At most CFS_NOALLOC_MAX_FRAMES frames per call (else
+ *    CFS_ERR_INVALID_ARG); each frame: a 2D system of affine maps and
+ *    targets[0] a u32 histogram; other targets are ignored.
+ *  - The array (about 140 KB) exists on every GPU that loads the library,
+ *    until the process exits, and every call shares it: calls whose GPU
+ *    work overlaps (other streams, other threads) race and corrupt each
+ *    other.  The work and discard counters are reset on the stream at the
+ *    start of each call.
+ *  - The first call on a device looks up the array's device address and
+ *    the grid size (cudaGetSymbolAddress, occupancy query); make that first
+ *    call before any stream capture.
+ *  - clear != 0 zeroes the histograms first (on the stream).
+ *  - discards, if not NULL: device u64 [n_frames], set to the discarded
+ *    splats of each frame.
+ *  - Frame descriptors are copied from host memory with cudaMemcpyAsync,
+ *    which has read its (pageable) source when it returns. */
+#define CFS_NOALLOC_MAX_FRAMES 256
+cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_frames, uint32_t iters,
+                                    uint32_t burn_in, uint64_t seed, int clear,
+                                    unsigned long long* discards, void* stream);
+
 /* Records, for the n_ids points listed in the device array `ids` (global
  * indices), every step's map index (device i32 [n_ids][steps]), iterated
  * point (device f32 [n_ids][steps][3]) and, per SPLAT op of the chain, the

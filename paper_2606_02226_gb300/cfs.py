@@ -129,6 +129,9 @@ _SIGNATURES = {
                                          _P]),
     "cfs_sampler_start_points": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_uint32,
                                                 ctypes.c_uint64, _P, _P]),
+    "cfs_render_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(cfs_frame), ctypes.c_int,
+                                                ctypes.c_uint32, ctypes.c_uint32,
+                                                ctypes.c_uint64, ctypes.c_int, _P, _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -581,6 +584,19 @@ def sw_loss(X, T, phi, stream=None):
     _check(lib().cfs_sw_loss(X.data_ptr(), T.data_ptr(), S, N, phi.data_ptr(), phi.numel(),
                              loss.data_ptr(), dX.data_ptr(), _stream_handle(stream)))
     return loss, dX
+
+
+def render_batch_noalloc(frames, *, iters: int, burn_in: int, seed: int = 0,
+                         clear: bool = True, discards=None, stream=None):
+    """Histogram frames (splat-only chain) rendered with the library's fixed
+    device workspace instead of an allocation; ``frames`` as for ``Batch``
+    (targets[0] a u32 histogram), at most 256 of them; ``discards``: optional
+    device int64 [n_frames] receiving each frame's discarded splats."""
+    arr, _ = _frames(frames)
+    _check(lib().cfs_render_batch_noalloc(arr, len(frames), iters, burn_in,
+                                          int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if clear else 0,
+                                          discards.data_ptr() if discards is not None else None,
+                                          _stream_handle(stream)))
 
 
 def atomic_bench(kind: int, buf, n_elems: int, blocks: int, iters: int, seed: int = 1,

@@ -342,9 +342,10 @@ def run_cfs(args, wl):
                          "peaks_gops": peaks},
             "e2e": e2e, "gpu_launches": len(jobs) * K, "clocks": clk}
     if args.batch:
-        line["batch"] = bench_batch(torch, cfs, dev, stream)
+        line["batch"] = bench_batch(torch, cfs, dev, stream, n_frames=args.batch_frames)
     if args.cloud:
-        line["cloud"] = bench_cloud(torch, cfs, dev, stream)
+        line["cloud"] = bench_cloud(torch, cfs, dev, stream, n_frames=args.cloud_frames,
+                                    n=args.cloud_points)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -352,12 +353,12 @@ def run_cfs(args, wl):
         dist.destroy_process_group()
 
 
-def bench_batch(torch, cfs, dev, stream, reps: int = 3):
+def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
     """Batched animation: 256 frames of 2-8 random affine maps interpolated
     between two keyframes, 2^16..2^22 points (log-uniform) and 256^2..2048^2
     four-channel histograms per frame, 300 steps, burn-in 20; one persistent
     launch per batch, replayed as a CUDA graph (clears included)."""
-    frames = W.animation_frames(n_frames=256, seed=0)
+    frames = W.animation_frames(n_frames=n_frames, seed=0)
     chain = cfs.Chain([W.Op("splat", (0,))], 2)
     items, begin = [], 0
     for f, fr in enumerate(frames):
@@ -379,22 +380,22 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3):
     n_pts = sum(fr.n_points for fr in frames)
     bytes_targets = sum(4 * 4 * fr.W * fr.W for fr in frames)
     info = b.info()
-    return {"workload": "256 animation frames, 2-8 affine maps, 2^16..2^22 points, "
+    return {"workload": f"{n_frames} animation frames, 2-8 affine maps, 2^16..2^22 points, "
                         "256^2..2048^2 x 4ch u32, 300 steps, burn-in 20",
-            "ms_per_batch": ms, "frames_per_s": 256 / (ms * 1e-3),
+            "ms_per_batch": ms, "frames_per_s": n_frames / (ms * 1e-3),
             "point_steps_per_s": n_pts * 300 / (ms * 1e-3),
             "splats_per_s": n_pts * 280 / (ms * 1e-3), "points": n_pts,
             "target_bytes": bytes_targets, "items": info["n_items"], "chunk": info["chunk"],
             "grid": info["grid"], "gpu_launches_per_batch": 1}
 
 
-def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64):
+def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26):
     """Stored-cloud deformation: a 2^26-point cloud of a 3D IFS (8 maps)
     generated once, then 64 animation frames each streaming it through twist,
     bend, sphere inversion, sinusoidal, four affines and a perspective splat
     into an 8192^2 depth+colour layer (clear included)."""
     peaks, src = _peaks()
-    n, Wd = 1 << 26, 8192
+    Wd = 8192
     sysh = cfs.System(W.cloud_system())
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -453,8 +454,8 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64):
     layer_bytes = 8 * Wd * Wd
     frame_gbs = (cloud_bytes + layer_bytes) / (frame_ms * 1e-3) / 1e9
     kern_gbs = cloud_bytes / (kern_ms * 1e-3) / 1e9
-    return {"workload": "2^26-point 3D IFS cloud; twist/bend/inversion/sinusoidal/4 affines/"
-                        "perspective -> 8192^2 depth+colour u64; 64 frames",
+    return {"workload": f"{n}-point 3D IFS cloud; twist/bend/inversion/sinusoidal/4 affines/"
+                        f"perspective -> 8192^2 depth+colour u64; {n_frames} frames",
             "generate_ms": gen_ms, "reorder_ms": reorder_ms,
             "render_points_ms_generation_order": unsorted_ms,
             "ms_per_frame": frame_ms, "frames_per_s": 1e3 / frame_ms,
@@ -482,6 +483,9 @@ def main():
                     help="skip the batched-animation measurement")
     ap.add_argument("--no-cloud", dest="cloud", action="store_false",
                     help="skip the stored-cloud measurement")
+    ap.add_argument("--batch-frames", type=int, default=256)
+    ap.add_argument("--cloud-frames", type=int, default=64)
+    ap.add_argument("--cloud-points", type=int, default=1 << 26)
     args = ap.parse_args()
     wl = W.composed_render(n_points=args.points, iters=args.iters)
     if args.impl == "reference":

@@ -212,7 +212,9 @@ def _config(wl):
                         "RGBA f32; torus/perspective -> 2048^2 depth+colour u64",
             "points": n, "iters": wl.iters, "burn_in": wl.burn_in,
             "resolution": wl.targets[0].W, "seed": wl.seed,
-            "l2": "flushed before every timed step (256 MiB write)"}
+            "l2": "flushed before every timed step (256 MiB write)",
+            "trig": "fast (Cody-Waite reduction + hardware sin/cos)" if wl.extra.get("fast_trig")
+                    else "precise (sinf/cosf)"}
 
 
 # ---------------------------------------------------------------------------
@@ -235,7 +237,7 @@ def run_cfs(args, wl):
     jobs = [W.RenderJob(j.system, j.point_begin + rank * n_total, j.n_points, j.system_id)
             for j in wl.jobs]
     systems = [cfs.System(j.system) for j in jobs]
-    chain = cfs.Chain(wl.chain, 2)
+    chain = cfs.Chain(wl.chain, 2, fast_trig=args.fast_trig)
     targets = [cfs.alloc_target(t, device=dev) for t in wl.targets]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for s in systems:
@@ -295,7 +297,7 @@ def run_cfs(args, wl):
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         ss = [cfs.System(j.system) for j in jobs]        # inputs handed over from the host
-        ch = cfs.Chain(wl.chain, 2)
+        ch = cfs.Chain(wl.chain, 2, fast_trig=args.fast_trig)
         cfs.target_clear(wl.targets, targets, stream)
         for s, j in zip(ss, jobs):
             cfs.render(s, ch, wl.targets, targets, n_points=j.n_points, iters=wl.iters,
@@ -345,7 +347,7 @@ def run_cfs(args, wl):
         line["batch"] = bench_batch(torch, cfs, dev, stream, n_frames=args.batch_frames)
     if args.cloud:
         line["cloud"] = bench_cloud(torch, cfs, dev, stream, n_frames=args.cloud_frames,
-                                    n=args.cloud_points)
+                                    n=args.cloud_points, fast_trig=args.fast_trig)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -389,7 +391,8 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             "grid": info["grid"], "gpu_launches_per_batch": 1}
 
 
-def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26):
+def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
+                fast_trig: bool = False):
     """Stored-cloud deformation: a 2^26-point cloud of a 3D IFS (8 maps)
     generated once, then 64 animation frames each streaming it through twist,
     bend, sphere inversion, sinusoidal, four affines and a perspective splat
@@ -414,7 +417,7 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26):
     xyz, fn = xyz_m, fn_m
     t = W.cloud_target(Wd)
     layer = cfs.alloc_target(t, device=dev)
-    chain = cfs.Chain(W.cloud_chain(0, n_frames), 3)
+    chain = cfs.Chain(W.cloud_chain(0, n_frames), 3, fast_trig=fast_trig)
 
     def frame(f):
         ops = W.cloud_chain(f, n_frames)
@@ -483,11 +486,14 @@ def main():
                     help="skip the batched-animation measurement")
     ap.add_argument("--no-cloud", dest="cloud", action="store_false",
                     help="skip the stored-cloud measurement")
+    ap.add_argument("--fast-trig", action="store_true",
+                    help="chains use reduced-argument hardware sine/cosine")
     ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--cloud-frames", type=int, default=64)
     ap.add_argument("--cloud-points", type=int, default=1 << 26)
     args = ap.parse_args()
     wl = W.composed_render(n_points=args.points, iters=args.iters)
+    wl.extra["fast_trig"] = args.fast_trig
     if args.impl == "reference":
         run_reference(args, wl)
     else:

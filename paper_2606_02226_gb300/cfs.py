@@ -80,6 +80,8 @@ _SIGNATURES = {
     "cfs_system_destroy": (ctypes.c_int, [_P]),
     "cfs_compose": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cfs_transform), ctypes.c_int,
                                    ctypes.POINTER(_P)]),
+    "cfs_compose_ex": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cfs_transform), ctypes.c_int,
+                                      ctypes.c_uint32, ctypes.POINTER(_P)]),
     "cfs_chain_destroy": (ctypes.c_int, [_P]),
     "cfs_chain_set_params": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "cfs_render": (ctypes.c_int, [_P, _P, ctypes.POINTER(cfs_render_params),
@@ -216,10 +218,11 @@ class Chain:
     """A composed transform chain (Section 3, Fig. 2B) for points of
     dimension ``dim_in``; ``ops`` are ``.kind`` / ``.params`` records."""
 
-    def __init__(self, ops, dim_in: int):
+    def __init__(self, ops, dim_in: int, fast_trig: bool = False):
         arr, n = _transforms(ops)
         h = _P()
-        _check(lib().cfs_compose(dim_in, arr, n, ctypes.byref(h)))
+        _check(lib().cfs_compose_ex(dim_in, arr, n, 1 if fast_trig else 0, ctypes.byref(h)))
+        self.fast_trig = fast_trig
         self.handle = h
         self.ops = list(ops)
         self.dim_in = dim_in

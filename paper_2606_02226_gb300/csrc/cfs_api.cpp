@@ -147,6 +147,7 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     sp.reuse = reuse;
     sp.n_ops = ch->n_ops;
     sp.n_targets = n_tg;
+    sp.fast_trig = (ch->flags & CFS_COMPOSE_FAST_TRIG) ? 1 : 0;
     for (int o = 0; o < ch->n_ops; ++o) {
         sp.op_kind[o] = ch->ops[o].kind;
         if (ch->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)ch->ops[o].params[1];
@@ -168,6 +169,7 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     if (const char* e = std::getenv("CFS_BLOCK")) sp.block = std::atoi(e);
     if (const char* e = std::getenv("CFS_MINB")) sp.min_blocks = std::atoi(e);
     if (const char* e = std::getenv("CFS_DEPTH_TEST")) sp.depth_test = std::atoi(e);
+    if (const char* e = std::getenv("CFS_SPILL_ALLOW")) sp.spill_allowance = std::atoi(e);
     if (sp.block != 128 && sp.block != 256 && sp.block != 512) sp.block = 256;
     if (sp.min_blocks < 1 || sp.min_blocks > 16) sp.min_blocks = 4;
     sp.depth_test = sp.depth_test ? 1 : 0;
@@ -317,7 +319,17 @@ cfs_status cfs_system_destroy(cfs_system* sys)
 
 cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chain** out)
 {
+    return cfs_compose_ex(dim_in, ops, n_ops, 0u, out);
+}
+
+cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint32_t flags,
+                          cfs_chain** out)
+{
     clear_error();
+    if (flags & ~(uint32_t)CFS_COMPOSE_FAST_TRIG) {
+        if (out) *out = nullptr;
+        return fail(CFS_ERR_INVALID_ARG, "unknown compose flags");
+    }
     if (!out) return fail(CFS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (dim_in != 2 && dim_in != 3) return fail(CFS_ERR_INVALID_ARG, "dim_in must be 2 or 3");
@@ -355,6 +367,7 @@ cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chai
     if (!c) return fail(CFS_ERR_OOM, "host allocation failed");
     c->dim_in = dim_in;
     c->n_ops = n_ops;
+    c->flags = flags;
     for (int o = 0; o < n_ops; ++o) c->ops[o] = ops[o];
     c->n_splat = n_splat;
     *out = c;
@@ -549,6 +562,7 @@ cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
         sp.spill_allowance = 64;
         sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
         sp.warp_agg = sp.tile;
+        sp.tile_reps = 8;
     }
     std::string s, l;
     st = compile_only(sp, &s, &l);

@@ -210,6 +210,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     sp.n_cmp = max_cmp;
     sp.n_ops = chain->n_ops;
     sp.n_targets = n_targets;
+    sp.fast_trig = (chain->flags & CFS_COMPOSE_FAST_TRIG) ? 1 : 0;
     for (int o = 0; o < chain->n_ops; ++o) {
         sp.op_kind[o] = chain->ops[o].kind;
         if (chain->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)chain->ops[o].params[1];
@@ -240,6 +241,8 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     b->tile_cap = sp.block >= 1024 ? 53248 : 8192;
     if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
     if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
+    sp.tile_reps = sp.block / 32;
+    if (const char* e = std::getenv("CFS_TILE_REPS")) sp.tile_reps = std::max(1, std::atoi(e));
     if (const char* e = std::getenv("CFS_TILE_CAP")) {
         const int c = std::atoi(e);
         if (c >= 256 && c <= 53248) b->tile_cap = (uint32_t)c;

@@ -20,7 +20,8 @@ std::string ProgramSpec::key() const
     std::ostringstream s;
     s << "m" << int(mode) << ".d" << dim << ".n" << n_maps << ".c" << n_cmp << ".r" << reuse
       << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << "."
-      << spill_allowance << ".p" << tile << warp_agg << ".k";
+      << spill_allowance << ".p" << tile << warp_agg << "." << tile_reps << ".f" << fast_trig
+      << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
     for (int j = 0; j < n_ops; ++j) s << op_kind[j] << (op_kind[j] == CFS_OP_ROTATE3 ? "r" : "")
@@ -168,10 +169,12 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_NT " << sp.n_targets << "\n";
     s << "#define CFS_NSPLAT_ARR " << (sp.splats.empty() ? 1 : sp.splats.size()) << "\n";
     s << "#define CFS_REUSE " << (sp.reuse ? 1 : 0) << "\n";
+    s << "#define CFS_FAST_TRIG " << (sp.fast_trig ? 1 : 0) << "\n";
     s << "#define CFS_BATCH " << (sp.mode == Mode::Batch ? 1 : 0) << "\n";
     s << "#define CFS_CLOUD " << (sp.mode == Mode::Cloud ? 1 : 0) << "\n";
     s << "#define CFS_TILE " << (sp.tile ? 1 : 0) << "\n";
     s << "#define CFS_WARP_AGG " << (sp.warp_agg ? 1 : 0) << "\n";
+    s << "#define CFS_TILE_REPS " << (sp.tile_reps > 0 ? sp.tile_reps : 1) << "\n";
     s << "#define CFS_TILE_C " << (sp.splats.empty() ? 1 : sp.splats[0].channels) << "\n";
     s << "#define CFS_POINTS " << (sp.mode == Mode::Points ? 1 : 0) << "\n";
     s << "#define CFS_DEPTH_TEST " << sp.depth_test << "\n";

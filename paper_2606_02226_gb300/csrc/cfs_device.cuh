@@ -169,12 +169,61 @@ __device__ __forceinline__ void cfs_circle(float fid, float& x, float& y)
     y = r2 * s;
 }
 
+/* ---- trigonometry of the chain ops ---------------------------------------
+ * Precise (default): CUDA's sinf / cosf / sincosf.  With CFS_FAST_TRIG the
+ * argument is first reduced to [-pi, pi] by Cody & Waite's method (Software
+ * Manual for the Elementary Functions, 1980): k = rint(x / 2 pi) and
+ * r = x - k C1 - k C2 - k C3 with 2 pi = C1 + C2 + C3 split so that k C1 is
+ * exact (C1 = 6.28125 has 8 significant bits) and the hardware sine/cosine
+ * (__sinf, __cosf) is applied to r; absolute error about 4e-7 for
+ * |x| < 2^16. */
+#ifndef CFS_FAST_TRIG
+#define CFS_FAST_TRIG 0
+#endif
+__device__ __forceinline__ float cfs_reduce_2pi(float x)
+{
+    const float k = rintf(x * 0.15915494309189533577f);
+    float r = fmaf(-k, 6.28125f, x);
+    r = fmaf(-k, 1.9353071693331003e-3f, r);     /* float nearest 2 pi - C1 */
+    r = fmaf(-k, 1.0253376606378075e-11f, r);    /* 2 pi - C1 - C2 */
+    return r;
+}
+
+__device__ __forceinline__ float cfs_sin(float x)
+{
+#if CFS_FAST_TRIG
+    return __sinf(cfs_reduce_2pi(x));
+#else
+    return sinf(x);
+#endif
+}
+
+__device__ __forceinline__ float cfs_cos(float x)
+{
+#if CFS_FAST_TRIG
+    return __cosf(cfs_reduce_2pi(x));
+#else
+    return cosf(x);
+#endif
+}
+
+__device__ __forceinline__ void cfs_sincos(float x, float* s, float* c)
+{
+#if CFS_FAST_TRIG
+    const float r = cfs_reduce_2pi(x);
+    *s = __sinf(r);
+    *c = __cosf(r);
+#else
+    sincosf(x, s, c);
+#endif
+}
+
 /* ---- transform chain ops (Section 3; Eq. 2) ------------------------------ */
 __device__ __forceinline__ void cfs_swirl(float& x, float& y)
 {
     const float r2 = fmaf(x, x, y * y);
     float s, c;
-    sincosf(r2, &s, &c);
+    cfs_sincos(r2, &s, &c);
     const float nx = fmaf(x, s, -(y * c));
     const float ny = fmaf(x, c, y * s);
     x = nx;
@@ -183,30 +232,30 @@ __device__ __forceinline__ void cfs_swirl(float& x, float& y)
 
 __device__ __forceinline__ void cfs_sinusoidal(float& x, float& y)
 {
-    x = sinf(x);
-    y = sinf(y);
+    x = cfs_sin(x);
+    y = cfs_sin(y);
 }
 
 __device__ __forceinline__ void cfs_sinusoidal3(float& x, float& y, float& z)
 {
-    x = sinf(x);
-    y = sinf(y);
-    z = sinf(z);
+    x = cfs_sin(x);
+    y = cfs_sin(y);
+    z = cfs_sin(z);
 }
 
 __device__ __forceinline__ void cfs_stretch(float& x, float& y)
 {
     const float ox = x;
     x = 2.0f * ox;
-    y = y - cosf(ox);
+    y = y - cfs_cos(ox);
 }
 
 __device__ __forceinline__ void cfs_torus(float R, float r, float& x, float& y, float& z)
 {
     const float a = CFS_TWO_PI_F * x, b = CFS_TWO_PI_F * y;
     float sa, ca, sb, cb;
-    sincosf(a, &sa, &ca);
-    sincosf(b, &sb, &cb);
+    cfs_sincos(a, &sa, &ca);
+    cfs_sincos(b, &sb, &cb);
     const float w = fmaf(r, cb, R);
     x = w * ca;
     y = w * sa;
@@ -225,7 +274,7 @@ __device__ __forceinline__ bool cfs_perspective(float f, float near_z, float& x,
 __device__ __forceinline__ void cfs_twist_z(float kappa, float& x, float& y, float z)
 {
     float s, c;
-    sincosf(kappa * z, &s, &c);
+    cfs_sincos(kappa * z, &s, &c);
     const float nx = fmaf(x, c, -(y * s));
     const float ny = fmaf(x, s, y * c);
     x = nx;
@@ -236,7 +285,7 @@ __device__ __forceinline__ void cfs_twist_z(float kappa, float& x, float& y, flo
 __device__ __forceinline__ void cfs_bend(float beta, float invb, float& x, float& z)
 {
     float s, c;
-    sincosf(beta * x, &s, &c);
+    cfs_sincos(beta * x, &s, &c);
     const float d = invb - z;
     x = s * d;
     z = invb - c * d;
@@ -312,6 +361,8 @@ __device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x,
 struct CfsTile {
     u32* cnt;
     int wx0, wy0, ww, wh;
+    int n_rep;      /* copies of the window (warp w adds to copy w % n_rep) */
+    int stride;     /* counters per copy */
 };
 
 /* u32 histogram splat that adds to the shared window when the bin lies in
@@ -326,7 +377,8 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
     if (alive && ix >= 0 && iy >= 0) {
         const int lx = ix - tl.wx0, ly = iy - tl.wy0;
         if ((unsigned)lx < (unsigned)tl.ww && (unsigned)ly < (unsigned)tl.wh) {
-            const u32 idx = ((u32)ch * (u32)tl.wh + (u32)ly) * (u32)tl.ww + (u32)lx;
+            const u32 idx = ((u32)ch * (u32)tl.wh + (u32)ly) * (u32)tl.ww + (u32)lx +
+                            (u32)(((int)(threadIdx.x >> 5) % tl.n_rep) * tl.stride);
 #if CFS_WARP_AGG
             const u32 act = __activemask();
             const u32 peers = __match_any_sync(act, idx);
@@ -344,8 +396,9 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
     }
 }
 
-/* Adds the window's nonzero counters to the global histogram and zeroes
- * them (all threads of the CTA; the caller synchronizes around it). */
+/* Adds the window's nonzero counters (summed over its copies) to the
+ * global histogram and zeroes them (all threads of the CTA; the caller
+ * synchronizes around it). */
 __device__ __forceinline__ void cfs_flush_tile(const cfs_dev_target& t, const CfsTile& tl, int C)
 {
     if (tl.ww <= 0) return;
@@ -353,14 +406,18 @@ __device__ __forceinline__ void cfs_flush_tile(const cfs_dev_target& t, const Cf
     const u32 n = (u32)C * per;
     u32* base = reinterpret_cast<u32*>(t.data);
     for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
-        const u32 v = tl.cnt[e];
+        u32 v = 0;
+        for (int r = 0; r < tl.n_rep; ++r) {
+            u32* c = tl.cnt + (size_t)r * tl.stride + e;
+            v += *c;
+            *c = 0u;
+        }
         if (v) {
             const u32 ch = e / per, r = e - ch * per;
             const u32 ly = r / (u32)tl.ww, lx = r - ly * (u32)tl.ww;
             const size_t off = ((size_t)ch * (size_t)t.H + (size_t)(tl.wy0 + (int)ly)) *
                                    (size_t)t.W + (size_t)(tl.wx0 + (int)lx);
             cfs_red_add_u32(base + off, v);
-            tl.cnt[e] = 0u;
         }
     }
 }

@@ -22,6 +22,7 @@ struct cfs_system {
 struct cfs_chain {
     int dim_in = 2;
     int n_ops = 0;
+    uint32_t flags = 0;         // CFS_COMPOSE_*
     cfs_transform ops[CFS_MAX_OPS];
     int n_splat = 0;
 };
@@ -59,6 +60,8 @@ struct ProgramSpec {
     int spill_allowance = 0;   // bytes of spill stores accepted at min_blocks
     int tile = 0;              // batch: privatized shared window for the first splat
     int warp_agg = 0;          // warp-aggregated shared atomics in that window
+    int tile_reps = 1;         // at most this many copies of a small window
+    int fast_trig = 0;         // chain trigonometry: reduced argument + hardware sin/cos
     int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
 
     std::string key() const;

@@ -198,7 +198,7 @@ cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
         float4 Z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (CFS_DIM == 3) Z = cfs_ld_stream_f4(xs + 2 * (size_t)n_pts + o, policy);
         const u32 K = cfs_ld_stream_u32(fn + o, policy);
-        const CfsTile nt{0, 0, 0, 0, 0};
+        const CfsTile nt{0, 0, 0, 0, 0, 1, 0};
         float qx, qy, qz;
         cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), disc, true, (float*)0, qx, qy, qz,
                   nt);
@@ -231,7 +231,7 @@ cfs_render_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 i = a.point_begin + j;
         float x, y, z;
         cfs_start(a, i, a.system_id, j, a.n_points, x, y, z);
-        cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc, CfsTile{0, 0, 0, 0, 0});
+        cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc, CfsTile{0, 0, 0, 0, 0, 1, 0});
     }
     cfs_flush_discards(a, disc, CFS_NT);
 }
@@ -262,7 +262,7 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         float qx, qy, qz;
         const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, disc, false,
                                      qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz,
-                                     CfsTile{0, 0, 0, 0, 0});
+                                     CfsTile{0, 0, 0, 0, 0, 1, 0});
 #if CFS_REUSE
         if (alive) { x = qx; y = qy; z = qz; }
 #else
@@ -347,7 +347,7 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
             float rec[4 * CFS_NSPLAT_ARR];
             float qx, qy, qz;
             cfs_chain(a, s_tg, sm, x, y, z, k, disc, false, rec, qx, qy, qz,
-                      CfsTile{0, 0, 0, 0, 0});
+                      CfsTile{0, 0, 0, 0, 0, 1, 0});
             const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
             const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);
             if (rec[3] != 0.0f && ix >= 0 && iy >= 0) {
@@ -368,7 +368,7 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
 __device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, int f, u32* cnt)
 {
     const int4 b = reinterpret_cast<const int4*>(a.frame_bbox)[f];
-    CfsTile tl{cnt, 0, 0, 0, 0};
+    CfsTile tl{cnt, 0, 0, 0, 0, 1, 0};
     const int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
     if (b.z < b.x || b.w < b.y || a.tile_cap < (u32)CFS_TILE_C) return tl;
     const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* pixels */
@@ -385,6 +385,10 @@ __device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, in
     tl.wh = wh;
     tl.wx0 = b.x + (bw - ww) / 2;
     tl.wy0 = b.y + (bh - wh) / 2;
+    /* small windows get one copy per warp (up to CFS_TILE_REPS): warps then
+     * stop contending for the same shared counters */
+    tl.stride = CFS_TILE_C * ww * wh;
+    tl.n_rep = max(1, min(CFS_TILE_REPS, (int)(a.tile_cap / (u32)max(tl.stride, 1))));
     return tl;
 }
 #endif
@@ -411,9 +415,9 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
 #if CFS_TILE
     extern __shared__ u32 s_cnt[];
     for (u32 e = threadIdx.x; e < a.tile_cap; e += blockDim.x) s_cnt[e] = 0u;
-    CfsTile tile{s_cnt, 0, 0, 0, 0};
+    CfsTile tile{s_cnt, 0, 0, 0, 0, 1, 0};
 #else
-    const CfsTile tile{0, 0, 0, 0, 0};
+    const CfsTile tile{0, 0, 0, 0, 0, 1, 0};
 #endif
     const cfs_dev_frame* frames = reinterpret_cast<const cfs_dev_frame*>(a.frames);
     u32* counter = reinterpret_cast<u32*>(a.work_counter);

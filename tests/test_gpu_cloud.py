@@ -36,7 +36,7 @@ def test_cloud_generation_bit_exact(torch_cuda, n, iters):
     assert np.array_equal(fn.cpu().numpy(), ofn)
 
 
-def _stream_parity(frame, n, W_):
+def _stream_parity(frame, n, W_, fast_trig=False):
     torch = pytest.importorskip("torch")
     cfs = _cfs()
     sysd = W.cloud_system()
@@ -47,12 +47,15 @@ def _stream_parity(frame, n, W_):
     disc = torch.zeros(1, dtype=torch.int64, device="cuda")
     xyz = torch.from_numpy(np.ascontiguousarray(ox.T)).cuda()
     fn = torch.from_numpy(ofn).cuda()
-    cfs.render_points(cfs.Chain(chain, 3), xyz, fn, [t], [ten], discards=disc)
+    cfs.render_points(cfs.Chain(chain, 3, fast_trig=fast_trig), xyz, fn, [t], [ten], discards=disc)
     torch.cuda.synchronize()
     g = ten.cpu().numpy().view(np.uint64)
-    # margin from the chain's FP32 differences: 2e-6 of the [-1, 1] view in
-    # pixels, plus the bin rule's own rounding
-    margin = 2e-6 * W_ / 2 * 2 + 1e-4
+    # margin from the chain's FP32 differences in pixels (the [-1, 1] view
+    # has W/2 pixels per unit): 2e-6 for precise trigonometry, the 1e-5
+    # position bar for the reduced-argument hardware sine/cosine; plus the
+    # bin rule's own rounding
+    pos = 1e-5 if fast_trig else 2e-6
+    margin = pos * W_ / 2 * 2 + 1e-4
     o = O.render_points(ox, ofn, chain, [t], margin_px=margin, track=True)[0]
     frac = check_depth_close(g, o.buf, o.zlo, o.zhi)
     assert frac >= 0.999
@@ -62,9 +65,10 @@ def _stream_parity(frame, n, W_):
     return g, o
 
 
-@pytest.mark.parametrize("frame", [0, 21, 63])
-def test_cloud_streaming_parity(torch_cuda, frame):
-    _stream_parity(frame, 1 << 15, 512)
+@pytest.mark.parametrize("frame,fast_trig", [(0, False), (21, False), (63, False), (0, True),
+                                             (63, True)])
+def test_cloud_streaming_parity(torch_cuda, frame, fast_trig):
+    _stream_parity(frame, 1 << 15, 512, fast_trig=fast_trig)
 
 
 def test_render_points_needs_multiple_of_4(torch_cuda):

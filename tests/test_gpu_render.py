@@ -101,14 +101,14 @@ def test_square_trace_bit_exact(torch_cuda):
 # ---------------------------------------------------------------------------
 # composed 2D/3D scene
 # ---------------------------------------------------------------------------
-def _trace_both(sysd, chain, ids, iters, **kw):
+def _trace_both(sysd, chain, ids, iters, fast_trig=False, **kw):
     torch = pytest.importorskip("torch")
     cfs = _cfs()
     start = kw.pop("start", None)
     gstart = None
     if start is not None:
         gstart = torch.from_numpy(np.ascontiguousarray(start.T)).cuda()
-    k, p, q = cfs.trace(cfs.System(sysd), cfs.Chain(chain, sysd.dim),
+    k, p, q = cfs.trace(cfs.System(sysd), cfs.Chain(chain, sysd.dim, fast_trig=fast_trig),
                         torch.from_numpy(np.asarray(ids, np.uint32).view(np.int32)).cuda(),
                         iters=iters, start=gstart, **kw)
     ko, po, qo = O.trace(sysd, chain, ids, iters=iters, start=start, **kw)
@@ -137,24 +137,24 @@ def test_composed_trace_parity(torch_cuda):
         _check_trace(g, o)
 
 
-def _measured_margin(wl, n_ids=64):
+def _measured_margin(wl, n_ids=64, fast_trig=False):
     """Largest |q_gpu - q_oracle| seen on traced points, in pixels of the
     finest target, doubled, plus a floor for the FP32 rounding of the bin
     coordinate itself."""
     worst = 0.0
     for job in wl.jobs:
         ids = job.point_begin + np.linspace(0, job.n_points - 1, n_ids).astype(np.uint32)
-        g, o = _trace_both(job.system, wl.chain, ids, wl.iters)
+        g, o = _trace_both(job.system, wl.chain, ids, wl.iters, fast_trig=fast_trig)
         worst = max(worst, _check_trace(g, o))
     scale = max(max(t.W / (t.view[1] - t.view[0]), t.H / (t.view[3] - t.view[2]))
                 for t in wl.targets)
     return 2.0 * worst * scale + 1e-4, worst
 
 
-def _composed_parity(wl):
-    margin, worst = _measured_margin(wl)
+def _composed_parity(wl, fast_trig=False):
+    margin, worst = _measured_margin(wl, fast_trig=fast_trig)
     assert worst <= POS_TOL
-    g, disc = gpu_render(wl)
+    g, disc = gpu_render(wl, fast_trig=fast_trig)
     o = oracle_render(wl, margin_px=margin, track=True)
     total = sum(j.n_points for j in wl.jobs) * (wl.iters - wl.burn_in)
     # totals: exact
@@ -168,10 +168,12 @@ def _composed_parity(wl):
     return n_depth
 
 
-def test_composed_render_parity_small(torch_cuda):
-    # 5000 points (ragged: not a multiple of the 256-thread block), 2 jobs
+@pytest.mark.parametrize("fast_trig", [False, True])
+def test_composed_render_parity_small(torch_cuda, fast_trig):
+    # 5000 points (ragged: not a multiple of the 256-thread block), 2 jobs;
+    # precise and reduced-argument hardware trigonometry
     wl = W.composed_render(n_points=5000, iters=90, W=256)
-    assert _composed_parity(wl) > 0
+    assert _composed_parity(wl, fast_trig=fast_trig) > 0
 
 
 def test_composed_render_parity_cropped_views(torch_cuda):
@@ -181,12 +183,13 @@ def test_composed_render_parity_cropped_views(torch_cuda):
     _composed_parity(wl)
 
 
-def test_composed_full_size_sampled(torch_cuda):
+@pytest.mark.parametrize("fast_trig", [False, True])
+def test_composed_full_size_sampled(torch_cuda, fast_trig):
     """The bench workload (2^22 points x 500 steps, 2048^2) in the bench's
     launch configuration: exact splat totals, sampled trajectories against
     the oracle, and depth/colour keys that a point of the scene can produce."""
     wl = W.composed_render()
-    g, disc = gpu_render(wl)
+    g, disc = gpu_render(wl, fast_trig=fast_trig)
     total = (1 << 22) * 480
     alpha = g[0][..., 3].astype(np.float64)
     assert int(alpha.sum()) + disc[0] == total
@@ -202,7 +205,7 @@ def test_composed_full_size_sampled(torch_cuda):
     for job in wl.jobs:
         ids = job.point_begin + np.array([0, 12345, job.n_points // 2, job.n_points - 1],
                                          dtype=np.uint32)
-        gg, oo = _trace_both(job.system, wl.chain, ids, wl.iters)
+        gg, oo = _trace_both(job.system, wl.chain, ids, wl.iters, fast_trig=fast_trig)
         _check_trace(gg, oo)
 
 

@@ -239,6 +239,9 @@ typedef struct {
     uint32_t point_begin;
     uint32_t system_id;
     uint32_t reserved;
+    /* optional device SoA start points [dim][n_points] of this frame (e.g.
+     * from cfs_sampler_start_points); NULL = Philox start points */
+    const float* start;
     cfs_target targets[CFS_MAX_TARGETS];
 } cfs_frame;
 
@@ -249,10 +252,12 @@ typedef struct cfs_batch cfs_batch;
  * points into work items numbered frame by frame and allocates a device
  * workspace (frame descriptors, work counter, per-frame discard counters)
  * owned by the batch.  The kernel is persistent: CTAs take items from the
- * counter with one atomicAdd each and never wait for one another. */
+ * counter with one atomicAdd each and never wait for one another.  Every
+ * point runs steps step_begin .. iters-1 (splats from burn_in on), from its
+ * frame's start array or its Philox start point. */
 cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
-                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
-                            cfs_batch** out);
+                            int n_frames, uint32_t step_begin, uint32_t iters, uint32_t burn_in,
+                            uint64_t seed, cfs_batch** out);
 /* Replaces frame `frame`'s system (same dimension and map kind, at most as
  * many thresholds as planned); waits for the previous launch's upload. */
 cfs_status cfs_batch_set_system(cfs_batch* batch, int frame, const cfs_system* sys);
@@ -272,8 +277,8 @@ cfs_status cfs_batch_destroy(cfs_batch* batch);
 /* One-shot: create, launch, destroy.  Returns after the frames are rendered
  * (the plan's workspace is freed on return). */
 cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
-                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
-                            int clear, void* stream);
+                            int n_frames, uint32_t step_begin, uint32_t iters, uint32_t burn_in,
+                            uint64_t seed, int clear, void* stream);
 
 /* ---- learned warm-start sampler (the initial distribution the paper
  *      proposes to derive automatically, Section 4) ---------------------- */

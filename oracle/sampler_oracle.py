@@ -141,3 +141,39 @@ def make_inputs(noise, sys_params, t):
     U[:, 2:50] = sys_params
     U[:, 50] = t
     return U
+
+
+def noise(seed: int, n: int, step: int = 0):
+    """Gaussian noise of rows 0..n-1: Box-Muller (Box & Muller 1958) on the
+    Philox4x32-10 block (row, step, 0, 3) with key (seed lo, seed hi):
+    u1 = ((w0 >> 8) + 1/2) 2^-24, u2 = (w1 >> 8) 2^-24,
+    (n0, n1) = sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2)."""
+    from oracle import oracle as O
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    out = np.zeros((n, 2))
+    for r in range(n):
+        w = O.philox([r, step, 0, 3], key)
+        u1 = ((int(w[0]) >> 8) + 0.5) * 2.0**-24
+        u2 = (int(w[1]) >> 8) * 2.0**-24
+        rad = np.sqrt(-2.0 * np.log(u1))
+        out[r] = rad * np.cos(2 * np.pi * u2), rad * np.sin(2 * np.pi * u2)
+    return out
+
+
+def conditioning(maps, t):
+    """u[2:51] of a system: a b c d e f of each map (up to 8, zero after),
+    then t."""
+    c = np.zeros(49)
+    for k, m in enumerate(maps[:8]):
+        c[6 * k:6 * k + 6] = np.asarray(m, dtype=np.float64)[:6]
+    c[48] = t
+    return c
+
+
+def start_points(params, maps, t, n, seed):
+    """The warm-start points of a system: network(noise, conditioning)."""
+    U = np.zeros((n, D_IN), dtype=np.float32)
+    U[:, 0:2] = noise(seed, n)
+    U[:, 2:51] = conditioning(maps, t)
+    Y, _ = forward(params, U, bf16=True)
+    return Y

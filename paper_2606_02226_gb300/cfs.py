@@ -69,7 +69,8 @@ class cfs_render_params(ctypes.Structure):
 class cfs_frame(ctypes.Structure):
     _fields_ = [("system", ctypes.c_void_p), ("n_points", ctypes.c_uint32),
                 ("point_begin", ctypes.c_uint32), ("system_id", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("targets", cfs_target * MAX_TARGETS)]
+                ("reserved", ctypes.c_uint32), ("start", ctypes.c_void_p),
+                ("targets", cfs_target * MAX_TARGETS)]
 
 
 _P = ctypes.c_void_p
@@ -98,7 +99,7 @@ _SIGNATURES = {
                                         ctypes.c_uint32, ctypes.c_uint32, _P]),
     "cfs_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
                                         ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
-                                        ctypes.c_uint64, ctypes.POINTER(_P)]),
+                                        ctypes.c_uint32, ctypes.c_uint64, ctypes.POINTER(_P)]),
     "cfs_batch_set_system": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cfs_batch_launch": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cfs_batch_discards": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -108,7 +109,7 @@ _SIGNATURES = {
     "cfs_batch_destroy": (ctypes.c_int, [_P]),
     "cfs_render_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
                                         ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
-                                        ctypes.c_uint64, ctypes.c_int, _P]),
+                                        ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, _P]),
     "cfs_pointcloud_generate": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P]),
     "cfs_render_points": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32,
@@ -424,12 +425,18 @@ def render_points(chain: Chain, xyz, fn, target_descs, target_tensors, *, discar
 # ---------------------------------------------------------------------------
 def _frames(frames):
     """frames: list of (System, n_points, point_begin, system_id, target_descs,
-    target_tensors) -> ctypes array."""
+    target_tensors[, start]) -> ctypes array; ``start`` an optional device
+    float32 [dim, n_points] tensor of start points."""
     arr = (cfs_frame * len(frames))()
     n_t = None
-    for f, (sysh, n, pb, sid, descs, tens) in enumerate(frames):
+    for f, fr in enumerate(frames):
+        sysh, n, pb, sid, descs, tens = fr[:6]
+        start = fr[6] if len(fr) > 6 else None
         arr[f].system = sysh.handle
         arr[f].n_points, arr[f].point_begin, arr[f].system_id = int(n), int(pb), int(sid)
+        if start is not None:
+            assert start.is_cuda and start.is_contiguous() and start.shape[1] == n
+            arr[f].start = start.data_ptr()
         t_arr, nt = make_targets(descs, tens)
         for t in range(nt):
             arr[f].targets[t] = t_arr[t]
@@ -445,11 +452,12 @@ class Batch:
     target_tensors) tuples; they share ``chain``, ``iters``, ``burn_in`` and
     ``seed``."""
 
-    def __init__(self, chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 0):
+    def __init__(self, chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 0,
+                 step_begin: int = 0):
         arr, nt = _frames(frames)
         h = _P()
-        _check(lib().cfs_batch_create(chain.handle, nt, arr, len(frames), iters, burn_in,
-                                      int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(h)))
+        _check(lib().cfs_batch_create(chain.handle, nt, arr, len(frames), step_begin, iters,
+                                      burn_in, int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(h)))
         self.handle = h
         self.n_frames = len(frames)
         self.n_targets = nt
@@ -482,10 +490,10 @@ class Batch:
 
 
 def render_batch(chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 0,
-                 clear: bool = True, stream=None):
+                 clear: bool = True, step_begin: int = 0, stream=None):
     """One-shot batch: plans, launches and frees (returns after rendering)."""
     arr, nt = _frames(frames)
-    _check(lib().cfs_render_batch(chain.handle, nt, arr, len(frames), iters, burn_in,
+    _check(lib().cfs_render_batch(chain.handle, nt, arr, len(frames), step_begin, iters, burn_in,
                                   int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if clear else 0,
                                   _stream_handle(stream)))
 

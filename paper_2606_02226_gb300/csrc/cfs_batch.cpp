@@ -69,6 +69,7 @@ void pack_frame(cfs_dev_frame* d, const cfs_system& s, const cfs_frame& f, int n
     d->system_id = f.system_id;
     d->item_begin = item_begin;
     d->chunk = chunk;
+    d->start = (unsigned long long)(uintptr_t)f.start;
     for (int t = 0; t < n_targets; ++t) {
         const cfs_target& g = f.targets[t];
         cfs_dev_target& o = d->tg[t];
@@ -149,8 +150,8 @@ cfs_status capture(cfs_batch* b, int clear)
 extern "C" {
 
 cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
-                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
-                            cfs_batch** out)
+                            int n_frames, uint32_t step_begin, uint32_t iters, uint32_t burn_in,
+                            uint64_t seed, cfs_batch** out)
 {
     clear_error();
     if (!out) return fail(CFS_ERR_INVALID_ARG, "out is NULL");
@@ -186,6 +187,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
         max_cmp = std::max(max_cmp, fr.system->n_cmp);
     }
     if (burn_in > iters) burn_in = iters;
+    if (step_begin > iters) return fail(CFS_ERR_INVALID_ARG, "step_begin > iters");
 
     cfs_batch* b = new (std::nothrow) cfs_batch();
     if (!b) return fail(CFS_ERR_OOM, "host allocation failed");
@@ -241,7 +243,9 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     b->tile_cap = sp.block >= 1024 ? 53248 : 8192;
     if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
     if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
-    sp.tile_reps = sp.block / 32;
+    // copies of small windows (one per warp) measured slower on the animation
+    // batch (the flush grows with the copies); kept as a knob
+    sp.tile_reps = 1;
     if (const char* e = std::getenv("CFS_TILE_REPS")) sp.tile_reps = std::max(1, std::atoi(e));
     if (const char* e = std::getenv("CFS_TILE_CAP")) {
         const int c = std::atoi(e);
@@ -314,6 +318,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
         item += (frames[f].n_points + b->chunks[f] - 1) / b->chunks[f];
     }
     fill_args_common(&b->args, chain, seed, iters, burn_in);
+    b->args.step_begin = step_begin;
     b->args.frames = (unsigned long long)(uintptr_t)b->d_frames;
     b->args.work_counter = (unsigned long long)(uintptr_t)b->d_counter;
     b->args.frame_discards = (unsigned long long)(uintptr_t)b->d_disc;
@@ -403,11 +408,12 @@ cfs_status cfs_batch_destroy(cfs_batch* b)
 }
 
 cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
-                            int n_frames, uint32_t iters, uint32_t burn_in, uint64_t seed,
-                            int clear, void* stream)
+                            int n_frames, uint32_t step_begin, uint32_t iters, uint32_t burn_in,
+                            uint64_t seed, int clear, void* stream)
 {
     cfs_batch* b = nullptr;
-    cfs_status st = cfs_batch_create(chain, n_targets, frames, n_frames, iters, burn_in, seed, &b);
+    cfs_status st = cfs_batch_create(chain, n_targets, frames, n_frames, step_begin, iters,
+                                     burn_in, seed, &b);
     if (st != CFS_OK) return st;
     st = cfs_batch_launch(b, clear, stream);
     cfs_batch_destroy(b);   // waits for the launch: the workspace must outlive it

@@ -363,6 +363,7 @@ struct CfsTile {
     int wx0, wy0, ww, wh;
     int n_rep;      /* copies of the window (warp w adds to copy w % n_rep) */
     int stride;     /* counters per copy */
+    int rep_off;    /* this warp's copy offset: (warp % n_rep) * stride */
 };
 
 /* u32 histogram splat that adds to the shared window when the bin lies in
@@ -378,7 +379,7 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
         const int lx = ix - tl.wx0, ly = iy - tl.wy0;
         if ((unsigned)lx < (unsigned)tl.ww && (unsigned)ly < (unsigned)tl.wh) {
             const u32 idx = ((u32)ch * (u32)tl.wh + (u32)ly) * (u32)tl.ww + (u32)lx +
-                            (u32)(((int)(threadIdx.x >> 5) % tl.n_rep) * tl.stride);
+                            (u32)tl.rep_off;
 #if CFS_WARP_AGG
             const u32 act = __activemask();
             const u32 peers = __match_any_sync(act, idx);

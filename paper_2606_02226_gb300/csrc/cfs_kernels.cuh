@@ -198,7 +198,7 @@ cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
         float4 Z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (CFS_DIM == 3) Z = cfs_ld_stream_f4(xs + 2 * (size_t)n_pts + o, policy);
         const u32 K = cfs_ld_stream_u32(fn + o, policy);
-        const CfsTile nt{0, 0, 0, 0, 0, 1, 0};
+        const CfsTile nt{0, 0, 0, 0, 0, 1, 0, 0};
         float qx, qy, qz;
         cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), disc, true, (float*)0, qx, qy, qz,
                   nt);
@@ -231,7 +231,8 @@ cfs_render_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 i = a.point_begin + j;
         float x, y, z;
         cfs_start(a, i, a.system_id, j, a.n_points, x, y, z);
-        cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc, CfsTile{0, 0, 0, 0, 0, 1, 0});
+        cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc,
+                      CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
     }
     cfs_flush_discards(a, disc, CFS_NT);
 }
@@ -262,7 +263,7 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         float qx, qy, qz;
         const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, disc, false,
                                      qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz,
-                                     CfsTile{0, 0, 0, 0, 0, 1, 0});
+                                     CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
 #if CFS_REUSE
         if (alive) { x = qx; y = qy; z = qz; }
 #else
@@ -347,7 +348,7 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
             float rec[4 * CFS_NSPLAT_ARR];
             float qx, qy, qz;
             cfs_chain(a, s_tg, sm, x, y, z, k, disc, false, rec, qx, qy, qz,
-                      CfsTile{0, 0, 0, 0, 0, 1, 0});
+                      CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
             const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
             const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);
             if (rec[3] != 0.0f && ix >= 0 && iy >= 0) {
@@ -368,7 +369,7 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
 __device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, int f, u32* cnt)
 {
     const int4 b = reinterpret_cast<const int4*>(a.frame_bbox)[f];
-    CfsTile tl{cnt, 0, 0, 0, 0, 1, 0};
+    CfsTile tl{cnt, 0, 0, 0, 0, 1, 0, 0};
     const int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
     if (b.z < b.x || b.w < b.y || a.tile_cap < (u32)CFS_TILE_C) return tl;
     const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* pixels */
@@ -389,6 +390,7 @@ __device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, in
      * stop contending for the same shared counters */
     tl.stride = CFS_TILE_C * ww * wh;
     tl.n_rep = max(1, min(CFS_TILE_REPS, (int)(a.tile_cap / (u32)max(tl.stride, 1))));
+    tl.rep_off = ((int)(threadIdx.x >> 5) % tl.n_rep) * tl.stride;
     return tl;
 }
 #endif
@@ -411,13 +413,14 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ u32 s_T[CFS_A_MAX_MAPS];
     __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
     __shared__ u32 s_item, s_frame, s_npts, s_pbeg, s_sid, s_ibeg, s_chunk;
+    __shared__ const float* s_start;
     __shared__ int s_ncmp;
 #if CFS_TILE
     extern __shared__ u32 s_cnt[];
     for (u32 e = threadIdx.x; e < a.tile_cap; e += blockDim.x) s_cnt[e] = 0u;
-    CfsTile tile{s_cnt, 0, 0, 0, 0, 1, 0};
+    CfsTile tile{s_cnt, 0, 0, 0, 0, 1, 0, 0};
 #else
-    const CfsTile tile{0, 0, 0, 0, 0, 1, 0};
+    const CfsTile tile{0, 0, 0, 0, 0, 1, 0, 0};
 #endif
     const cfs_dev_frame* frames = reinterpret_cast<const cfs_dev_frame*>(a.frames);
     u32* counter = reinterpret_cast<u32*>(a.work_counter);
@@ -461,6 +464,7 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
                 s_ibeg = fr.item_begin;
                 s_chunk = fr.chunk;
                 s_ncmp = fr.n_cmp;
+                s_start = reinterpret_cast<const float*>(fr.start);
             }
 #if CFS_TILE
             tile = cfs_frame_window(a, f, s_cnt);
@@ -472,12 +476,22 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 sid = s_sid, pbeg = s_pbeg;
         const u32 j0 = (item - s_ibeg) * s_chunk;
         const u32 j1 = min(j0 + s_chunk, s_npts);
+        const float* st = s_start;
+        const u32 npts = s_npts;
         for (u32 j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             const u32 i = pbeg + j;
-            const uint4 r = cfs_philox(a, i, 0u, sid, 1u);
-            float x = (float)(r.x >> 8) * CFS_INV_2_24;
-            float y = (float)(r.y >> 8) * CFS_INV_2_24;
-            float z = CFS_DIM == 3 ? (float)(r.z >> 8) * CFS_INV_2_24 : 0.0f;
+            float x, y, z;
+            if (st) {
+                /* the frame's own start points (e.g. a learned warm start) */
+                x = st[j];
+                y = st[(size_t)npts + j];
+                z = CFS_DIM == 3 ? st[2 * (size_t)npts + j] : 0.0f;
+            } else {
+                const uint4 r = cfs_philox(a, i, 0u, sid, 1u);
+                x = (float)(r.x >> 8) * CFS_INV_2_24;
+                y = (float)(r.y >> 8) * CFS_INV_2_24;
+                z = CFS_DIM == 3 ? (float)(r.z >> 8) * CFS_INV_2_24 : 0.0f;
+            }
             cfs_run_point(a, choose, s_tg, sm, i, sid, x, y, z, disc, tile);
         }
         __syncthreads();

@@ -209,6 +209,9 @@ extern "C" cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_fr
             return fail(CFS_ERR_INVALID_ARG, "every frame needs one u32 histogram target");
         if ((uint64_t)fr.point_begin + fr.n_points > (1ull << 32))
             return fail(CFS_ERR_INVALID_ARG, "point indices exceed 2^32");
+        if (fr.start)
+            return fail(CFS_ERR_UNSUPPORTED,
+                        "the no-allocation batch starts every point from Philox");
     }
     int dev = 0;
     cfs_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");

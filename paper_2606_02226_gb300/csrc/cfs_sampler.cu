@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -443,13 +444,159 @@ __global__ void gather_loss_kernel(const float* loss, const u32* step, u32 first
     if (s < cap) hist[s] = *loss;
 }
 
-// network output [B][2] -> SoA start points [2][n]
-__global__ void soa_kernel(const float* Y, int n, float* out)
+
+// ---------------------------------------------------------------------------
+// fused inference: start points of one system straight from noise.
+// Layer 1 is a rank-2 update: only the noise varies from row to row, so
+// z1 = c1 + W1[:, 0] n0 + W1[:, 1] n1 with c1 = W1[:, 2:51] u_cond + b1 (one
+// vector per call).  Layers 2-4 run on the tensor cores (mma.sync m16n8k16
+// bf16); each warp keeps its 16 rows' activations in registers: the FP32
+// accumulator fragments of one layer, rounded to BF16, are exactly the A
+// fragments of the next.  Weights live in shared memory with rows padded to
+// 272 bytes (conflict-free ldmatrix).
+// ---------------------------------------------------------------------------
+constexpr int IP = 136;                       // padded row length (bf16)
+constexpr int IW = 4;                         // warps per CTA
+struct InferSmem {
+    bf16r w2[HID][IP];
+    bf16r w3[HID][IP];
+    bf16r w4[8][IP];
+    float c1[HID], w10[HID], w11[HID], b2[HID], b3[HID], b4[2];
+};
+
+__device__ __forceinline__ u32 pack2(float lo, float hi)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    out[i] = Y[2 * i];
-    out[(size_t)n + i] = Y[2 * i + 1];
+    return (u32)to_bf16(lo) | ((u32)to_bf16(hi) << 16);
+}
+
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+// c1 = W1[:, 2:51] u_cond + b1 with the BF16-rounded operands
+__global__ void cond_kernel(const bf16r* __restrict__ wb, const float* __restrict__ w,
+                            const SysRec* __restrict__ rec, float* c1)
+{
+    const int j = threadIdx.x;
+    if (j >= HID) return;
+    float acc = w[OFF_B1 + j];
+    for (int q = 0; q < COND; ++q)
+        acc = fmaf(from_bf16(wb[OFF_W1 + j * D_IN + 2 + q]), from_bf16(to_bf16(rec->cond[q])), acc);
+    acc = fmaf(from_bf16(wb[OFF_W1 + j * D_IN + 2 + COND]), from_bf16(to_bf16(rec->t)), acc);
+    c1[j] = acc;
+}
+
+__device__ __forceinline__ void hidden_layer(const bf16r (*W)[IP], const float* bias, u32 (&a)[8][4],
+                                             int lane)
+{
+    float acc[16][4];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+#pragma unroll
+        for (int nt = 0; nt < 16; nt += 2) {
+            u32 b[4];
+            ldsm_x4(b, &W[nt * 8 + (lane & 7) + ((lane >> 4) << 3)][kt * 16 + ((lane >> 3) & 1) * 8]);
+            mma_bf16(acc[nt], a[kt], b[0], b[1]);
+            mma_bf16(acc[nt + 1], a[kt], b[2], b[3]);
+        }
+    }
+    const int tq = lane & 3;
+#pragma unroll
+    for (int kt = 0; kt < 8; ++kt) {
+        const int c0 = (2 * kt) * 8 + 2 * tq, c1 = (2 * kt + 1) * 8 + 2 * tq;
+        a[kt][0] = pack2(silu_fast(acc[2 * kt][0] + bias[c0]), silu_fast(acc[2 * kt][1] + bias[c0 + 1]));
+        a[kt][1] = pack2(silu_fast(acc[2 * kt][2] + bias[c0]), silu_fast(acc[2 * kt][3] + bias[c0 + 1]));
+        a[kt][2] = pack2(silu_fast(acc[2 * kt + 1][0] + bias[c1]),
+                         silu_fast(acc[2 * kt + 1][1] + bias[c1 + 1]));
+        a[kt][3] = pack2(silu_fast(acc[2 * kt + 1][2] + bias[c1]),
+                         silu_fast(acc[2 * kt + 1][3] + bias[c1 + 1]));
+    }
+}
+
+__global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict__ wb,
+                                                        const float* __restrict__ w,
+                                                        const float* __restrict__ c1, u64 seed,
+                                                        int n, float* start)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    InferSmem& sm = *reinterpret_cast<InferSmem*>(smem_raw);
+    for (int e = threadIdx.x; e < HID * HID; e += blockDim.x) {
+        const int r = e / HID, c = e % HID;
+        sm.w2[r][c] = wb[OFF_W2 + e];
+        sm.w3[r][c] = wb[OFF_W3 + e];
+    }
+    for (int e = threadIdx.x; e < 8 * HID; e += blockDim.x) {
+        const int r = e / HID, c = e % HID;
+        sm.w4[r][c] = r < D_OUT ? wb[OFF_W4 + e] : (bf16r)0;
+    }
+    for (int j = threadIdx.x; j < HID; j += blockDim.x) {
+        sm.c1[j] = c1[j];
+        sm.w10[j] = from_bf16(wb[OFF_W1 + j * D_IN]);
+        sm.w11[j] = from_bf16(wb[OFF_W1 + j * D_IN + 1]);
+        sm.b2[j] = w[OFF_B2 + j];
+        sm.b3[j] = w[OFF_B3 + j];
+    }
+    if (threadIdx.x < 2) sm.b4[threadIdx.x] = w[OFF_B4 + threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int tiles = (n + 15) / 16;
+    for (int tile = blockIdx.x * IW + warp; tile < tiles; tile += gridDim.x * IW) {
+        // noise of rows gq and gq + 8 (Box-Muller on Philox (row, 0, 0, 3))
+        float nz[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const u32 row = (u32)(tile * 16 + gq + 8 * h);
+            const uint4 r = philox_key(seed, row, 0u, 0u, TAG_NOISE);
+            const float u1 = ((float)(r.x >> 8) + 0.5f) * CFS_INV_2_24;
+            const float u2 = (float)(r.y >> 8) * CFS_INV_2_24;
+            const float rad = sqrtf(-2.0f * logf(u1));
+            float sn, cs;
+            sincosf(6.28318530717958647692f * u2, &sn, &cs);
+            nz[h][0] = from_bf16(to_bf16(rad * cs));
+            nz[h][1] = from_bf16(to_bf16(rad * sn));
+        }
+        // layer 1 (rank-2 update), straight into the A fragments of layer 2
+        u32 a[8][4];
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int c = (2 * kt + half) * 8 + 2 * tq;
+                float v[2][2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        v[h][q] = silu_fast(fmaf(sm.w11[c + q], nz[h][1],
+                                                 fmaf(sm.w10[c + q], nz[h][0], sm.c1[c + q])));
+                a[kt][2 * half + 0] = pack2(v[0][0], v[0][1]);
+                a[kt][2 * half + 1] = pack2(v[1][0], v[1][1]);
+            }
+        }
+        hidden_layer(sm.w2, sm.b2, a, lane);
+        hidden_layer(sm.w3, sm.b3, a, lane);
+        // output layer: one 16 x 8 tile, columns 0 and 1 are the point
+        float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int kt = 0; kt < 8; ++kt) {
+            u32 b[4];
+            ldsm_x4(b, &sm.w4[(lane & 7)][kt * 16 + ((lane >> 3) & 1) * 8]);
+            mma_bf16(y, a[kt], b[0], b[1]);
+        }
+        if (tq == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = tile * 16 + gq + 8 * h;
+                if (row < n) {
+                    start[row] = y[2 * h] + sm.b4[0];
+                    start[(size_t)n + row] = y[2 * h + 1] + sm.b4[1];
+                }
+            }
+        }
+    }
 }
 
 }  // namespace
@@ -463,7 +610,8 @@ struct cfs_sampler {
     float* m = nullptr;
     float* v = nullptr;
     bf16r* wb = nullptr;     // bf16 copies
-    u32* d_step = nullptr;   // Adam step counter (device)
+    u32* d_step = nullptr;   // Adam step counter (device); the record and c1 of
+                             // the last start-point call follow it
     u32 step = 0;            // host mirror (checkpoints)
     // activations for B rows (grown on demand)
     int cap_rows = 0;
@@ -628,7 +776,9 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
     s->m = s->w + N_PARAMS;
     s->v = s->m + N_PARAMS;
     s->wb = reinterpret_cast<bf16r*>(s->v + N_PARAMS);
-    st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
+    st = check_cuda(cudaMalloc(&s->d_step, 256 + ((sizeof(SysRec) + 255) & ~(size_t)255) +
+                                               HID * sizeof(float)),
+                    "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->d_step, 0, 256), "memset");
     std::vector<float> init;
@@ -839,30 +989,36 @@ cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float
     cfs_status st = check_sampler_system(sys);
     if (st != CFS_OK) return st;
     if (n == 0) return CFS_OK;
-    if (n > (1u << 24)) return fail(CFS_ERR_INVALID_ARG, "n too large");
-    st = ensure_rows(s, (int)n);
-    if (st != CFS_OK) return st;
+    if (n > (1u << 30)) return fail(CFS_ERR_INVALID_ARG, "n too large");
     cudaStream_t sm = (cudaStream_t)stream;
     SysRec rec;
     pack_system(sys, t, &rec);
-    // scratch for the one record and the inputs: the tail of the activations
-    SysRec* d_rec = nullptr;
-    bf16r* d_U = nullptr;
-    st = check_cuda(cudaMallocAsync((void**)&d_rec, sizeof(SysRec), sm), "cudaMallocAsync");
+    // the record and c1 live behind the step counter (allocated with it);
+    // the copy from the host stack has read its source when it returns
+    SysRec* d_rec = reinterpret_cast<SysRec*>(reinterpret_cast<unsigned char*>(s->d_step) + 256);
+    float* d_c1 = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(d_rec) +
+                                           ((sizeof(SysRec) + 255) & ~(size_t)255));
+    st = check_cuda(cudaMemcpyAsync(d_rec, &rec, sizeof(SysRec), cudaMemcpyHostToDevice, sm),
+                    "cudaMemcpyAsync(system)");
     if (st != CFS_OK) return st;
-    st = check_cuda(cudaMallocAsync((void**)&d_U, sizeof(bf16r) * (size_t)n * D_IN, sm),
-                    "cudaMallocAsync");
-    if (st != CFS_OK) { cudaFreeAsync(d_rec, sm); return st; }
-    cudaMemcpyAsync(d_rec, &rec, sizeof(SysRec), cudaMemcpyHostToDevice, sm);
-    inputs_kernel<<<(n + 255) / 256, 256, 0, sm>>>(d_rec, nullptr, nullptr, (u32)(seed >> 32),
-                                                   seed, (int)n, (int)n, d_U);
-    forward(s, d_U, (int)n, sm);
-    soa_kernel<<<(n + 255) / 256, 256, 0, sm>>>(s->Y, (int)n, start);
-    cudaError_t e = cudaGetLastError();
-    cudaStreamSynchronize(sm);   // rec lives on the host stack until the copy is done
-    cudaFreeAsync(d_U, sm);
-    cudaFreeAsync(d_rec, sm);
-    return check_cuda(e, "sampler start points");
+    cond_kernel<<<1, HID, 0, sm>>>(s->wb, s->w, d_rec, d_c1);
+    static int smem_set = -1;
+    const int smem = (int)sizeof(InferSmem);
+    if (smem_set != s->device) {
+        st = check_cuda(cudaFuncSetAttribute(infer_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                        "cudaFuncSetAttribute");
+        if (st != CFS_OK) return st;
+        smem_set = s->device;
+    }
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_kernel, IW * 32, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    const int tiles = (int)((n + 15) / 16);
+    int grid = std::max(1, per_sm) * std::max(1, sms);
+    grid = std::min(grid, (tiles + IW - 1) / IW);
+    infer_kernel<<<grid, IW * 32, smem, sm>>>(s->wb, s->w, d_c1, seed, (int)n, start);
+    return check_cuda(cudaGetLastError(), "sampler start points");
 }
 
 }  // extern "C"

@@ -157,12 +157,17 @@ def _composed_parity(wl, fast_trig=False):
     g, disc = gpu_render(wl, fast_trig=fast_trig)
     o = oracle_render(wl, margin_px=margin, track=True)
     total = sum(j.n_points for j in wl.jobs) * (wl.iters - wl.burn_in)
+    # histogram L1 bar: 1e-5 of the total with precise trigonometry; the
+    # hardware sine/cosine moves positions by ~1e-6, which carries ~1e-4 of
+    # the splats across bin edges at this resolution (every one of them
+    # within the near-edge slack checked per bin below)
+    rel_l1 = 1e-3 if fast_trig else 1e-5
     # totals: exact
     assert int(round(float(g[0][..., 3].sum(dtype=np.float64)))) + disc[0] == total
     assert o[0].n_splat + o[0].n_discard == total
     n_depth = int((g[1] != EMPTY).sum())
     assert disc[1] <= o[1].n_discard + o[1].n_amb and disc[1] >= o[1].n_discard - o[1].n_amb
-    check_rgba_close(g[0], o[0].buf, o[0].amb, total)
+    check_rgba_close(g[0], o[0].buf, o[0].amb, total, rel_l1=rel_l1)
     frac = check_depth_close(g[1], o[1].buf, o[1].zlo, o[1].zhi)
     assert frac >= 0.999
     return n_depth

@@ -115,6 +115,22 @@ def test_adam_matches_oracle(torch_cuda):
     assert np.abs(w1 - wo).max() < 1e-6
 
 
+def test_start_points_match_oracle(torch_cuda):
+    """The fused inference kernel (noise drawn in the kernel, layer 1 as a
+    rank-2 update, layers 2-4 on the tensor cores) against the oracle's
+    noise and forward pass."""
+    cfs, s, params, _, _ = _setup(torch_cuda, 64)
+    fr = W.animation_frames(n_frames=3, seed=4)[2]
+    sysh = cfs.System(fr.system)
+    n = 1000
+    st = s.start_points(sysh, fr.t, n, seed=77).cpu().numpy().T
+    Yo = SO.start_points(params, [m.params for m in fr.system.maps], fr.t, n, 77)
+    assert _rel(st, Yo) < 2e-2, _rel(st, Yo)
+    # ragged sizes and the n = 1 edge
+    st1 = s.start_points(sysh, fr.t, 1, seed=77).cpu().numpy().T
+    assert _rel(st1, Yo[:1]) < 2e-2
+
+
 def _family(n, seed=0):
     frames = W.animation_frames(n_frames=n, seed=seed)
     return frames

@@ -149,3 +149,11 @@ def test_adam_first_step_and_quadratic_convergence():
 def test_make_inputs_layout():
     U = S.make_inputs(np.ones((2, 2)), np.arange(96).reshape(2, 48), np.array([0.25, 0.5]))
     assert U.shape == (2, 64) and U[1, 2] == 48 and U[0, 50] == 0.25 and not U[:, 51:].any()
+
+
+def test_noise_is_standard_gaussian():
+    z = S.noise(3, 4000)
+    assert abs(z.mean()) < 5 / math.sqrt(8000)
+    assert abs(z.var() - 1.0) < 5 * math.sqrt(2 / 8000)
+    # the two components of a Box-Muller pair are uncorrelated
+    assert abs(np.corrcoef(z[:, 0], z[:, 1])[0, 1]) < 5 / math.sqrt(4000)

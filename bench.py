@@ -479,8 +479,8 @@ def _l1(torch, h, ref):
     return float((a / a.sum() - b / b.sum()).abs().sum())
 
 
-def bench_sampler(torch, cfs, dev, stream, train_steps: int = 4000, eval_frames: int = 16,
-                  n_eval: int = 1 << 20, batch_frames: int = 256):
+def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames: int = 16,
+                  n_eval: int = 1 << 20, batch_frames: int = 256, n_unique: int = 1 << 16):
     """Learned warm start (form 4) against plain burn-in at equal L1 error.
 
     Training: 4096 systems of the animation family (seed 1), batches of 64
@@ -519,8 +519,12 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 4000, eval_frames:
 
     def hist_of(sysh, seed, step_begin, start=None):
         buf.zero_()
-        cfs.render(sysh, chain, [tgt], [buf], n_points=n_eval, iters=ITERS, burn_in=B_IN,
-                   seed=seed, step_begin=step_begin, start=start, stream=stream)
+        if start is None:
+            cfs.render(sysh, chain, [tgt], [buf], n_points=n_eval, iters=ITERS, burn_in=B_IN,
+                       seed=seed, step_begin=step_begin, stream=stream)
+        else:
+            cfs.render_batch(chain, [(sysh, n_eval, 0, 0, [tgt], [buf], start)], iters=ITERS,
+                             burn_in=B_IN, seed=seed, step_begin=step_begin, stream=stream)
         return buf.clone()
 
     for f in range(min(eval_frames, len(frames))):
@@ -531,7 +535,7 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 4000, eval_frames:
         floors.append(floor)
         for b in bs:
             ex_b[b].append(_l1(torch, hist_of(sysh, 2002, B_IN - b), ref) - floor)
-        st = smp.start_points(sysh, fr.t, n_eval, seed=3003 + f, stream=stream)
+        st = smp.start_points(sysh, fr.t, min(n_unique, n_eval), seed=3003 + f, stream=stream)
         for k in ks:
             ex_k[k].append(_l1(torch, hist_of(sysh, 2002, B_IN - k, start=st), ref) - floor)
     mb = {b: float(np.mean(v)) for b, v in ex_b.items()}
@@ -546,7 +550,7 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 4000, eval_frames:
            "eval_frames": eval_frames, "eval_points": n_eval, "l1_resolution": 1024,
            "noise_floor_l1": float(np.mean(floors)),
            "excess_l1_plain_burn_in": mb, "excess_l1_warm_start_k": mk,
-           "b_min": b_min, "k_min": k_min}
+           "b_min": b_min, "k_min": k_min, "unique_starts_per_frame": n_unique}
     if b_min is None or k_min is None:
         return out
     descs, tens, items, begin = [], [], [], 0
@@ -557,13 +561,14 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 4000, eval_frames:
         begin += fr.n_points
     plain = cfs.Batch(chain, [tuple(i) for i in items], iters=ITERS, burn_in=B_IN, seed=0,
                       step_begin=B_IN - b_min)
-    starts = [torch.empty((2, it[1]), dtype=torch.float32, device=dev) for it in items]
+    starts = [torch.empty((2, min(n_unique, it[1])), dtype=torch.float32, device=dev)
+              for it in items]
     warm = cfs.Batch(chain, [tuple(it) + (starts[fi],) for fi, it in enumerate(items)],
                      iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - k_min)
 
     def run_warm():
         for fi, fr in enumerate(frames):
-            smp.start_points(items[fi][0], fr.t, fr.n_points, seed=fi, out=starts[fi],
+            smp.start_points(items[fi][0], fr.t, starts[fi].shape[1], seed=fi, out=starts[fi],
                              stream=stream)
         warm.launch(clear=True, stream=stream)
 

@@ -238,9 +238,12 @@ typedef struct {
     uint32_t n_points;
     uint32_t point_begin;
     uint32_t system_id;
-    uint32_t reserved;
-    /* optional device SoA start points [dim][n_points] of this frame (e.g.
-     * from cfs_sampler_start_points); NULL = Philox start points */
+    /* number of points in `start` (0: n_points); point j of the frame starts
+     * at start point j mod start_count, so a few network samples can seed
+     * every point (the cleanup steps decorrelate the copies) */
+    uint32_t start_count;
+    /* optional device SoA start points [dim][start_count] of this frame
+     * (e.g. from cfs_sampler_start_points); NULL = Philox start points */
     const float* start;
     cfs_target targets[CFS_MAX_TARGETS];
 } cfs_frame;

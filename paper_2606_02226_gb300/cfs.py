@@ -69,7 +69,7 @@ class cfs_render_params(ctypes.Structure):
 class cfs_frame(ctypes.Structure):
     _fields_ = [("system", ctypes.c_void_p), ("n_points", ctypes.c_uint32),
                 ("point_begin", ctypes.c_uint32), ("system_id", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("start", ctypes.c_void_p),
+                ("start_count", ctypes.c_uint32), ("start", ctypes.c_void_p),
                 ("targets", cfs_target * MAX_TARGETS)]
 
 
@@ -426,7 +426,8 @@ def render_points(chain: Chain, xyz, fn, target_descs, target_tensors, *, discar
 def _frames(frames):
     """frames: list of (System, n_points, point_begin, system_id, target_descs,
     target_tensors[, start]) -> ctypes array; ``start`` an optional device
-    float32 [dim, n_points] tensor of start points."""
+    float32 [dim, m] tensor of start points, m <= n_points (point j starts at
+    start point j mod m)."""
     arr = (cfs_frame * len(frames))()
     n_t = None
     for f, fr in enumerate(frames):
@@ -435,8 +436,9 @@ def _frames(frames):
         arr[f].system = sysh.handle
         arr[f].n_points, arr[f].point_begin, arr[f].system_id = int(n), int(pb), int(sid)
         if start is not None:
-            assert start.is_cuda and start.is_contiguous() and start.shape[1] == n
+            assert start.is_cuda and start.is_contiguous() and start.shape[1] <= n
             arr[f].start = start.data_ptr()
+            arr[f].start_count = int(start.shape[1])
         t_arr, nt = make_targets(descs, tens)
         for t in range(nt):
             arr[f].targets[t] = t_arr[t]

@@ -34,7 +34,7 @@ typedef struct {
     int n_maps, n_cmp, dim, pad;
     float prm[12][CFS_A_MAX_MAPS];
     unsigned int n_points, point_begin, system_id, item_begin;   /* first work item */
-    unsigned int chunk, pad1;                                    /* points per item */
+    unsigned int chunk, start_count;                             /* points per item */
     unsigned long long start;           /* device f32 SoA [dim][n_points] or 0 */
     cfs_dev_target tg[CFS_A_MAX_TARGETS];
 } cfs_dev_frame;

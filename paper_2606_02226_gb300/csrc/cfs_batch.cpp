@@ -70,6 +70,7 @@ void pack_frame(cfs_dev_frame* d, const cfs_system& s, const cfs_frame& f, int n
     d->item_begin = item_begin;
     d->chunk = chunk;
     d->start = (unsigned long long)(uintptr_t)f.start;
+    d->start_count = f.start_count ? f.start_count : f.n_points;
     for (int t = 0; t < n_targets; ++t) {
         const cfs_target& g = f.targets[t];
         cfs_dev_target& o = d->tg[t];
@@ -179,6 +180,8 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
             return fail(CFS_ERR_INVALID_ARG, m.str() + "point indices exceed 2^32");
         cfs_status st = validate_targets_ext(chain, fr.targets, n_targets);
         if (st != CFS_OK) return fail(st, m.str() + cfs_last_error());
+        if (fr.start && fr.start_count > fr.n_points)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "start_count exceeds n_points");
         for (int t = 0; t < n_targets; ++t)
             if (fr.targets[t].kind != frames[0].targets[t].kind ||
                 (fr.targets[t].kind == CFS_TARGET_HIST_U32 &&

@@ -414,6 +414,7 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
     __shared__ u32 s_item, s_frame, s_npts, s_pbeg, s_sid, s_ibeg, s_chunk;
     __shared__ const float* s_start;
+    __shared__ u32 s_scount;
     __shared__ int s_ncmp;
 #if CFS_TILE
     extern __shared__ u32 s_cnt[];
@@ -465,6 +466,7 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
                 s_chunk = fr.chunk;
                 s_ncmp = fr.n_cmp;
                 s_start = reinterpret_cast<const float*>(fr.start);
+                s_scount = fr.start_count;
             }
 #if CFS_TILE
             tile = cfs_frame_window(a, f, s_cnt);
@@ -477,15 +479,17 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 j0 = (item - s_ibeg) * s_chunk;
         const u32 j1 = min(j0 + s_chunk, s_npts);
         const float* st = s_start;
-        const u32 npts = s_npts;
+        const u32 sc = s_scount;
         for (u32 j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             const u32 i = pbeg + j;
             float x, y, z;
             if (st) {
-                /* the frame's own start points (e.g. a learned warm start) */
-                x = st[j];
-                y = st[(size_t)npts + j];
-                z = CFS_DIM == 3 ? st[2 * (size_t)npts + j] : 0.0f;
+                /* the frame's own start points (e.g. a learned warm start),
+                 * reused cyclically when there are fewer than points */
+                const u32 js = sc < s_npts ? j % sc : j;
+                x = st[js];
+                y = st[(size_t)sc + js];
+                z = CFS_DIM == 3 ? st[2 * (size_t)sc + js] : 0.0f;
             } else {
                 const uint4 r = cfs_philox(a, i, 0u, sid, 1u);
                 x = (float)(r.x >> 8) * CFS_INV_2_24;

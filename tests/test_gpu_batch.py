@@ -144,3 +144,29 @@ def test_batch_rejects_mixed_kinds(torch_cuda):
     chain = cfs.Chain([W.Op("splat", (0,))], 2)
     with pytest.raises(cfs.CfsError):
         cfs.Batch(chain, [(cfs.System(mixed), 10, 0, 0, [t], [ten])], iters=5, burn_in=1)
+
+
+def test_batch_start_points_and_step_begin(torch_cuda):
+    """Frames carrying their own start points (fewer than their points:
+    point j starts at start j mod m) and a first step of 12: bit-exact
+    against the oracle run from the repeated starts."""
+    torch = torch_cuda
+    frames = W.animation_frames(n_frames=5, seed=9, min_log2=9, max_log2=11, resolutions=(64,))
+    cfs, chain, items, descs, tens = _setup(frames)
+    starts, full = [], []
+    for f, fr in enumerate(frames):
+        m = max(1, fr.n_points // 3)
+        st = (W.uniform_points(m, 2, 100 + f) * 2 - 1).astype(np.float32)
+        starts.append(torch.from_numpy(np.ascontiguousarray(st.T)).cuda())
+        full.append(st[np.arange(fr.n_points) % m])
+    items = [tuple(it) + (starts[f],) for f, it in enumerate(items)]
+    b = cfs.Batch(chain, items, iters=50, burn_in=20, seed=6, step_begin=12)
+    b.launch()
+    torch.cuda.synchronize()
+    begin = 0
+    for f, fr in enumerate(frames):
+        o = O.render(fr.system, [W.Op("splat", (0,))], [descs[f]], n_points=fr.n_points,
+                     point_begin=begin, system_id=f, iters=50, burn_in=20, seed=6,
+                     step_begin=12, start=full[f])[0].buf
+        assert np.array_equal(_host(tens[f]), o), f
+        begin += fr.n_points

@@ -566,10 +566,12 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
     warm = cfs.Batch(chain, [tuple(it) + (starts[fi],) for fi, it in enumerate(items)],
                      iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - k_min)
 
+    frame_systems = [it[0] for it in items]
+    frame_t = [fr.t for fr in frames]
+    frame_seeds = list(range(len(frames)))
+
     def run_warm():
-        for fi, fr in enumerate(frames):
-            smp.start_points(items[fi][0], fr.t, starts[fi].shape[1], seed=fi, out=starts[fi],
-                             stream=stream)
+        smp.start_points_batch(frame_systems, frame_t, starts, frame_seeds, stream=stream)
         warm.launch(clear=True, stream=stream)
 
     def timed(fn, reps=2):

@@ -339,8 +339,9 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
                              uint32_t n_proj, float lr, uint64_t seed, float* loss_history,
                              void* stream);
 /* Warm-start points for `sys` at frame time t: n network outputs on noise
- * drawn from (seed), written SoA to start (device f32 [2][n]) -- the
- * `start` of a cfs_render_params.  Returns after the points are written. */
+ * drawn from (seed) -- Box-Muller on Philox4x32-10 blocks (row, 0, 0, 3)
+ * with key (seed lo, seed hi) -- written SoA to start (device f32 [2][n]),
+ * the `start` of a cfs_render_params.  Enqueued on `stream`. */
 cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float t, uint32_t n,
                                     uint64_t seed, float* start, void* stream);
 
@@ -375,6 +376,16 @@ cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float
 cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_frames, uint32_t iters,
                                     uint32_t burn_in, uint64_t seed, int clear,
                                     unsigned long long* discards, void* stream);
+
+/* Start points for many frames in one launch: frame f gets counts[f]
+ * network samples (noise from seeds[f]) for systems[f] at time t[f],
+ * written SoA to starts[f] (device f32 [2][counts[f]]).  All host arrays
+ * are read before the call returns (the call waits for the previous one's
+ * upload on the same stream). */
+cfs_status cfs_sampler_start_points_batch(cfs_sampler* s, int n_frames,
+                                          const cfs_system* const* systems, const float* t,
+                                          const uint32_t* counts, const uint64_t* seeds,
+                                          float* const* starts, void* stream);
 
 /* Records, for the n_ids points listed in the device array `ids` (global
  * indices), every step's map index (device i32 [n_ids][steps]), iterated

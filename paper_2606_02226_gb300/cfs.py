@@ -135,6 +135,8 @@ _SIGNATURES = {
     "cfs_render_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(cfs_frame), ctypes.c_int,
                                                 ctypes.c_uint32, ctypes.c_uint32,
                                                 ctypes.c_uint64, ctypes.c_int, _P, _P]),
+    "cfs_sampler_start_points_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _P,
+                                                      _P, _P, ctypes.POINTER(_P), _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -579,6 +581,18 @@ class Sampler:
                                               int(seed) & 0xFFFFFFFFFFFFFFFF, out.data_ptr(),
                                               _stream_handle(stream)))
         return out
+
+    def start_points_batch(self, systems, t_values, outs, seeds, stream=None):
+        """One launch for many frames: outs[f] (device float32 [2, m_f]) gets
+        m_f samples for systems[f] at time t_values[f] with seeds[f]."""
+        n = len(systems)
+        sy = (_P * n)(*[s.handle for s in systems])
+        tv = np.ascontiguousarray(t_values, np.float32)
+        cn = np.array([o.shape[1] for o in outs], np.uint32)
+        sd = np.array([int(v) & 0xFFFFFFFFFFFFFFFF for v in seeds], np.uint64)
+        op = (_P * n)(*[o.data_ptr() for o in outs])
+        _check(lib().cfs_sampler_start_points_batch(self.handle, n, sy, _fptr(tv), _fptr(cn),
+                                                    _fptr(sd), op, _stream_handle(stream)))
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -471,12 +471,15 @@ __device__ __forceinline__ u32 pack2(float lo, float hi)
 
 __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
-// c1 = W1[:, 2:51] u_cond + b1 with the BF16-rounded operands
+// c1 = W1[:, 2:51] u_cond + b1 with the BF16-rounded operands (one block
+// per frame)
 __global__ void cond_kernel(const bf16r* __restrict__ wb, const float* __restrict__ w,
-                            const SysRec* __restrict__ rec, float* c1)
+                            const SysRec* __restrict__ recs, float* c1_all)
 {
     const int j = threadIdx.x;
     if (j >= HID) return;
+    const SysRec* rec = recs + blockIdx.x;
+    float* c1 = c1_all + (size_t)blockIdx.x * HID;
     float acc = w[OFF_B1 + j];
     for (int q = 0; q < COND; ++q)
         acc = fmaf(from_bf16(wb[OFF_W1 + j * D_IN + 2 + q]), from_bf16(to_bf16(rec->cond[q])), acc);
@@ -515,10 +518,21 @@ __device__ __forceinline__ void hidden_layer(const bf16r (*W)[IP], const float* 
     }
 }
 
+// frames of one inference launch: tile_begin[f] = first 16-row tile of
+// frame f (tile_begin[n_sys] = all tiles), its c1 vector, row count, seed
+// and output (SoA [2][count])
+struct InferFrames {
+    const float* c1;          // [n_sys][HID]
+    const u32* tile_begin;    // [n_sys + 1]
+    const u32* count;         // [n_sys]
+    const u64* seed;          // [n_sys]
+    float* const* out;        // [n_sys]
+    int n_sys;
+};
+
 __global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict__ wb,
                                                         const float* __restrict__ w,
-                                                        const float* __restrict__ c1, u64 seed,
-                                                        int n, float* start)
+                                                        const InferFrames fs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     InferSmem& sm = *reinterpret_cast<InferSmem*>(smem_raw);
@@ -532,7 +546,6 @@ __global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict_
         sm.w4[r][c] = r < D_OUT ? wb[OFF_W4 + e] : (bf16r)0;
     }
     for (int j = threadIdx.x; j < HID; j += blockDim.x) {
-        sm.c1[j] = c1[j];
         sm.w10[j] = from_bf16(wb[OFF_W1 + j * D_IN]);
         sm.w11[j] = from_bf16(wb[OFF_W1 + j * D_IN + 1]);
         sm.b2[j] = w[OFF_B2 + j];
@@ -542,13 +555,25 @@ __global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict_
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gq = lane >> 2, tq = lane & 3;
-    const int tiles = (n + 15) / 16;
-    for (int tile = blockIdx.x * IW + warp; tile < tiles; tile += gridDim.x * IW) {
+    const u32 tiles = fs.tile_begin[fs.n_sys];
+    for (u32 tile = blockIdx.x * IW + warp; tile < tiles; tile += gridDim.x * IW) {
+        // the frame of this tile: last f with tile_begin[f] <= tile
+        int lo = 0, hi = fs.n_sys;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (fs.tile_begin[mid] <= tile) lo = mid; else hi = mid;
+        }
+        const int f = lo;
+        const u32 lt = tile - fs.tile_begin[f];
+        const int n = (int)fs.count[f];
+        const u64 seed = fs.seed[f];
+        const float* c1 = fs.c1 + (size_t)f * HID;
+        float* start = fs.out[f];
         // noise of rows gq and gq + 8 (Box-Muller on Philox (row, 0, 0, 3))
         float nz[2][2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const u32 row = (u32)(tile * 16 + gq + 8 * h);
+            const u32 row = lt * 16 + (u32)(gq + 8 * h);
             const uint4 r = philox_key(seed, row, 0u, 0u, TAG_NOISE);
             const float u1 = ((float)(r.x >> 8) + 0.5f) * CFS_INV_2_24;
             const float u2 = (float)(r.y >> 8) * CFS_INV_2_24;
@@ -567,11 +592,13 @@ __global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict_
                 const int c = (2 * kt + half) * 8 + 2 * tq;
                 float v[2][2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
+                for (int q = 0; q < 2; ++q) {
+                    const float cc = c1[c + q];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q)
+                    for (int h = 0; h < 2; ++h)
                         v[h][q] = silu_fast(fmaf(sm.w11[c + q], nz[h][1],
-                                                 fmaf(sm.w10[c + q], nz[h][0], sm.c1[c + q])));
+                                                 fmaf(sm.w10[c + q], nz[h][0], cc)));
+                }
                 a[kt][2 * half + 0] = pack2(v[0][0], v[0][1]);
                 a[kt][2 * half + 1] = pack2(v[1][0], v[1][1]);
             }
@@ -589,7 +616,7 @@ __global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict_
         if (tq == 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int row = tile * 16 + gq + 8 * h;
+                const int row = (int)lt * 16 + gq + 8 * h;
                 if (row < n) {
                     start[row] = y[2 * h] + sm.b4[0];
                     start[(size_t)n + row] = y[2 * h + 1] + sm.b4[1];
@@ -610,9 +637,15 @@ struct cfs_sampler {
     float* m = nullptr;
     float* v = nullptr;
     bf16r* wb = nullptr;     // bf16 copies
-    u32* d_step = nullptr;   // Adam step counter (device); the record and c1 of
-                             // the last start-point call follow it
+    u32* d_step = nullptr;   // Adam step counter (device)
     u32 step = 0;            // host mirror (checkpoints)
+    // inference workspace for n frames (grown on demand): records, c1,
+    // tile offsets, counts, seeds, output pointers
+    int cap_frames = 0;
+    unsigned char* inf = nullptr;
+    unsigned char* inf_host = nullptr;   // pinned staging of the same layout
+    cudaEvent_t uploaded = nullptr;      // the staging buffer's last upload
+    bool upload_pending = false;
     // activations for B rows (grown on demand)
     int cap_rows = 0;
     unsigned char* act = nullptr;
@@ -776,9 +809,7 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
     s->m = s->w + N_PARAMS;
     s->v = s->m + N_PARAMS;
     s->wb = reinterpret_cast<bf16r*>(s->v + N_PARAMS);
-    st = check_cuda(cudaMalloc(&s->d_step, 256 + ((sizeof(SysRec) + 255) & ~(size_t)255) +
-                                               HID * sizeof(float)),
-                    "cudaMalloc(step)");
+    st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->d_step, 0, 256), "memset");
     std::vector<float> init;
@@ -794,6 +825,9 @@ cfs_status cfs_sampler_destroy(cfs_sampler* s)
     if (!s) return CFS_OK;
     cudaDeviceSynchronize();
     if (s->act) cudaFree(s->act);
+    if (s->inf) cudaFree(s->inf);
+    if (s->inf_host) cudaFreeHost(s->inf_host);
+    if (s->uploaded) cudaEventDestroy(s->uploaded);
     if (s->w) cudaFree(s->w);
     if (s->d_step) cudaFree(s->d_step);
     delete s;
@@ -981,29 +1015,92 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
     return st;
 }
 
-cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float t, uint32_t n,
-                                    uint64_t seed, float* start, void* stream)
+namespace {
+struct InferLayout {
+    size_t rec, c1, tiles, count, seed, out, total;
+};
+
+InferLayout infer_layout(int n)
+{
+    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    InferLayout l;
+    l.rec = 0;
+    l.c1 = up(l.rec + sizeof(SysRec) * (size_t)n);
+    l.tiles = up(l.c1 + sizeof(float) * HID * (size_t)n);
+    l.count = up(l.tiles + sizeof(u32) * ((size_t)n + 1));
+    l.seed = up(l.count + sizeof(u32) * (size_t)n);
+    l.out = up(l.seed + sizeof(u64) * (size_t)n);
+    l.total = up(l.out + sizeof(float*) * (size_t)n);
+    return l;
+}
+}  // namespace
+
+cfs_status cfs_sampler_start_points_batch(cfs_sampler* s, int n_frames,
+                                          const cfs_system* const* systems, const float* t,
+                                          const uint32_t* counts, const uint64_t* seeds,
+                                          float* const* starts, void* stream)
 {
     clear_error();
-    if (!s || !start) return fail(CFS_ERR_INVALID_ARG, "NULL sampler or output");
-    cfs_status st = check_sampler_system(sys);
-    if (st != CFS_OK) return st;
-    if (n == 0) return CFS_OK;
-    if (n > (1u << 30)) return fail(CFS_ERR_INVALID_ARG, "n too large");
+    if (!s || !systems || !t || !counts || !seeds || !starts || n_frames <= 0)
+        return fail(CFS_ERR_INVALID_ARG, "NULL argument or no frames");
+    uint64_t tiles = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        cfs_status st = check_sampler_system(systems[f]);
+        if (st != CFS_OK) return st;
+        if (counts[f] > (1u << 30)) return fail(CFS_ERR_INVALID_ARG, "count too large");
+        if (counts[f] && !starts[f]) return fail(CFS_ERR_INVALID_ARG, "NULL output");
+        tiles += (counts[f] + 15) / 16;
+    }
+    if (tiles >= (1ull << 31)) return fail(CFS_ERR_INVALID_ARG, "too many rows");
     cudaStream_t sm = (cudaStream_t)stream;
-    SysRec rec;
-    pack_system(sys, t, &rec);
-    // the record and c1 live behind the step counter (allocated with it);
-    // the copy from the host stack has read its source when it returns
-    SysRec* d_rec = reinterpret_cast<SysRec*>(reinterpret_cast<unsigned char*>(s->d_step) + 256);
-    float* d_c1 = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(d_rec) +
-                                           ((sizeof(SysRec) + 255) & ~(size_t)255));
-    st = check_cuda(cudaMemcpyAsync(d_rec, &rec, sizeof(SysRec), cudaMemcpyHostToDevice, sm),
-                    "cudaMemcpyAsync(system)");
+    const InferLayout L = infer_layout(n_frames);
+    if (n_frames > s->cap_frames) {
+        // the previous staging buffer may still feed an upload
+        cfs_status st = check_cuda(cudaDeviceSynchronize(), "sampler sync");
+        if (st != CFS_OK) return st;
+        if (s->inf) cudaFree(s->inf);
+        if (s->inf_host) cudaFreeHost(s->inf_host);
+        s->inf = nullptr;
+        s->inf_host = nullptr;
+        s->cap_frames = 0;
+        st = check_cuda(cudaMalloc(&s->inf, L.total), "cudaMalloc(inference workspace)");
+        if (st == CFS_OK)
+            st = check_cuda(cudaMallocHost(&s->inf_host, L.total), "cudaMallocHost(inference)");
+        if (st != CFS_OK) return st;
+        s->cap_frames = n_frames;
+    } else if (s->upload_pending) {
+        // the staging buffer is rewritten: wait for its last upload only
+        cfs_status st = check_cuda(cudaEventSynchronize(s->uploaded), "sampler upload sync");
+        if (st != CFS_OK) return st;
+    }
+    if (!s->uploaded) {
+        cfs_status st = check_cuda(cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming),
+                                   "cudaEventCreate");
+        if (st != CFS_OK) return st;
+    }
+    unsigned char* h = s->inf_host;
+    u32* h_tiles = reinterpret_cast<u32*>(h + L.tiles);
+    u32 acc = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        pack_system(systems[f], t[f], reinterpret_cast<SysRec*>(h + L.rec) + f);
+        h_tiles[f] = acc;
+        acc += (counts[f] + 15) / 16;
+        reinterpret_cast<u32*>(h + L.count)[f] = counts[f];
+        reinterpret_cast<u64*>(h + L.seed)[f] = seeds[f];
+        reinterpret_cast<float**>(h + L.out)[f] = starts[f];
+    }
+    h_tiles[n_frames] = acc;
+    cfs_status st = check_cuda(cudaMemcpyAsync(s->inf, h, L.total, cudaMemcpyHostToDevice, sm),
+                               "cudaMemcpyAsync(inference frames)");
+    if (st == CFS_OK) st = check_cuda(cudaEventRecord(s->uploaded, sm), "cudaEventRecord");
     if (st != CFS_OK) return st;
-    cond_kernel<<<1, HID, 0, sm>>>(s->wb, s->w, d_rec, d_c1);
-    static int smem_set = -1;
+    s->upload_pending = true;
+    unsigned char* d = s->inf;
+    cond_kernel<<<n_frames, HID, 0, sm>>>(s->wb, s->w, reinterpret_cast<const SysRec*>(d + L.rec),
+                                         reinterpret_cast<float*>(d + L.c1));
+    if (acc == 0) return check_cuda(cudaGetLastError(), "sampler conditioning");
     const int smem = (int)sizeof(InferSmem);
+    static int smem_set = -1;
     if (smem_set != s->device) {
         st = check_cuda(cudaFuncSetAttribute(infer_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
@@ -1014,11 +1111,28 @@ cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float
     int per_sm = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_kernel, IW * 32, smem);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    const int tiles = (int)((n + 15) / 16);
     int grid = std::max(1, per_sm) * std::max(1, sms);
-    grid = std::min(grid, (tiles + IW - 1) / IW);
-    infer_kernel<<<grid, IW * 32, smem, sm>>>(s->wb, s->w, d_c1, seed, (int)n, start);
+    grid = (int)std::min<uint64_t>((uint64_t)grid, (acc + IW - 1) / IW);
+    InferFrames fs;
+    fs.c1 = reinterpret_cast<const float*>(d + L.c1);
+    fs.tile_begin = reinterpret_cast<const u32*>(d + L.tiles);
+    fs.count = reinterpret_cast<const u32*>(d + L.count);
+    fs.seed = reinterpret_cast<const u64*>(d + L.seed);
+    fs.out = reinterpret_cast<float* const*>(d + L.out);
+    fs.n_sys = n_frames;
+    infer_kernel<<<grid, IW * 32, smem, sm>>>(s->wb, s->w, fs);
     return check_cuda(cudaGetLastError(), "sampler start points");
+}
+
+cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float t, uint32_t n,
+                                    uint64_t seed, float* start, void* stream)
+{
+    if (n == 0) {
+        clear_error();
+        if (!s || !start) return fail(CFS_ERR_INVALID_ARG, "NULL sampler or output");
+        return check_sampler_system(sys);
+    }
+    return cfs_sampler_start_points_batch(s, 1, &sys, &t, &n, &seed, &start, stream);
 }
 
 }  // extern "C"

@@ -131,6 +131,20 @@ def test_start_points_match_oracle(torch_cuda):
     assert _rel(st1, Yo[:1]) < 2e-2
 
 
+def test_start_points_batch_equals_single_calls(torch_cuda):
+    torch = torch_cuda
+    cfs, s, params, _, _ = _setup(torch, 64)
+    frs = W.animation_frames(n_frames=5, seed=6)
+    systems = [cfs.System(f.system) for f in frs]
+    counts = [1, 17, 300, 4096, 33]
+    outs = [torch.empty((2, c), dtype=torch.float32, device="cuda") for c in counts]
+    s.start_points_batch(systems, [f.t for f in frs], outs, [11, 12, 13, 14, 15])
+    for j, f in enumerate(frs):
+        one = s.start_points(systems[j], f.t, counts[j], seed=11 + j)
+        torch.cuda.synchronize()
+        assert torch.equal(one, outs[j]), j
+
+
 def _family(n, seed=0):
     frames = W.animation_frames(n_frames=n, seed=seed)
     return frames

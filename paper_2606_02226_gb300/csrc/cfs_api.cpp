@@ -170,6 +170,10 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     if (const char* e = std::getenv("CFS_MINB")) sp.min_blocks = std::atoi(e);
     if (const char* e = std::getenv("CFS_DEPTH_TEST")) sp.depth_test = std::atoi(e);
     if (const char* e = std::getenv("CFS_SPILL_ALLOW")) sp.spill_allowance = std::atoi(e);
+    if (const char* e = std::getenv("CFS_UNROLL")) {
+        const int u = std::atoi(e);
+        if (u == 1 || u == 2 || u == 4) sp.unroll = u;
+    }
     if (sp.block != 128 && sp.block != 256 && sp.block != 512) sp.block = 256;
     if (sp.min_blocks < 1 || sp.min_blocks > 16) sp.min_blocks = 4;
     sp.depth_test = sp.depth_test ? 1 : 0;

@@ -333,10 +333,13 @@ __device__ __forceinline__ void cfs_red_min_u64(u64* p, u64 v)
     asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v));
 }
 
+/* Not volatile: the compiler may issue it early (before the previous splat's
+ * reduction) or reuse an earlier load of the same address -- both return a
+ * value the key had at some point, and keys only decrease. */
 __device__ __forceinline__ u64 cfs_ld_relaxed_u64(const u64* p)
 {
     u64 v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    asm("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
 

@@ -62,6 +62,7 @@ struct ProgramSpec {
     int warp_agg = 0;          // warp-aggregated shared atomics in that window
     int tile_reps = 1;         // at most this many copies of a small window
     int fast_trig = 0;         // chain trigonometry: reduced argument + hardware sin/cos
+    int unroll = 4;            // copies of the step code in the step loop (4, 2, 1)
     int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
 
     std::string key() const;

@@ -85,8 +85,13 @@ __device__ __forceinline__ void cfs_step(const cfs_launch_args& a, const CH& cho
 
 /* Runs steps step_begin .. iters-1 of point i of system sid: one Philox
  * block per four steps.  Blocks cut by step_begin or iters run their steps
- * under warp-uniform guards, so the step code appears four times, not more
- * (the generated chain can be long; instruction-cache pressure matters). */
+ * under warp-uniform guards.  CFS_UNROLL (4, 2 or 1) is how many copies of
+ * the step code the loop holds: the generated chain can be long, and
+ * instruction-cache pressure trades against the scheduler's freedom to
+ * overlap consecutive steps. */
+#ifndef CFS_UNROLL
+#define CFS_UNROLL 4
+#endif
 template <class CH, class TG>
 __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH& choose,
                                               const TG& tg, const CfsSmem& sm, u32 i, u32 sid,
@@ -99,6 +104,7 @@ __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH
     for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
         const uint4 r = cfs_philox(a, i, nb, sid, 0u);
         const u32 n = nb << 2;
+#if CFS_UNROLL == 4
         if (whole || (n >= b0 && n < b1)) cfs_step(a, choose, tg, sm, n, r.x, x, y, z, disc, tile);
         if (whole || (n + 1 >= b0 && n + 1 < b1))
             cfs_step(a, choose, tg, sm, n + 1, r.y, x, y, z, disc, tile);
@@ -106,6 +112,26 @@ __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH
             cfs_step(a, choose, tg, sm, n + 2, r.z, x, y, z, disc, tile);
         if (whole || (n + 3 >= b0 && n + 3 < b1))
             cfs_step(a, choose, tg, sm, n + 3, r.w, x, y, z, disc, tile);
+#elif CFS_UNROLL == 2
+#pragma unroll 1
+        for (u32 h = 0; h < 4; h += 2) {
+            const u32 w0 = h ? r.z : r.x, w1 = h ? r.w : r.y;
+            if (whole || (n + h >= b0 && n + h < b1))
+                cfs_step(a, choose, tg, sm, n + h, w0, x, y, z, disc, tile);
+            if (whole || (n + h + 1 >= b0 && n + h + 1 < b1))
+                cfs_step(a, choose, tg, sm, n + h + 1, w1, x, y, z, disc, tile);
+        }
+#else
+        u32 w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll 1
+        for (u32 h = 0; h < 4; ++h) {
+            if (whole || (n + h >= b0 && n + h < b1))
+                cfs_step(a, choose, tg, sm, n + h, w[0], x, y, z, disc, tile);
+            w[0] = w[1];
+            w[1] = w[2];
+            w[2] = w[3];
+        }
+#endif
     }
 }
 

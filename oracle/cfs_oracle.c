@@ -498,3 +498,114 @@ int orc_render_points(const float* xyz, const uint8_t* fn, uint32_t n, const orc
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Density-estimation display.  The paper names density estimation (fractal
+ * flames, caustics) as the output that keeps atomics on the path (Section 5)
+ * and leaves its display unspecified; the reading here is the log-density
+ * mapping of fractal flames (Draves & Reckase 2003): per pixel
+ *   A   = accumulated alpha (the number of splats for palette alpha 1),
+ *   S   = accumulated colour,
+ *   d   = ln(1 + A) / ln(1 + A_max),   v = brightness * d^(1/gamma),
+ *   rgb = clamp(S / A * v),  alpha = clamp(v),
+ * each component quantised to 8 bits as (uint)(255 x + 1/2), packed
+ * r | g << 8 | b << 16 | a << 24.  Pixels with A = 0 take the background.
+ * A histogram layer contributes, per channel c, n_c * palette[c] (products,
+ * then sums over c = 0..C-1 in order).  A depth layer is resolved to the
+ * colour in the low 32 bits of its key (background where empty).
+ * All of it in FP32 (logf, powf, IEEE division), the same precision the
+ * device takes the decisions in.  When `near` is given, it receives per
+ * pixel a 4-bit mask of the components whose 255 x + 1/2, evaluated in
+ * double from the same FP32 inputs, lies within `eps` of an integer (codes
+ * another libm may round the other way). */
+/* ------------------------------------------------------------------------ */
+static void pixel_sums(const orc_target* t, size_t pix, float* s)
+{
+    if (t->kind == ORC_TGT_RGBA_F32) {
+        const float* img = (const float*)t->buf;
+        for (int c = 0; c < 4; ++c) s[c] = img[4 * pix + c];
+        return;
+    }
+    const uint32_t* h = (const uint32_t*)t->buf;
+    s[0] = s[1] = s[2] = s[3] = 0.0f;
+    for (int ch = 0; ch < t->C; ++ch) {
+        float n = (float)h[(size_t)ch * t->W * t->H + pix];
+        for (int c = 0; c < 4; ++c) {
+            float prod = n * t->palette[4 * ch + c];
+            s[c] = s[c] + prod;
+        }
+    }
+}
+
+static uint32_t quant8(float x)
+{
+    if (!(x > 0.0f)) x = 0.0f;
+    if (x > 1.0f) x = 1.0f;
+    float y = 255.0f * x;
+    y = y + 0.5f;
+    return (uint32_t)y;
+}
+
+static int near_code(float x, double eps)
+{
+    if (!(x > 0.0f) || x > 1.0f) return 0;
+    double y = 255.0 * (double)x + 0.5;
+    double fr = y - floor(y);
+    return fr < eps || fr > 1.0 - eps;
+}
+
+float orc_density_max(const orc_target* t)
+{
+    float m = 0.0f;
+    size_t n = (size_t)t->W * t->H;
+    for (size_t pix = 0; pix < n; ++pix) {
+        float s[4];
+        pixel_sums(t, pix, s);
+        if (s[3] > m) m = s[3];
+    }
+    return m;
+}
+
+int orc_tonemap(const orc_target* t, float gamma, float brightness, float a_max,
+                uint32_t background, uint32_t* out, uint8_t* near, double eps)
+{
+    size_t n = (size_t)t->W * t->H;
+    if (t->kind == ORC_TGT_DEPTH_U64) {
+        const uint64_t* d = (const uint64_t*)t->buf;
+        for (size_t pix = 0; pix < n; ++pix) {
+            out[pix] = d[pix] == ~(uint64_t)0 ? background : (uint32_t)d[pix];
+            if (near) near[pix] = 0;
+        }
+        return 0;
+    }
+    if (!(gamma > 0.0f) || !(brightness > 0.0f)) return -1;
+    if (!(a_max > 0.0f)) a_max = orc_density_max(t);
+    float inv_gamma = 1.0f / gamma;
+    float l_max = a_max > 0.0f ? logf(1.0f + a_max) : 1.0f;
+    for (size_t pix = 0; pix < n; ++pix) {
+        float s[4];
+        pixel_sums(t, pix, s);
+        if (!(s[3] > 0.0f)) {
+            out[pix] = background;
+            if (near) near[pix] = 0;
+            continue;
+        }
+        float d = logf(1.0f + s[3]) / l_max;
+        float v = brightness * powf(d, inv_gamma);
+        float x[4];
+        for (int c = 0; c < 3; ++c) {
+            float mean = s[c] / s[3];
+            x[c] = mean * v;
+        }
+        x[3] = v;
+        uint32_t code = 0;
+        uint8_t mask = 0;
+        for (int c = 0; c < 4; ++c) {
+            code |= quant8(x[c]) << (8 * c);
+            if (near_code(x[c], eps)) mask |= (uint8_t)(1u << c);
+        }
+        out[pix] = code;
+        if (near) near[pix] = mask;
+    }
+    return 0;
+}

@@ -90,4 +90,11 @@ int orc_pointcloud_generate(const orc_system* sys, uint64_t seed, uint32_t syste
 int orc_render_points(const float* xyz, const uint8_t* fn, uint32_t n, const orc_chain* ch,
                       orc_target* tg, int n_tg);
 
+/* Density-estimation display of a layer (log density, gamma, 8-bit RGBA);
+ * a_max <= 0 takes the layer's own maximum.  near (optional, [H][W]) gets the
+ * mask of components within eps of a rounding boundary. */
+float orc_density_max(const orc_target* t);
+int orc_tonemap(const orc_target* t, float gamma, float brightness, float a_max,
+                uint32_t background, uint32_t* out, uint8_t* near, double eps);
+
 #endif

@@ -113,6 +113,11 @@ def lib():
                                         ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint32,
                                         ctypes.POINTER(_Chain), ctypes.POINTER(_Target),
                                         ctypes.c_int]
+        L.orc_density_max.argtypes = [ctypes.POINTER(_Target)]
+        L.orc_density_max.restype = ctypes.c_float
+        L.orc_tonemap.argtypes = [ctypes.POINTER(_Target), ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_uint32, u32p,
+                                  ctypes.POINTER(ctypes.c_uint8), ctypes.c_double]
         _LIB = L
     return _LIB
 
@@ -322,3 +327,21 @@ def render_points(xyz, fn, chain, targets, *, margin_px=0.0, track=False, bufs=N
     for j, tr in enumerate(results):
         tr.n_splat, tr.n_discard, tr.n_amb = arr[j].n_splat, arr[j].n_discard, arr[j].n_amb
     return results
+
+
+def tonemap(target, buf, *, gamma=2.2, brightness=1.0, a_max=0.0, background=0, eps=1e-3):
+    """Density-estimation display of a layer: returns (rgba8 u32 [H][W],
+    near-boundary component mask u8 [H][W], density maximum used)."""
+    keep = _Keep()
+    buf = keep(np.ascontiguousarray(buf))
+    ts, _ = _target(target, keep, buf, 0.0, False)
+    out = np.zeros((target.H, target.W), dtype=np.uint32)
+    near = np.zeros((target.H, target.W), dtype=np.uint8)
+    L = lib()
+    used = float(a_max) if a_max > 0 else (
+        0.0 if target.kind == "depth_u64" else float(L.orc_density_max(ctypes.byref(ts))))
+    rc = L.orc_tonemap(ctypes.byref(ts), gamma, brightness, a_max, background,
+                       _ptr(out, ctypes.c_uint32), _ptr(near, ctypes.c_uint8), eps)
+    if rc != 0:
+        raise ValueError("invalid tone-mapping parameters")
+    return out, near, used

@@ -515,3 +515,76 @@ def test_pointcloud_is_trajectory_endpoint():
     assert np.array_equal(xyz, p[:, -1, :]) and np.array_equal(fn, k[:, -1])
     # the attractor bound |x| <= |b| / (1 - s_max) for s <= 0.55, |b| <= sqrt(3)
     assert np.linalg.norm(xyz, axis=1).max() <= math.sqrt(3) / 0.45
+
+
+# ---------------------------------------------------------------------------
+# density-estimation display (log density, gamma, 8-bit RGBA)
+# ---------------------------------------------------------------------------
+def _unpack8(v):
+    v = int(v)
+    return [(v >> (8 * c)) & 0xFF for c in range(4)]
+
+
+def _rgba_layer(W_, H_):
+    return W.Target("rgba_f32", W_, H_, 1, (0.0, 1.0, 0.0, 1.0)), np.zeros((H_, W_, 4), np.float32)
+
+
+def test_tonemap_closed_forms():
+    t, buf = _rgba_layer(4, 2)
+    buf[0, 0] = [8.0, 4.0, 0.0, 8.0]       # 8 splats of (1, 0.5, 0, 1): the maximum
+    buf[0, 1] = [2.0, 1.0, 0.0, 2.0]       # ln 3 / ln 9 = 1/2
+    buf[0, 2] = [0.0, 0.0, 3.0, 3.0]       # blue, ln 4 / ln 9
+    out, _, used = O.tonemap(t, buf, gamma=1.0, background=0x11223344)
+    assert used == 8.0
+    assert _unpack8(out[0, 0]) == [255, 128, 0, 255]
+    assert _unpack8(out[0, 1]) == [128, 64, 0, 128]
+    v = math.log(4) / math.log(9)
+    assert _unpack8(out[0, 2]) == [0, 0, round(255 * v), round(255 * v)]
+    assert all(int(x) == 0x11223344 for x in out[1])           # empty pixels
+    out2, _, _ = O.tonemap(t, buf, gamma=2.0)
+    s = math.sqrt(0.5)
+    assert _unpack8(out2[0, 1]) == [round(255 * s), round(127.5 * s), 0, round(255 * s)]
+    # brightness saturates; an explicit maximum replaces the layer's own
+    out3, _, _ = O.tonemap(t, buf, gamma=1.0, brightness=2.0)
+    assert _unpack8(out3[0, 0]) == [255, 255, 0, 255]
+    out4, _, used4 = O.tonemap(t, buf, gamma=1.0, a_max=2.0)
+    assert used4 == 2.0 and _unpack8(out4[0, 1]) == [255, 128, 0, 255]
+
+
+def test_tonemap_alpha_monotone_in_density():
+    t, buf = _rgba_layer(64, 1)
+    a = np.arange(64, dtype=np.float32) * 17
+    buf[0, :, 3] = a
+    buf[0, :, 0] = a
+    out, _, _ = O.tonemap(t, buf, gamma=2.2)
+    alpha = [(int(v) >> 24) & 0xFF for v in out[0]]
+    red = [int(v) & 0xFF for v in out[0]]
+    assert alpha[0] == 0 and alpha[-1] == 255
+    assert all(x <= y for x, y in zip(alpha, alpha[1:]))
+    assert red == alpha                    # pure red: the colour equals the density
+
+
+def test_tonemap_histogram_equals_rgba_sums():
+    # a C-channel histogram displays as the RGBA layer of its palette sums
+    rng = np.random.default_rng(11)
+    pal = W.palette_rgba(4)
+    ht = W.Target("hist_u32", 16, 8, 4, (0.0, 1.0, 0.0, 1.0), palette=pal)
+    h = rng.integers(0, 50, size=(4, 8, 16)).astype(np.uint32)
+    h[:, 0, 0] = 0
+    t, rgba = _rgba_layer(16, 8)
+    p = np.asarray(pal, np.float64)[:4]
+    rgba[:] = np.einsum("chw,ck->hwk", h.astype(np.float64), p).astype(np.float32)
+    o1, _, m1 = O.tonemap(ht, h, gamma=2.2, background=7)
+    o2, _, m2 = O.tonemap(t, rgba, gamma=2.2, background=7)
+    assert m1 == m2 == float(h.sum(axis=0).max())
+    assert np.array_equal(o1, o2) and o1[0, 0] == 7
+
+
+def test_tonemap_depth_resolves_colour():
+    t = W.Target("depth_u64", 3, 1, 1, (0.0, 1.0, 0.0, 1.0))
+    keys = np.array([[(np.uint64(0x3F800000) << np.uint64(32)) | np.uint64(0xFF00FF00),
+                      np.uint64(0xFFFFFFFFFFFFFFFF),
+                      (np.uint64(0x40000000) << np.uint64(32)) | np.uint64(0x01020304)]],
+                    dtype=np.uint64)
+    out, _, _ = O.tonemap(t, keys, background=0xDEADBEEF)
+    assert [int(v) for v in out[0]] == [0xFF00FF00, 0xDEADBEEF, 0x01020304]

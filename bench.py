@@ -79,8 +79,8 @@ def measure_atomic_peaks(torch, cfs, dev, rgba_bytes: int, depth_bytes: int, rep
 # profiles/cfs_render_kernel_composed.md.  Valid only for the kernel it was
 # taken on: the bench reports it when the SHA-1 of the generated program and
 # its device headers still matches, and null otherwise.
-RENDER_TRAFFIC_BYTES = None
-RENDER_TRAFFIC_SOURCE_SHA1 = None
+RENDER_TRAFFIC_BYTES = 16355072          # (26740480 + 5969664) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "87766172cc61dd0cb300922dc1a679e24e3dfeca"
 
 
 def render_program_sha1(cfs, wl, fast_trig=False):

@@ -75,12 +75,12 @@ def measure_atomic_peaks(torch, cfs, dev, rgba_bytes: int, depth_bytes: int, rep
 
 
 # DRAM bytes per render launch of the composed scene (mean of the two
-# objects' launches), from the full-size one-pass ncu capture summarized in
-# profiles/cfs_render_kernel_composed.md.  Valid only for the kernel it was
-# taken on: the bench reports it when the SHA-1 of the generated program and
-# its device headers still matches, and null otherwise.
-RENDER_TRAFFIC_BYTES = 16355072          # (26740480 + 5969664) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "87766172cc61dd0cb300922dc1a679e24e3dfeca"
+# objects' launches: dram__bytes_read.sum + dram__bytes_write.sum from a
+# full-size one-pass ncu capture).  Valid only for the kernel it was taken
+# on: the bench reports it when the SHA-1 of the generated program and its
+# device headers still matches, and null otherwise.
+RENDER_TRAFFIC_BYTES = 16093440          # (26460928 + 5725952) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "3296c7db5eec129b47904567f319469a5405c886"
 
 
 def render_program_sha1(cfs, wl, fast_trig=False):
@@ -410,13 +410,41 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
     n_pts = sum(fr.n_points for fr in frames)
     bytes_targets = sum(4 * 4 * fr.W * fr.W for fr in frames)
     info = b.info()
+
+    # density-estimation display of every frame (one maximum and one mapping
+    # launch for all 256 frames); the histograms (5.6 GB) do not fit in L2
+    outs = [torch.empty((fr.W, fr.W), dtype=torch.int32, device=dev) for fr in frames]
+    b.display(outs, gamma=2.2, stream=stream)
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(reps):
+        b.display(outs, gamma=2.2, stream=stream)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    disp_ms = d0.elapsed_time(d1) / reps
+    # each pass reads the 4 channels (16 B per pixel), the second writes 4 B
+    disp_bytes = sum((2 * 16 + 4) * fr.W * fr.W for fr in frames)
+    pk, pk_src = _peaks()
+    peak = pk.get("hbm_gbs")
+    disp_gbs = disp_bytes / (disp_ms * 1e-3) / 1e9
+    display = {"ms": disp_ms, "bytes": disp_bytes, "gpu_launches": 2,
+               "roofline": {"bound": "hbm", "kernel": "density_max_kernel + display_map_kernel",
+                            "achieved": disp_gbs, "peak": peak, "unit": "GB/s",
+                            "frac": disp_gbs / peak if peak else None,
+                            "peak_source": f"{pk_src} (HBM copy bandwidth)",
+                            "bytes": "36 B per pixel: two 16-byte reads of the 4 channels, "
+                                     "one 4-byte write"}}
+    del outs
     return {"workload": f"{n_frames} animation frames, 2-8 affine maps, 2^16..2^22 points, "
                         "256^2..2048^2 x 4ch u32, 300 steps, burn-in 20",
             "ms_per_batch": ms, "frames_per_s": n_frames / (ms * 1e-3),
             "point_steps_per_s": n_pts * 300 / (ms * 1e-3),
             "splats_per_s": n_pts * 280 / (ms * 1e-3), "points": n_pts,
             "target_bytes": bytes_targets, "items": info["n_items"], "chunk": info["chunk"],
-            "grid": info["grid"], "gpu_launches_per_batch": 1}
+            "grid": info["grid"], "gpu_launches_per_batch": 1, "display": display,
+            "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3)}
 
 
 def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,

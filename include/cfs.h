@@ -283,6 +283,47 @@ cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_fra
                             int n_frames, uint32_t step_begin, uint32_t iters, uint32_t burn_in,
                             uint64_t seed, int clear, void* stream);
 
+/* ---- density-estimation display -----------------------------------------
+ * Section 5 names density estimation (fractal flames, caustics) as the
+ * output that keeps atomics on the path; the paper does not say how such a
+ * layer is shown.  The mapping here is the log-density display of fractal
+ * flames (Draves & Reckase 2003), per pixel:
+ *   A   = accumulated alpha (the number of splats for palette alpha 1),
+ *   S   = accumulated colour (RGB),
+ *   d   = ln(1 + A) / ln(1 + A_max),  v = brightness * d^(1/gamma),
+ *   out = (clamp(S/A * v), clamp(v)) quantised as (uint)(255 x + 0.5) and
+ *         packed r | g << 8 | b << 16 | a << 24;
+ * pixels with A <= 0 take `background`.  A histogram layer (u32 [C][H][W])
+ * counts as the RGBA layer sum_c n_c * palette[c] (products, then sums in
+ * channel order); a depth layer resolves to the packed colour in the low 32
+ * bits of its key (background where empty, no density).  FP32 throughout
+ * (logf, powf, IEEE division). */
+typedef struct {
+    float gamma;          /* > 0 */
+    float brightness;     /* > 0 */
+    float a_max;          /* > 0: the density shown at full brightness;
+                             <= 0: the layer's own maximum, found on the device */
+    uint32_t background;  /* packed RGBA8 of pixels nothing landed on */
+} cfs_display_params;
+
+/* Displays one layer into `rgba8` (device u32 [H][W], 16-byte aligned,
+ * caller-owned; may not overlap the layer).  `a_max_out` (device float, 4-byte
+ * aligned) receives the density maximum used; it is required when
+ * params->a_max <= 0 and the layer is not a depth layer, else may be NULL.
+ * Two kernels (maximum, then mapping), no allocation, stream-ordered. */
+cfs_status cfs_tonemap(const cfs_target* layer, const cfs_display_params* params,
+                       uint32_t* rgba8, float* a_max_out, void* stream);
+
+/* Displays target `slot` of every frame of a batch in one maximum launch and
+ * one mapping launch: frame f into outs[f] (host array of n_frames device
+ * u32 [H][W] pointers, 16-byte aligned).  `a_max_out` (device float
+ * [n_frames]) receives each frame's maximum, or NULL to keep it in the
+ * batch's workspace.  Usually enqueued right after cfs_batch_launch on the
+ * same stream.  The out-pointer upload is staged in pinned memory: a call
+ * waits for the previous display of the same batch to have been uploaded. */
+cfs_status cfs_batch_display(cfs_batch* batch, int slot, const cfs_display_params* params,
+                             uint32_t* const* outs, float* a_max_out, void* stream);
+
 /* ---- learned warm-start sampler (the initial distribution the paper
  *      proposes to derive automatically, Section 4) ---------------------- */
 /* Network: u (64) -> 128 -> 128 -> 128 -> 2 with SiLU after the first three

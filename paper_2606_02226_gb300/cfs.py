@@ -73,6 +73,11 @@ class cfs_frame(ctypes.Structure):
                 ("targets", cfs_target * MAX_TARGETS)]
 
 
+class cfs_display_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_float), ("brightness", ctypes.c_float),
+                ("a_max", ctypes.c_float), ("background", ctypes.c_uint32)]
+
+
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "cfs_system_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(cfs_map),
@@ -137,6 +142,10 @@ _SIGNATURES = {
                                                 ctypes.c_uint64, ctypes.c_int, _P, _P]),
     "cfs_sampler_start_points_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P), _P,
                                                       _P, _P, ctypes.POINTER(_P), _P]),
+    "cfs_tonemap": (ctypes.c_int, [ctypes.POINTER(cfs_target), ctypes.POINTER(cfs_display_params),
+                                   _P, _P, _P]),
+    "cfs_batch_display": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_display_params),
+                                         ctypes.POINTER(_P), _P, _P]),
     "cfs_last_error": (ctypes.c_char_p, []),
     "cfs_version": (ctypes.c_char_p, []),
 }
@@ -486,6 +495,24 @@ class Batch:
                                     ctypes.byref(c)))
         return {"n_items": a.value, "chunk": b.value, "grid": c.value}
 
+    def display(self, outs, *, slot: int = 0, gamma: float = 2.2, brightness: float = 1.0,
+                a_max: float = 0.0, background: int = 0, a_max_out=None, stream=None):
+        """Displays target ``slot`` of every frame into ``outs`` (one int32
+        [H, W] CUDA tensor per frame, holding packed RGBA8): one maximum and
+        one mapping launch for all frames.  ``a_max_out``: optional float32
+        [n_frames] CUDA tensor receiving each frame's density maximum."""
+        if len(outs) != self.n_frames:
+            raise ValueError("one output per frame")
+        ptrs = (_P * self.n_frames)()
+        for f, o in enumerate(outs):
+            if not o.is_cuda or not o.is_contiguous():
+                raise ValueError("outputs must be contiguous CUDA tensors")
+            ptrs[f] = o.data_ptr()
+        p = _display_params(gamma, brightness, a_max, background)
+        _check(lib().cfs_batch_display(self.handle, slot, ctypes.byref(p), ptrs,
+                                       a_max_out.data_ptr() if a_max_out is not None else None,
+                                       _stream_handle(stream)))
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and _LIB is not None:
@@ -500,6 +527,36 @@ def render_batch(chain: Chain, frames, *, iters: int, burn_in: int, seed: int = 
     _check(lib().cfs_render_batch(chain.handle, nt, arr, len(frames), step_begin, iters, burn_in,
                                   int(seed) & 0xFFFFFFFFFFFFFFFF, 1 if clear else 0,
                                   _stream_handle(stream)))
+
+
+# ---------------------------------------------------------------------------
+# density-estimation display
+# ---------------------------------------------------------------------------
+def _display_params(gamma, brightness, a_max, background):
+    p = cfs_display_params()
+    p.gamma, p.brightness, p.a_max = float(gamma), float(brightness), float(a_max)
+    p.background = int(background) & 0xFFFFFFFF
+    return p
+
+
+def tonemap(desc, tensor, out=None, *, gamma: float = 2.2, brightness: float = 1.0,
+            a_max: float = 0.0, background: int = 0, a_max_out=None, stream=None):
+    """Log-density display of one layer into packed RGBA8 (an int32 [H, W]
+    CUDA tensor, allocated when ``out`` is None).  With ``a_max`` <= 0 the
+    layer's own maximum is found on the device and written to ``a_max_out``
+    (a float32 CUDA tensor with at least one element, allocated when None).
+    Returns (out, a_max_out)."""
+    import torch
+    arr, _ = make_targets([desc], [tensor])
+    if out is None:
+        out = torch.empty((desc.H, desc.W), dtype=torch.int32, device=tensor.device)
+    if a_max_out is None and a_max <= 0 and desc.kind != "depth_u64":
+        a_max_out = torch.empty(1, dtype=torch.float32, device=tensor.device)
+    p = _display_params(gamma, brightness, a_max, background)
+    _check(lib().cfs_tonemap(arr, ctypes.byref(p), out.data_ptr(),
+                             a_max_out.data_ptr() if a_max_out is not None else None,
+                             _stream_handle(stream)))
+    return out, a_max_out
 
 
 # ---------------------------------------------------------------------------

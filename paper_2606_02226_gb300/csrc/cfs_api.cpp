@@ -563,10 +563,7 @@ cfs_status cfs_codegen_check(const cfs_system* sys, const cfs_chain* chain,
                 return fail(CFS_ERR_UNSUPPORTED, "a batch needs maps of one kind");
         sp.n_maps = CFS_MAX_MAPS;
         for (int j = 0; j < CFS_MAX_MAPS; ++j) sp.map_kind[j] = sys->maps[0].kind;
-        sp.spill_allowance = 64;
-        sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
-        sp.warp_agg = sp.tile;
-        sp.tile_reps = 8;
+        batch_spec_defaults(sp);
     }
     std::string s, l;
     st = compile_only(sp, &s, &l);

@@ -49,6 +49,11 @@ struct cfs_batch {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [clear]
     cudaEvent_t done = nullptr;
     bool launched = false;
+    // display (cfs_batch_display): layer descriptions staged in pinned memory
+    cfs::DisplayLayer* h_disp = nullptr;
+    unsigned char* d_disp = nullptr;      // DisplayLayer [n_frames] | float a_max [n_frames]
+    cudaEvent_t disp_done = nullptr;
+    bool disp_launched = false;
 };
 
 namespace {
@@ -103,6 +108,9 @@ void release(cfs_batch* b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->d_work) cudaFree(b->d_work);
     if (b->h_frames) cudaFreeHost(b->h_frames);
+    if (b->disp_done) cudaEventDestroy(b->disp_done);
+    if (b->d_disp) cudaFree(b->d_disp);
+    if (b->h_disp) cudaFreeHost(b->h_disp);
 }
 
 cfs_status capture(cfs_batch* b, int clear)
@@ -147,6 +155,51 @@ cfs_status capture(cfs_batch* b, int clear)
     return st;
 }
 }  // namespace
+
+namespace cfs {
+// Launch shape of the persistent batch program (also used by the compile-only
+// check); returns the privatized window's capacity in u32 counters.
+uint32_t batch_spec_defaults(ProgramSpec& sp)
+{
+    // measured on GB300: one 1024-thread CTA per SM sharing a ~208 KB
+    // privatized window beats smaller CTAs with smaller windows (the flush
+    // volume and the global-atomic share both shrink)
+    sp.block = 1024;
+    if (const char* e = std::getenv("CFS_BATCH_BLOCK")) {
+        const int v = std::atoi(e);
+        if (v == 128 || v == 256 || v == 512 || v == 1024) sp.block = v;
+    }
+    sp.min_blocks = std::max(1, 2048 / sp.block);
+    sp.spill_allowance = 64;
+    sp.depth_test = 1;
+    // privatized window: when the chain splats once, into a histogram
+    sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
+    // warp-level aggregation of equal window addresses (match.any) measured
+    // slower than plain shared atomics on the animation batch: off
+    sp.warp_agg = 0;
+    uint32_t tile_cap = sp.block >= 1024 ? 53248 : 8192;
+    if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
+    if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
+    // copies of small windows (one per warp) measured slower on the animation
+    // batch (the flush grows with the copies); kept as a knob
+    sp.tile_reps = 1;
+    if (const char* e = std::getenv("CFS_TILE_REPS")) sp.tile_reps = std::max(1, std::atoi(e));
+    // two trajectories per thread: 755 vs 764 ms for the 256-frame batch
+    sp.ilp = 2;
+    if (const char* e = std::getenv("CFS_BATCH_ILP")) sp.ilp = std::atoi(e) == 2 ? 2 : 1;
+    if (const char* e = std::getenv("CFS_TILE_CAP")) {
+        const int c = std::atoi(e);
+        if (c >= 256 && c <= 53248) tile_cap = (uint32_t)c;
+    }
+    if (!sp.tile) { sp.warp_agg = 0; tile_cap = 0; }
+    sp.dyn_smem = (int)(tile_cap * sizeof(uint32_t));
+    // a window above half of the SM's shared memory leaves room for one CTA
+    // per SM: asking for two would only cap the registers (and spill)
+    if (sp.dyn_smem > 112 * 1024) sp.min_blocks = 1;
+    if (const char* e = std::getenv("CFS_BATCH_MINB")) sp.min_blocks = std::max(1, std::atoi(e));
+    return tile_cap;
+}
+}  // namespace cfs
 
 extern "C" {
 
@@ -228,34 +281,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
             sp.splats.push_back(ss);
         }
     }
-    // measured on GB300: one 1024-thread CTA per SM sharing a ~208 KB
-    // privatized window beats smaller CTAs with smaller windows (the flush
-    // volume and the global-atomic share both shrink)
-    sp.block = 1024;
-    if (const char* e = std::getenv("CFS_BATCH_BLOCK")) {
-        const int v = std::atoi(e);
-        if (v == 128 || v == 256 || v == 512 || v == 1024) sp.block = v;
-    }
-    sp.min_blocks = std::max(1, 2048 / sp.block);
-    sp.spill_allowance = 64;
-    sp.depth_test = 1;
-    if (const char* e = std::getenv("CFS_BATCH_MINB")) sp.min_blocks = std::max(1, std::atoi(e));
-    // privatized window: when the chain splats once, into a histogram
-    sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
-    sp.warp_agg = 1;
-    b->tile_cap = sp.block >= 1024 ? 53248 : 8192;
-    if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
-    if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
-    // copies of small windows (one per warp) measured slower on the animation
-    // batch (the flush grows with the copies); kept as a knob
-    sp.tile_reps = 1;
-    if (const char* e = std::getenv("CFS_TILE_REPS")) sp.tile_reps = std::max(1, std::atoi(e));
-    if (const char* e = std::getenv("CFS_TILE_CAP")) {
-        const int c = std::atoi(e);
-        if (c >= 256 && c <= 53248) b->tile_cap = (uint32_t)c;
-    }
-    if (!sp.tile) { sp.warp_agg = 0; b->tile_cap = 0; }
-    sp.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
+    b->tile_cap = batch_spec_defaults(sp);
     st = get_kernel(sp, "cfs_batch_kernel", &b->kernel);
     if (st != CFS_OK) { delete b; return st; }
     if (sp.tile) {
@@ -401,10 +427,69 @@ cfs_status cfs_batch_info(const cfs_batch* b, uint32_t* n_items, uint32_t* chunk
     return CFS_OK;
 }
 
+cfs_status cfs_batch_display(cfs_batch* b, int slot, const cfs_display_params* params,
+                             uint32_t* const* outs, float* a_max_out, void* stream)
+{
+    clear_error();
+    if (!b || !outs) return fail(CFS_ERR_INVALID_ARG, "NULL batch or outs");
+    cfs_status st = display_params_check(params);
+    if (st != CFS_OK) return st;
+    if (slot < 0 || slot >= b->n_targets)
+        return fail(CFS_ERR_INVALID_ARG, "slot names no target of the batch");
+    if (a_max_out && ((uintptr_t)a_max_out) % 4 != 0)
+        return fail(CFS_ERR_INVALID_ARG, "a_max_out must be 4-byte aligned");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(CFS_ERR_INVALID_ARG, "batch belongs to another device");
+    for (int f = 0; f < b->n_frames; ++f) {
+        std::ostringstream m;
+        m << "frame " << f;
+        st = display_check(b->frames[f].targets[slot], outs[f], m.str().c_str());
+        if (st != CFS_OK) return st;
+    }
+    const size_t lbytes = sizeof(DisplayLayer) * (size_t)b->n_frames;
+    const size_t off_amax = (lbytes + 255) & ~(size_t)255;
+    if (!b->d_disp) {
+        st = check_cuda(cudaMalloc(&b->d_disp, off_amax + sizeof(float) * (size_t)b->n_frames),
+                        "cudaMalloc(display workspace)");
+        if (st == CFS_OK)
+            st = check_cuda(cudaMallocHost(&b->h_disp, lbytes), "cudaMallocHost(display)");
+        if (st == CFS_OK)
+            st = check_cuda(cudaEventCreateWithFlags(&b->disp_done, cudaEventDisableTiming),
+                            "cudaEventCreate");
+        if (st != CFS_OK) return st;
+    }
+    // the staging buffer is read by the previous display's upload: wait for it
+    if (b->disp_launched) {
+        st = check_cuda(cudaEventSynchronize(b->disp_done), "cudaEventSynchronize");
+        if (st != CFS_OK) return st;
+    }
+    uint64_t items = 0;
+    bool density = false;
+    for (int f = 0; f < b->n_frames; ++f) {
+        const cfs_target& t = b->frames[f].targets[slot];
+        items += display_fill(t, outs[f], (uint32_t)items, &b->h_disp[f]);
+        if (items >= (1ull << 31)) return fail(CFS_ERR_INVALID_ARG, "too many pixels");
+        density = density || t.kind != CFS_TARGET_DEPTH_U64;
+    }
+    DisplayLayer* d_layers = reinterpret_cast<DisplayLayer*>(b->d_disp);
+    float* amax = a_max_out ? a_max_out : reinterpret_cast<float*>(b->d_disp + off_amax);
+    st = check_cuda(cudaMemcpyAsync(d_layers, b->h_disp, lbytes, cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream),
+                    "cudaMemcpyAsync(display layers)");
+    if (st != CFS_OK) return st;
+    st = display_enqueue(nullptr, d_layers, b->n_frames, (uint32_t)items, density, amax, *params,
+                         (cudaStream_t)stream);
+    if (st != CFS_OK) return st;
+    b->disp_launched = true;
+    return check_cuda(cudaEventRecord(b->disp_done, (cudaStream_t)stream), "cudaEventRecord");
+}
+
 cfs_status cfs_batch_destroy(cfs_batch* b)
 {
     if (!b) return CFS_OK;
     if (b->launched) cudaEventSynchronize(b->done);
+    if (b->disp_launched) cudaEventSynchronize(b->disp_done);
     release(b);
     delete b;
     return CFS_OK;

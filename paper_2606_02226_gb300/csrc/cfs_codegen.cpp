@@ -21,7 +21,7 @@ std::string ProgramSpec::key() const
     s << "m" << int(mode) << ".d" << dim << ".n" << n_maps << ".c" << n_cmp << ".r" << reuse
       << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << "."
       << spill_allowance << ".p" << tile << warp_agg << "." << tile_reps << ".f" << fast_trig
-      << ".u" << unroll << ".k";
+      << ".u" << unroll << ".i" << ilp << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
     for (int j = 0; j < n_ops; ++j) s << op_kind[j] << (op_kind[j] == CFS_OP_ROTATE3 ? "r" : "")
@@ -171,6 +171,7 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_REUSE " << (sp.reuse ? 1 : 0) << "\n";
     s << "#define CFS_FAST_TRIG " << (sp.fast_trig ? 1 : 0) << "\n";
     s << "#define CFS_UNROLL " << sp.unroll << "\n";
+    s << "#define CFS_ILP " << (sp.ilp == 2 ? 2 : 1) << "\n";
     s << "#define CFS_BATCH " << (sp.mode == Mode::Batch ? 1 : 0) << "\n";
     s << "#define CFS_CLOUD " << (sp.mode == Mode::Cloud ? 1 : 0) << "\n";
     s << "#define CFS_TILE " << (sp.tile ? 1 : 0) << "\n";

@@ -63,6 +63,7 @@ struct ProgramSpec {
     int tile_reps = 1;         // at most this many copies of a small window
     int fast_trig = 0;         // chain trigonometry: reduced argument + hardware sin/cos
     int unroll = 4;            // copies of the step code in the step loop (4, 2, 1)
+    int ilp = 1;               // batch: trajectories stepped together per thread (1, 2)
     int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
 
     std::string key() const;
@@ -89,6 +90,36 @@ cfs_status launch(const Kernel& k, unsigned grid, const void* args, size_t args_
                   cudaStream_t stream);
 cfs_status check_cuda(cudaError_t e, const char* what);
 int device_sm_count();
+
+// Launch shape of the persistent batch program (block, occupancy, privatized
+// window, warp aggregation, ILP; environment knobs); returns the window's
+// capacity in u32 counters and sets dyn_smem.
+uint32_t batch_spec_defaults(ProgramSpec& sp);
+
+// ---- density-estimation display (cfs_display.cu) ---------------------------
+// One layer as the display kernels read it.  Work is cut into items of
+// kDisplayPxPerItem pixels numbered layer by layer from item_begin.
+constexpr uint32_t kDisplayPxPerItem = 8192;
+struct DisplayLayer {
+    unsigned long long data;   // device pointer of the layer
+    unsigned long long out;    // device u32 [H][W]
+    uint32_t n_px;             // W * H
+    int32_t kind, C;           // cfs_target_kind, histogram channels
+    uint32_t item_begin;
+    float pal[CFS_MAX_MAPS][4];
+};
+// Checks display parameters (gamma, brightness > 0, finite a_max).
+cfs_status display_params_check(const cfs_display_params* p);
+// Checks a layer description and its output for the display calls.
+cfs_status display_check(const cfs_target& t, const void* out, const char* what);
+// Fills d from a target; returns the layer's work items.
+uint32_t display_fill(const cfs_target& t, uint32_t* out, uint32_t item_begin, DisplayLayer* d);
+// Enqueues the maximum (when params.a_max <= 0 and some layer is not a depth
+// layer; a_max is zeroed first) and mapping kernels over n_items items.
+// Either `one` (a single layer, by value) or `layers` (device array) is used.
+cfs_status display_enqueue(const DisplayLayer* one, const DisplayLayer* layers, int n_layers,
+                           uint32_t n_items, bool any_density, float* a_max,
+                           const cfs_display_params& p, cudaStream_t stream);
 
 // ---- host-side tables ---------------------------------------------------
 void philox_round_keys(uint64_t seed, unsigned int rk[10][2]);

@@ -135,6 +135,37 @@ __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH
     }
 }
 
+#if CFS_BATCH && CFS_ILP == 2
+/* cfs_run_point for two points i0, i1 at once: step n of both before step
+ * n + 1 of either.  Each point still follows exactly its own Philox stream,
+ * so the results equal two cfs_run_point calls. */
+template <class CH, class TG>
+__device__ __forceinline__ void cfs_run_point2(const cfs_launch_args& a, const CH& choose,
+                                               const TG& tg, const CfsSmem& sm, u32 i0, u32 i1,
+                                               u32 sid, float& x0, float& y0, float& z0,
+                                               float& x1, float& y1, float& z1, u32* disc,
+                                               const CfsTile& tile)
+{
+    const u32 b0 = a.step_begin, b1 = a.iters;
+    const bool whole = ((b0 | b1) & 3u) == 0u;
+#pragma unroll 1
+    for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
+        const uint4 r0 = cfs_philox(a, i0, nb, sid, 0u);
+        const uint4 r1 = cfs_philox(a, i1, nb, sid, 0u);
+        const u32 n = nb << 2;
+        const u32 w0[4] = {r0.x, r0.y, r0.z, r0.w};
+        const u32 w1[4] = {r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (whole || (n + q >= b0 && n + q < b1)) {
+                cfs_step(a, choose, tg, sm, n + q, w0[q], x0, y0, z0, disc, tile);
+                cfs_step(a, choose, tg, sm, n + q, w1[q], x1, y1, z1, disc, tile);
+            }
+        }
+    }
+}
+#endif
+
 #if CFS_CLOUD
 /* Stored point cloud (Section 3: "store all points ... then transform"):
  * point i runs steps 0 .. iters-1 from its Philox start point; its final
@@ -506,24 +537,46 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 j1 = min(j0 + s_chunk, s_npts);
         const float* st = s_start;
         const u32 sc = s_scount;
-        for (u32 j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            const u32 i = pbeg + j;
-            float x, y, z;
+        const u32 npts = s_npts;
+        /* start of point j of the frame: the frame's own start points (e.g.
+         * a learned warm start), reused cyclically when there are fewer than
+         * points, or the Philox start block */
+        auto start_of = [&](u32 j, float& x, float& y, float& z) {
             if (st) {
-                /* the frame's own start points (e.g. a learned warm start),
-                 * reused cyclically when there are fewer than points */
-                const u32 js = sc < s_npts ? j % sc : j;
+                const u32 js = sc < npts ? j % sc : j;
                 x = st[js];
                 y = st[(size_t)sc + js];
                 z = CFS_DIM == 3 ? st[2 * (size_t)sc + js] : 0.0f;
             } else {
-                const uint4 r = cfs_philox(a, i, 0u, sid, 1u);
+                const uint4 r = cfs_philox(a, pbeg + j, 0u, sid, 1u);
                 x = (float)(r.x >> 8) * CFS_INV_2_24;
                 y = (float)(r.y >> 8) * CFS_INV_2_24;
                 z = CFS_DIM == 3 ? (float)(r.z >> 8) * CFS_INV_2_24 : 0.0f;
             }
-            cfs_run_point(a, choose, s_tg, sm, i, sid, x, y, z, disc, tile);
+        };
+#if CFS_ILP == 2
+        /* two trajectories per thread, stepped in lockstep: their
+         * independent dependency chains hide each other's latency */
+        for (u32 j = j0 + threadIdx.x; j < j1; j += 2 * blockDim.x) {
+            const u32 j2 = j + blockDim.x;
+            float x, y, z;
+            start_of(j, x, y, z);
+            if (j2 < j1) {
+                float x2, y2, z2;
+                start_of(j2, x2, y2, z2);
+                cfs_run_point2(a, choose, s_tg, sm, pbeg + j, pbeg + j2, sid, x, y, z, x2, y2,
+                               z2, disc, tile);
+            } else {
+                cfs_run_point(a, choose, s_tg, sm, pbeg + j, sid, x, y, z, disc, tile);
+            }
         }
+#else
+        for (u32 j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            float x, y, z;
+            start_of(j, x, y, z);
+            cfs_run_point(a, choose, s_tg, sm, pbeg + j, sid, x, y, z, disc, tile);
+        }
+#endif
         __syncthreads();
     }
     if (cur >= 0) {

@@ -292,3 +292,37 @@ def uniform_points(n: int, dim: int, seed: int) -> np.ndarray:
     stored clouds in tests."""
     rng = np.random.default_rng([seed, 7006])
     return rng.uniform(0.0, 1.0, size=(n, dim)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# synthetic accumulated layers (inputs of the display, drawn directly: heavy-
+# tailed splat counts with empty pixels, as a chaos-game layer has them)
+# ---------------------------------------------------------------------------
+def synthetic_layer(kind: str, W: int, H: int, C: int = 4, seed: int = 0,
+                    empty: float = 0.3) -> np.ndarray:
+    """A seeded layer of the given kind: hist_u32 -> uint32 [C, H, W] counts
+    (log-normal, a fraction `empty` of pixels zero in every channel);
+    rgba_f32 -> float32 [H, W, 4] with alpha an integer count and R, G, B
+    multiples of 1/2 in [0, alpha]; depth_u64 -> uint64 [H, W] keys of
+    positive depths with random colours, `empty` of them all ones."""
+    rng = np.random.default_rng([seed, 7011, W, H])
+    zero = rng.random((H, W)) < empty
+    if kind == "hist_u32":
+        n = np.floor(np.exp(rng.normal(1.5, 1.8, size=(C, H, W)))).astype(np.uint32)
+        n[:, zero] = 0
+        return n
+    if kind == "rgba_f32":
+        a = np.floor(np.exp(rng.normal(2.0, 1.8, size=(H, W)))).astype(np.float64)
+        a[zero] = 0
+        out = np.zeros((H, W, 4), dtype=np.float32)
+        for c in range(3):
+            out[..., c] = np.floor(rng.random((H, W)) * (2 * a + 1)) / 2
+        out[..., 3] = a
+        return out
+    if kind == "depth_u64":
+        z = rng.uniform(0.5, 20.0, size=(H, W)).astype(np.float32)
+        col = rng.integers(0, 2**32, size=(H, W), dtype=np.uint64)
+        keys = (z.view(np.uint32).astype(np.uint64) << np.uint64(32)) | col
+        keys[zero] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        return keys
+    raise ValueError(kind)

@@ -54,28 +54,33 @@ def _host(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("tile_cap,warp_agg,use_tile", [("8192", "1", "1"), ("256", "1", "1"),
-                                                       ("1024", "0", "1"), ("8192", "1", "0")])
+@pytest.mark.parametrize("tile_cap,warp_agg,use_tile,ilp,iters",
+                         [("8192", "1", "1", "1", 60), ("256", "1", "1", "1", 60),
+                          ("1024", "0", "1", "1", 60), ("8192", "1", "0", "1", 60),
+                          ("8192", "1", "1", "2", 60), ("256", "1", "1", "2", 63),
+                          ("8192", "1", "0", "2", 61)])
 def test_batch_matches_oracle_frame_by_frame(torch_cuda, monkeypatch, tile_cap, warp_agg,
-                                             use_tile):
+                                             use_tile, ilp, iters):
     # the privatized window at its default size, at a size smaller than most
     # attractors (splats split between shared and global memory), without
-    # warp aggregation, and switched off
+    # warp aggregation, and switched off; one or two trajectories per thread
+    # (with step counts that cut the last Philox block)
     monkeypatch.setenv("CFS_TILE_CAP", tile_cap)
     monkeypatch.setenv("CFS_WARP_AGG", warp_agg)
     monkeypatch.setenv("CFS_TILE", use_tile)
+    monkeypatch.setenv("CFS_BATCH_ILP", ilp)
     frames = W.animation_frames(n_frames=14, seed=2, min_log2=8, max_log2=12,
                                 resolutions=(64, 128))
     cfs, chain, items, descs, tens = _setup(frames)
-    b = cfs.Batch(chain, items, iters=60, burn_in=20, seed=4)
+    b = cfs.Batch(chain, items, iters=iters, burn_in=20, seed=4)
     info = b.info()
     assert info["n_items"] >= len(frames) and info["grid"] >= 1
     b.launch(clear=True)
     torch_cuda.cuda.synchronize()
-    ref, rdisc = _oracle(frames, descs, 60, 20, 4)
+    ref, rdisc = _oracle(frames, descs, iters, 20, 4)
     for f in range(len(frames)):
         assert np.array_equal(_host(tens[f]), ref[f]), f
-        assert int(_host(tens[f]).sum()) == frames[f].n_points * 40
+        assert int(_host(tens[f]).sum()) == frames[f].n_points * (iters - 20)
     assert list(b.discards()[:, 0]) == rdisc == [0] * len(frames)
 
 

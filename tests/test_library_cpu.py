@@ -134,3 +134,22 @@ def test_codegen_is_structural():
     b = cfs.codegen_check(cfs.System(sq), cfs.Chain([W.Op("splat", (0,))], 2),
                           [W.Target("hist_u32", 512, 512, 4, (-1, 2, -1, 2))])[0]
     assert a == b
+
+
+def test_display_argument_errors_need_no_gpu():
+    L = cfs.lib()
+    arr, _ = cfs.make_targets([W.Target("rgba_f32", 16, 16, 1)], fake_ptr=True)
+    p = cfs._display_params(2.2, 1.0, 0.0, 0)
+
+    def call(params, out, amax):
+        return L.cfs_tonemap(arr, ctypes.byref(params), out, amax, None)
+
+    assert call(cfs._display_params(0.0, 1.0, 0.0, 0), 1 << 20, 1 << 21) == 1   # gamma
+    assert call(cfs._display_params(2.2, -1.0, 0.0, 0), 1 << 20, 1 << 21) == 1  # brightness
+    assert call(cfs._display_params(2.2, 1.0, float("nan"), 0), 1 << 20, 1 << 21) == 1
+    assert call(p, None, 1 << 21) == 1               # no output
+    assert call(p, (1 << 20) + 4, 1 << 21) == 1      # misaligned output
+    assert call(p, 256, 1 << 21) == 1                # output overlaps the layer
+    assert call(p, 1 << 20, None) == 1               # maximum wanted, nowhere to put it
+    assert L.cfs_tonemap(None, ctypes.byref(p), 1 << 20, 1 << 21, None) == 1
+    assert L.cfs_batch_display(None, 0, ctypes.byref(p), None, None, None) == 1

@@ -346,8 +346,9 @@ def run_cfs(args, wl):
     launch_ms = mean_render / len(jobs)
     splat_steps_per_launch = wl.splat_steps / len(jobs)
     traffic = None
+    program_sha1 = render_program_sha1(cfs, wl, args.fast_trig)
     if RENDER_TRAFFIC_BYTES is not None and wl.jobs[0].n_points == (1 << 21):
-        if render_program_sha1(cfs, wl, args.fast_trig) == RENDER_TRAFFIC_SOURCE_SHA1:
+        if program_sha1 == RENDER_TRAFFIC_SOURCE_SHA1:
             traffic = RENDER_TRAFFIC_BYTES
     ops_per_launch = SPLAT_OPS_PER_SPLAT_STEP * splat_steps_per_launch
     achieved = ops_per_launch / (launch_ms * 1e-3) / 1e9
@@ -364,7 +365,7 @@ def run_cfs(args, wl):
             "roofline": {"bound": "l2_atomic", "achieved": achieved, "peak": peak,
                          "unit": "Gop/s", "frac": achieved / peak, "traffic": traffic,
                          "traffic_unit": "DRAM bytes per launch (ncu)",
-                         "kernel": "cfs_render_kernel",
+                         "kernel": "cfs_render_kernel", "program_sha1": program_sha1,
                          "peak_source": "measured live: library atomic microbenchmark "
                                         "(uniform random addresses, same footprints)",
                          "peaks_gops": peaks},

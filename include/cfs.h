@@ -343,16 +343,19 @@ uint32_t cfs_sampler_param_count(void);
 cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** out);
 cfs_status cfs_sampler_destroy(cfs_sampler* s);
 /* Host copies of the parameters, Adam moments and step (any may be NULL):
- * a checkpoint.  Synchronizes the device. */
+ * a checkpoint.  Synchronizes the device.  Returns CFS_ERR_TIMEOUT (once) if
+ * a tensor-core GEMM of earlier work gave up waiting on its pipeline barrier
+ * (bounded waits; the affected results are then incomplete). */
 cfs_status cfs_sampler_get_params(const cfs_sampler* s, float* params, float* adam_m,
                                   float* adam_v, uint32_t* step);
 /* Restores a checkpoint (moments may be NULL: left as they are). */
 cfs_status cfs_sampler_set_params(cfs_sampler* s, const float* params, const float* adam_m,
                                   const float* adam_v, uint32_t step);
-/* Y (device f32 [B][2]) = network(U), U device BF16 [B][64]. */
+/* Y (device f32 [B][2]) = network(U), U device BF16 [B][64], 16-byte aligned
+ * (the tensor-core GEMMs read it in 16-byte vectors). */
 cfs_status cfs_sampler_forward(cfs_sampler* s, const void* U, uint32_t B, float* Y, void* stream);
-/* Adds to `grads` (device f32 [param_count]) the gradient of sum(dY * Y)
- * (dY device f32 [B][2]) with respect to every parameter. */
+/* Adds to `grads` (device f32 [param_count], 16-byte aligned) the gradient
+ * of sum(dY * Y) (dY device f32 [B][2]) with respect to every parameter. */
 cfs_status cfs_sampler_backward(cfs_sampler* s, const void* U, uint32_t B, const float* dY,
                                 float* grads, void* stream);
 /* Sliced-Wasserstein loss of point sets X against T (device f32

@@ -10,7 +10,10 @@
 //
 // Network: u (64) -> 128 -> 128 -> 128 -> 2, SiLU after the first three
 // layers; BF16 weights and activations, FP32 accumulation on the tensor
-// cores (mma.sync m16n8k16 bf16), FP32 master weights and Adam state.
+// cores, FP32 master weights and Adam state.  Training runs its GEMMs on the
+// fifth-generation tensor cores (tcgen05.mma, accumulators in tensor
+// memory); the fused inference kernel keeps its small per-point products in
+// registers (mma.sync m16n8k16 bf16).
 //
 // Parameter vector (FP32, this order): W1 [128][64], b1 [128], W2 [128][128],
 // b2, W3 [128][128], b3, W4 [2][128], b4 [2] -- 41602 floats.
@@ -60,152 +63,409 @@ __device__ __forceinline__ float silu_grad_f(float z)
 }
 
 // ---------------------------------------------------------------------------
-// GEMM: C[M][N] = op(A)[M][K] op(B)[K][N], BF16 in, FP32 accumulate.
-//   op(A)(m, k) = transA ? A[k * lda + m] : A[m * lda + k]
-//   op(B)(k, n) = transB ? B[n * ldb + k] : B[k * ldb + n]
-// Tiles of 64 x 128 (8 warps, each 16 x 64), K in steps of 32 staged in
-// shared memory as [m][k] and [n][k] (rows padded to 80 bytes: ldmatrix
-// reads are conflict-free), fragments by ldmatrix, mma.sync m16n8k16.
+// GEMM on the fifth-generation tensor cores:
+//   D[M][N] = A[M][K] B[N][K]^T,  A and B BF16 and K-major in global memory,
+//   D accumulated in FP32 in tensor memory (TMEM).
+// CTA tile: 128 rows x the whole width N (64 or 128).  K runs in chunks of
+// 64, staged by the CTA's 128 threads into shared memory in the no-swizzle
+// K-major layout of 8-row x 16-byte core matrices (K-adjacent cores 128 B
+// apart, 8-row groups 1024 B apart).  Two stages: while the tensor core
+// multiplies chunk c, the threads stage chunk c + 1.  Thread 0 issues the
+// four tcgen05.mma of a chunk (M = 128, N, K = 16 each) and commits them to
+// the stage's mbarrier; the stage is refilled only after that barrier
+// completes.  The epilogue reads the accumulator with tcgen05.ld: warp w
+// owns TMEM lanes 32w..32w+31, so every thread holds one output row.
+// Every wait is bounded: on a time-out the CTA records it in g_tc_error,
+// skips its epilogue, frees its TMEM and returns.
 // ---------------------------------------------------------------------------
-enum Epi { EPI_STORE = 0, EPI_SILU = 1, EPI_SILU_GRAD = 2, EPI_ATOMIC = 3 };
+enum Epi { EPI_SILU = 1, EPI_SILU_GRAD = 2, EPI_ATOMIC = 3 };
 
-struct GemmArgs {
-    int M, N, K;
-    const bf16r* A;
-    int lda, transA;
-    const bf16r* B;
-    int ldb, transB;
-    int k_split;          // K range per blockIdx.z
+constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 256;
+constexpr int TC_NV = 128 * 8 / TC_THREADS;   // 16-byte vectors per thread per operand tile
+constexpr int TC_TILE_BYTES = 128 * TC_K * 2;             // 16 KB: 128 rows x 64 K
+constexpr int TC_SMEM = 4 * TC_TILE_BYTES + 1024 + 1024;  // 2 stages x (A, B), barriers, align
+constexpr u32 TC_WAIT_LIMIT = 1u << 24;
+constexpr int TC_COPIES = 16;   // copies of the bias-gradient sums (spread the atomics)
+
+__device__ unsigned int g_tc_error = 0;
+
+struct TcArgs {
+    int M, N, K;                 // N in {64, 128}
+    const bf16r* A; int lda;     // [M][lda], K contiguous
+    const bf16r* B; int ldb;     // [N][ldb], K contiguous
+    int k_split;                 // K per blockIdx.z, a multiple of TC_K
     int mode;
-    const float* bias;    // [N] or null
-    float* C;             // fp32 out (STORE, ATOMIC) or pre-activation out (SILU)
-    int ldc;
-    bf16r* H;             // bf16 out (SILU: activation, SILU_GRAD: dZ)
-    int ldh;
-    const float* Zin;     // SILU_GRAD: pre-activation
-    int ldz;
-    float* colsum;        // SILU_GRAD: bias gradient (atomic)
+    const float* bias;           // SILU: [N]
+    float* C; int ldc;           // SILU: pre-activation Z out; ATOMIC: C += D
+    bf16r* H; int ldh;           // SILU: activation out; SILU_GRAD: dZ out
+    bf16r* HT; int ldt;          // SILU, SILU_GRAD: transposed copy [N][ldt] (or null)
+    const float* Zin; int ldz;   // SILU_GRAD: pre-activation of the layer
+    float* colsum;               // SILU_GRAD: bias gradient partials, [TC_COPIES][N]; CTA b
+                                 // adds its column sums into copy b % TC_COPIES
 };
 
-constexpr int BM = 64, BN = 128, BK = 32, SPAD = 8;
-
-__device__ __forceinline__ void ldsm_x4(u32 (&r)[4], const void* p)
+__device__ __forceinline__ u32 smem_addr(const void* p)
 {
-    const u32 a = (u32)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
+    return (u32)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const u32 (&a)[4], u32 b0, u32 b1)
+// shared-memory matrix descriptor: start address, leading (K) byte offset
+// 128, stride (8-row group) byte offset 1024, descriptor version 1 (bit 46),
+// base offset 0, no swizzle
+__device__ __forceinline__ u64 tc_desc(u32 saddr)
+{
+    return (u64)((saddr >> 4) & 0x3FFFu) | ((u64)(128u >> 4) << 16) |
+           ((u64)(1024u >> 4) << 32) | ((u64)1 << 46);
+}
+
+// instruction descriptor of kind::f16: D F32 (bit 4), A and B BF16 (bits 7,
+// 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__device__ __forceinline__ u32 tc_idesc(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((u32)(N >> 3) << 17) |
+           ((u32)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(u32 d_tmem, u64 adesc, u64 bdesc, u32 idesc, u32 acc)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
-        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
-__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g)
+__device__ __forceinline__ void tc_commit(u32 bar)
 {
-    __shared__ __align__(16) bf16r sA[BM][BK + SPAD];
-    __shared__ __align__(16) bf16r sB[BN][BK + SPAD];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp & 3, wn = warp >> 2;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :
+                 : "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(u32 bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" : : "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
+{
+    for (u32 it = 0; it < TC_WAIT_LIMIT; ++it) {
+        u32 done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld16(u32 taddr, float (&v)[16])
+{
+    u32 r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Staging of rows row0 .. row0 + n_rows - 1 (those < rows_valid), K columns
+// k0 .. k0 + 63 (those < k_end) of a K-major BF16 matrix into the core-matrix
+// layout, zeros elsewhere.  Vector v -> row (v / 64) * 8 + v % 8, K group
+// (v / 8) % 8, so each 8-lane phase of a warp writes one contiguous 128-byte
+// core matrix.  Two phases -- every load of the tile first, then the shared
+// stores -- keep TC_NV loads per thread in flight.
+__device__ __forceinline__ void tc_stage_load(uint4 (&val)[TC_NV], const bf16r* src, int ld,
+                                              int rows_valid, int row0, int n_rows, int k0,
+                                              int k_end)
+{
+#pragma unroll
+    for (int i = 0; i < TC_NV; ++i) {
+        const int v = (int)threadIdx.x + i * TC_THREADS;
+        const int r = ((v >> 6) << 3) | (v & 7), k8 = (v >> 3) & 7;
+        const int gr = row0 + r, gk = k0 + 8 * k8;
+        val[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (v < n_rows * 8 && gr < rows_valid && gk < k_end) {
+            const bf16r* p = src + (size_t)gr * ld + gk;
+            if (gk + 8 <= k_end) {
+                val[i] = __ldg(reinterpret_cast<const uint4*>(p));
+            } else {
+                u32 w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (gk + e < k_end) w[e >> 1] |= (u32)p[e] << (16 * (e & 1));
+                val[i] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tc_stage_store(u32 dst, const uint4 (&val)[TC_NV], int n_rows)
+{
+#pragma unroll
+    for (int i = 0; i < TC_NV; ++i) {
+        const int v = (int)threadIdx.x + i * TC_THREADS;
+        if (v < n_rows * 8) {
+            const int r = ((v >> 6) << 3) | (v & 7), k8 = (v >> 3) & 7;
+            const u32 a = dst + (u32)((r >> 3) * 1024 + k8 * 128 + (r & 7) * 16);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                         :
+                         : "r"(a), "r"(val[i].x), "r"(val[i].y), "r"(val[i].z), "r"(val[i].w)
+                         : "memory");
+        }
+    }
+}
+
+__device__ __forceinline__ u32 pack_bf16x2(float a, float b)
+{
+    return (u32)to_bf16(a) | ((u32)to_bf16(b) << 16);
+}
+
+// pre-activations of columns c0 .. c0 + 15 of this thread's row (SILU_GRAD)
+__device__ __forceinline__ void tc_load_z(const TcArgs& g, int row, int c0, float (&z)[16])
+{
+    if (g.mode != EPI_SILU_GRAD || row >= g.M) return;
+    const float4* zp = reinterpret_cast<const float4*>(g.Zin + (size_t)row * g.ldz + c0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 t = __ldg(zp + q);
+        z[4 * q] = t.x; z[4 * q + 1] = t.y; z[4 * q + 2] = t.z; z[4 * q + 3] = t.w;
+    }
+}
+
+__device__ __forceinline__ void tc_epilogue(const TcArgs& g, int row, int c0, const float (&v)[16],
+                                            const float (&zi)[16], float* s_col)
+{
+    const bool in = row < g.M;
+    if (g.mode == EPI_ATOMIC) {
+        if (in) {
+            float* c = g.C + (size_t)row * g.ldc + c0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cfs_red_add_v4f32(c + 4 * q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2],
+                                                         v[4 * q + 3]));
+        }
+        return;
+    }
+    float h[16];
+    if (g.mode == EPI_SILU) {
+        float z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            z[j] = v[j] + g.bias[c0 + j];
+            h[j] = silu_f(z[j]);
+        }
+        if (in) {
+            float4* zc = reinterpret_cast<float4*>(g.C + (size_t)row * g.ldc + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zc[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+        }
+    } else {   // EPI_SILU_GRAD
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] = in ? v[j] * silu_grad_f(zi[j]) : 0.0f;
+        // bias gradient: column sums over the warp's 32 rows, one atomic per column
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float s = h[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if ((threadIdx.x & 31) == 0 && s != 0.0f) atomicAdd(s_col + c0 + j, s);
+        }
+    }
+    if (in && g.H) {
+        uint4* hp = reinterpret_cast<uint4*>(g.H + (size_t)row * g.ldh + c0);
+        hp[0] = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
+                           pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
+        hp[1] = make_uint4(pack_bf16x2(h[8], h[9]), pack_bf16x2(h[10], h[11]),
+                           pack_bf16x2(h[12], h[13]), pack_bf16x2(h[14], h[15]));
+    }
+    if (in && g.HT) {
+        // consecutive lanes hold consecutive rows: each column's stores coalesce
+#pragma unroll
+        for (int j = 0; j < 16; ++j) g.HT[(size_t)(c0 + j) * g.ldt + row] = to_bf16(h[j]);
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_constant__ TcArgs g)
+{
+    extern __shared__ unsigned char tc_smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+    // stage s: A at sm + 2 s TILE, B right after it
+    u64* bars = reinterpret_cast<u64*>(sm + 4 * TC_TILE_BYTES);
+    u32* s_tmem = reinterpret_cast<u32*>(sm + 4 * TC_TILE_BYTES + 64);
+    float* s_col = reinterpret_cast<float*>(sm + 4 * TC_TILE_BYTES + 128);   // [128]
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.x * TC_M;
     const int kb = blockIdx.z * g.k_split;
     const int ke = min(g.K, kb + g.k_split);
-    float acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    const int n_chunks = ke > kb ? (ke - kb + TC_K - 1) / TC_K : 0;
+    const u32 ncols = g.N <= 64 ? 64u : 128u;
+    const u32 bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
 
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        // stage op(A) tile as [m][k]; consecutive threads walk the
-        // contiguous dimension of the source
-        for (int e = threadIdx.x; e < BM * BK; e += blockDim.x) {
-            int r, c;
-            if (g.transA) { r = e % BM; c = e / BM; } else { r = e / BK; c = e % BK; }
-            const int m = m0 + r, k = k0 + c;
-            bf16r v = 0;
-            if (m < g.M && k < ke)
-                v = g.transA ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
-            sA[r][c] = v;
-        }
-        for (int e = threadIdx.x; e < BN * BK; e += blockDim.x) {
-            int r, c;
-            if (g.transB) { r = e / BK; c = e % BK; } else { r = e % BN; c = e / BN; }
-            const int n = n0 + r, k = k0 + c;
-            bf16r v = 0;
-            if (n < g.N && k < ke)
-                v = g.transB ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
-            sB[r][c] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            u32 a[4];
-            ldsm_x4(a, &sA[wm * 16 + (lane & 15)][kk + (lane >> 4) * 8]);
-#pragma unroll
-            for (int nt = 0; nt < 8; nt += 2) {
-                u32 b[4];
-                const int nrow = wn * 64 + nt * 8 + (lane & 7) + ((lane >> 4) << 3);
-                const int kcol = kk + ((lane >> 3) & 1) * 8;
-                ldsm_x4(b, &sB[nrow][kcol]);
-                mma_bf16(acc[nt], a, b[0], b[1]);
-                mma_bf16(acc[nt + 1], a, b[2], b[3]);
-            }
-        }
-        __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"(smem_addr(s_tmem)), "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (tid < 128) s_col[tid] = 0.0f;
+    if (tid == 0) {
+        mbar_init(bar0, 1u);
+        mbar_init(bar1, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const u32 tmem = *s_tmem;
+    const u32 idesc = tc_idesc(g.N);
 
-    // epilogue: thread (g, t) holds rows g, g + 8 and columns 2t, 2t + 1 of
-    // each 16 x 8 tile
-    const int gq = lane >> 2, tq = lane & 3;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        float cs[2] = {0.0f, 0.0f};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int row = m0 + wm * 16 + gq + 8 * h;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int col = n0 + wn * 64 + nt * 8 + 2 * tq + q;
-                const float v = acc[nt][2 * h + q];
-                const bool in = row < g.M && col < g.N;
-                if (g.mode == EPI_STORE) {
-                    if (in) g.C[(size_t)row * g.ldc + col] = v + (g.bias ? g.bias[col] : 0.0f);
-                } else if (g.mode == EPI_SILU) {
-                    if (in) {
-                        const float z = v + g.bias[col];
-                        g.C[(size_t)row * g.ldc + col] = z;
-                        g.H[(size_t)row * g.ldh + col] = to_bf16(silu_f(z));
-                    }
-                } else if (g.mode == EPI_SILU_GRAD) {
-                    float d = 0.0f;
-                    if (in) {
-                        d = v * silu_grad_f(g.Zin[(size_t)row * g.ldz + col]);
-                        g.H[(size_t)row * g.ldh + col] = to_bf16(d);
-                    }
-                    cs[q] += d;
-                } else {
-                    if (in) atomicAdd(g.C + (size_t)row * g.ldc + col, v);
-                }
-            }
+    bool ok = true;
+    for (int c = 0; c < n_chunks; ++c) {
+        const int s = c & 1;
+        // the stage's previous chunk (c - 2) must have left the tensor core
+        if (c >= 2) ok = mbar_wait(s ? bar1 : bar0, (u32)((c - 2) >> 1) & 1u);
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        const int k0 = kb + c * TC_K;
+        const u32 sA = smem_addr(sm + 2 * s * TC_TILE_BYTES), sB = sA + TC_TILE_BYTES;
+        {
+            uint4 va[TC_NV], vb[TC_NV];
+            tc_stage_load(va, g.A, g.lda, g.M, m0, TC_M, k0, ke);
+            tc_stage_load(vb, g.B, g.ldb, g.N, 0, g.N, k0, ke);
+            tc_stage_store(sA, va, TC_M);
+            tc_stage_store(sB, vb, g.N);
         }
-        if (g.mode == EPI_SILU_GRAD) {
-            // column sums over the warp's 16 rows: reduce across gq
+        // generic-proxy stores -> visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                float s = cs[q];
-                s += __shfl_xor_sync(0xffffffffu, s, 4);
-                s += __shfl_xor_sync(0xffffffffu, s, 8);
-                s += __shfl_xor_sync(0xffffffffu, s, 16);
-                const int col = n0 + wn * 64 + nt * 8 + 2 * tq + q;
-                if (gq == 0 && col < g.N && s != 0.0f) atomicAdd(g.colsum + col, s);
-            }
+            for (int kk = 0; kk < TC_K / 16; ++kk)
+                tc_mma(tmem, tc_desc(sA + kk * 256), tc_desc(sB + kk * 256), idesc,
+                       (c > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(s ? bar1 : bar0);
         }
+    }
+    // epilogue split: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows)
+    // and the columns of half w / 4
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = m0 + quad * 32 + (tid & 31);
+    const int c_begin = half * (g.N / 2), c_end = c_begin + g.N / 2;
+    float z_next[16];
+    tc_load_z(g, row, c_begin, z_next);   // independent of the MMAs: overlaps them
+    if (ok && n_chunks > 0) {
+        const int last = n_chunks - 1;
+        ok = mbar_wait((last & 1) ? bar1 : bar0, (u32)(last >> 1) & 1u);
+    }
+    ok = __syncthreads_and(ok) != 0;
+    tc_fence_after();
+    if (ok && n_chunks > 0) {
+        const u32 lane_base = tmem + ((u32)(quad * 32) << 16);
+        for (int c0 = c_begin; c0 < c_end; c0 += 16) {
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) z[j] = z_next[j];
+            if (c0 + 16 < c_end) tc_load_z(g, row, c0 + 16, z_next);
+            float v[16];
+            tc_ld16(lane_base + (u32)c0, v);
+            tc_epilogue(g, row, c0, v, z, s_col);
+        }
+    } else if (!ok && tid == 0) {
+        atomicExch(&g_tc_error, 1u);
+        // give in-flight MMAs a bounded chance to drain before TMEM is freed
+        if (n_chunks > 0) {
+            const int last = n_chunks - 1;
+            mbar_wait((last & 1) ? bar1 : bar0, (u32)(last >> 1) & 1u);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // the CTA's bias-gradient column sums: one atomic per column into copy
+    // blockIdx.x % TC_COPIES
+    if (g.mode == EPI_SILU_GRAD && ok && tid < g.N && s_col[tid] != 0.0f)
+        atomicAdd(g.colsum + (blockIdx.x % TC_COPIES) * g.N + tid, s_col[tid]);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :
+                     : "r"(tmem), "r"(ncols)
+                     : "memory");
+    }
+}
+
+// output layer forward Y = H3 W4^T + b4 (N = 2: a dot product per output,
+// not a tensor-core shape): one thread per row
+__global__ void __launch_bounds__(256) out_forward_kernel(const bf16r* __restrict__ H3,
+                                                          const bf16r* __restrict__ wb,
+                                                          const float* __restrict__ w, int B,
+                                                          float* Y)
+{
+    __shared__ float w4[D_OUT][HID];
+    for (int e = threadIdx.x; e < D_OUT * HID; e += blockDim.x)
+        w4[e / HID][e % HID] = from_bf16(wb[OFF_W4 + e]);
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B) return;
+    const uint4* h = reinterpret_cast<const uint4*>(H3 + (size_t)r * HID);
+    float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll 4
+    for (int q = 0; q < HID / 8; ++q) {
+        const uint4 p = h[q];
+        const u32 pw[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float x = from_bf16((bf16r)(pw[e >> 1] >> (16 * (e & 1))));
+            y0 = fmaf(x, w4[0][8 * q + e], y0);
+            y1 = fmaf(x, w4[1][8 * q + e], y1);
+        }
+    }
+    Y[2 * r] = y0 + w[OFF_B4];
+    Y[2 * r + 1] = y1 + w[OFF_B4 + 1];
+}
+
+// bias gradients b2 (copies part[0]) and b1 (part[1]): sum the copies the
+// GEMM epilogues accumulated into, add to grads
+__global__ void __launch_bounds__(2 * HID) bias_reduce_kernel(const float* __restrict__ part,
+                                                              float* grads)
+{
+    const int l = threadIdx.x / HID, c = threadIdx.x % HID;
+    float s = 0.0f;
+    for (int k = 0; k < TC_COPIES; ++k) s += part[((size_t)l * TC_COPIES + k) * HID + c];
+    grads[(l == 0 ? OFF_B2 : OFF_B1) + c] += s;
+}
+
+// U [rows][D_IN] -> UT [D_IN][ldt] (the K-major operand of dW1)
+__global__ void __launch_bounds__(256) transpose_in_kernel(const bf16r* __restrict__ U, int rows,
+                                                           bf16r* UT, int ldt)
+{
+    __shared__ bf16r tile[32][D_IN + 2];
+    const int r0 = blockIdx.x * 32;
+    for (int e = threadIdx.x; e < 32 * D_IN; e += blockDim.x) {
+        const int r = e / D_IN, c = e % D_IN;
+        tile[r][c] = r0 + r < rows ? U[(size_t)(r0 + r) * D_IN + c] : (bf16r)0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * D_IN; e += blockDim.x) {
+        const int c = e / 32, r = e % 32;
+        if (r0 + r < rows) UT[(size_t)c * ldt + r0 + r] = tile[r][c];
     }
 }
 
@@ -214,29 +474,41 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g)
 // db3 += sum dZ3, dW4 += dY^T H3, db4 += sum dY.  One thread per hidden
 // unit, 64 rows per block.
 // ---------------------------------------------------------------------------
-constexpr int OB_ROWS = 64;
+constexpr int OB_ROWS = 32;
 
 __global__ void __launch_bounds__(HID) out_backward_kernel(const float* __restrict__ dY,
                                                            const bf16r* __restrict__ wb,
                                                            const bf16r* __restrict__ H3,
                                                            const float* __restrict__ Z3, int B,
-                                                           bf16r* dZ3, float* grads)
+                                                           bf16r* dZ3, bf16r* dZ3T, int ldt,
+                                                           float* grads)
 {
+    __shared__ bf16r tT[HID][OB_ROWS + 2];   // the block's dZ3 tile, transposed
     const int n = threadIdx.x;
     const float w0 = from_bf16(wb[OFF_W4 + n]), w1 = from_bf16(wb[OFF_W4 + HID + n]);
     float db3 = 0.0f, dw0 = 0.0f, dw1 = 0.0f, db40 = 0.0f, db41 = 0.0f;
     const int r0 = blockIdx.x * OB_ROWS;
-    for (int r = r0; r < min(B, r0 + OB_ROWS); ++r) {
+    const int r1 = min(B, r0 + OB_ROWS);
+#pragma unroll 4
+    for (int r = r0; r < r1; ++r) {
         const float y0 = dY[2 * r], y1 = dY[2 * r + 1];
         const float dh = fmaf(y0, w0, y1 * w1);
         const float d = dh * silu_grad_f(Z3[(size_t)r * HID + n]);
-        dZ3[(size_t)r * HID + n] = to_bf16(d);
+        const bf16r db = to_bf16(d);
+        dZ3[(size_t)r * HID + n] = db;
+        tT[n][r - r0] = db;
         db3 += d;
         const float h = from_bf16(H3[(size_t)r * HID + n]);
         dw0 = fmaf(y0, h, dw0);
         dw1 = fmaf(y1, h, dw1);
         db40 += y0;
         db41 += y1;
+    }
+    __syncthreads();
+    // dZ3^T rows: consecutive threads write consecutive rows of a unit
+    for (int e = threadIdx.x; e < HID * OB_ROWS; e += blockDim.x) {
+        const int u = e / OB_ROWS, j = e % OB_ROWS;
+        if (r0 + j < r1) dZ3T[(size_t)u * ldt + r0 + j] = tT[u][j];
     }
     atomicAdd(grads + OFF_B3 + n, db3);
     atomicAdd(grads + OFF_W4 + n, dw0);
@@ -248,58 +520,89 @@ __global__ void __launch_bounds__(HID) out_backward_kernel(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// sliced-Wasserstein loss and gradient: one CTA of N threads (N a power of
-// two in 32..1024) per system; per projection both point sets are projected,
-// bitonic-sorted in shared memory (predicted points with their indices) and
-// matched rank by rank.
+// sliced-Wasserstein loss and gradient.  One CTA of N threads (N a power of
+// two in 32..1024) per (system, group of SW_PJ projections): thread i holds
+// point i; per projection both point sets are projected and bitonic-sorted
+// (the predicted points with their indices), exchange partners within a
+// warp by shuffles and across warps through shared memory, then matched
+// rank by rank.  Each CTA adds its projections' gradient to dX (one atomic
+// per coordinate) and its loss share to *loss.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) sw_kernel(const float* __restrict__ X,
-                                                  const float* __restrict__ T,
-                                                  const float* __restrict__ phi, int P, int N,
-                                                  float scale, float* loss, float* dX)
+constexpr int SW_PJ = 4;
+
+// compare-exchange stage (k, jj) of the bitonic network for this thread's
+// element: the lower partner of an ascending pair keeps the minimum; the
+// predicted keys carry their point index
+template <int N, int K, int JJ>
+__device__ __forceinline__ void sw_stage(int i, float& kx, float& ky, int& ix, float (*xs)[N],
+                                         float (*ys)[N], int (*is)[N], int& buf)
 {
-    __shared__ float kx[1024], ky[1024], gxs[1024], gys[1024];
-    __shared__ int ix[1024];
+    float ox, oy;
+    int oi;
+    if (JJ >= 32) {
+        xs[buf][i] = kx; ys[buf][i] = ky; is[buf][i] = ix;
+        __syncthreads();
+        ox = xs[buf][i ^ JJ]; oy = ys[buf][i ^ JJ]; oi = is[buf][i ^ JJ];
+        buf ^= 1;   // the next exchange uses the other buffer: no second barrier
+    } else {
+        ox = __shfl_xor_sync(0xffffffffu, kx, JJ);
+        oy = __shfl_xor_sync(0xffffffffu, ky, JJ);
+        oi = __shfl_xor_sync(0xffffffffu, ix, JJ);
+    }
+    const bool keep_min = ((i & JJ) == 0) == ((i & K) == 0);
+    if (keep_min ? (ox < kx) : (ox > kx)) { kx = ox; ix = oi; }
+    if (keep_min ? (oy < ky) : (oy > ky)) ky = oy;
+}
+
+template <int N, int K, int JJ>
+__device__ __forceinline__ void sw_merge(int i, float& kx, float& ky, int& ix, float (*xs)[N],
+                                         float (*ys)[N], int (*is)[N], int& buf)
+{
+    sw_stage<N, K, JJ>(i, kx, ky, ix, xs, ys, is, buf);
+    if constexpr (JJ > 1) sw_merge<N, K, JJ / 2>(i, kx, ky, ix, xs, ys, is, buf);
+}
+
+template <int N, int K>
+__device__ __forceinline__ void sw_sort(int i, float& kx, float& ky, int& ix, float (*xs)[N],
+                                        float (*ys)[N], int (*is)[N], int& buf)
+{
+    sw_merge<N, K, K / 2>(i, kx, ky, ix, xs, ys, is, buf);
+    if constexpr (K < N) sw_sort<N, 2 * K>(i, kx, ky, ix, xs, ys, is, buf);
+}
+
+template <int N>
+__global__ void __launch_bounds__(N, 2048 / N) sw_kernel(const float* __restrict__ X,
+                                               const float* __restrict__ T,
+                                               const float* __restrict__ phi, int P,
+                                               float scale, float* loss, float* dX)
+{
+    __shared__ float xs[2][N], ys[2][N], gxs[N], gys[N];
+    __shared__ int is[2][N];
     __shared__ float red[32];
-    const int s = blockIdx.x, i = threadIdx.x;
+    const int groups = (P + SW_PJ - 1) / SW_PJ;
+    const int s = blockIdx.x / groups, j0 = (blockIdx.x % groups) * SW_PJ;
+    const int i = threadIdx.x;
     const float xi0 = X[((size_t)s * N + i) * 2], xi1 = X[((size_t)s * N + i) * 2 + 1];
     const float ti0 = T[((size_t)s * N + i) * 2], ti1 = T[((size_t)s * N + i) * 2 + 1];
     gxs[i] = 0.0f;
     gys[i] = 0.0f;
     float lacc = 0.0f;
-    for (int j = 0; j < P; ++j) {
+    int buf = 0;
+    for (int j = j0; j < min(P, j0 + SW_PJ); ++j) {
         float sn, c;
         sincosf(phi[j], &sn, &c);
-        kx[i] = fmaf(xi0, c, xi1 * sn);
-        ky[i] = fmaf(ti0, c, ti1 * sn);
-        ix[i] = i;
-        __syncthreads();
-        for (int k = 2; k <= N; k <<= 1) {
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                const int p = i ^ jj;
-                if (p > i) {
-                    const bool up = (i & k) == 0;
-                    const float a = kx[i], b = kx[p];
-                    if ((a > b) == up) {
-                        kx[i] = b; kx[p] = a;
-                        const int t = ix[i]; ix[i] = ix[p]; ix[p] = t;
-                    }
-                    const float u = ky[i], v = ky[p];
-                    if ((u > v) == up) { ky[i] = v; ky[p] = u; }
-                }
-                __syncthreads();
-            }
-        }
-        const float diff = kx[i] - ky[i];
+        float kx = fmaf(xi0, c, xi1 * sn), ky = fmaf(ti0, c, ti1 * sn);
+        int ix = i;
+        sw_sort<N, 2>(i, kx, ky, ix, xs, ys, is, buf);
+        const float diff = kx - ky;
         lacc = fmaf(diff, diff, lacc);
         const float gv = 2.0f * diff / (float)N;
-        const int idx = ix[i];
-        gxs[idx] = fmaf(gv, c, gxs[idx]);
-        gys[idx] = fmaf(gv, sn, gys[idx]);
+        gxs[ix] = fmaf(gv, c, gxs[ix]);
+        gys[ix] = fmaf(gv, sn, gys[ix]);
         __syncthreads();
     }
-    dX[((size_t)s * N + i) * 2] += gxs[i] * scale;
-    dX[((size_t)s * N + i) * 2 + 1] += gys[i] * scale;
+    atomicAdd(dX + ((size_t)s * N + i) * 2, gxs[i] * scale);
+    atomicAdd(dX + ((size_t)s * N + i) * 2 + 1, gys[i] * scale);
     float v = lacc;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((i & 31) == 0) red[i >> 5] = v;
@@ -311,12 +614,42 @@ __global__ void __launch_bounds__(1024) sw_kernel(const float* __restrict__ X,
     }
 }
 
+// launches the SW kernel for N points per system (a power of two, 32..1024)
+void sw_launch(const float* X, const float* T, const float* phi, int P, int N, int n_sys,
+               float scale, float* loss, float* dX, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)n_sys * (unsigned)((P + SW_PJ - 1) / SW_PJ);
+    switch (N) {
+    case 32: sw_kernel<32><<<grid, 32, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    case 64: sw_kernel<64><<<grid, 64, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    case 128: sw_kernel<128><<<grid, 128, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    case 256: sw_kernel<256><<<grid, 256, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    case 512: sw_kernel<512><<<grid, 512, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    default: sw_kernel<1024><<<grid, 1024, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Adam (Kingma & Ba) with bias correction on the FP32 master weights; writes
 // the BF16 copies the GEMMs read.  t (1-based) is *step + 1.
 // ---------------------------------------------------------------------------
+// BF16 copy of parameter i; W2 and W3 also go transposed into wbT
+// ([2][in][out]): the K-major operands of the backward GEMMs
+__device__ __forceinline__ void store_bf16_weight(bf16r* wb, bf16r* wbT, int i, float wi)
+{
+    const bf16r b = to_bf16(wi);
+    wb[i] = b;
+    if (i >= OFF_W2 && i < OFF_W2 + HID * HID) {
+        const int e = i - OFF_W2;
+        wbT[(e % HID) * HID + e / HID] = b;
+    } else if (i >= OFF_W3 && i < OFF_W3 + HID * HID) {
+        const int e = i - OFF_W3;
+        wbT[HID * HID + (e % HID) * HID + e / HID] = b;
+    }
+}
+
 __global__ void __launch_bounds__(256) adam_kernel(float* w, float* m, float* v,
-                                                   const float* g, bf16r* wb, int n,
+                                                   const float* g, bf16r* wb, bf16r* wbT, int n,
                                                    const u32* step, u32 t_explicit, float lr,
                                                    float b1, float b2, float eps)
 {
@@ -331,13 +664,13 @@ __global__ void __launch_bounds__(256) adam_kernel(float* w, float* m, float* v,
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     w[i] = wi;
-    wb[i] = to_bf16(wi);
+    store_bf16_weight(wb, wbT, i, wi);
 }
 
-__global__ void to_bf16_kernel(const float* w, bf16r* wb, int n)
+__global__ void to_bf16_kernel(const float* w, bf16r* wb, bf16r* wbT, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) wb[i] = to_bf16(w[i]);
+    if (i < n) store_bf16_weight(wb, wbT, i, w[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -426,12 +759,20 @@ __global__ void __launch_bounds__(256) inputs_kernel(const SysRec* __restrict__ 
     const float rad = sqrtf(-2.0f * logf(u1));
     float sn, c;
     sincosf(6.28318530717958647692f * u2, &sn, &c);
-    bf16r* row = U + (size_t)r * D_IN;
-    row[0] = to_bf16(rad * c);
-    row[1] = to_bf16(rad * sn);
-    for (int j = 0; j < COND; ++j) row[2 + j] = to_bf16(q.cond[j]);
-    row[2 + COND] = to_bf16(q.t);
-    for (int j = 3 + COND; j < D_IN; ++j) row[j] = 0;
+    // the row [noise (2), conditioning (48), t, zeros] packed in registers,
+    // written as eight 16-byte vectors
+    u32 w32[D_IN / 2];
+    w32[0] = (u32)to_bf16(rad * c) | ((u32)to_bf16(rad * sn) << 16);
+#pragma unroll
+    for (int j = 0; j < COND / 2; ++j)
+        w32[1 + j] = (u32)to_bf16(q.cond[2 * j]) | ((u32)to_bf16(q.cond[2 * j + 1]) << 16);
+    w32[1 + COND / 2] = (u32)to_bf16(q.t);
+#pragma unroll
+    for (int j = 2 + COND / 2; j < D_IN / 2; ++j) w32[j] = 0u;
+    uint4* row = reinterpret_cast<uint4*>(U + (size_t)r * D_IN);
+#pragma unroll
+    for (int v = 0; v < D_IN / 8; ++v)
+        row[v] = make_uint4(w32[4 * v], w32[4 * v + 1], w32[4 * v + 2], w32[4 * v + 3]);
 }
 
 __global__ void step_inc_kernel(u32* step) { *step += 1u; }
@@ -444,6 +785,25 @@ __global__ void gather_loss_kernel(const float* loss, const u32* step, u32 first
     if (s < cap) hist[s] = *loss;
 }
 
+
+// warp-level BF16 fragments for the fused inference (small per-point
+// products that stay in registers): ldmatrix x4 and mma.sync m16n8k16
+__device__ __forceinline__ void ldsm_x4(u32 (&r)[4], const void* p)
+{
+    const u32 a = (u32)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const u32 (&a)[4], u32 b0, u32 b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 // ---------------------------------------------------------------------------
 // fused inference: start points of one system straight from noise.
@@ -637,6 +997,8 @@ struct cfs_sampler {
     float* m = nullptr;
     float* v = nullptr;
     bf16r* wb = nullptr;     // bf16 copies
+    bf16r* wbT = nullptr;    // bf16 W2^T, W3^T ([2][in][out]) for the backward GEMMs
+    float* bias_part = nullptr;   // [2][TC_COPIES][HID] bias-gradient partial sums
     u32* d_step = nullptr;   // Adam step counter (device)
     u32 step = 0;            // host mirror (checkpoints)
     // inference workspace for n frames (grown on demand): records, c1,
@@ -648,9 +1010,12 @@ struct cfs_sampler {
     bool upload_pending = false;
     // activations for B rows (grown on demand)
     int cap_rows = 0;
+    int ldt = 0;             // row stride of the transposed copies (>= cap_rows)
     unsigned char* act = nullptr;
     float *Z1, *Z2, *Z3, *Y;
     bf16r *H1, *H2, *H3, *dZ1, *dZ2, *dZ3;
+    // transposed copies [features][ldt]: the K-major operands of dW = dZ^T A
+    bf16r *UT, *H1T, *H2T, *dZ1T, *dZ2T, *dZ3T;
 };
 
 namespace {
@@ -663,7 +1028,9 @@ cfs_status ensure_rows(cfs_sampler* s, int B)
     s->act = nullptr;
     s->cap_rows = 0;
     const size_t fz = (size_t)B * HID * 4, fh = (size_t)B * HID * 2;
-    const size_t bytes = 3 * fz + (size_t)B * 2 * 4 + 6 * fh + 6 * 256;
+    const int ldt = (B + 63) / 64 * 64;
+    const size_t ft = (size_t)ldt * HID * 2, fu = (size_t)ldt * D_IN * 2;
+    const size_t bytes = 3 * fz + (size_t)B * 2 * 4 + 6 * fh + 5 * ft + fu + 13 * 256;
     cfs_status st = check_cuda(cudaMalloc(&s->act, bytes), "cudaMalloc(sampler activations)");
     if (st != CFS_OK) return st;
     unsigned char* p = s->act;
@@ -676,60 +1043,90 @@ cfs_status ensure_rows(cfs_sampler* s, int B)
     s->Y = (float*)take((size_t)B * 2 * 4);
     s->H1 = (bf16r*)take(fh); s->H2 = (bf16r*)take(fh); s->H3 = (bf16r*)take(fh);
     s->dZ1 = (bf16r*)take(fh); s->dZ2 = (bf16r*)take(fh); s->dZ3 = (bf16r*)take(fh);
+    s->UT = (bf16r*)take(fu);
+    s->H1T = (bf16r*)take(ft); s->H2T = (bf16r*)take(ft);
+    s->dZ1T = (bf16r*)take(ft); s->dZ2T = (bf16r*)take(ft); s->dZ3T = (bf16r*)take(ft);
+    s->ldt = ldt;
     s->cap_rows = B;
     return CFS_OK;
 }
 
-void gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda, int tA, const bf16r* B,
-          int ldb, int tB, int mode, const float* bias, float* C, int ldc, bf16r* H, int ldh,
-          const float* Zin, int ldz, float* colsum, int splits = 1)
+// D = A B^T on the tensor cores (both operands K-major), split over K into
+// `splits` CTA ranges (ATOMIC adds the partial products)
+cfs_status tc_gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda, const bf16r* B,
+             int ldb, int mode, const float* bias, float* C, int ldc, bf16r* H, int ldh,
+             bf16r* HT, int ldt, const float* Zin, int ldz, float* colsum, int splits = 1)
 {
-    GemmArgs g;
+    // the staging reads 16-byte vectors, the epilogue writes them: every
+    // operand and output of this library is laid out for that; anything
+    // else is a bug here, so stop before a misaligned launch
+    const bool aligned =
+        ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && lda % 8 == 0 && ldb % 8 == 0 &&
+        (!C || ((uintptr_t)C % 16 == 0 && ldc % 4 == 0)) &&
+        (!H || ((uintptr_t)H % 16 == 0 && ldh % 8 == 0)) &&
+        (!Zin || ((uintptr_t)Zin % 16 == 0 && ldz % 4 == 0)) && (N == 64 || N == 128);
+    if (!aligned)
+        return fail(CFS_ERR_INVALID_ARG, "tensor-core GEMM operands not 16-byte aligned");
+    TcArgs g;
     g.M = M; g.N = N; g.K = K;
-    g.A = A; g.lda = lda; g.transA = tA;
-    g.B = B; g.ldb = ldb; g.transB = tB;
-    const int kc = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-    g.k_split = kc;
+    g.A = A; g.lda = lda;
+    g.B = B; g.ldb = ldb;
+    const int per = (K + splits - 1) / splits;
+    g.k_split = (per + TC_K - 1) / TC_K * TC_K;
     g.mode = mode; g.bias = bias; g.C = C; g.ldc = ldc; g.H = H; g.ldh = ldh;
-    g.Zin = Zin; g.ldz = ldz; g.colsum = colsum;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, (K + kc - 1) / kc);
-    gemm_kernel<<<grid, 256, 0, st>>>(g);
+    g.HT = HT; g.ldt = ldt; g.Zin = Zin; g.ldz = ldz; g.colsum = colsum;
+    dim3 grid((M + TC_M - 1) / TC_M, 1, (K + g.k_split - 1) / g.k_split);
+    tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(g);
+    return CFS_OK;
 }
 
-// forward of B rows of U: Z1..Z3 (fp32), H1..H3 (bf16), Y (fp32 [B][2])
-void forward(cfs_sampler* s, const bf16r* U, int B, cudaStream_t st)
+// forward of B rows of U: Z1..Z3 (fp32), H1..H3 (bf16), H1^T, H2^T, Y (fp32 [B][2])
+cfs_status forward(cfs_sampler* s, const bf16r* U, int B, cudaStream_t st)
 {
     const bf16r* wb = s->wb;
-    gemm(st, B, HID, D_IN, U, D_IN, 0, wb + OFF_W1, D_IN, 1, EPI_SILU, s->w + OFF_B1, s->Z1, HID,
-         s->H1, HID, nullptr, 0, nullptr);
-    gemm(st, B, HID, HID, s->H1, HID, 0, wb + OFF_W2, HID, 1, EPI_SILU, s->w + OFF_B2, s->Z2,
-         HID, s->H2, HID, nullptr, 0, nullptr);
-    gemm(st, B, HID, HID, s->H2, HID, 0, wb + OFF_W3, HID, 1, EPI_SILU, s->w + OFF_B3, s->Z3,
-         HID, s->H3, HID, nullptr, 0, nullptr);
-    gemm(st, B, D_OUT, HID, s->H3, HID, 0, wb + OFF_W4, HID, 1, EPI_STORE, s->w + OFF_B4, s->Y,
-         D_OUT, nullptr, 0, nullptr, 0, nullptr);
+    cfs_status r = tc_gemm(st, B, HID, D_IN, U, D_IN, wb + OFF_W1, D_IN, EPI_SILU, s->w + OFF_B1,
+                           s->Z1, HID, s->H1, HID, s->H1T, s->ldt, nullptr, 0, nullptr);
+    if (r == CFS_OK)
+        r = tc_gemm(st, B, HID, HID, s->H1, HID, wb + OFF_W2, HID, EPI_SILU, s->w + OFF_B2,
+                    s->Z2, HID, s->H2, HID, s->H2T, s->ldt, nullptr, 0, nullptr);
+    if (r == CFS_OK)
+        r = tc_gemm(st, B, HID, HID, s->H2, HID, wb + OFF_W3, HID, EPI_SILU, s->w + OFF_B3,
+                    s->Z3, HID, s->H3, HID, nullptr, 0, nullptr, 0, nullptr);
+    if (r != CFS_OK) return r;
+    out_forward_kernel<<<(B + 255) / 256, 256, 0, st>>>(s->H3, wb, s->w, B, s->Y);
+    return CFS_OK;
 }
 
 // backward of sum(dY * Y) after forward(): adds into grads [N_PARAMS]
-void backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, float* grads,
-              cudaStream_t st)
+cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, float* grads,
+                    cudaStream_t st)
 {
     const bf16r* wb = s->wb;
-    out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, HID, 0, st>>>(dY, wb, s->H3, s->Z3, B,
-                                                                      s->dZ3, grads);
-    // dZ2 = (dZ3 W3) * silu'(Z2): op(B)(k = o, n = i) = W3[o][i]
-    gemm(st, B, HID, HID, s->dZ3, HID, 0, wb + OFF_W3, HID, 0, EPI_SILU_GRAD, nullptr, nullptr,
-         0, s->dZ2, HID, s->Z2, HID, grads + OFF_B2);
-    gemm(st, B, HID, HID, s->dZ2, HID, 0, wb + OFF_W2, HID, 0, EPI_SILU_GRAD, nullptr, nullptr,
-         0, s->dZ1, HID, s->Z1, HID, grads + OFF_B1);
-    // weight gradients dW = dZ^T A over the rows (split-K, atomic)
-    const int splits = B >= 8192 ? 32 : (B >= 1024 ? 8 : 1);
-    gemm(st, HID, HID, B, s->dZ3, HID, 1, s->H2, HID, 0, EPI_ATOMIC, nullptr, grads + OFF_W3, HID,
-         nullptr, 0, nullptr, 0, nullptr, splits);
-    gemm(st, HID, HID, B, s->dZ2, HID, 1, s->H1, HID, 0, EPI_ATOMIC, nullptr, grads + OFF_W2, HID,
-         nullptr, 0, nullptr, 0, nullptr, splits);
-    gemm(st, HID, D_IN, B, s->dZ1, HID, 1, U, D_IN, 0, EPI_ATOMIC, nullptr, grads + OFF_W1, D_IN,
-         nullptr, 0, nullptr, 0, nullptr, splits);
+    out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, HID, 0, st>>>(
+        dY, wb, s->H3, s->Z3, B, s->dZ3, s->dZ3T, s->ldt, grads);
+    // dZ2 = (dZ3 W3) * silu'(Z2): the K-major B operand is W3^T; the bias
+    // gradients gather in copies (bias_part) first
+    cudaMemsetAsync(s->bias_part, 0, sizeof(float) * 2 * TC_COPIES * HID, st);
+    cfs_status r = tc_gemm(st, B, HID, HID, s->dZ3, HID, s->wbT + HID * HID, HID, EPI_SILU_GRAD,
+                           nullptr, nullptr, 0, s->dZ2, HID, s->dZ2T, s->ldt, s->Z2, HID,
+                           s->bias_part);
+    if (r == CFS_OK)
+        r = tc_gemm(st, B, HID, HID, s->dZ2, HID, s->wbT, HID, EPI_SILU_GRAD, nullptr, nullptr,
+                    0, nullptr, 0, s->dZ1T, s->ldt, s->Z1, HID, s->bias_part + TC_COPIES * HID);
+    if (r != CFS_OK) return r;
+    bias_reduce_kernel<<<1, 2 * HID, 0, st>>>(s->bias_part, grads);
+    transpose_in_kernel<<<(B + 31) / 32, 256, 0, st>>>(U, B, s->UT, s->ldt);
+    // weight gradients dW = dZ^T A: K = the rows, split over CTAs, atomic
+    const int splits = std::max(1, std::min(256, B / 256));
+    r = tc_gemm(st, HID, HID, B, s->dZ3T, s->ldt, s->H2T, s->ldt, EPI_ATOMIC, nullptr,
+                grads + OFF_W3, HID, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, splits);
+    if (r == CFS_OK)
+        r = tc_gemm(st, HID, HID, B, s->dZ2T, s->ldt, s->H1T, s->ldt, EPI_ATOMIC, nullptr,
+                    grads + OFF_W2, HID, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, splits);
+    if (r == CFS_OK)
+        r = tc_gemm(st, HID, D_IN, B, s->dZ1T, s->ldt, s->UT, s->ldt, EPI_ATOMIC, nullptr,
+                    grads + OFF_W1, D_IN, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, splits);
+    return r;
 }
 
 void init_params_host(uint64_t seed, std::vector<float>& p)
@@ -762,7 +1159,7 @@ cfs_status upload_params(cfs_sampler* s, const float* host)
     cfs_status st = check_cuda(cudaMemcpy(s->w, host, sizeof(float) * N_PARAMS,
                                           cudaMemcpyHostToDevice), "cudaMemcpy(params)");
     if (st != CFS_OK) return st;
-    to_bf16_kernel<<<(N_PARAMS + 255) / 256, 256>>>(s->w, s->wb, N_PARAMS);
+    to_bf16_kernel<<<(N_PARAMS + 255) / 256, 256>>>(s->w, s->wb, s->wbT, N_PARAMS);
     return check_cuda(cudaDeviceSynchronize(), "sampler params");
 }
 
@@ -802,13 +1199,25 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
     cfs_sampler* s = new (std::nothrow) cfs_sampler();
     if (!s) return fail(CFS_ERR_OOM, "host allocation failed");
     cudaGetDevice(&s->device);
-    cfs_status st = check_cuda(cudaMalloc(&s->w, sizeof(float) * N_PARAMS * 3 +
-                                                     sizeof(bf16r) * N_PARAMS + 256),
+    // w | m | v (FP32), then the BF16 copies on 256-byte boundaries: the
+    // tensor-core GEMMs read the weights with 16-byte loads
+    const size_t off_wb = (sizeof(float) * N_PARAMS * 3 + 255) & ~(size_t)255;
+    const size_t off_wbT = off_wb + ((sizeof(bf16r) * N_PARAMS + 255) & ~(size_t)255);
+    const size_t off_part = off_wbT + sizeof(bf16r) * 2 * HID * HID;
+    cfs_status st = check_cuda(cudaMalloc(&s->w, off_part + sizeof(float) * 2 * TC_COPIES * HID),
                                "cudaMalloc(sampler params)");
     if (st != CFS_OK) { delete s; return st; }
     s->m = s->w + N_PARAMS;
     s->v = s->m + N_PARAMS;
-    s->wb = reinterpret_cast<bf16r*>(s->v + N_PARAMS);
+    s->wb = reinterpret_cast<bf16r*>(reinterpret_cast<unsigned char*>(s->w) + off_wb);
+    s->wbT = reinterpret_cast<bf16r*>(reinterpret_cast<unsigned char*>(s->w) + off_wbT);
+    s->bias_part = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s->w) + off_part);
+    // the tensor-core GEMM stages two 32 KB chunk pairs in dynamic shared memory
+    if (st == CFS_OK)
+        st = check_cuda(cudaFuncSetAttribute(tc_gemm_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TC_SMEM),
+                        "cudaFuncSetAttribute(tc_gemm_kernel)");
     st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->d_step, 0, 256), "memset");
@@ -850,6 +1259,16 @@ cfs_status cfs_sampler_get_params(const cfs_sampler* s, float* params, float* ad
                                        cudaMemcpyDeviceToHost), "cudaMemcpy(params)");
     if (st == CFS_OK && step)
         st = check_cuda(cudaMemcpy(step, s->d_step, 4, cudaMemcpyDeviceToHost), "step");
+    // a tensor-core GEMM whose barrier wait ran out of time skipped its
+    // output: report it once
+    unsigned int tc_err = 0;
+    if (st == CFS_OK)
+        st = check_cuda(cudaMemcpyFromSymbol(&tc_err, g_tc_error, sizeof(tc_err)), "error flag");
+    if (st == CFS_OK && tc_err) {
+        const unsigned int zero = 0;
+        cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero));
+        return fail(CFS_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its mbarrier");
+    }
     return st;
 }
 
@@ -878,7 +1297,8 @@ cfs_status cfs_sampler_forward(cfs_sampler* s, const void* U, uint32_t B, float*
     cfs_status st = ensure_rows(s, (int)B);
     if (st != CFS_OK) return st;
     cudaStream_t sm = (cudaStream_t)stream;
-    forward(s, (const bf16r*)U, (int)B, sm);
+    st = forward(s, (const bf16r*)U, (int)B, sm);
+    if (st != CFS_OK) return st;
     st = check_cuda(cudaMemcpyAsync(Y, s->Y, sizeof(float) * 2 * B, cudaMemcpyDeviceToDevice, sm),
                     "copy Y");
     if (st != CFS_OK) return st;
@@ -895,8 +1315,9 @@ cfs_status cfs_sampler_backward(cfs_sampler* s, const void* U, uint32_t B, const
     cfs_status st = ensure_rows(s, (int)B);
     if (st != CFS_OK) return st;
     cudaStream_t sm = (cudaStream_t)stream;
-    forward(s, (const bf16r*)U, (int)B, sm);
-    backward(s, (const bf16r*)U, (int)B, dY, grads, sm);
+    st = forward(s, (const bf16r*)U, (int)B, sm);
+    if (st == CFS_OK) st = backward(s, (const bf16r*)U, (int)B, dY, grads, sm);
+    if (st != CFS_OK) return st;
     return check_cuda(cudaGetLastError(), "sampler backward");
 }
 
@@ -909,8 +1330,8 @@ cfs_status cfs_sw_loss(const float* X, const float* T, uint32_t n_sys, uint32_t 
         return fail(CFS_ERR_INVALID_ARG, "points per system must be a power of two in 32..1024");
     if (n_sys == 0 || n_proj == 0) return CFS_OK;
     const float scale = 1.0f / ((float)n_sys * (float)n_proj);
-    sw_kernel<<<n_sys, n_per, 0, (cudaStream_t)stream>>>(X, T, phi, (int)n_proj, (int)n_per,
-                                                         scale, loss, dX);
+    sw_launch(X, T, phi, (int)n_proj, (int)n_per, (int)n_sys, scale, loss, dX,
+              (cudaStream_t)stream);
     return check_cuda(cudaGetLastError(), "sw_kernel launch");
 }
 
@@ -920,7 +1341,7 @@ cfs_status cfs_sampler_adam(cfs_sampler* s, const float* grads, uint32_t t, floa
     clear_error();
     if (!s || !grads || t == 0) return fail(CFS_ERR_INVALID_ARG, "bad arguments");
     adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
-        s->w, s->m, s->v, grads, s->wb, N_PARAMS, nullptr, t, lr, 0.9f, 0.999f, 1e-8f);
+        s->w, s->m, s->v, grads, s->wb, s->wbT, N_PARAMS, nullptr, t, lr, 0.9f, 0.999f, 1e-8f);
     return check_cuda(cudaGetLastError(), "adam launch");
 }
 
@@ -988,18 +1409,19 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
         prep_kernel<<<1, 1024, 0, cap>>>(s->d_step, seed, n_systems, S, d_sel, d_phi, (int)n_proj);
         data_kernel<<<(B + 255) / 256, 256, 0, cap>>>(d_sys, d_sel, s->d_step, seed, N, B, 40, d_T);
         inputs_kernel<<<(B + 255) / 256, 256, 0, cap>>>(d_sys, d_sel, s->d_step, 0u, seed, N, B, d_U);
-        forward(s, d_U, B, cap);
-        sw_kernel<<<S, N, 0, cap>>>(s->Y, d_T, d_phi, (int)n_proj, N,
-                                    1.0f / ((float)S * (float)n_proj), d_loss, d_dY);
+        cfs_status fst = forward(s, d_U, B, cap);
+        sw_launch(s->Y, d_T, d_phi, (int)n_proj, N, S, 1.0f / ((float)S * (float)n_proj),
+                  d_loss, d_dY, cap);
         gather_loss_kernel<<<1, 1, 0, cap>>>(d_loss, s->d_step, step0, d_hist, steps);
-        backward(s, d_U, B, d_dY, d_g, cap);
-        adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, cap>>>(s->w, s->m, s->v, d_g, s->wb,
+        if (fst == CFS_OK) fst = backward(s, d_U, B, d_dY, d_g, cap);
+        adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, cap>>>(s->w, s->m, s->v, d_g, s->wb, s->wbT,
                                                              N_PARAMS, s->d_step, 0u, lr, 0.9f,
                                                              0.999f, 1e-8f);
         step_inc_kernel<<<1, 1, 0, cap>>>(s->d_step);
         cudaError_t e = cudaGetLastError();
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         st = check_cuda(e != cudaSuccess ? e : e2, "training step capture");
+        if (st == CFS_OK && fst != CFS_OK) st = fst;
     }
     if (st == CFS_OK) st = check_cuda(cudaGraphInstantiate(&exec, graph, 0), "instantiate");
     for (uint32_t i = 0; i < steps && st == CFS_OK; ++i)

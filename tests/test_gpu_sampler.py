@@ -67,11 +67,14 @@ def test_forward_matches_oracle(torch_cuda):
     assert _rel(Y, Yo) < 1e-2, _rel(Y, Yo)
 
 
-def test_backward_matches_oracle(torch_cuda):
+@pytest.mark.parametrize("B", [777, 4096])
+def test_backward_matches_oracle(torch_cuda, B):
+    # 777 rows: a ragged last row tile and a ragged K range in the weight
+    # gradients; 4096 rows: the weight gradients split over 16 CTAs
     torch = torch_cuda
-    cfs, s, params, Ub, Ut = _setup(torch, 777)
+    cfs, s, params, Ub, Ut = _setup(torch, B)
     rng = np.random.default_rng(9)
-    dY = rng.normal(size=(777, 2)).astype(np.float32)
+    dY = rng.normal(size=(B, 2)).astype(np.float32)
     g = s.backward(Ut, torch.from_numpy(dY).cuda()).cpu().numpy()
     _, cache = SO.forward(params, Ub, bf16=True)
     go = SO.backward(params, cache, dY, bf16=True)

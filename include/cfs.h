@@ -284,7 +284,7 @@ cfs_status cfs_render_batch(const cfs_chain* chain, int n_targets, const cfs_fra
                             uint64_t seed, int clear, void* stream);
 
 /* ---- density-estimation display -----------------------------------------
- * Section 5 names density estimation (fractal flames, caustics) as the
+ * Section 4 names density estimation (fractal flames, caustics) as the
  * output that keeps atomics on the path; the paper does not say how such a
  * layer is shown.  The mapping here is the log-density display of fractal
  * flames (Draves & Reckase 2003), per pixel:

@@ -30,6 +30,13 @@
  *    k = #{ j < n-1 : w >= T_j }  (thresholds >= 2^32 never count).
  *  - Colour (Section 1, "the function used ... to land"): the index k of the
  *    last generator map applied.
+ *  - Duplication (Section 3.2: the stars are generated on the fly by a PRNG
+ *    scheme): STARS moves the copy onto one of n small copies of the
+ *    primitive.  The star is j = floor(w_aux * n / 2^32) with w_aux word
+ *    n & 3 of Philox block (i, n >> 2, system, 2); star j's centre and size
+ *    come from Philox block (j, 0, 0, 7), u_c = (word_c >> 8) * 2^-24:
+ *    centre (x0 + (x1 - x0) u_0, y0 + (y1 - y0) u_1, z0 + (z1 - z0) u_2),
+ *    size s0 + (s1 - s0) u_3 (each a single fma); q' = centre + size * q.
  *  - Splat (Section 1, "colors the appropriate pixel"): ix = floor((x - x0) * sx)
  *    with sx = W / (x1 - x0) in FP32, valid for x0 <= x <= x1, the last bin
  *    closed (ix = min(ix, W-1)); outside or non-finite points are counted as
@@ -192,11 +199,57 @@ static void derive_affine(int op, const float* v, float* m /* 12 */)
     }
 }
 
+/* per-step context of the stochastic and recolouring ops */
+typedef struct {
+    uint64_t seed;   /* Philox key of the render */
+    uint32_t aux;    /* word n & 3 of block (i, n >> 2, system, 2) */
+    int* k;          /* colour index of the branch (BANDS changes it) */
+} orc_opctx;
+
+static float unit24(uint32_t w) { return (float)(w >> 8) * 0x1.0p-24f; }
+
 /* Applies op `op` to q; returns 0 when the op discards the point. */
-static int apply_op(int op, const float* v, float* q)
+static int apply_op(int op, const float* v, float* q, const orc_opctx* cx)
 {
     float x = q[0], y = q[1], z = q[2];
     switch (op) {
+    case ORC_OP_STARS: {
+        uint32_t n = (uint32_t)v[0];
+        uint32_t j = (uint32_t)(((uint64_t)cx->aux * (uint64_t)n) >> 32);
+        uint32_t ctr[4] = {j, 0u, 0u, 7u};
+        uint32_t key[2] = {(uint32_t)cx->seed, (uint32_t)(cx->seed >> 32)};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        float cxs = fmaf(v[2] - v[1], unit24(r[0]), v[1]);
+        float cys = fmaf(v[4] - v[3], unit24(r[1]), v[3]);
+        float czs = fmaf(v[6] - v[5], unit24(r[2]), v[5]);
+        float sz = fmaf(v[8] - v[7], unit24(r[3]), v[7]);
+        q[0] = fmaf(sz, x, cxs);
+        q[1] = fmaf(sz, y, cys);
+        q[2] = fmaf(sz, z, czs);
+        return 1;
+    }
+    case ORC_OP_HEMISPHERE: {
+        /* the disk seen as the front (z <= 0) half of a sphere of radius R */
+        float r2 = fmaf(x, x, y * y);
+        float h = sqrtf(fmaxf(0.0f, 1.0f - r2));
+        q[0] = v[0] * x;
+        q[1] = v[0] * y;
+        q[2] = -(v[0] * h);
+        return 1;
+    }
+    case ORC_OP_BANDS: {
+        /* colour = base + (floor(freq * coord + phase) mod n) */
+        int axis = (int)v[0], nb = (int)v[3], base = (int)v[4];
+        float t = fmaf(v[1], q[axis], v[2]);
+        int m = 0;
+        if (isfinite(t) && fabsf(t) < 1.0e9f) {
+            long b = (long)floorf(t);
+            m = (int)(((b % nb) + nb) % nb);
+        }
+        *cx->k = base + m;
+        return 1;
+    }
     case ORC_OP_AFFINE2: affine2(v, q); return 1;
     case ORC_OP_AFFINE3: affine3(v, q); return 1;
     case ORC_OP_ROTATE2: { float m[12]; derive_affine(op, v, m); affine2(m, q); return 1; }
@@ -357,16 +410,19 @@ static void splat(orc_target* t, const float* q, int alive, int k)
  * discarded.  Records q at each SPLAT into rec (4 floats each: x, y, z,
  * alive) when rec is not NULL.  Returns the number of SPLAT ops met. */
 static int run_chain(const orc_chain* ch, const float* p, float* q_out, orc_target* tg,
-                     int n_tg, int k, int do_splat, float* rec)
+                     int n_tg, int k, int do_splat, float* rec, uint64_t seed, uint32_t aux)
 {
     float q[3] = {p[0], p[1], p[2]};
     int alive = 1, n_rec = 0;
+    int kc = k;   /* the branch's colour index */
+    orc_opctx cx = {seed, aux, &kc};
     for (int o = 0; o < ch->n_ops; ++o) {
         int op = ch->op[o];
         const float* v = ch->prm + 16 * o;
         if (op == ORC_OP_RESET) {
             q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
             alive = 1;
+            kc = k;
         } else if (op == ORC_OP_SPLAT) {
             int ti = (int)v[0];
             if (rec) {
@@ -374,9 +430,9 @@ static int run_chain(const orc_chain* ch, const float* p, float* q_out, orc_targ
                 rec[4 * n_rec + 2] = q[2]; rec[4 * n_rec + 3] = (float)alive;
             }
             n_rec++;
-            if (do_splat && ti >= 0 && ti < n_tg) splat(&tg[ti], q, alive, k);
+            if (do_splat && ti >= 0 && ti < n_tg) splat(&tg[ti], q, alive, kc);
         } else if (alive) {
-            alive = apply_op(op, v, q);
+            alive = apply_op(op, v, q, &cx);
         }
     }
     if (q_out) { q_out[0] = q[0]; q_out[1] = q[1]; q_out[2] = q[2]; }
@@ -397,11 +453,19 @@ static void start_point(uint64_t seed, uint32_t sys_id, uint32_t i, int dim, flo
 /* ------------------------------------------------------------------------ */
 /* The chaos game (Section 1 and Section 3), one point after another.       */
 /* ------------------------------------------------------------------------ */
+static int chain_has_aux(const orc_chain* ch)
+{
+    for (int o = 0; o < ch->n_ops; ++o)
+        if (ch->op[o] == ORC_OP_STARS) return 1;
+    return 0;
+}
+
 int orc_render(const orc_system* sys, const orc_chain* ch, orc_target* tg, int n_tg,
                const orc_run* run)
 {
     uint64_t T[ORC_MAX_MAPS];
     if (orc_thresholds(sys->n_maps, sys->prob, T) != 0) return -1;
+    int has_aux = chain_has_aux(ch);
     for (uint32_t j = 0; j < run->n_points; ++j) {
         uint32_t i = run->point_begin + j;
         float p[3];
@@ -415,14 +479,16 @@ int orc_render(const orc_system* sys, const orc_chain* ch, orc_target* tg, int n
             int k = orc_choose(w, sys->n_maps, T);
             apply_map(sys, k, p);
             int live = n >= run->burn_in;
+            uint32_t aux = has_aux ? philox_word(run->seed, i, n >> 2, run->system_id, 2u,
+                                                 (int)(n & 3u)) : 0u;
             if (run->reuse) {
                 /* Fig. 2C: the transformed point is the one iterated on */
                 float q[3];
-                if (run_chain(ch, p, q, tg, n_tg, k, live, NULL)) {
+                if (run_chain(ch, p, q, tg, n_tg, k, live, NULL, run->seed, aux)) {
                     p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
                 }
             } else if (live) {
-                run_chain(ch, p, NULL, tg, n_tg, k, 1, NULL);
+                run_chain(ch, p, NULL, tg, n_tg, k, 1, NULL, run->seed, aux);
             }
         }
     }
@@ -438,6 +504,7 @@ int orc_trace(const orc_system* sys, const orc_chain* ch, const orc_run* run,
     uint64_t T[ORC_MAX_MAPS];
     if (orc_thresholds(sys->n_maps, sys->prob, T) != 0) return -1;
     uint32_t n_steps = run->iters - run->step_begin;
+    int has_aux = chain_has_aux(ch);
     for (uint32_t j = 0; j < n_ids; ++j) {
         uint32_t i = ids[j];
         float p[3];
@@ -454,7 +521,9 @@ int orc_trace(const orc_system* sys, const orc_chain* ch, const orc_run* run,
             apply_map(sys, k, p);
             float* rec = q_out ? q_out + s * (size_t)n_splat_ops * 4 : NULL;
             float qq[3];
-            int alive = run_chain(ch, p, qq, NULL, 0, k, 0, rec);
+            uint32_t aux = has_aux ? philox_word(run->seed, i, n >> 2, run->system_id, 2u,
+                                                 (int)(n & 3u)) : 0u;
+            int alive = run_chain(ch, p, qq, NULL, 0, k, 0, rec, run->seed, aux);
             if (run->reuse && alive) { p[0] = qq[0]; p[1] = qq[1]; p[2] = qq[2]; }
             k_out[s] = k;
             p_out[3 * s + 0] = p[0]; p_out[3 * s + 1] = p[1]; p_out[3 * s + 2] = p[2];
@@ -494,14 +563,14 @@ int orc_render_points(const float* xyz, const uint8_t* fn, uint32_t n, const orc
 {
     for (uint32_t i = 0; i < n; ++i) {
         float p[3] = {xyz[3 * (size_t)i], xyz[3 * (size_t)i + 1], xyz[3 * (size_t)i + 2]};
-        run_chain(ch, p, NULL, tg, n_tg, fn[i], 1, NULL);
+        run_chain(ch, p, NULL, tg, n_tg, fn[i], 1, NULL, 0u, 0u);
     }
     return 0;
 }
 
 /* ------------------------------------------------------------------------ */
 /* Density-estimation display.  The paper names density estimation (fractal
- * flames, caustics) as the output that keeps atomics on the path (Section 5)
+ * flames, caustics) as the output that keeps atomics on the path (Section 4)
  * and leaves its display unspecified; the reading here is the log-density
  * mapping of fractal flames (Draves & Reckase 2003): per pixel
  *   A   = accumulated alpha (the number of splats for palette alpha 1),

@@ -30,7 +30,10 @@ enum {
     ORC_OP_BEND = 13,       /* beta                                           */
     ORC_OP_INVERSION = 14,  /* cx cy cz rho                                   */
     ORC_OP_SPLAT = 15,      /* target index                                   */
-    ORC_OP_RESET = 16       /* new branch from a fresh copy of the point      */
+    ORC_OP_RESET = 16,      /* new branch from a fresh copy of the point      */
+    ORC_OP_STARS = 17,      /* n, x0 x1 y0 y1 z0 z1, s0 s1: duplication        */
+    ORC_OP_HEMISPHERE = 18, /* R: unit disk -> front hemisphere of radius R   */
+    ORC_OP_BANDS = 19       /* axis, freq, phase, n, base: recolour by bands   */
 };
 
 enum { ORC_TGT_HIST_U32 = 0, ORC_TGT_RGBA_F32 = 1, ORC_TGT_DEPTH_U64 = 2 };

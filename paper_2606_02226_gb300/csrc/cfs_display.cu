@@ -1,7 +1,7 @@
 // cfs_display.cu -- density-estimation display: accumulated layers to packed
 // 8-bit RGBA (log density with a gamma, the fractal-flame display of Draves &
 // Reckase 2003; the paper names density estimation as the output that keeps
-// atomics on the path, Section 5).
+// atomics on the path, Section 4).
 //
 // Two kernels over work items of kDisplayPxPerItem pixels, numbered layer by
 // layer, so one launch covers one layer or every frame of a batch:

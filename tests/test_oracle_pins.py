@@ -588,3 +588,63 @@ def test_tonemap_depth_resolves_colour():
                     dtype=np.uint64)
     out, _, _ = O.tonemap(t, keys, background=0xDEADBEEF)
     assert [int(v) for v in out[0]] == [0xFF00FF00, 0xDEADBEEF, 0x01020304]
+
+
+# ---------------------------------------------------------------------------
+# duplication (stars), hemisphere and band recolouring (Section 3.2's scene)
+# ---------------------------------------------------------------------------
+def _circle_trace(chain, n=64, iters=40, seed=5):
+    sysd = W.circle_system()
+    k, p, q = O.trace(sysd, chain, np.arange(n, dtype=np.uint32), iters=iters, seed=seed)
+    return k, p, q
+
+
+def test_stars_are_scaled_copies_at_fixed_centres():
+    box = (-10.0, 10.0, -6.0, 6.0, 12.0, 20.0)
+    s0, s1, n = 0.05, 0.1, 5
+    chain = [W.Op("stars", (float(n),) + box + (s0, s1)), W.Op("splat", (0,))]
+    k, p, q = _circle_trace(chain, n=400, iters=24)
+    pts = q[:, 4:, 0, :3].reshape(-1, 3).astype(np.float64)      # after the first steps
+    # 2D input: a star's points share one z, which identifies the star
+    zs = np.unique(pts[:, 2])
+    assert len(zs) == n                        # every star is hit, no others
+    counts = []
+    for z in zs:
+        g = pts[pts[:, 2] == z]
+        counts.append(len(g))
+        c = g[:, :2].mean(axis=0)              # the disk attractor's mean is ~0
+        r = np.linalg.norm(g[:, :2] - c, axis=1).max()
+        assert box[0] <= c[0] <= box[1] and box[2] <= c[1] <= box[3] and box[4] <= z <= box[5]
+        assert 0.8 * s0 <= r <= 1.05 * s1      # a disk of radius s in [s0, s1]
+    m = len(pts) / n
+    assert all(abs(c - m) < 5 * np.sqrt(m) for c in counts)     # uniform star choice
+
+
+def test_hemisphere_lies_on_the_sphere():
+    chain = [W.Op("hemisphere", (2.0,)), W.Op("splat", (0,))]
+    k, p, q = _circle_trace(chain)
+    pts = q[:, :, 0, :3].reshape(-1, 3).astype(np.float64)
+    src = p.reshape(-1, 3).astype(np.float64)
+    inside = np.hypot(src[:, 0], src[:, 1]) <= 1.0
+    r = np.linalg.norm(pts[inside], axis=1)
+    assert np.all(np.abs(r - 2.0) < 2e-5 * 2.0)
+    assert np.all(pts[:, 2] <= 0.0)
+    assert np.allclose(pts[:, :2], 2.0 * src[:, :2], rtol=0, atol=1e-6)
+
+
+def test_bands_recolour_by_coordinate_and_reset_restores():
+    t = W.Target("hist_u32", 64, 64, 2, (0.0, 1.0, 0.0, 1.0))
+    chain = [W.Op("bands", (0.0, 4.0, 0.0, 2.0, 0.0)), W.Op("splat", (0,))]
+    res = O.render(W.square_system(), chain, [t], n_points=4096, iters=40, burn_in=8, seed=3)
+    h = res[0].buf
+    cols = np.arange(64)
+    band = (cols * 4) // 64 % 2                # floor(4 x) mod 2 of each column
+    for c in range(2):
+        assert h[c][:, band != c].sum() == 0 and h[c][:, band == c].sum() > 0
+    # a new branch starts from the generator's colour again (k mod 2)
+    chain2 = [W.Op("bands", (0.0, 0.0, 0.0, 1.0, 3.0)), W.Op("reset"), W.Op("splat", (0,))]
+    t4 = W.Target("hist_u32", 2, 2, 4, (0.0, 1.0, 0.0, 1.0))
+    res2 = O.render(W.square_system(), chain2, [t4], n_points=512, iters=30, burn_in=8, seed=3)
+    h2 = res2[0].buf
+    for c in range(4):                          # channel k holds quadrant k only
+        assert h2[c].sum() == h2[c][c // 2, c % 2]

@@ -78,9 +78,12 @@ def measure_atomic_peaks(torch, cfs, dev, rgba_bytes: int, depth_bytes: int, rep
 # objects' launches: dram__bytes_read.sum + dram__bytes_write.sum from a
 # full-size one-pass ncu capture).  Valid only for the kernel it was taken
 # on: the bench reports it when the SHA-1 of the generated program and its
-# device headers still matches, and null otherwise.
-RENDER_TRAFFIC_BYTES = 16093440          # (26460928 + 5725952) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "3296c7db5eec129b47904567f319469a5405c886"
+# device headers still matches, and null otherwise.  The hash is the one the
+# GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
+# spills) depends on the NVRTC build the process loads, so the generated text
+# can differ between machines.
+RENDER_TRAFFIC_BYTES = 16265856          # (26720768 + 5810944) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "f2d2df19caa3be2ae3ec733457b131ee954ebe0e"
 
 
 def render_program_sha1(cfs, wl, fast_trig=False):
@@ -374,6 +377,8 @@ def run_cfs(args, wl):
         line["batch"] = bench_batch(torch, cfs, dev, stream, n_frames=args.batch_frames)
     if args.sampler:
         line["sampler"] = bench_sampler(torch, cfs, dev, stream, train_steps=args.sampler_steps)
+    if args.space:
+        line["space"] = bench_space(torch, cfs, dev, stream)
     if args.cloud:
         line["cloud"] = bench_cloud(torch, cfs, dev, stream, n_frames=args.cloud_frames,
                                     n=args.cloud_points, fast_trig=args.fast_trig)
@@ -446,6 +451,55 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             "target_bytes": bytes_targets, "items": info["n_items"], "chunk": info["chunk"],
             "grid": info["grid"], "gpu_launches_per_batch": 1, "display": display,
             "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3)}
+
+
+def bench_space(torch, cfs, dev, stream, reps: int = 5):
+    """Many objects from one primitive (Section 3.2): the circle IFS of Eq. 1
+    drawn as stars (duplication), a banded planet and its ring into one
+    1920 x 1080 depth+colour layer, then resolved to packed RGBA8 (the
+    paper's output format).  2^20 points x 200 steps, burn-in 20: three depth
+    tests per point-step after burn-in."""
+    wl = W.space_render()
+    t = wl.targets[0]
+    job = wl.jobs[0]
+    sysh = cfs.System(job.system)
+    chain = cfs.Chain(wl.chain, 2)
+    layer = cfs.alloc_target(t, device=dev)
+    out = torch.empty((t.H, t.W), dtype=torch.int32, device=dev)
+    cfs.prepare(sysh, chain, [t], [layer])
+
+    def frame():
+        cfs.target_clear([t], [layer], stream)
+        cfs.render(sysh, chain, [t], [layer], n_points=job.n_points, iters=wl.iters,
+                   burn_in=wl.burn_in, seed=wl.seed, stream=stream)
+        cfs.tonemap(t, layer, out, stream=stream)
+
+    frame()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        frame()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ops = 3 * job.n_points * (wl.iters - wl.burn_in)
+    peaks = measure_atomic_peaks(torch, cfs, dev, 1 << 24, 8 * t.W * t.H)
+    achieved = ops / (ms * 1e-3) / 1e9
+    return {"workload": "circle IFS (Eq. 1) -> 400 stars + banded hemisphere planet + torus "
+                        "ring, 1920x1080 depth+colour layer -> RGBA8888; 2^20 points x 200 "
+                        "steps, burn-in 20",
+            "ms_per_frame": ms, "frames_per_s": 1e3 / ms,
+            "point_steps_per_s": job.n_points * wl.iters / (ms * 1e-3),
+            "depth_tests_per_s": ops / (ms * 1e-3), "gpu_launches_per_frame": 2,
+            "roofline": {"bound": "l2_atomic", "kernel": "cfs_render_kernel",
+                         "achieved": achieved, "peak": peaks["depth_test_u64"],
+                         "unit": "Gop/s", "frac": achieved / peaks["depth_test_u64"],
+                         "peak_source": "measured live: library depth-test microbenchmark "
+                                        "over the layer's footprint"},
+            "paper_context": "0.0215 s per frame for the paper's own scene on an AMD 6700 XT "
+                             "(point count not stated): context, not the same workload"}
 
 
 def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
@@ -680,6 +734,8 @@ def main():
                     help="skip the stored-cloud measurement")
     ap.add_argument("--fast-trig", action="store_true",
                     help="chains use reduced-argument hardware sine/cosine")
+    ap.add_argument("--no-space", dest="space", action="store_false",
+                    help="skip the many-objects scene measurement")
     ap.add_argument("--no-sampler", dest="sampler", action="store_false",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--sampler-steps", type=int, default=4000)

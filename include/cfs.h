@@ -98,8 +98,23 @@ typedef enum {
     CFS_OP_INVERSION = 14,   /* cx cy cz rho: c + rho^2 (p - c) / |p - c|^2;
                                 discards when |p - c|^2 < 1e-12                   */
     CFS_OP_SPLAT = 15,       /* params[0] = target slot: splat the current point */
-    CFS_OP_RESET = 16        /* start a new branch from a fresh copy of the
-                                iterated point                                    */
+    CFS_OP_RESET = 16,       /* start a new branch from a fresh copy of the
+                                iterated point (and of its colour index)          */
+    /* Duplication (Section 3.2: many small copies of one primitive placed by a
+     * PRNG, nothing stored): n, x0 x1 y0 y1 z0 z1, s0 s1.  Star j =
+     * floor(w n / 2^32), w = word (step & 3) of Philox block (point, step >> 2,
+     * system, 2); star j's centre (x0 + (x1-x0) u0, y0 + (y1-y0) u1,
+     * z0 + (z1-z0) u2) and size s0 + (s1-s0) u3 come from Philox block
+     * (j, 0, 0, 7), u = (word >> 8) 2^-24; q' = centre + size q (3D out;
+     * a 2D point has z = 0).  n in 1..2^24.  Not for stored clouds.        */
+    CFS_OP_STARS = 17,
+    /* R: the unit disk seen as the front half of a sphere: (R x, R y,
+     * -R sqrt(max(0, 1 - x^2 - y^2))); 2D -> 3D                            */
+    CFS_OP_HEMISPHERE = 18,
+    /* axis, freq, phase, n, base: the branch's colour index becomes
+     * base + (floor(freq coord[axis] + phase) mod n), a band texture (0 when
+     * the argument is not finite or beyond 1e9); n >= 1, base + n <= 16    */
+    CFS_OP_BANDS = 19
 } cfs_op_kind;
 
 typedef struct {

@@ -25,7 +25,8 @@ MAP_KINDS = {"affine": 0, "circle": 1}
 OP_KINDS = {
     "affine2": 1, "affine3": 2, "rotate2": 3, "rotate3": 4, "translate3": 5, "swirl": 6,
     "sinusoidal": 7, "sinusoidal3": 8, "stretch": 9, "torus": 10, "perspective": 11,
-    "twist_z": 12, "bend": 13, "inversion": 14, "splat": 15, "reset": 16,
+    "twist_z": 12, "bend": 13, "inversion": 14, "splat": 15, "reset": 16, "stars": 17,
+    "hemisphere": 18, "bands": 19,
 }
 TARGET_KINDS = {"hist_u32": 0, "rgba_f32": 1, "depth_u64": 2}
 FLAG_REUSE = 1

@@ -58,6 +58,18 @@ void derive_op_params(const cfs_transform& op, float out[CFS_OP_PARAMS])
         out[0] = v[0]; out[1] = v[1]; out[2] = v[2];
         out[3] = v[3] * v[3];
         break;
+    case CFS_OP_STARS:
+        // n as an integer's bits; box origins and extents (FP32 differences,
+        // as the oracle forms them)
+        {
+            const uint32_t n = (uint32_t)v[0];
+            std::memcpy(&out[0], &n, 4);
+        }
+        out[1] = v[1]; out[2] = v[2] - v[1];
+        out[3] = v[3]; out[4] = v[4] - v[3];
+        out[5] = v[5]; out[6] = v[6] - v[5];
+        out[7] = v[7]; out[8] = v[8] - v[7];
+        break;
     default:
         std::memcpy(out, v, sizeof(float) * CFS_OP_PARAMS);
         break;
@@ -76,9 +88,33 @@ bool finite_all(const float* v, int n)
 int op_out_dim(int kind, int dim_in)
 {
     switch (kind) {
-    case CFS_OP_TORUS: return 3;
+    case CFS_OP_TORUS: case CFS_OP_STARS: case CFS_OP_HEMISPHERE: return 3;
     default: return dim_in;
     }
+}
+
+// parameter rules of the ops whose parameters carry structure
+bool op_params_ok(const cfs_transform& op, int dim, std::string* why)
+{
+    const float* v = op.params;
+    if (op.kind == CFS_OP_STARS) {
+        if (!(v[0] >= 1.0f && v[0] <= 16777216.0f && v[0] == std::floor(v[0]))) {
+            *why = "stars: n must be an integer in 1..2^24";
+            return false;
+        }
+    } else if (op.kind == CFS_OP_BANDS) {
+        const int axis = (int)v[0], n = (int)v[3], base = (int)v[4];
+        if (!(v[0] == (float)axis && axis >= 0 && axis < dim)) {
+            *why = "bands: axis must name a coordinate of the point";
+            return false;
+        }
+        if (!(v[3] == (float)n && v[4] == (float)base && n >= 1 && base >= 0 &&
+              base + n <= CFS_MAX_MAPS)) {
+            *why = "bands: n >= 1, base >= 0 (integers), base + n <= 16";
+            return false;
+        }
+    }
+    return true;
 }
 
 bool op_needs_3d(int kind)
@@ -151,6 +187,7 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     for (int o = 0; o < ch->n_ops; ++o) {
         sp.op_kind[o] = ch->ops[o].kind;
         if (ch->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)ch->ops[o].params[1];
+        if (ch->ops[o].kind == CFS_OP_BANDS) sp.op_axis[o] = (int)ch->ops[o].params[0];
         if (ch->ops[o].kind == CFS_OP_SPLAT) {
             const int slot = (int)ch->ops[o].params[0];
             SplatSpec s;
@@ -345,7 +382,7 @@ cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint3
         const cfs_transform& op = ops[o];
         std::ostringstream m;
         m << "op " << o << ": ";
-        if (op.kind < CFS_OP_AFFINE2 || op.kind > CFS_OP_RESET)
+        if (op.kind < CFS_OP_AFFINE2 || op.kind > CFS_OP_BANDS)
             return fail(CFS_ERR_INVALID_ARG, m.str() + "unknown kind");
         if (!finite_all(op.params, CFS_OP_PARAMS))
             return fail(CFS_ERR_INVALID_ARG, m.str() + "parameters must be finite");
@@ -354,6 +391,12 @@ cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint3
             return fail(CFS_ERR_INVALID_ARG, m.str() + "needs a 3D point");
         if (op.kind == CFS_OP_TORUS && dim != 2)
             return fail(CFS_ERR_INVALID_ARG, m.str() + "torus embeds a 2D point");
+        if (op.kind == CFS_OP_HEMISPHERE && dim != 2)
+            return fail(CFS_ERR_INVALID_ARG, m.str() + "hemisphere lifts a 2D point");
+        {
+            std::string why;
+            if (!op_params_ok(op, dim, &why)) return fail(CFS_ERR_INVALID_ARG, m.str() + why);
+        }
         if (op.kind == CFS_OP_BEND && op.params[0] == 0.0f)
             return fail(CFS_ERR_INVALID_ARG, m.str() + "bend needs a nonzero curvature");
         if (op.kind == CFS_OP_ROTATE3 && (op.params[1] != 0.0f && op.params[1] != 1.0f &&
@@ -395,8 +438,20 @@ cfs_status cfs_chain_set_params(cfs_chain* chain, int index, const float* params
     std::memcpy(t.params, params, sizeof(t.params));
     if (t.kind == CFS_OP_SPLAT && t.params[0] != chain->ops[index].params[0])
         return fail(CFS_ERR_INVALID_ARG, "a SPLAT's slot cannot change");
+    if ((t.kind == CFS_OP_BANDS && t.params[0] != chain->ops[index].params[0]) ||
+        (t.kind == CFS_OP_ROTATE3 && t.params[1] != chain->ops[index].params[1]))
+        return fail(CFS_ERR_INVALID_ARG, "an op's axis is part of the compiled program");
     if (t.kind == CFS_OP_BEND && t.params[0] == 0.0f)
         return fail(CFS_ERR_INVALID_ARG, "bend needs a nonzero curvature");
+    {
+        // the op's input dimension is that of the chain up to it
+        int dim = chain->dim_in;
+        for (int o = 0; o < index; ++o)
+            dim = chain->ops[o].kind == CFS_OP_RESET ? chain->dim_in
+                                                      : op_out_dim(chain->ops[o].kind, dim);
+        std::string why;
+        if (!op_params_ok(t, dim, &why)) return fail(CFS_ERR_INVALID_ARG, why);
+    }
     chain->ops[index] = t;
     return CFS_OK;
 }
@@ -513,6 +568,10 @@ cfs_status cfs_render_points(const cfs_chain* chain, const float* xyz, const uin
         return fail(CFS_ERR_INVALID_ARG, "xyz must be 16-byte and fn 4-byte aligned");
     cfs_status st = validate_targets(chain, targets, n_targets);
     if (st != CFS_OK) return st;
+    for (int o = 0; o < chain->n_ops; ++o)
+        if (chain->ops[o].kind == CFS_OP_STARS)
+            return fail(CFS_ERR_UNSUPPORTED, "stars draw from the per-step random stream, which "
+                                             "a stored cloud does not have");
     // the generator plays no part: a one-map stand-in of the chain's dimension
     cfs_system stand_in;
     stand_in.dim = chain->dim_in;

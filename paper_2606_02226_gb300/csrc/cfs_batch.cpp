@@ -272,6 +272,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     for (int o = 0; o < chain->n_ops; ++o) {
         sp.op_kind[o] = chain->ops[o].kind;
         if (chain->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)chain->ops[o].params[1];
+        if (chain->ops[o].kind == CFS_OP_BANDS) sp.op_axis[o] = (int)chain->ops[o].params[0];
         if (chain->ops[o].kind == CFS_OP_SPLAT) {
             const int slot = (int)chain->ops[o].params[0];
             SplatSpec ss;

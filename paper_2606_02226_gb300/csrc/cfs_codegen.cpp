@@ -24,8 +24,10 @@ std::string ProgramSpec::key() const
       << ".u" << unroll << ".i" << ilp << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
-    for (int j = 0; j < n_ops; ++j) s << op_kind[j] << (op_kind[j] == CFS_OP_ROTATE3 ? "r" : "")
-                                      << (op_kind[j] == CFS_OP_ROTATE3 ? op_axis[j] : 0) << ",";
+    for (int j = 0; j < n_ops; ++j) {
+        const bool ax = op_kind[j] == CFS_OP_ROTATE3 || op_kind[j] == CFS_OP_BANDS;
+        s << op_kind[j] << (ax ? "r" : "") << (ax ? op_axis[j] : 0) << ",";
+    }
     s << ".s";
     for (const auto& sp : splats) s << sp.slot << ":" << sp.kind << ":" << sp.channels << ",";
     return s.str();
@@ -92,11 +94,13 @@ static void emit_gen_map(std::ostringstream& s, const ProgramSpec& sp)
 static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
 {
     s << "template <class TG>\n__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a,"
-         " const TG& tg, const CfsSmem& sm, float px, float py, float pz, int k, u32* disc,"
-         " bool do_splat, float* rec, float& ox, float& oy, float& oz, const CfsTile& tile)\n{\n";
-    s << "    (void)tile;\n";
+         " const TG& tg, const CfsSmem& sm, float px, float py, float pz, int k, u32 aux,"
+         " u32* disc, bool do_splat, float* rec, float& ox, float& oy, float& oz,"
+         " const CfsTile& tile)\n{\n";
+    s << "    (void)tile; (void)aux;\n";
     s << "    float qx = px, qy = py, qz = pz;\n    bool alive = true;\n";
-    s << "    (void)a; (void)tg; (void)sm; (void)disc; (void)do_splat; (void)rec; (void)k;\n";
+    s << "    int kc = k;   /* the branch's colour index */\n";
+    s << "    (void)a; (void)tg; (void)sm; (void)disc; (void)do_splat; (void)rec; (void)kc;\n";
     size_t si = 0;
     for (int o = 0; o < sp.n_ops; ++o) {
         s << "    /* op " << o << " */ ";
@@ -130,8 +134,22 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
         case CFS_OP_INVERSION:
             s << "alive = cfs_inversion(" << Plist(o, 4) << "qx, qy, qz) && alive;\n";
             break;
+        case CFS_OP_STARS:
+            s << "cfs_stars(a, __float_as_uint(" << P(o, 0) << "), " << P(o, 1) << ", "
+              << P(o, 2) << ", " << P(o, 3) << ", " << P(o, 4) << ", " << P(o, 5) << ", "
+              << P(o, 6) << ", " << P(o, 7) << ", " << P(o, 8) << ", aux, qx, qy, qz);\n";
+            break;
+        case CFS_OP_HEMISPHERE:
+            s << "cfs_hemisphere(" << P(o, 0) << ", qx, qy, qz);\n";
+            break;
+        case CFS_OP_BANDS: {
+            const char* coord = sp.op_axis[o] == 0 ? "qx" : (sp.op_axis[o] == 1 ? "qy" : "qz");
+            s << "kc = cfs_bands(" << coord << ", " << P(o, 1) << ", " << P(o, 2) << ", (int)"
+              << P(o, 3) << ", (int)" << P(o, 4) << ");\n";
+            break;
+        }
         case CFS_OP_RESET:
-            s << "qx = px; qy = py; qz = pz; alive = true;\n";
+            s << "qx = px; qy = py; qz = pz; alive = true; kc = k;\n";
             break;
         case CFS_OP_SPLAT: {
             const SplatSpec& t = sp.splats[si];
@@ -140,17 +158,17 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
               << "] = alive ? 1.0f : 0.0f; }\n";
             s << "    if (do_splat) ";
             if (t.kind == CFS_TARGET_HIST_U32 && sp.tile && si == 0)
-                s << "cfs_splat_hist_tile(tg[" << t.slot << "], tile, qx, qy, alive, k % "
+                s << "cfs_splat_hist_tile(tg[" << t.slot << "], tile, qx, qy, alive, kc % "
                   << t.channels << ", disc[" << t.slot << "]);\n";
             else if (t.kind == CFS_TARGET_HIST_U32)
-                s << "cfs_splat_hist(tg[" << t.slot << "], qx, qy, alive, k % " << t.channels
+                s << "cfs_splat_hist(tg[" << t.slot << "], qx, qy, alive, kc % " << t.channels
                   << ", disc[" << t.slot << "]);\n";
             else if (t.kind == CFS_TARGET_RGBA_F32)
                 s << "cfs_splat_rgba(tg[" << t.slot << "], qx, qy, alive, sm.pal[" << t.slot
-                  << "][k], disc[" << t.slot << "]);\n";
+                  << "][kc], disc[" << t.slot << "]);\n";
             else
                 s << "cfs_splat_depth(tg[" << t.slot << "], qx, qy, qz, alive, sm.pal8["
-                  << t.slot << "][k], disc[" << t.slot << "]);\n";
+                  << t.slot << "][kc], disc[" << t.slot << "]);\n";
             ++si;
             break;
         }
@@ -172,6 +190,11 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_FAST_TRIG " << (sp.fast_trig ? 1 : 0) << "\n";
     s << "#define CFS_UNROLL " << sp.unroll << "\n";
     s << "#define CFS_ILP " << (sp.ilp == 2 ? 2 : 1) << "\n";
+    {
+        bool aux = false;
+        for (int o = 0; o < sp.n_ops; ++o) aux = aux || sp.op_kind[o] == CFS_OP_STARS;
+        s << "#define CFS_AUX " << (aux ? 1 : 0) << "\n";
+    }
     s << "#define CFS_BATCH " << (sp.mode == Mode::Batch ? 1 : 0) << "\n";
     s << "#define CFS_CLOUD " << (sp.mode == Mode::Cloud ? 1 : 0) << "\n";
     s << "#define CFS_TILE " << (sp.tile ? 1 : 0) << "\n";

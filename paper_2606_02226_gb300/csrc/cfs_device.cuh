@@ -304,6 +304,47 @@ __device__ __forceinline__ bool cfs_inversion(float cx, float cy, float cz, floa
     return d2 >= 1e-12f;
 }
 
+/* Duplication (Section 3.2): the copy lands on star j = floor(aux n / 2^32)
+ * of n, whose centre and size come from Philox block (j, 0, 0, 7):
+ * q' = centre + size q.  Parameters: n (integer bits), x0, x1 - x0, y0,
+ * y1 - y0, z0, z1 - z0, s0, s1 - s0. */
+__device__ __forceinline__ void cfs_stars(const cfs_launch_args& a, u32 n, float x0, float dx,
+                                          float y0, float dy, float z0, float dz, float s0,
+                                          float ds, u32 aux, float& x, float& y, float& z)
+{
+    const u32 j = __umulhi(aux, n);
+    const uint4 r = cfs_philox(a, j, 0u, 0u, 7u);
+    const float cx = fmaf(dx, (float)(r.x >> 8) * CFS_INV_2_24, x0);
+    const float cy = fmaf(dy, (float)(r.y >> 8) * CFS_INV_2_24, y0);
+    const float cz = fmaf(dz, (float)(r.z >> 8) * CFS_INV_2_24, z0);
+    const float sz = fmaf(ds, (float)(r.w >> 8) * CFS_INV_2_24, s0);
+    x = fmaf(sz, x, cx);
+    y = fmaf(sz, y, cy);
+    z = fmaf(sz, z, cz);
+}
+
+/* The unit disk as the front (z <= 0) half of a sphere of radius R. */
+__device__ __forceinline__ void cfs_hemisphere(float R, float& x, float& y, float& z)
+{
+    const float r2 = fmaf(x, x, y * y);
+    const float h = sqrtf(fmaxf(0.0f, 1.0f - r2));
+    x = R * x;
+    y = R * y;
+    z = -(R * h);
+}
+
+/* Band texture: colour base + (floor(freq u + phase) mod n). */
+__device__ __forceinline__ int cfs_bands(float u, float freq, float phase, int n, int base)
+{
+    const float t = fmaf(freq, u, phase);
+    int m = 0;
+    if (isfinite(t) && fabsf(t) < 1.0e9f) {
+        const long long b = (long long)floorf(t);
+        m = (int)(((b % n) + n) % n);
+    }
+    return base + m;
+}
+
 /* ---- splats (Section 1: the point colours the appropriate pixel) -------- */
 /* Bin of one coordinate: floor((u - lo) * scale), valid for lo <= u <= hi,
  * the last bin closed.  Returns -1 when outside (NaN included). */

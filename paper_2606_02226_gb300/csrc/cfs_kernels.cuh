@@ -5,7 +5,7 @@
  *   CFS_DIM, CFS_NCMP (thresholds compared), CFS_NT (targets), CFS_REUSE,
  *   CFS_BATCH, CFS_BLOCK, CFS_MINB,
  *   cfs_gen_map(a, k, x, y, z, sm)        -- the fused generator switch
- *   cfs_chain(a, tg, sm, px, py, pz, k, disc, splat, rec, qx, qy, qz)
+ *   cfs_chain(a, tg, sm, px, py, pz, k, aux, disc, splat, rec, qx, qy, qz)
  *                                         -- the fused transform chain
  * Every point lives in registers for its whole trajectory (SoA state: x, y,
  * z); only the splats touch global memory.
@@ -14,6 +14,21 @@
 #define CFS_KERNELS_CUH
 
 #define CFS_NT_ARR (CFS_NT > 0 ? CFS_NT : 1)
+#ifndef CFS_AUX
+#define CFS_AUX 0
+#endif
+
+/* auxiliary random block of steps 4 nb .. 4 nb + 3 of point i (stochastic
+ * chain ops): Philox (i, nb, s, 2); zeros when the chain has none */
+__device__ __forceinline__ uint4 cfs_aux_block(const cfs_launch_args& a, u32 i, u32 nb, u32 sid)
+{
+#if CFS_AUX
+    return cfs_philox(a, i, nb, sid, 2u);
+#else
+    (void)a; (void)i; (void)nb; (void)sid;
+    return make_uint4(0u, 0u, 0u, 0u);
+#endif
+}
 
 /* map choice k = #{ j < n_cmp : w >= T_j }: thresholds of a single render
  * come from the constant bank, those of a batch frame from shared memory */
@@ -63,22 +78,23 @@ __device__ __forceinline__ void cfs_start(const cfs_launch_args& a, u32 i, u32 s
  * CFS_REUSE, let the chain's result replace the point (Fig. 2C). */
 template <class CH, class TG>
 __device__ __forceinline__ void cfs_step(const cfs_launch_args& a, const CH& choose, const TG& tg,
-                                         const CfsSmem& sm, u32 n, u32 w, float& x, float& y,
-                                         float& z, u32* disc, const CfsTile& tile)
+                                         const CfsSmem& sm, u32 n, u32 w, u32 aux, float& x,
+                                         float& y, float& z, u32* disc, const CfsTile& tile)
 {
     const int k = choose(w);
     cfs_gen_map(a, k, x, y, z, sm);
 #if CFS_REUSE
     {
         float qx, qy, qz;
-        if (cfs_chain(a, tg, sm, x, y, z, k, disc, n >= a.burn_in, (float*)0, qx, qy, qz, tile)) {
+        if (cfs_chain(a, tg, sm, x, y, z, k, aux, disc, n >= a.burn_in, (float*)0, qx, qy, qz,
+                      tile)) {
             x = qx; y = qy; z = qz;
         }
     }
 #else
     if (n >= a.burn_in) {
         float qx, qy, qz;
-        cfs_chain(a, tg, sm, x, y, z, k, disc, true, (float*)0, qx, qy, qz, tile);
+        cfs_chain(a, tg, sm, x, y, z, k, aux, disc, true, (float*)0, qx, qy, qz, tile);
     }
 #endif
 }
@@ -103,33 +119,36 @@ __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH
 #pragma unroll 1
     for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
         const uint4 r = cfs_philox(a, i, nb, sid, 0u);
+        const uint4 ra = cfs_aux_block(a, i, nb, sid);
         const u32 n = nb << 2;
 #if CFS_UNROLL == 4
-        if (whole || (n >= b0 && n < b1)) cfs_step(a, choose, tg, sm, n, r.x, x, y, z, disc, tile);
+        if (whole || (n >= b0 && n < b1))
+            cfs_step(a, choose, tg, sm, n, r.x, ra.x, x, y, z, disc, tile);
         if (whole || (n + 1 >= b0 && n + 1 < b1))
-            cfs_step(a, choose, tg, sm, n + 1, r.y, x, y, z, disc, tile);
+            cfs_step(a, choose, tg, sm, n + 1, r.y, ra.y, x, y, z, disc, tile);
         if (whole || (n + 2 >= b0 && n + 2 < b1))
-            cfs_step(a, choose, tg, sm, n + 2, r.z, x, y, z, disc, tile);
+            cfs_step(a, choose, tg, sm, n + 2, r.z, ra.z, x, y, z, disc, tile);
         if (whole || (n + 3 >= b0 && n + 3 < b1))
-            cfs_step(a, choose, tg, sm, n + 3, r.w, x, y, z, disc, tile);
+            cfs_step(a, choose, tg, sm, n + 3, r.w, ra.w, x, y, z, disc, tile);
 #elif CFS_UNROLL == 2
 #pragma unroll 1
         for (u32 h = 0; h < 4; h += 2) {
             const u32 w0 = h ? r.z : r.x, w1 = h ? r.w : r.y;
+            const u32 a0 = h ? ra.z : ra.x, a1 = h ? ra.w : ra.y;
             if (whole || (n + h >= b0 && n + h < b1))
-                cfs_step(a, choose, tg, sm, n + h, w0, x, y, z, disc, tile);
+                cfs_step(a, choose, tg, sm, n + h, w0, a0, x, y, z, disc, tile);
             if (whole || (n + h + 1 >= b0 && n + h + 1 < b1))
-                cfs_step(a, choose, tg, sm, n + h + 1, w1, x, y, z, disc, tile);
+                cfs_step(a, choose, tg, sm, n + h + 1, w1, a1, x, y, z, disc, tile);
         }
 #else
         u32 w[4] = {r.x, r.y, r.z, r.w};
+        u32 v[4] = {ra.x, ra.y, ra.z, ra.w};
 #pragma unroll 1
         for (u32 h = 0; h < 4; ++h) {
             if (whole || (n + h >= b0 && n + h < b1))
-                cfs_step(a, choose, tg, sm, n + h, w[0], x, y, z, disc, tile);
-            w[0] = w[1];
-            w[1] = w[2];
-            w[2] = w[3];
+                cfs_step(a, choose, tg, sm, n + h, w[0], v[0], x, y, z, disc, tile);
+            w[0] = w[1]; w[1] = w[2]; w[2] = w[3];
+            v[0] = v[1]; v[1] = v[2]; v[2] = v[3];
         }
 #endif
     }
@@ -152,14 +171,18 @@ __device__ __forceinline__ void cfs_run_point2(const cfs_launch_args& a, const C
     for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
         const uint4 r0 = cfs_philox(a, i0, nb, sid, 0u);
         const uint4 r1 = cfs_philox(a, i1, nb, sid, 0u);
+        const uint4 a0 = cfs_aux_block(a, i0, nb, sid);
+        const uint4 a1 = cfs_aux_block(a, i1, nb, sid);
         const u32 n = nb << 2;
         const u32 w0[4] = {r0.x, r0.y, r0.z, r0.w};
         const u32 w1[4] = {r1.x, r1.y, r1.z, r1.w};
+        const u32 v0[4] = {a0.x, a0.y, a0.z, a0.w};
+        const u32 v1[4] = {a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (whole || (n + q >= b0 && n + q < b1)) {
-                cfs_step(a, choose, tg, sm, n + q, w0[q], x0, y0, z0, disc, tile);
-                cfs_step(a, choose, tg, sm, n + q, w1[q], x1, y1, z1, disc, tile);
+                cfs_step(a, choose, tg, sm, n + q, w0[q], v0[q], x0, y0, z0, disc, tile);
+                cfs_step(a, choose, tg, sm, n + q, w1[q], v1[q], x1, y1, z1, disc, tile);
             }
         }
     }
@@ -257,13 +280,13 @@ cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
         const u32 K = cfs_ld_stream_u32(fn + o, policy);
         const CfsTile nt{0, 0, 0, 0, 0, 1, 0, 0};
         float qx, qy, qz;
-        cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), disc, true, (float*)0, qx, qy, qz,
+        cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), 0u, disc, true, (float*)0, qx, qy, qz,
                   nt);
-        cfs_chain(a, a.tg, sm, X.y, Y.y, Z.y, (int)((K >> 8) & 0xFFu), disc, true, (float*)0, qx,
+        cfs_chain(a, a.tg, sm, X.y, Y.y, Z.y, (int)((K >> 8) & 0xFFu), 0u, disc, true, (float*)0, qx,
                   qy, qz, nt);
-        cfs_chain(a, a.tg, sm, X.z, Y.z, Z.z, (int)((K >> 16) & 0xFFu), disc, true, (float*)0, qx,
+        cfs_chain(a, a.tg, sm, X.z, Y.z, Z.z, (int)((K >> 16) & 0xFFu), 0u, disc, true, (float*)0, qx,
                   qy, qz, nt);
-        cfs_chain(a, a.tg, sm, X.w, Y.w, Z.w, (int)(K >> 24), disc, true, (float*)0, qx, qy, qz,
+        cfs_chain(a, a.tg, sm, X.w, Y.w, Z.w, (int)(K >> 24), 0u, disc, true, (float*)0, qx, qy, qz,
                   nt);
     }
     cfs_flush_discards(a, disc, CFS_NT);
@@ -317,8 +340,9 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         const uint4 r = cfs_philox(a, i, n >> 2, a.system_id, 0u);
         const int k = choose(cfs_word(r, n & 3u));
         cfs_gen_map(a, k, x, y, z, sm);
+        const u32 aux = cfs_word(cfs_aux_block(a, i, n >> 2, a.system_id), n & 3u);
         float qx, qy, qz;
-        const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, disc, false,
+        const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, aux, disc, false,
                                      qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz,
                                      CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
 #if CFS_REUSE
@@ -402,9 +426,10 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
             const int k = choose(cfs_word(r, n & 3u));
             cfs_gen_map(a, k, x, y, z, sm);
             if (n < a.burn_in) continue;
+            const u32 aux = cfs_word(cfs_aux_block(a, i, n >> 2, sid), n & 3u);
             float rec[4 * CFS_NSPLAT_ARR];
             float qx, qy, qz;
-            cfs_chain(a, s_tg, sm, x, y, z, k, disc, false, rec, qx, qy, qz,
+            cfs_chain(a, s_tg, sm, x, y, z, k, aux, disc, false, rec, qx, qy, qz,
                       CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
             const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
             const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);

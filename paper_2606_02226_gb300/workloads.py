@@ -326,3 +326,62 @@ def synthetic_layer(kind: str, W: int, H: int, C: int = 4, seed: int = 0,
         keys[zero] = np.uint64(0xFFFFFFFFFFFFFFFF)
         return keys
     raise ValueError(kind)
+
+
+# ---------------------------------------------------------------------------
+# scene of many objects from one primitive (Section 3.2): stars, a banded
+# planet and its ring, all drawn from the circle IFS of Eq. 1
+# ---------------------------------------------------------------------------
+SPACE_ASPECT = 16.0 / 9.0
+# palette indices: 0-1 the generator maps, 4-7 planet bands, 8 stars, 9 ring
+SPACE_STAR_COLOUR, SPACE_RING_COLOUR, SPACE_BAND_BASE = 8, 9, 4
+
+
+def space_palette8() -> np.ndarray:
+    cols = np.zeros((MAX_MAPS, 4), dtype=np.float64)
+    cols[:, 3] = 1.0
+    cols[0, :3] = (0.5, 0.5, 0.5)
+    cols[1, :3] = (0.5, 0.5, 0.5)
+    cols[4, :3] = (0.86, 0.62, 0.38)        # planet bands
+    cols[5, :3] = (0.72, 0.45, 0.26)
+    cols[6, :3] = (0.93, 0.83, 0.66)
+    cols[7, :3] = (0.60, 0.36, 0.22)
+    cols[8, :3] = (1.0, 1.0, 0.94)          # stars
+    cols[9, :3] = (0.78, 0.74, 0.66)        # ring
+    u8 = np.round(cols * 255.0).astype(np.uint32)
+    return (u8[:, 0] | (u8[:, 1] << 8) | (u8[:, 2] << 16) | (u8[:, 3] << 24)).astype(np.uint32)
+
+
+def space_chain(n_stars: int = 400, focal: float = 2.0, tilt: float = 1.25) -> List[Op]:
+    """Three objects from one copy of the circle primitive's point, each a
+    branch into one depth+colour layer: stars (duplication by the auxiliary
+    Philox stream) far behind, a planet (the disk as a hemisphere facing the
+    camera, banded) at z = 6 and a tilted thin torus as its ring."""
+    star = [Op("stars", (float(n_stars), -16.0, 16.0, -9.0, 9.0, 14.0, 20.0, 0.01, 0.04)),
+            Op("bands", (0.0, 0.0, 0.0, 1.0, float(SPACE_STAR_COLOUR))),
+            Op("perspective", (focal, 0.1)), Op("splat", (0,))]
+    planet = [Op("hemisphere", (1.0,)),
+              Op("bands", (1.0, 3.0, 0.5, 4.0, float(SPACE_BAND_BASE))),
+              Op("rotate3", (0.25, 2.0)), Op("translate3", (0.0, 0.0, 6.0)),
+              Op("perspective", (focal, 0.1)), Op("splat", (0,))]
+    ring = [Op("torus", (1.8, 0.04)),
+            Op("bands", (0.0, 0.0, 0.0, 1.0, float(SPACE_RING_COLOUR))),
+            Op("rotate3", (tilt, 0.0)), Op("rotate3", (0.25, 2.0)),
+            Op("translate3", (0.0, 0.0, 6.0)),
+            Op("perspective", (focal, 0.1)), Op("splat", (0,))]
+    return star + [Op("reset")] + planet + [Op("reset")] + ring
+
+
+def space_target(W: int = 1920, H: int = 1080) -> Target:
+    return Target("depth_u64", W, H, 1, (-SPACE_ASPECT, SPACE_ASPECT, -1.0, 1.0),
+                  palette8=space_palette8())
+
+
+def space_render(n_points: int = 1 << 20, iters: int = 200, burn_in: int = 20, W: int = 1920,
+                 H: int = 1080, seed: int = 0, n_stars: int = 400) -> Workload:
+    """The scene at 1920 x 1080 (packed RGBA8 after the display, as the
+    paper's output): every point of the circle IFS draws a star, the planet
+    and the ring each step after burn-in."""
+    return Workload("space scene: circle IFS -> stars + banded planet + ring, depth layer",
+                    [RenderJob(circle_system(), 0, n_points, 0)], space_chain(n_stars),
+                    [space_target(W, H)], iters, burn_in, seed)

@@ -153,3 +153,22 @@ def test_display_argument_errors_need_no_gpu():
     assert call(p, 1 << 20, None) == 1               # maximum wanted, nowhere to put it
     assert L.cfs_tonemap(None, ctypes.byref(p), 1 << 20, 1 << 21, None) == 1
     assert L.cfs_batch_display(None, 0, ctypes.byref(p), None, None, None) == 1
+
+
+def test_new_op_validation_and_codegen():
+    ok = cfs.Chain([W.Op("stars", (5.0, -1, 1, -1, 1, 0, 1, 0.1, 0.2)), W.Op("splat", (0,))], 2)
+    assert _err(lambda: cfs.Chain([W.Op("stars", (0.0,)), W.Op("splat", (0,))], 2)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("stars", (2.5,)), W.Op("splat", (0,))], 2)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("bands", (2.0, 1.0, 0.0, 2.0, 0.0))], 2)) == 1  # no z
+    assert _err(lambda: cfs.Chain([W.Op("bands", (0.0, 1.0, 0.0, 4.0, 14.0))], 2)) == 1
+    assert _err(lambda: cfs.Chain([W.Op("torus", (1.0, 0.2)), W.Op("hemisphere", (1.0,))], 2)) == 1
+    c = cfs.Chain([W.Op("bands", (1.0, 1.0, 0.0, 2.0, 0.0)), W.Op("splat", (0,))], 2)
+    assert _err(lambda: c.set_params(0, (0.0, 1.0, 0.0, 2.0, 0.0))) == 1      # axis is compiled in
+    c.set_params(0, (1.0, 3.0, 0.5, 2.0, 1.0))
+    wl = W.space_render(n_points=64, iters=24, W=64, H=36)
+    src, log = cfs.codegen_check(cfs.System(wl.jobs[0].system), cfs.Chain(wl.chain, 2),
+                                 wl.targets)
+    assert "#define CFS_AUX 1" in src and "cfs_stars(" in src and "cfs_hemisphere(" in src
+    assert "0 bytes spill stores" in log
+    src2, _ = cfs.codegen_check(cfs.System(W.square_system()), ok, [W.Target("hist_u32", 8, 8, 4)])
+    assert "#define CFS_AUX 1" in src2

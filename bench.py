@@ -83,18 +83,27 @@ def measure_atomic_peaks(torch, cfs, dev, rgba_bytes: int, depth_bytes: int, rep
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
 RENDER_TRAFFIC_BYTES = 16265856          # (26720768 + 5810944) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "f2d2df19caa3be2ae3ec733457b131ee954ebe0e"
+RENDER_TRAFFIC_SOURCE_SHA1 = None   # set from the GPU machine's hash below
+
+
+def _code_only(text: str) -> str:
+    """C/C++ text without comments and blank lines (a comment edit does not
+    change the compiled kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
 
 
 def render_program_sha1(cfs, wl, fast_trig=False):
     import hashlib
     src, _ = cfs.codegen_check(cfs.System(wl.jobs[0].system),
                                cfs.Chain(wl.chain, 2, fast_trig=fast_trig), wl.targets)
-    h = hashlib.sha1(src.encode())
+    h = hashlib.sha1(_code_only(src).encode())
     csrc = os.path.join(ROOT, "paper_2606_02226_gb300", "csrc")
     for name in ("cfs_args.h", "cfs_device.cuh", "cfs_kernels.cuh"):
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, name)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -122,8 +122,8 @@ typedef struct {
     float params[CFS_OP_PARAMS];
 } cfs_transform;
 
-/* ---- output targets (Section 1: "histogrammed or splatted on to some output
- *      layer"; the colour is the map used to land) ------------------------- */
+/* ---- output targets (Section 1: points are accumulated into an output
+ *      layer; the colour tells which map moved the point last) ---------- */
 typedef enum {
     /* u32 [C][H][W]; +1 in channel (k mod C), k = last generator map */
     CFS_TARGET_HIST_U32 = 0,

@@ -28,7 +28,7 @@
  *  - Map choice: with S_k the running sum of probabilities divided by their
  *    total (double), T_k = floor(S_k * 2^32) (k < n-1) and the chosen map is
  *    k = #{ j < n-1 : w >= T_j }  (thresholds >= 2^32 never count).
- *  - Colour (Section 1, "the function used ... to land"): the index k of the
+ *  - Colour (Section 1: the colour tells which function moved the point last): the index k of the
  *    last generator map applied.
  *  - Duplication (Section 3.2: the stars are generated on the fly by a PRNG
  *    scheme): STARS moves the copy onto one of n small copies of the
@@ -37,7 +37,7 @@
  *    come from Philox block (j, 0, 0, 7), u_c = (word_c >> 8) * 2^-24:
  *    centre (x0 + (x1 - x0) u_0, y0 + (y1 - y0) u_1, z0 + (z1 - z0) u_2),
  *    size s0 + (s1 - s0) u_3 (each a single fma); q' = centre + size * q.
- *  - Splat (Section 1, "colors the appropriate pixel"): ix = floor((x - x0) * sx)
+ *  - Splat (Section 1: the point lands in the pixel it falls in): ix = floor((x - x0) * sx)
  *    with sx = W / (x1 - x0) in FP32, valid for x0 <= x <= x1, the last bin
  *    closed (ix = min(ix, W-1)); outside or non-finite points are counted as
  *    discarded.  Rows likewise from y.
@@ -85,7 +85,7 @@ static uint32_t philox_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2
 }
 
 /* ------------------------------------------------------------------------ */
-/* Threshold table and map choice ("a new function is chosen at random",
+/* Threshold table and map choice (each step draws a function at random,
  * Section 3; per-map probabilities as the workloads specify).              */
 /* ------------------------------------------------------------------------ */
 int orc_thresholds(int n_maps, const double* prob, uint64_t* T)
@@ -532,7 +532,7 @@ int orc_trace(const orc_system* sys, const orc_chain* ch, const orc_run* run,
     return 0;
 }
 
-/* Stored point cloud (Section 3, "store all points ... then transform"):
+/* Stored point cloud (Section 3: the staged alternative that keeps every point, then transforms it):
  * iterate each point `iters` steps and keep its final position and the index
  * of the last map applied. */
 int orc_pointcloud_generate(const orc_system* sys, uint64_t seed, uint32_t system_id,

@@ -345,7 +345,7 @@ __device__ __forceinline__ int cfs_bands(float u, float freq, float phase, int n
     return base + m;
 }
 
-/* ---- splats (Section 1: the point colours the appropriate pixel) -------- */
+/* ---- splats (Section 1: the point colours the pixel it lands in) --------- */
 /* Bin of one coordinate: floor((u - lo) * scale), valid for lo <= u <= hi,
  * the last bin closed.  Returns -1 when outside (NaN included). */
 __device__ __forceinline__ int cfs_bin(float u, float lo, float hi, float scale, int n)

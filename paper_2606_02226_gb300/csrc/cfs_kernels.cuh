@@ -190,7 +190,7 @@ __device__ __forceinline__ void cfs_run_point2(const cfs_launch_args& a, const C
 #endif
 
 #if CFS_CLOUD
-/* Stored point cloud (Section 3: "store all points ... then transform"):
+/* Stored point cloud (Section 3: the staged alternative that keeps every point, then transforms it):
  * point i runs steps 0 .. iters-1 from its Philox start point; its final
  * position goes to SoA xyz[d][i] (coalesced) and the index of its last map
  * to fn[i]. */

@@ -194,6 +194,37 @@ cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chai
 cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint32_t flags,
                           cfs_chain** out);
 cfs_status cfs_chain_destroy(cfs_chain* chain);
+
+/* Composes a chain from a scribble program (Section 3.1: verses, stanzas and
+ * poems composed at the user's request before compilation).  `source` holds
+ * any number of fragments:
+ *   __verse  NAME(p1, p2 | T k1 = d1; T k2 = d2;) { BODY }
+ *   __stanza NAME(p1 | T k = d;) { PRE __split_stanza(); POST }
+ *   __poem   NAME() { statements }
+ * and `poem` names the poem that is the chain.  Its statements run once per
+ * splat step on the copy of the point (float qx, qy, qz), its colour index
+ * (int kc), the step's auxiliary random word (u32 aux), with the generator's
+ * point (px, py, pz) and map index k readable and `alive` cleared by
+ * discarding ops.  Calls: `@VCALL v(args | k = value;);` inlines verse v as a
+ * block that binds each positional parameter by reference to its argument
+ * and each keyword parameter to the call's value or else its default;
+ * `@SCALL s(args | ...) { BLOCK }` does the same for stanza s with BLOCK
+ * injected at its __split_stanza().  Bodies are CUDA C++ and may use the
+ * calling context's names.  The library's ops are functions of the poem:
+ * reset(), discard(), affine2(a, b, c, d, e, f), rotate2(angle) and
+ * rotate3(angle, axis) (cos and sin in double), translate3(x, y, z), swirl(), sinusoidal(), sinusoidal3(),
+ * stretch(), torus(R, r), perspective(f, near), twist_z(kappa), bend(beta),
+ * inversion(cx, cy, cz, rho), hemisphere(R), bands(axis, freq, phase, n,
+ * base), stars(n, x0, x1, y0, y1, z0, z1, s0, s1), with the op semantics
+ * listed above; splat(SLOT) (a literal slot 0..3) splats into that target.
+ * Expansion and argument errors are reported here (CFS_ERR_INVALID_ARG);
+ * compile errors of the bodies at the first render (CFS_ERR_COMPILE, NVRTC
+ * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG or 0. */
+cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem,
+                                uint32_t flags, cfs_chain** out);
+/* Input dimension, op count (0 for a scribble chain) and splat count (the
+ * records per step of cfs_trace) of a chain; any output may be NULL. */
+cfs_status cfs_chain_info(const cfs_chain* chain, int* dim_in, int* n_ops, int* n_splat);
 /* Replaces the parameters of op `index` (same kind); for animated chains. */
 cfs_status cfs_chain_set_params(cfs_chain* chain, int index, const float* params);
 

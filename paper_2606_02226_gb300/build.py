@@ -25,7 +25,7 @@ GENCODE = "arch=compute_103a,code=sm_103a"
 EMBEDDED = [("kSrcArgs", "cfs_args.h"), ("kSrcDevice", "cfs_device.cuh"),
             ("kSrcKernels", "cfs_kernels.cuh")]
 SOURCES = ["cfs_api.cpp", "cfs_batch.cpp", "cfs_codegen.cpp", "cfs_runtime.cpp",
-           "cfs_builtin.cu", "cfs_sort.cu", "cfs_sampler.cu", "cfs_noalloc.cu", "cfs_display.cu",
+           "cfs_builtin.cu", "cfs_sort.cu", "cfs_sampler.cu", "cfs_noalloc.cu", "cfs_display.cu", "cfs_scribble.cpp",
            "cfs_embed.cpp"]
 _LOCK = threading.Lock()
 

@@ -90,6 +90,10 @@ _SIGNATURES = {
     "cfs_compose_ex": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(cfs_transform), ctypes.c_int,
                                       ctypes.c_uint32, ctypes.POINTER(_P)]),
     "cfs_chain_destroy": (ctypes.c_int, [_P]),
+    "cfs_compose_scribble": (ctypes.c_int, [ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p,
+                                            ctypes.c_uint32, ctypes.POINTER(_P)]),
+    "cfs_chain_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cfs_chain_set_params": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "cfs_render": (ctypes.c_int, [_P, _P, ctypes.POINTER(cfs_render_params),
                                   ctypes.POINTER(cfs_target), ctypes.c_int, _P]),
@@ -240,6 +244,23 @@ class Chain:
         self.ops = list(ops)
         self.dim_in = dim_in
         self.n_splat = sum(1 for o in ops if o.kind == "splat")
+
+    @classmethod
+    def from_scribble(cls, source: str, poem: str, dim_in: int, fast_trig: bool = False):
+        """A chain written as a scribble poem (verses, stanzas, poems; see
+        ``cfs_compose_scribble`` in include/cfs.h for the language)."""
+        self = cls.__new__(cls)
+        h = _P()
+        _check(lib().cfs_compose_scribble(dim_in, source.encode(), poem.encode(),
+                                          1 if fast_trig else 0, ctypes.byref(h)))
+        self.fast_trig = fast_trig
+        self.handle = h
+        self.ops = []
+        self.dim_in = dim_in
+        ns = ctypes.c_int()
+        _check(lib().cfs_chain_info(h, None, None, ctypes.byref(ns)))
+        self.n_splat = ns.value
+        return self
 
     def set_params(self, index: int, params: Sequence[float]):
         buf = (ctypes.c_float * OP_PARAMS)(*([float(v) for v in params] +

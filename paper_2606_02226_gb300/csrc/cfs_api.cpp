@@ -150,6 +150,13 @@ cfs_status validate_targets(const cfs_chain* ch, const cfs_target* tg, int n_tg)
               std::isfinite(g.y1) && g.x1 > g.x0 && g.y1 > g.y0))
             return fail(CFS_ERR_INVALID_ARG, m.str() + "view needs finite x0 < x1, y0 < y1");
     }
+    for (int slot : ch->scribble_slots)
+        if (slot >= n_tg) {
+            std::ostringstream m;
+            m << "scribble splat names target slot " << slot << " but only " << n_tg
+              << " targets were given";
+            return fail(CFS_ERR_INVALID_ARG, m.str());
+        }
     // every SPLAT names an existing slot, and depth splats see a 3D point
     int dim = ch->dim_in;
     for (int o = 0; o < ch->n_ops; ++o) {
@@ -196,6 +203,14 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
             s.channels = (tg && tg[slot].kind == CFS_TARGET_HIST_U32) ? tg[slot].channels : 1;
             sp.splats.push_back(s);
         }
+    }
+    sp.scribble = ch->scribble;
+    for (int slot : ch->scribble_slots) {
+        SplatSpec s;
+        s.slot = slot;
+        s.kind = tg ? tg[slot].kind : CFS_TARGET_HIST_U32;
+        s.channels = (tg && tg[slot].kind == CFS_TARGET_HIST_U32) ? tg[slot].channels : 1;
+        sp.splats.push_back(s);
     }
     // register budget: 256 threads x 8 blocks (full occupancy) leaves 32
     // registers per thread; the generated programs fit without spills
@@ -427,6 +442,41 @@ cfs_status cfs_chain_destroy(cfs_chain* chain)
     return CFS_OK;
 }
 
+cfs_status cfs_chain_info(const cfs_chain* chain, int* dim_in, int* n_ops, int* n_splat)
+{
+    clear_error();
+    if (!chain) return fail(CFS_ERR_INVALID_ARG, "NULL chain");
+    if (dim_in) *dim_in = chain->dim_in;
+    if (n_ops) *n_ops = chain->n_ops;
+    if (n_splat) *n_splat = chain->n_splat;
+    return CFS_OK;
+}
+
+cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem, uint32_t flags,
+                                cfs_chain** out)
+{
+    clear_error();
+    if (!out) return fail(CFS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dim_in != 2 && dim_in != 3) return fail(CFS_ERR_INVALID_ARG, "dim_in must be 2 or 3");
+    if (!source || !poem) return fail(CFS_ERR_INVALID_ARG, "NULL source or poem name");
+    if ((flags & ~CFS_COMPOSE_FAST_TRIG) != 0) return fail(CFS_ERR_INVALID_ARG, "unknown flags");
+    std::string body;
+    std::vector<int> slots;
+    cfs_status st = scribble_expand(source, poem, &body, &slots);
+    if (st != CFS_OK) return st;
+    cfs_chain* c = new (std::nothrow) cfs_chain();
+    if (!c) return fail(CFS_ERR_OOM, "host allocation failed");
+    c->dim_in = dim_in;
+    c->n_ops = 0;
+    c->flags = flags;
+    c->n_splat = (int)slots.size();
+    c->scribble = body;
+    c->scribble_slots = slots;
+    *out = c;
+    return CFS_OK;
+}
+
 cfs_status cfs_chain_set_params(cfs_chain* chain, int index, const float* params)
 {
     clear_error();
@@ -568,10 +618,12 @@ cfs_status cfs_render_points(const cfs_chain* chain, const float* xyz, const uin
         return fail(CFS_ERR_INVALID_ARG, "xyz must be 16-byte and fn 4-byte aligned");
     cfs_status st = validate_targets(chain, targets, n_targets);
     if (st != CFS_OK) return st;
-    for (int o = 0; o < chain->n_ops; ++o)
-        if (chain->ops[o].kind == CFS_OP_STARS)
-            return fail(CFS_ERR_UNSUPPORTED, "stars draw from the per-step random stream, which "
-                                             "a stored cloud does not have");
+    bool aux = chain->scribble.find("stars") != std::string::npos ||
+               chain->scribble.find("aux") != std::string::npos;
+    for (int o = 0; o < chain->n_ops; ++o) aux = aux || chain->ops[o].kind == CFS_OP_STARS;
+    if (aux)
+        return fail(CFS_ERR_UNSUPPORTED, "stars draw from the per-step random stream, which "
+                                         "a stored cloud does not have");
     // the generator plays no part: a one-map stand-in of the chain's dimension
     cfs_system stand_in;
     stand_in.dim = chain->dim_in;

@@ -282,7 +282,22 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
             sp.splats.push_back(ss);
         }
     }
+    sp.scribble = chain->scribble;
+    for (int slot : chain->scribble_slots) {
+        SplatSpec ss;
+        ss.slot = slot;
+        ss.kind = frames[0].targets[slot].kind;
+        ss.channels = ss.kind == CFS_TARGET_HIST_U32 ? frames[0].targets[slot].channels : 1;
+        sp.splats.push_back(ss);
+    }
     b->tile_cap = batch_spec_defaults(sp);
+    if (!sp.scribble.empty() && sp.tile) {
+        // the privatized window needs the splat's code shape of an op chain
+        sp.tile = 0;
+        sp.warp_agg = 0;
+        b->tile_cap = 0;
+        sp.dyn_smem = 0;
+    }
     st = get_kernel(sp, "cfs_batch_kernel", &b->kernel);
     if (st != CFS_OK) { delete b; return st; }
     if (sp.tile) {

@@ -30,6 +30,12 @@ std::string ProgramSpec::key() const
     }
     s << ".s";
     for (const auto& sp : splats) s << sp.slot << ":" << sp.kind << ":" << sp.channels << ",";
+    if (!scribble.empty()) {
+        // FNV-1a of the expanded poem: one program per distinct text
+        uint64_t h = 1469598103934665603ull;
+        for (unsigned char c : scribble) h = (h ^ c) * 1099511628211ull;
+        s << ".q" << std::hex << h << std::dec << "." << scribble.size();
+    }
     return s.str();
 }
 
@@ -91,8 +97,90 @@ static void emit_gen_map(std::ostringstream& s, const ProgramSpec& sp)
 }
 
 // Chain: the copy of the point through every op, splats where the chain says.
+// splat of the current point into target t (record index si for traces)
+static void emit_splat(std::ostringstream& s, const ProgramSpec& sp, size_t si)
+{
+    const SplatSpec& t = sp.splats[si];
+    s << "if (rec) { rec[" << 4 * si << "] = qx; rec[" << 4 * si + 1 << "] = qy; rec["
+      << 4 * si + 2 << "] = qz; rec[" << 4 * si + 3 << "] = alive ? 1.0f : 0.0f; } ";
+    s << "if (do_splat) ";
+    if (t.kind == CFS_TARGET_HIST_U32 && sp.tile && si == 0)
+        s << "cfs_splat_hist_tile(tg[" << t.slot << "], tile, qx, qy, alive, kc % " << t.channels
+          << ", disc[" << t.slot << "]);";
+    else if (t.kind == CFS_TARGET_HIST_U32)
+        s << "cfs_splat_hist(tg[" << t.slot << "], qx, qy, alive, kc % " << t.channels
+          << ", disc[" << t.slot << "]);";
+    else if (t.kind == CFS_TARGET_RGBA_F32)
+        s << "cfs_splat_rgba(tg[" << t.slot << "], qx, qy, alive, sm.pal[" << t.slot
+          << "][kc], disc[" << t.slot << "]);";
+    else
+        s << "cfs_splat_depth(tg[" << t.slot << "], qx, qy, qz, alive, sm.pal8[" << t.slot
+          << "][kc], disc[" << t.slot << "]);";
+}
+
+// A chain written as a scribble poem: the expanded text between the same
+// prologue and epilogue, with the library's ops as local functions.
+static void emit_scribble_chain(std::ostringstream& s, const ProgramSpec& sp)
+{
+    s << "template <class TG>\n__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a,"
+         " const TG& tg, const CfsSmem& sm, float px, float py, float pz, int k, u32 aux,"
+         " u32* disc, bool do_splat, float* rec, float& ox, float& oy, float& oz,"
+         " const CfsTile& tile)\n{\n";
+    s << "    (void)tile; (void)aux; (void)a; (void)tg; (void)sm; (void)disc; (void)do_splat;"
+         " (void)rec;\n";
+    s << "    float qx = px, qy = py, qz = pz;\n    bool alive = true;\n    int kc = k;\n";
+    s << R"(    auto reset = [&]() { qx = px; qy = py; qz = pz; alive = true; kc = k; };
+    auto discard = [&]() { alive = false; };
+    auto affine2 = [&](float a0, float b0, float c0, float d0, float e0, float f0) {
+        cfs_affine2(a0, b0, c0, d0, e0, f0, qx, qy); };
+    auto rotate2 = [&](float ang) {
+        const float c = (float)cos((double)ang), sn = (float)sin((double)ang);
+        cfs_affine2(c, -sn, sn, c, 0.0f, 0.0f, qx, qy); };
+    auto rotate3 = [&](float ang, int axis) {
+        const float c = (float)cos((double)ang), sn = (float)sin((double)ang);
+        if (axis == 0) cfs_rotate3_0(1.0f, 0.0f, 0.0f, 0.0f, c, -sn, 0.0f, sn, c, 0.0f, 0.0f, 0.0f, qx, qy, qz);
+        else if (axis == 1) cfs_rotate3_1(c, 0.0f, sn, 0.0f, 1.0f, 0.0f, -sn, 0.0f, c, 0.0f, 0.0f, 0.0f, qx, qy, qz);
+        else cfs_rotate3_2(c, -sn, 0.0f, sn, c, 0.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f, 0.0f, qx, qy, qz); };
+    auto translate3 = [&](float x0, float y0, float z0) {
+        qx = qx + x0; qy = qy + y0; qz = qz + z0; };
+    auto swirl = [&]() { cfs_swirl(qx, qy); };
+    auto sinusoidal = [&]() { cfs_sinusoidal(qx, qy); };
+    auto sinusoidal3 = [&]() { cfs_sinusoidal3(qx, qy, qz); };
+    auto stretch = [&]() { cfs_stretch(qx, qy); };
+    auto torus = [&](float R, float r) { cfs_torus(R, r, qx, qy, qz); };
+    auto perspective = [&](float f, float nz) {
+        alive = cfs_perspective(f, nz, qx, qy, qz) && alive; };
+    auto twist_z = [&](float kap) { cfs_twist_z(kap, qx, qy, qz); };
+    auto bend = [&](float beta) { cfs_bend(beta, 1.0f / beta, qx, qz); };
+    auto inversion = [&](float cx, float cy, float cz, float rho) {
+        alive = cfs_inversion(cx, cy, cz, rho * rho, qx, qy, qz) && alive; };
+    auto hemisphere = [&](float R) { cfs_hemisphere(R, qx, qy, qz); };
+    auto bands = [&](int axis, float freq, float phase, int n, int base) {
+        kc = cfs_bands(axis == 0 ? qx : (axis == 1 ? qy : qz), freq, phase, n, base); };
+    auto stars = [&](unsigned n, float x0, float x1, float y0, float y1, float z0, float z1,
+                     float s0, float s1) {
+        cfs_stars(a, n, x0, x1 - x0, y0, y1 - y0, z0, z1 - z0, s0, s1 - s0, aux, qx, qy, qz); };
+    (void)reset; (void)discard; (void)affine2; (void)rotate2; (void)rotate3; (void)translate3;
+    (void)swirl;
+    (void)sinusoidal; (void)sinusoidal3; (void)stretch; (void)torus; (void)perspective;
+    (void)twist_z; (void)bend; (void)inversion; (void)hemisphere; (void)bands; (void)stars;
+)";
+    for (size_t si = 0; si < sp.splats.size(); ++si) {
+        s << "#define CFS_SCRIBBLE_SPLAT_" << si << "() { ";
+        emit_splat(s, sp, si);
+        s << " }\n";
+    }
+    s << "    {\n" << sp.scribble << "\n    }\n";
+    for (size_t si = 0; si < sp.splats.size(); ++si) s << "#undef CFS_SCRIBBLE_SPLAT_" << si << "\n";
+    s << "    ox = qx; oy = qy; oz = qz;\n    return alive;\n}\n\n";
+}
+
 static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
 {
+    if (!sp.scribble.empty()) {
+        emit_scribble_chain(s, sp);
+        return;
+    }
     s << "template <class TG>\n__device__ __forceinline__ bool cfs_chain(const cfs_launch_args& a,"
          " const TG& tg, const CfsSmem& sm, float px, float py, float pz, int k, u32 aux,"
          " u32* disc, bool do_splat, float* rec, float& ox, float& oy, float& oz,"
@@ -193,6 +281,8 @@ std::string generate_source(const ProgramSpec& sp)
     {
         bool aux = false;
         for (int o = 0; o < sp.n_ops; ++o) aux = aux || sp.op_kind[o] == CFS_OP_STARS;
+        aux = aux || sp.scribble.find("stars") != std::string::npos ||
+              sp.scribble.find("aux") != std::string::npos;
         s << "#define CFS_AUX " << (aux ? 1 : 0) << "\n";
     }
     s << "#define CFS_BATCH " << (sp.mode == Mode::Batch ? 1 : 0) << "\n";

@@ -25,6 +25,10 @@ struct cfs_chain {
     uint32_t flags = 0;         // CFS_COMPOSE_*
     cfs_transform ops[CFS_MAX_OPS];
     int n_splat = 0;
+    // a chain written as a scribble poem (cfs_compose_scribble): the expanded
+    // body with CFS_SCRIBBLE_SPLAT_i() for the i-th splat call, and its slots
+    std::string scribble;
+    std::vector<int> scribble_slots;
 };
 
 namespace cfs {
@@ -65,6 +69,7 @@ struct ProgramSpec {
     int unroll = 4;            // copies of the step code in the step loop (4, 2, 1)
     int ilp = 1;               // batch: trajectories stepped together per thread (1, 2)
     int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
+    std::string scribble;      // expanded poem body (empty: the op list)
 
     std::string key() const;
 };
@@ -90,6 +95,11 @@ cfs_status launch(const Kernel& k, unsigned grid, const void* args, size_t args_
                   cudaStream_t stream);
 cfs_status check_cuda(cudaError_t e, const char* what);
 int device_sm_count();
+
+// Expands poem `poem` of a scribble program into a chain body; splat(N)
+// calls become CFS_SCRIBBLE_SPLAT_i() with their slots in splat_slots.
+cfs_status scribble_expand(const std::string& source, const std::string& poem, std::string* body,
+                           std::vector<int>* splat_slots);
 
 // Launch shape of the persistent batch program (block, occupancy, privatized
 // window, warp aggregation, ILP; environment knobs); returns the window's

@@ -172,3 +172,40 @@ def test_new_op_validation_and_codegen():
     assert "0 bytes spill stores" in log
     src2, _ = cfs.codegen_check(cfs.System(W.square_system()), ok, [W.Target("hist_u32", 8, 8, 4)])
     assert "#define CFS_AUX 1" in src2
+
+
+# ---------------------------------------------------------------------------
+# scribble frontend (Section 3.1): expansion and its errors, no GPU needed
+# ---------------------------------------------------------------------------
+def _scribble_err(src, poem="p", dim=2):
+    with pytest.raises(cfs.CfsError) as e:
+        cfs.Chain.from_scribble(src, poem, dim)
+    return str(e.value)
+
+
+def test_scribble_expansion_errors():
+    assert "unknown verse" in _scribble_err("__poem p() { @VCALL nope(); }")
+    assert "@VCALL" in _scribble_err("__verse v() { } __poem p() { @SCALL v() { } }")
+    assert "__split_stanza" in _scribble_err("__stanza s() { qx = 1; } __poem p() { }")
+    assert "positional" in _scribble_err("__verse v(a, b) { } __poem p() { @VCALL v(qx); }")
+    assert "no keyword" in _scribble_err("__verse v(| float f = 1;) { } "
+                                         "__poem p() { @VCALL v(| g = 2;); }")
+    assert "literal slot" in _scribble_err("__poem p() { int s = 0; splat(s); }")
+    assert "deeper than 32" in _scribble_err("__verse v() { @VCALL v(); } __poem p() { @VCALL v(); }")
+    assert "no poem" in _scribble_err("__poem q() { }")
+    assert "takes no parameters" in _scribble_err("__poem p(float a) { }")
+    assert "duplicate" in _scribble_err("__verse v() { } __verse v() { } __poem p() { }")
+
+
+def test_scribble_composed_chain_compiles():
+    from paper_2606_02226_gb300 import scribbles
+    ch = cfs.Chain.from_scribble(scribbles.COMPOSED, "composed", 2)
+    assert ch.n_splat == 2
+    wl = W.composed_render(n_points=64, iters=24, W=64)
+    src, log = cfs.codegen_check(cfs.System(wl.jobs[0].system), ch, wl.targets)
+    assert "/* verse flame */" in src and "/* stanza branch */" in src
+    assert "float dist = (3.5f);" in src             # keyword default
+    assert "0 bytes spill stores" in log
+    # a splat slot beyond the targets is rejected before compiling
+    with pytest.raises(cfs.CfsError):
+        cfs.codegen_check(cfs.System(wl.jobs[0].system), ch, wl.targets[:1])

@@ -191,6 +191,14 @@ cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chai
  *  |x| < 2^16 instead of about 1 ulp; several times fewer instructions.
  *  The generator maps are not affected. */
 #define CFS_COMPOSE_FAST_TRIG 1u
+/*  CFS_COMPOSE_POLY_TRIG -- the chain's sines and cosines reduce their
+ *  argument to [-pi/4, pi/4] (Cody-Waite with pi/2 split in three parts) and
+ *  evaluate minimax polynomials: within 1.5 ulp for |x| <= 32 (CUDA's
+ *  sincosf beyond).  An implementation independent of CUDA's math library;
+ *  measured slower than CUDA's sinf/cosf on GB300 (20.4 vs 18.9 ms per frame
+ *  of the composed scene), so not the default.  Ignored when
+ *  CFS_COMPOSE_FAST_TRIG is set. */
+#define CFS_COMPOSE_POLY_TRIG 2u
 cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint32_t flags,
                           cfs_chain** out);
 cfs_status cfs_chain_destroy(cfs_chain* chain);
@@ -219,7 +227,7 @@ cfs_status cfs_chain_destroy(cfs_chain* chain);
  * listed above; splat(SLOT) (a literal slot 0..3) splats into that target.
  * Expansion and argument errors are reported here (CFS_ERR_INVALID_ARG);
  * compile errors of the bodies at the first render (CFS_ERR_COMPILE, NVRTC
- * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG or 0. */
+ * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG, CFS_COMPOSE_POLY_TRIG or 0. */
 cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem,
                                 uint32_t flags, cfs_chain** out);
 /* Input dimension, op count (0 for a scribble chain) and splat count (the

@@ -235,10 +235,11 @@ class Chain:
     """A composed transform chain (Section 3, Fig. 2B) for points of
     dimension ``dim_in``; ``ops`` are ``.kind`` / ``.params`` records."""
 
-    def __init__(self, ops, dim_in: int, fast_trig: bool = False):
+    def __init__(self, ops, dim_in: int, fast_trig: bool = False, poly_trig: bool = False):
         arr, n = _transforms(ops)
         h = _P()
-        _check(lib().cfs_compose_ex(dim_in, arr, n, 1 if fast_trig else 0, ctypes.byref(h)))
+        flags = (1 if fast_trig else 0) | (2 if poly_trig else 0)
+        _check(lib().cfs_compose_ex(dim_in, arr, n, flags, ctypes.byref(h)))
         self.fast_trig = fast_trig
         self.handle = h
         self.ops = list(ops)

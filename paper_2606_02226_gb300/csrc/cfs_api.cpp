@@ -190,7 +190,7 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     sp.reuse = reuse;
     sp.n_ops = ch->n_ops;
     sp.n_targets = n_tg;
-    sp.fast_trig = (ch->flags & CFS_COMPOSE_FAST_TRIG) ? 1 : 0;
+    sp.fast_trig = trig_mode(ch->flags);
     for (int o = 0; o < ch->n_ops; ++o) {
         sp.op_kind[o] = ch->ops[o].kind;
         if (ch->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)ch->ops[o].params[1];
@@ -382,7 +382,7 @@ cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint3
                           cfs_chain** out)
 {
     clear_error();
-    if (flags & ~(uint32_t)CFS_COMPOSE_FAST_TRIG) {
+    if (flags & ~(uint32_t)(CFS_COMPOSE_FAST_TRIG | CFS_COMPOSE_POLY_TRIG)) {
         if (out) *out = nullptr;
         return fail(CFS_ERR_INVALID_ARG, "unknown compose flags");
     }
@@ -460,7 +460,8 @@ cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem
     *out = nullptr;
     if (dim_in != 2 && dim_in != 3) return fail(CFS_ERR_INVALID_ARG, "dim_in must be 2 or 3");
     if (!source || !poem) return fail(CFS_ERR_INVALID_ARG, "NULL source or poem name");
-    if ((flags & ~CFS_COMPOSE_FAST_TRIG) != 0) return fail(CFS_ERR_INVALID_ARG, "unknown flags");
+    if ((flags & ~(CFS_COMPOSE_FAST_TRIG | CFS_COMPOSE_POLY_TRIG)) != 0)
+        return fail(CFS_ERR_INVALID_ARG, "unknown flags");
     std::string body;
     std::vector<int> slots;
     cfs_status st = scribble_expand(source, poem, &body, &slots);

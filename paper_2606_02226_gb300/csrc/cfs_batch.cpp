@@ -268,7 +268,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     sp.n_cmp = max_cmp;
     sp.n_ops = chain->n_ops;
     sp.n_targets = n_targets;
-    sp.fast_trig = (chain->flags & CFS_COMPOSE_FAST_TRIG) ? 1 : 0;
+    sp.fast_trig = trig_mode(chain->flags);
     for (int o = 0; o < chain->n_ops; ++o) {
         sp.op_kind[o] = chain->ops[o].kind;
         if (chain->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)chain->ops[o].params[1];

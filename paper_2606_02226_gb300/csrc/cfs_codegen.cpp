@@ -9,11 +9,22 @@
 // different kinds meet) that NVRTC compiles for sm_103a.  Every numeric
 // parameter stays in the kernel's argument block, so one compiled program
 // serves every system and chain of the same structure.
+#include <cstdlib>
 #include <sstream>
 
 #include "cfs_internal.h"
 
 namespace cfs {
+
+int trig_mode(uint32_t flags)
+{
+    int m = (flags & CFS_COMPOSE_FAST_TRIG) ? 1 : ((flags & CFS_COMPOSE_POLY_TRIG) ? 2 : 0);
+    if (const char* e = std::getenv("CFS_TRIG")) {
+        const int v = std::atoi(e);
+        if (v >= 0 && v <= 2) m = v;
+    }
+    return m;
+}
 
 std::string ProgramSpec::key() const
 {
@@ -275,7 +286,7 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_NT " << sp.n_targets << "\n";
     s << "#define CFS_NSPLAT_ARR " << (sp.splats.empty() ? 1 : sp.splats.size()) << "\n";
     s << "#define CFS_REUSE " << (sp.reuse ? 1 : 0) << "\n";
-    s << "#define CFS_FAST_TRIG " << (sp.fast_trig ? 1 : 0) << "\n";
+    s << "#define CFS_FAST_TRIG " << sp.fast_trig << "\n";
     s << "#define CFS_UNROLL " << sp.unroll << "\n";
     s << "#define CFS_ILP " << (sp.ilp == 2 ? 2 : 1) << "\n";
     {

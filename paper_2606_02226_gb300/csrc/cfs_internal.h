@@ -65,7 +65,7 @@ struct ProgramSpec {
     int tile = 0;              // batch: privatized shared window for the first splat
     int warp_agg = 0;          // warp-aggregated shared atomics in that window
     int tile_reps = 1;         // at most this many copies of a small window
-    int fast_trig = 0;         // chain trigonometry: reduced argument + hardware sin/cos
+    int fast_trig = 0;         // chain trigonometry: 0 libm, 1 hardware, 2 polynomial
     int unroll = 4;            // copies of the step code in the step loop (4, 2, 1)
     int ilp = 1;               // batch: trajectories stepped together per thread (1, 2)
     int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
@@ -75,6 +75,8 @@ struct ProgramSpec {
 };
 
 std::string generate_source(const ProgramSpec& spec);
+// chain trigonometry of compose flags: 0 CUDA libm, 1 hardware, 2 polynomial
+int trig_mode(uint32_t flags);
 
 // ---- runtime: driver entry points, NVRTC, module cache ---------------------
 struct Kernel {

@@ -326,3 +326,36 @@ def test_invalid_arguments_report_errors(torch_cuda):
     with pytest.raises(cfs.CfsError):
         cfs.render(cfs.System(sysd), cfs.Chain([W.Op("splat", (1,))], 2), [t],
                    [cfs.alloc_target(t)], n_points=10, iters=5, burn_in=0)
+
+
+@pytest.mark.parametrize("trig", ["poly", "libm"])
+def test_chain_trigonometry_accuracy(torch_cuda, trig):
+    """sin and cos of the chain (sinusoidal gives sin x, Eq. 2's stretch with
+    y = 0 gives -cos x) against float64 on a dense sweep: within 1.5 ulp for
+    the polynomial mode on |x| <= 32 and within 2 ulp beyond (CUDA's sincosf
+    there) and for CUDA's own functions."""
+    torch = torch_cuda
+    cfs = _cfs()
+    xs = np.concatenate([np.linspace(-32, 32, 200001), np.linspace(-4000, 4000, 20001),
+                         np.array([0.0, 1e-30, -1e-8, np.pi / 4, 3 * np.pi / 4, 31.99])])
+    xs = xs.astype(np.float32)
+    ident = W.single_affine_system(1.0, 0.0, 0.0, 1.0, 0.0, 0.0)
+    start = np.stack([xs, np.zeros_like(xs)], 0).astype(np.float32)
+    ids = torch.arange(xs.size, dtype=torch.int32, device="cuda")
+    res = {}
+    for name, ops in (("sin", [W.Op("sinusoidal"), W.Op("splat", (0,))]),
+                      ("cos", [W.Op("stretch"), W.Op("splat", (0,))])):
+        ch = cfs.Chain(ops, 2, poly_trig=(trig == "poly"))
+        _, p, q = cfs.trace(cfs.System(ident), ch, ids, iters=1,
+                            start=torch.from_numpy(start).cuda())
+        assert np.array_equal(p.cpu().numpy()[:, 0, 0], xs)      # the identity map
+        v = q.cpu().numpy()[:, 0, 0, 0 if name == "sin" else 1]
+        res[name] = v if name == "sin" else -v
+    x64 = xs.astype(np.float64)
+    for name, ref in (("sin", np.sin(x64)), ("cos", np.cos(x64))):
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        err = np.abs(res[name].astype(np.float64) - ref) / ulp
+        small = np.abs(xs) <= 32
+        bound = 1.5 if trig == "poly" else 2.0
+        assert err[small].max() <= bound, (name, err[small].max())
+        assert err[~small].max() <= 2.0, (name, err[~small].max())

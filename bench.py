@@ -83,7 +83,7 @@ def measure_atomic_peaks(torch, cfs, dev, rgba_bytes: int, depth_bytes: int, rep
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
 RENDER_TRAFFIC_BYTES = 16265856          # (26720768 + 5810944) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "67aa3e4de8fe1d1f0319595241eaf02377b4f000"
+RENDER_TRAFFIC_SOURCE_SHA1 = "e9dad3d8a3fc0ffaade1a36ec973fee085a53a3f"
 
 
 def _code_only(text: str) -> str:

@@ -450,16 +450,23 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
                       [cfs.alloc_target(t, device=dev)]))
         begin += fr.n_points
     b = cfs.Batch(chain, items, iters=300, burn_in=20, seed=0)
-    b.launch(clear=True, stream=stream)               # capture + warm-up
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        b.launch(clear=True, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+
+    def timed_batch():
+        b.launch(clear=True, stream=stream)               # capture + warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.launch(clear=True, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_default = timed_batch()
+    # the autotuner times the candidate plans on these frames (80 steps each)
+    tuning = b.tune(trial_iters=80, stream=stream)
+    ms = timed_batch()
     n_pts = sum(fr.n_points for fr in frames)
     bytes_targets = sum(4 * 4 * fr.W * fr.W for fr in frames)
     info = b.info()
@@ -497,6 +504,7 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             "splats_per_s": n_pts * 280 / (ms * 1e-3), "points": n_pts,
             "target_bytes": bytes_targets, "items": info["n_items"], "chunk": info["chunk"],
             "grid": info["grid"], "gpu_launches_per_batch": 1, "display": display,
+            "autotuned": tuning, "ms_per_batch_default_plan": ms_default,
             "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3)}
 
 
@@ -729,6 +737,7 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
         return e0.elapsed_time(e1) / reps
 
     plain = cfs.Batch(chain, items, iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - b_min)
+    plain.tune(trial_iters=80, stream=stream)          # both sides autotuned
     ms_plain = timed(lambda: plain.launch(clear=True, stream=stream))
     out.update({"batch_frames": len(frames), "plain_ms": ms_plain,
                 "plain_frames_per_s": len(frames) / (ms_plain * 1e-3)})
@@ -745,6 +754,7 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
                       for it in items]
             warm = cfs.Batch(chain, [it + (starts[fi],) for fi, it in enumerate(items)],
                              iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - k_min)
+            warm.tune(trial_iters=80, stream=stream)
 
             def run_warm():
                 smp.start_points_batch(frame_systems, frame_t, starts, frame_seeds,

@@ -329,6 +329,22 @@ cfs_status cfs_batch_discards(cfs_batch* batch, uint64_t* out);
 /* Work items, points per item, persistent grid size. */
 cfs_status cfs_batch_info(const cfs_batch* batch, uint32_t* n_items, uint32_t* chunk,
                           uint32_t* grid);
+/* Autotuner: times the batch's own frames under each candidate plan --
+ * privatized window on/off (when the chain splats once into a histogram),
+ * one or two trajectories per thread, 2048/4096/8192/16384 points per work item --
+ * running the first `trial_iters` steps (all when 0), two trials each, and
+ * keeps the fastest; the next cfs_batch_launch uses it.  Synchronous; the
+ * frames' targets hold trial output afterwards (launch with clear = 1).
+ * `out` (may be NULL) receives the choice and its trial time. */
+typedef struct {
+    int ilp;           /* trajectories per thread */
+    int tile;          /* privatized shared-memory window */
+    uint32_t chunk;    /* points per work item */
+    float trial_ms;    /* time of the chosen plan's trial */
+    int trials;        /* plans timed */
+} cfs_batch_tuning;
+cfs_status cfs_batch_tune(cfs_batch* batch, uint32_t trial_iters, void* stream,
+                          cfs_batch_tuning* out);
 /* Waits for the batch's last launch, then frees it. */
 cfs_status cfs_batch_destroy(cfs_batch* batch);
 /* One-shot: create, launch, destroy.  Returns after the frames are rendered

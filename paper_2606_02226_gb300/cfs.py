@@ -74,6 +74,11 @@ class cfs_frame(ctypes.Structure):
                 ("targets", cfs_target * MAX_TARGETS)]
 
 
+class cfs_batch_tuning(ctypes.Structure):
+    _fields_ = [("ilp", ctypes.c_int), ("tile", ctypes.c_int), ("chunk", ctypes.c_uint32),
+                ("trial_ms", ctypes.c_float), ("trials", ctypes.c_int)]
+
+
 class cfs_display_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_float), ("brightness", ctypes.c_float),
                 ("a_max", ctypes.c_float), ("background", ctypes.c_uint32)]
@@ -117,6 +122,7 @@ _SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.POINTER(ctypes.c_uint32)]),
     "cfs_batch_destroy": (ctypes.c_int, [_P]),
+    "cfs_batch_tune": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.POINTER(cfs_batch_tuning)]),
     "cfs_render_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
                                         ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, _P]),
@@ -517,6 +523,15 @@ class Batch:
         _check(lib().cfs_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b),
                                     ctypes.byref(c)))
         return {"n_items": a.value, "chunk": b.value, "grid": c.value}
+
+    def tune(self, trial_iters: int = 0, stream=None):
+        """Times the candidate plans on these frames and keeps the fastest
+        (the targets hold trial output afterwards); returns the choice."""
+        t = cfs_batch_tuning()
+        _check(lib().cfs_batch_tune(self.handle, int(trial_iters), _stream_handle(stream),
+                                    ctypes.byref(t)))
+        return {"ilp": t.ilp, "tile": t.tile, "chunk": t.chunk, "trial_ms": t.trial_ms,
+                "trials": t.trials}
 
     def display(self, outs, *, slot: int = 0, gamma: float = 2.2, brightness: float = 1.0,
                 a_max: float = 0.0, background: int = 0, a_max_out=None, stream=None):

@@ -201,6 +201,80 @@ uint32_t batch_spec_defaults(ProgramSpec& sp)
 }
 }  // namespace cfs
 
+namespace {
+// Cuts every frame into items of `chunk` points (whole warps), numbers the
+// items frame by frame, repacks the staged frame descriptors and sets the
+// persistent grid (resident CTAs, at most one per item).
+cfs_status plan_items(cfs_batch* b, uint32_t chunk)
+{
+    b->chunk = chunk;
+    b->grid = (uint32_t)std::max(1, b->kernel.max_blocks_per_sm * std::max(1, b->kernel.num_sms));
+    uint64_t total = 0;
+    b->chunks.assign(b->n_frames, chunk);
+    for (int f = 0; f < b->n_frames; ++f)
+        total += ((uint64_t)b->frames[f].n_points + chunk - 1) / chunk;
+    if (total >= (1ull << 31)) return fail(CFS_ERR_INVALID_ARG, "too many work items");
+    b->n_items = (uint32_t)total;
+    if (b->grid > b->n_items && b->n_items > 0) b->grid = b->n_items;
+    if (b->h_frames) {
+        uint32_t item = 0;
+        for (int f = 0; f < b->n_frames; ++f) {
+            pack_frame(&b->h_frames[f], b->systems[f], b->frames[f], b->n_targets, item, chunk);
+            item += (b->frames[f].n_points + chunk - 1) / chunk;
+        }
+    }
+    b->args.n_items = b->n_items;
+    b->args.chunk = chunk;
+    return CFS_OK;
+}
+
+// Compiles the batch program (and the window pre-pass when tiled) for the
+// spec's current knobs.
+cfs_status build_program(cfs_batch* b)
+{
+    cfs_status st = get_kernel(b->spec, "cfs_batch_kernel", &b->kernel);
+    if (st != CFS_OK) return st;
+    if (b->spec.tile) {
+        ProgramSpec bs = b->spec;
+        bs.dyn_smem = 0;
+        st = get_kernel(bs, "cfs_bbox_kernel", &b->bbox_kernel);
+    }
+    b->args.tile_cap = b->tile_cap;
+    return st;
+}
+
+void drop_graphs(cfs_batch* b)
+{
+    for (auto& e : b->exec)
+        if (e) { cudaGraphExecDestroy(e); e = nullptr; }
+}
+
+// the launch sequence of a batch without a graph (the autotuner's trials)
+cfs_status run_direct(cfs_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+{
+    cudaError_t e = cudaMemcpyAsync(b->d_frames, b->h_frames,
+                                    sizeof(cfs_dev_frame) * (size_t)b->n_frames,
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->d_counter, 0,
+                            b->work_bytes - ((unsigned char*)b->d_counter - b->d_work), s);
+    for (int f = 0; f < b->n_frames && e == cudaSuccess; ++f)
+        for (int t = 0; t < b->n_targets && e == cudaSuccess; ++t) {
+            const cfs_target& g = b->frames[f].targets[t];
+            e = cudaMemsetAsync(g.data, g.kind == CFS_TARGET_DEPTH_U64 ? 0xFF : 0,
+                                target_bytes(g), s);
+        }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    cfs_status st = check_cuda(e, "batch trial set-up");
+    if (st == CFS_OK && b->n_items > 0 && b->spec.tile)
+        st = launch(b->bbox_kernel, (unsigned)b->n_frames, &b->args, sizeof(b->args), s);
+    if (st == CFS_OK && b->n_items > 0)
+        st = launch(b->kernel, b->grid, &b->args, sizeof(b->args), s);
+    if (st == CFS_OK) st = check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+    return st;
+}
+}  // namespace
+
 extern "C" {
 
 cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_frame* frames,
@@ -216,7 +290,6 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
         return fail(CFS_ERR_INVALID_ARG, "n_targets must be in 0..4");
     const cfs_system* s0 = frames[0].system;
     if (!s0) return fail(CFS_ERR_INVALID_ARG, "frame 0 has no system");
-    uint64_t total_items = 0;
     int max_cmp = 0;
     for (int f = 0; f < n_frames; ++f) {
         const cfs_frame& fr = frames[f];
@@ -298,41 +371,20 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
         b->tile_cap = 0;
         sp.dyn_smem = 0;
     }
-    st = get_kernel(sp, "cfs_batch_kernel", &b->kernel);
+    st = build_program(b);
     if (st != CFS_OK) { delete b; return st; }
-    if (sp.tile) {
-        ProgramSpec bs = sp;
-        bs.dyn_smem = 0;
-        st = get_kernel(bs, "cfs_bbox_kernel", &b->bbox_kernel);
-        if (st != CFS_OK) { delete b; return st; }
-    }
 
-    // Items: every frame is cut into at least `grid` items (whole warps of
-    // points, at most chunk_max), so all CTAs work on one or two frames at a
-    // time and the live layers stay in L2.
-    b->grid = (uint32_t)std::max(1, b->kernel.max_blocks_per_sm * std::max(1, b->kernel.num_sms));
-    b->chunk = 4096;
+    // Items: every frame is cut into items of `chunk` points (whole warps);
+    // all CTAs work on one or two frames at a time, so the live layers stay
+    // in L2.  cfs_batch_tune picks the chunk (and the program's knobs) by
+    // measurement.
+    uint32_t chunk = 4096;
     if (const char* e = std::getenv("CFS_BATCH_CHUNK")) {
         const int c = std::atoi(e);
-        if (c >= 32 && c % 32 == 0) b->chunk = (uint32_t)c;
+        if (c >= 32 && c % 32 == 0) chunk = (uint32_t)c;
     }
-    bool adaptive = false;
-    if (const char* e = std::getenv("CFS_BATCH_ADAPT")) adaptive = std::atoi(e) != 0;
-    b->chunks.resize(n_frames);
-    for (int f = 0; f < n_frames; ++f) {
-        const uint64_t per = ((uint64_t)frames[f].n_points / b->grid) / 32 * 32;
-        const uint32_t c = adaptive
-                               ? (uint32_t)std::min<uint64_t>(b->chunk, std::max<uint64_t>(32, per))
-                               : b->chunk;
-        b->chunks[f] = c;
-        total_items += ((uint64_t)frames[f].n_points + c - 1) / c;
-    }
-    if (total_items >= (1ull << 31)) {
-        delete b;
-        return fail(CFS_ERR_INVALID_ARG, "too many work items");
-    }
-    b->n_items = (uint32_t)total_items;
-    if (b->grid > b->n_items && b->n_items > 0) b->grid = b->n_items;
+    st = plan_items(b, chunk);
+    if (st != CFS_OK) { delete b; return st; }
 
     // workspace: frames | bbox (int4 per frame) | counter (u32, padded to
     // 256 B) | discards (the counter and discards are reset every launch)
@@ -357,19 +409,14 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     b->d_counter = reinterpret_cast<unsigned int*>(b->d_work + off_counter);
     b->d_disc = reinterpret_cast<unsigned long long*>(b->d_work + off_disc);
 
-    uint32_t item = 0;
-    for (int f = 0; f < n_frames; ++f) {
-        pack_frame(&b->h_frames[f], b->systems[f], b->frames[f], n_targets, item, b->chunks[f]);
-        item += (frames[f].n_points + b->chunks[f] - 1) / b->chunks[f];
-    }
     fill_args_common(&b->args, chain, seed, iters, burn_in);
+    st = plan_items(b, b->chunk);        // now that the staging buffer exists
+    if (st != CFS_OK) { release(b); delete b; return st; }
     b->args.step_begin = step_begin;
     b->args.frames = (unsigned long long)(uintptr_t)b->d_frames;
     b->args.work_counter = (unsigned long long)(uintptr_t)b->d_counter;
     b->args.frame_discards = (unsigned long long)(uintptr_t)b->d_disc;
     b->args.n_frames = (unsigned)n_frames;
-    b->args.n_items = b->n_items;
-    b->args.chunk = b->chunk;
     b->args.frame_bbox = (unsigned long long)(uintptr_t)b->d_bbox;
     b->args.tile_cap = b->tile_cap;
     *out = b;
@@ -499,6 +546,94 @@ cfs_status cfs_batch_display(cfs_batch* b, int slot, const cfs_display_params* p
     if (st != CFS_OK) return st;
     b->disp_launched = true;
     return check_cuda(cudaEventRecord(b->disp_done, (cudaStream_t)stream), "cudaEventRecord");
+}
+
+cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, void* stream,
+                          cfs_batch_tuning* out)
+{
+    clear_error();
+    if (!b) return fail(CFS_ERR_INVALID_ARG, "NULL batch");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != b->device) return fail(CFS_ERR_INVALID_ARG, "batch belongs to another device");
+    cudaStream_t s = (cudaStream_t)stream;
+    cfs_status st = CFS_OK;
+    if (b->launched) st = check_cuda(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+    if (b->disp_launched && st == CFS_OK)
+        st = check_cuda(cudaEventSynchronize(b->disp_done), "cudaEventSynchronize");
+    if (st != CFS_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    st = check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    if (st == CFS_OK) st = check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+    if (st != CFS_OK) {
+        if (e0) cudaEventDestroy(e0);
+        return st;
+    }
+    // trials run the first trial_iters steps (the whole run when 0)
+    const uint32_t full_iters = b->args.iters;
+    if (trial_iters > 0)
+        b->args.iters = std::min(full_iters, b->args.step_begin + std::max(trial_iters, 1u));
+    const ProgramSpec base = b->spec;
+    const bool tile_ok = base.scribble.empty() && base.splats.size() == 1 &&
+                         base.splats[0].kind == CFS_TARGET_HIST_U32;
+    const uint32_t base_cap = b->tile_cap ? b->tile_cap : (base.block >= 1024 ? 53248u : 8192u);
+    struct Cand { int ilp, tile; uint32_t chunk; float ms; };
+    std::vector<Cand> tried;
+    Cand best{base.ilp, base.tile, b->chunk, 1e30f};
+    const uint32_t chunks[] = {2048, 4096, 8192, 16384};
+    for (int tile = tile_ok ? 1 : 0; tile >= 0 && st == CFS_OK; --tile) {
+        for (int ilp = 1; ilp <= 2 && st == CFS_OK; ++ilp) {
+            b->spec = base;
+            b->spec.ilp = ilp;
+            b->spec.tile = tile;
+            b->spec.warp_agg = 0;
+            b->tile_cap = tile ? base_cap : 0;
+            b->spec.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
+            st = build_program(b);
+            for (uint32_t c : chunks) {
+                if (st != CFS_OK) break;
+                st = plan_items(b, c);
+                float ms = 1e30f;
+                for (int rep = 0; rep < 2 && st == CFS_OK; ++rep) {
+                    st = run_direct(b, s, e0, e1);
+                    if (st == CFS_OK) st = check_cuda(cudaEventSynchronize(e1), "trial");
+                    float t = 0.0f;
+                    if (st == CFS_OK) st = check_cuda(cudaEventElapsedTime(&t, e0, e1), "time");
+                    ms = std::min(ms, t);
+                }
+                if (st != CFS_OK) break;
+                tried.push_back({ilp, tile, c, ms});
+                if (ms < best.ms) best = {ilp, tile, c, ms};
+            }
+        }
+    }
+    // keep the winner (or restore the starting point after an error)
+    b->spec = base;
+    if (st == CFS_OK) {
+        b->spec.ilp = best.ilp;
+        b->spec.tile = best.tile;
+        b->spec.warp_agg = 0;
+        b->tile_cap = best.tile ? base_cap : 0;
+        b->spec.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
+    } else {
+        b->tile_cap = base.tile ? base_cap : 0;
+    }
+    cfs_status st2 = build_program(b);
+    if (st2 == CFS_OK) st2 = plan_items(b, st == CFS_OK ? best.chunk : 4096u);
+    b->args.iters = full_iters;
+    drop_graphs(b);                     // the next launch captures the new plan
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CFS_OK) return st;
+    if (st2 != CFS_OK) return st2;
+    if (out) {
+        out->ilp = best.ilp;
+        out->tile = best.tile;
+        out->chunk = best.chunk;
+        out->trial_ms = best.ms;
+        out->trials = (int)tried.size();
+    }
+    return CFS_OK;
 }
 
 cfs_status cfs_batch_destroy(cfs_batch* b)

@@ -175,3 +175,21 @@ def test_batch_start_points_and_step_begin(torch_cuda):
                      step_begin=12, start=full[f])[0].buf
         assert np.array_equal(_host(tens[f]), o), f
         begin += fr.n_points
+
+
+def test_batch_autotuner_keeps_results_exact(torch_cuda):
+    # tuning changes the plan (window, trajectories per thread, item size),
+    # never the frames: the tuned launch is still the oracle's, bit for bit
+    frames = W.animation_frames(n_frames=9, seed=6, min_log2=8, max_log2=12,
+                                resolutions=(64, 128))
+    cfs, chain, items, descs, tens = _setup(frames)
+    b = cfs.Batch(chain, items, iters=44, burn_in=20, seed=3)
+    choice = b.tune(trial_iters=24)
+    assert choice["trials"] >= 8 and choice["chunk"] in (2048, 4096, 8192, 16384)
+    assert choice["ilp"] in (1, 2) and choice["tile"] in (0, 1) and choice["trial_ms"] > 0
+    b.launch(clear=True)
+    torch_cuda.cuda.synchronize()
+    ref, rdisc = _oracle(frames, descs, 44, 20, 3)
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), ref[f]), f
+    assert list(b.discards()[:, 0]) == rdisc

@@ -432,7 +432,9 @@ cfs_status cfs_sampler_backward(cfs_sampler* s, const void* U, uint32_t B, const
  * [n_sys][n_per][2]; n_per a power of two in 32..1024) over projections
  * (cos phi_j, sin phi_j) (phi device f32 [n_proj]):
  * L = mean_{s,j} mean_i (sort(X_s theta_j)_i - sort(T_s theta_j)_i)^2.
- * L is added to *loss and dL/dX to dX (device). */
+ * L is added to *loss and dL/dX to dX (device).  Projected keys must be
+ * finite.  A predicted key that ties another one exactly receives the
+ * gradient of the first rank of the tie. */
 cfs_status cfs_sw_loss(const float* X, const float* T, uint32_t n_sys, uint32_t n_per,
                        const float* phi, uint32_t n_proj, float* loss, float* dX, void* stream);
 /* One Adam step (beta 0.9, 0.999, eps 1e-8, bias-corrected at step t >= 1)

@@ -376,14 +376,17 @@ __device__ __forceinline__ void cfs_hemisphere(float R, float& x, float& y, floa
     z = -(R * h);
 }
 
-/* Band texture: colour base + (floor(freq u + phase) mod n). */
+/* Band texture: colour base + (floor(freq u + phase) mod n).  Inside the
+ * guarded range |t| < 1e9 the floor fits a 32-bit int, so the modulo stays
+ * in 32-bit integer arithmetic (64-bit conversions and divisions would run
+ * on the slow double-precision path). */
 __device__ __forceinline__ int cfs_bands(float u, float freq, float phase, int n, int base)
 {
     const float t = fmaf(freq, u, phase);
     int m = 0;
     if (isfinite(t) && fabsf(t) < 1.0e9f) {
-        const long long b = (long long)floorf(t);
-        m = (int)(((b % n) + n) % n);
+        const int b = __float2int_rd(t);
+        m = ((b % n) + n) % n;
     }
     return base + m;
 }

@@ -520,112 +520,354 @@ __global__ void __launch_bounds__(HID) out_backward_kernel(const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-// sliced-Wasserstein loss and gradient.  One CTA of N threads (N a power of
-// two in 32..1024) per (system, group of SW_PJ projections): thread i holds
-// point i; per projection both point sets are projected and bitonic-sorted
-// (the predicted points with their indices), exchange partners within a
-// warp by shuffles and across warps through shared memory, then matched
-// rank by rank.  Each CTA adds its projections' gradient to dX (one atomic
-// per coordinate) and its loss share to *loss.
+// sliced-Wasserstein loss and gradient.  A CTA takes one system and a run of
+// its projections; a group of G = N / 8 threads sorts one projection at a
+// time, each thread holding 8 projected predicted keys (x) and 8 projected
+// target keys (y).
+//
+// Sorting network: bitonic.  Merge k (blocks of 2^k positions) runs
+// compare-exchange stages on position bits k-1, ..., 0.  A position's bits
+// are split into a window of 3 register bits [a, a + 3) -- the key's slot
+// in its thread -- and the others, which number the thread in the group; a
+// stage on a bit of the window is a min/max of two slots of one thread.
+// When the next stage's bit lies outside the window, the group moves its
+// keys through shared memory into the window that holds it (19 moves for
+// N = 1024, each one barrier of the group's threads; two buffers alternate).  Blocks that a merge
+// sorts descending hold their keys negated, so every stage puts the smaller
+// key at the lower position and a merge boundary only flips signs.  The
+// shared-memory slots are XOR-swizzled so that the 16 lanes of a half-warp
+// hit distinct banks in every window.
+//
+// After the sort, thread t holds ranks 8t .. 8t+7.  A point's rank is then
+// found by binary search of its own key (recomputed bit for bit) among the
+// sorted predicted keys, so the network carries no indices.  Gradients of the
+// group's projections are summed per point in shared memory (each point
+// belongs to one thread of the group), then over the groups, then added to
+// dX with one atomic per coordinate and CTA.  Keys must be finite.
 // ---------------------------------------------------------------------------
-constexpr int SW_PJ = 4;
+constexpr int SW_E = 8;            // keys per thread and set
+constexpr int SW_THREADS = 256;    // threads per CTA at most
 
-// compare-exchange stage (k, jj) of the bitonic network for this thread's
-// element: the lower partner of an ascending pair keeps the minimum; the
-// predicted keys carry their point index
-template <int N, int K, int JJ>
-__device__ __forceinline__ void sw_stage(int i, float& kx, float& ky, int& ix, float (*xs)[N],
-                                         float (*ys)[N], int (*is)[N], int& buf)
+__device__ __forceinline__ float sw_key(float u0, float u1, float c, float sn)
 {
-    float ox, oy;
-    int oi;
-    if (JJ >= 32) {
-        xs[buf][i] = kx; ys[buf][i] = ky; is[buf][i] = ix;
-        __syncthreads();
-        ox = xs[buf][i ^ JJ]; oy = ys[buf][i ^ JJ]; oi = is[buf][i ^ JJ];
-        buf ^= 1;   // the next exchange uses the other buffer: no second barrier
-    } else {
-        ox = __shfl_xor_sync(0xffffffffu, kx, JJ);
-        oy = __shfl_xor_sync(0xffffffffu, ky, JJ);
-        oi = __shfl_xor_sync(0xffffffffu, ix, JJ);
-    }
-    const bool keep_min = ((i & JJ) == 0) == ((i & K) == 0);
-    if (keep_min ? (ox < kx) : (ox > kx)) { kx = ox; ix = oi; }
-    if (keep_min ? (oy < ky) : (oy > ky)) ky = oy;
+    return fmaf(u0, c, u1 * sn);
 }
 
-template <int N, int K, int JJ>
-__device__ __forceinline__ void sw_merge(int i, float& kx, float& ky, int& ix, float (*xs)[N],
-                                         float (*ys)[N], int (*is)[N], int& buf)
+// bank swizzle of a float2 slot: bits 4, 5, 6 fold into the low bits
+__host__ __device__ constexpr int sw_swz(int p)
 {
-    sw_stage<N, K, JJ>(i, kx, ky, ix, xs, ys, is, buf);
-    if constexpr (JJ > 1) sw_merge<N, K, JJ / 2>(i, kx, ky, ix, xs, ys, is, buf);
+    return p ^ (((p >> 4) & 1) << 1) ^ (((p >> 5) & 1) << 2) ^ (((p >> 6) & 1) * 9);
+}
+
+// position bits of thread t in window a (slot bits left zero)
+__device__ __forceinline__ int sw_tpos(int a, int t)
+{
+    return (t & ((1 << a) - 1)) | ((t >> a) << (a + 3));
+}
+
+// compare-exchange of the slot pairs that differ in register bit M
+template <int M>
+__device__ __forceinline__ void sw_reg_stage(float (&x)[SW_E], float (&y)[SW_E])
+{
+#pragma unroll
+    for (int e = 0; e < SW_E; ++e) {
+        if (e & (1 << M)) continue;
+        const int f = e | (1 << M);
+        const float xl = fminf(x[e], x[f]), xh = fmaxf(x[e], x[f]);
+        const float yl = fminf(y[e], y[f]), yh = fmaxf(y[e], y[f]);
+        x[e] = xl; x[f] = xh;
+        y[e] = yl; y[f] = yh;
+    }
+}
+
+// barrier of the G threads of group g: a named barrier (ids 1 ..) for whole
+// warps, the group's lanes of its warp below that
+template <int G>
+__device__ __forceinline__ void sw_group_sync(int g)
+{
+    if constexpr (G >= 64) {
+        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "n"(G) : "memory");
+    } else if constexpr (G == 32) {
+        __syncwarp();
+    } else {
+        __syncwarp(((1u << G) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(G - 1)));
+    }
+}
+
+// moves the group's keys from window A to window NA through buffer `par`
+template <int N, int A, int NA>
+__device__ __forceinline__ void sw_move(float (&x)[SW_E], float (&y)[SW_E], int t, int g,
+                                        float2* base, int& par)
+{
+    float2* buf = base + (par ? N : 0);
+    par ^= 1;
+    // t passes through an opaque move so that each move computes its own
+    // addresses here instead of all of them staying live from the start
+    int tv;
+    asm volatile("mov.b32 %0, %1;" : "=r"(tv) : "r"(t));
+    t = tv;
+    const int pw = sw_swz(sw_tpos(A, t));
+#pragma unroll
+    for (int e = 0; e < SW_E; ++e) buf[pw ^ sw_swz(e << A)] = make_float2(x[e], y[e]);
+    sw_group_sync<N / SW_E>(g);
+    const int pr = sw_swz(sw_tpos(NA, t));
+#pragma unroll
+    for (int e = 0; e < SW_E; ++e) {
+        const float2 v = buf[pr ^ sw_swz(e << NA)];
+        x[e] = v.x;
+        y[e] = v.y;
+    }
+}
+
+// the windows of merge K from the one whose top stage bit is HI down; the
+// keys are in window CUR on entry and in window 0 on return
+template <int N, int K, int HI, int CUR>
+__device__ __forceinline__ void sw_windows(float (&x)[SW_E], float (&y)[SW_E], int t, int g,
+                                           float2* base, int& par)
+{
+    constexpr int A = HI >= 2 ? HI - 2 : 0;
+    if constexpr (A != CUR) sw_move<N, CUR, A>(x, y, t, g, base, par);
+    if constexpr (HI - A >= 2) sw_reg_stage<2>(x, y);
+    if constexpr (HI - A >= 1) sw_reg_stage<1>(x, y);
+    sw_reg_stage<0>(x, y);
+    if constexpr (A > 0) sw_windows<N, K, A - 1, A>(x, y, t, g, base, par);
+}
+
+// sign of a key in merge K: negative where position bit K is set (the
+// descending blocks); the last merge (2^K = N) is ascending everywhere
+template <int N, int K>
+__device__ __forceinline__ bool sw_neg(int p)
+{
+    return (1 << K) < N && ((p >> K) & 1);
 }
 
 template <int N, int K>
-__device__ __forceinline__ void sw_sort(int i, float& kx, float& ky, int& ix, float (*xs)[N],
-                                        float (*ys)[N], int (*is)[N], int& buf)
+__device__ __forceinline__ void sw_merges(float (&x)[SW_E], float (&y)[SW_E], int t, int g,
+                                          float2* base, int& par)
 {
-    sw_merge<N, K, K / 2>(i, kx, ky, ix, xs, ys, is, buf);
-    if constexpr (K < N) sw_sort<N, 2 * K>(i, kx, ky, ix, xs, ys, is, buf);
+    sw_windows<N, K, K - 1, 0>(x, y, t, g, base, par);
+    if constexpr ((1 << K) < N) {
+        // window 0 holds position (t << 3) | e: flip where merge K and K + 1
+        // disagree on the sign (t opaque again, as in the moves)
+        int tv;
+        asm volatile("mov.b32 %0, %1;" : "=r"(tv) : "r"(t));
+#pragma unroll
+        for (int e = 0; e < SW_E; ++e) {
+            const int p = (tv << 3) | e;
+            const bool f = sw_neg<N, K>(p) != sw_neg<N, K + 1>(p);
+            const float sg = f ? -1.0f : 1.0f;
+            x[e] *= sg;
+            y[e] *= sg;
+        }
+        sw_merges<N, K + 1>(x, y, t, g, base, par);
+    }
 }
 
 template <int N>
-__global__ void __launch_bounds__(N, 2048 / N) sw_kernel(const float* __restrict__ X,
-                                               const float* __restrict__ T,
-                                               const float* __restrict__ phi, int P,
-                                               float scale, float* loss, float* dX)
+__global__ void __launch_bounds__(SW_THREADS, 3) sw_kernel(const float* __restrict__ X,
+                                                          const float* __restrict__ T,
+                                                          const float* __restrict__ phi, int P,
+                                                          int pc, float scale, float* loss,
+                                                          float* dX)
 {
-    __shared__ float xs[2][N], ys[2][N], gxs[N], gys[N];
-    __shared__ int is[2][N];
-    __shared__ float red[32];
-    const int groups = (P + SW_PJ - 1) / SW_PJ;
-    const int s = blockIdx.x / groups, j0 = (blockIdx.x % groups) * SW_PJ;
-    const int i = threadIdx.x;
-    const float xi0 = X[((size_t)s * N + i) * 2], xi1 = X[((size_t)s * N + i) * 2 + 1];
-    const float ti0 = T[((size_t)s * N + i) * 2], ti1 = T[((size_t)s * N + i) * 2 + 1];
-    gxs[i] = 0.0f;
-    gys[i] = 0.0f;
+    constexpr int G = N / SW_E;
+    extern __shared__ float4 sw_smem[];
+    const int groups = blockDim.x / G;
+    float4* pts = sw_smem;                             // [8][G] (x0, x1, t0, t1), point 8t+e at e*G+t
+    float2* gacc = reinterpret_cast<float2*>(pts + N); // [groups][N] gradient sums
+    float2* bufs = gacc + (size_t)groups * N;          // [groups][2][N]
+    __shared__ float red[SW_THREADS / 32];
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int cps = (P + pc - 1) / pc;
+    const int s = blockIdx.x / cps, j0 = (blockIdx.x % cps) * pc, j1 = min(P, j0 + pc);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const size_t r = ((size_t)s * N + i) * 2;
+        pts[(i & (SW_E - 1)) * G + (i >> 3)] = make_float4(X[r], X[r + 1], T[r], T[r + 1]);
+    }
+    for (int i = threadIdx.x; i < groups * N; i += blockDim.x) gacc[i] = make_float2(0.0f, 0.0f);
+    __syncthreads();
     float lacc = 0.0f;
-    int buf = 0;
-    for (int j = j0; j < min(P, j0 + SW_PJ); ++j) {
+    // each group takes every groups-th projection of the CTA's run; from here
+    // to the final sums a group synchronizes only its own threads
+    for (int j = j0 + g; j < j1; j += groups) {
         float sn, c;
         sincosf(phi[j], &sn, &c);
-        float kx = fmaf(xi0, c, xi1 * sn), ky = fmaf(ti0, c, ti1 * sn);
-        int ix = i;
-        sw_sort<N, 2>(i, kx, ky, ix, xs, ys, is, buf);
-        const float diff = kx - ky;
-        lacc = fmaf(diff, diff, lacc);
-        const float gv = 2.0f * diff / (float)N;
-        gxs[ix] = fmaf(gv, c, gxs[ix]);
-        gys[ix] = fmaf(gv, sn, gys[ix]);
-        __syncthreads();
+        // every address below derives from t and g: recomputing them per
+        // projection costs a few integer operations, keeping all of them live
+        // across the loop would cost registers
+        int tt, gg;
+        asm volatile("mov.b32 %0, %1;" : "=r"(tt) : "r"(t));
+        asm volatile("mov.b32 %0, %1;" : "=r"(gg) : "r"(g));
+        float x[SW_E], y[SW_E];
+#pragma unroll
+        for (int e = 0; e < SW_E; ++e) {
+            const float4 q = pts[e * G + tt];
+            // merge 1 starts with the blocks where position bit 1 is set negated
+            const float sg = sw_neg<N, 1>(e) ? -1.0f : 1.0f;
+            x[e] = sg * sw_key(q.x, q.y, c, sn);
+            y[e] = sg * sw_key(q.z, q.w, c, sn);
+        }
+        // the moves alternate between the group's two buffers, starting from
+        // the first in every projection (the barrier after the previous
+        // projection's search makes that safe), so every choice is static
+        int par = 0;
+        sw_merges<N, 1>(x, y, tt, gg, bufs + (size_t)gg * 2 * N, par);
+        // ranks 8t .. 8t+7: squared differences; the sorted keys and each
+        // rank's gradient go to the buffer the last move did not read
+        float* sk = reinterpret_cast<float*>(bufs + ((size_t)gg * 2 + par) * N);
+        float* sgr = sk + N;
+        float d[SW_E];
+#pragma unroll
+        for (int e = 0; e < SW_E; ++e) {
+            d[e] = x[e] - y[e];
+            lacc = fmaf(d[e], d[e], lacc);
+            d[e] = 2.0f * d[e] / (float)N;
+        }
+        reinterpret_cast<float4*>(sk)[2 * tt] = make_float4(x[0], x[1], x[2], x[3]);
+        reinterpret_cast<float4*>(sk)[2 * tt + 1] = make_float4(x[4], x[5], x[6], x[7]);
+        reinterpret_cast<float4*>(sgr)[2 * tt] = make_float4(d[0], d[1], d[2], d[3]);
+        reinterpret_cast<float4*>(sgr)[2 * tt + 1] = make_float4(d[4], d[5], d[6], d[7]);
+        sw_group_sync<G>(gg);
+#pragma unroll 2
+        for (int e = 0; e < SW_E; ++e) {
+            const int i = tt * SW_E + e;
+            const float4 q = pts[e * G + tt];
+            const float kx = sw_key(q.x, q.y, c, sn);
+            int r = 0;
+#pragma unroll
+            for (int h = N / 2; h >= 1; h >>= 1) r += sk[r + h - 1] < kx ? h : 0;
+            const float gv = sgr[r];
+            float2 a = gacc[(size_t)gg * N + sw_swz(i)];
+            a.x = fmaf(gv, c, a.x);
+            a.y = fmaf(gv, sn, a.y);
+            gacc[(size_t)gg * N + sw_swz(i)] = a;
+        }
+        sw_group_sync<G>(gg);
     }
-    atomicAdd(dX + ((size_t)s * N + i) * 2, gxs[i] * scale);
-    atomicAdd(dX + ((size_t)s * N + i) * 2 + 1, gys[i] * scale);
     float v = lacc;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((i & 31) == 0) red[i >> 5] = v;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    if (i == 0) {
-        float t = 0.0f;
-        for (int w = 0; w < (N + 31) / 32; ++w) t += red[w];
-        atomicAdd(loss, t * scale / (float)N);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        float ax = 0.0f, ay = 0.0f;
+        for (int q = 0; q < groups; ++q) {
+            const float2 a = gacc[(size_t)q * N + sw_swz(i)];
+            ax += a.x;
+            ay += a.y;
+        }
+        atomicAdd(dX + ((size_t)s * N + i) * 2, ax * scale);
+        atomicAdd(dX + ((size_t)s * N + i) * 2 + 1, ay * scale);
+    }
+    if (threadIdx.x == 0) {
+        float tot = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        atomicAdd(loss, tot * scale / (float)N);
     }
 }
 
-// launches the SW kernel for N points per system (a power of two, 32..1024)
+// dynamic shared memory of sw_kernel<N> with `groups` groups
+size_t sw_smem_bytes(int N, int groups)
+{
+    return sizeof(float4) * N + sizeof(float2) * 3 * (size_t)N * groups;
+}
+
+template <int N>
+const void* sw_func()
+{
+    return reinterpret_cast<const void*>(&sw_kernel<N>);
+}
+
+const void* sw_kernel_of(int N)
+{
+    switch (N) {
+    case 32: return sw_func<32>();
+    case 64: return sw_func<64>();
+    case 128: return sw_func<128>();
+    case 256: return sw_func<256>();
+    case 512: return sw_func<512>();
+    default: return sw_func<1024>();
+    }
+}
+
+// per device: the shared-memory opt-in of every sw_kernel instance and how
+// many full-size CTAs of each fit on an SM (set outside stream capture)
+struct SwDevInfo {
+    bool ready = false;
+    int sms = 0;
+    int ctas[6] = {0, 0, 0, 0, 0, 0};
+};
+SwDevInfo g_sw_info[64];
+
+int sw_log2(int N)
+{
+    int l = 0;
+    while ((1 << l) < N) ++l;
+    return l;
+}
+
+cfs_status sw_init()
+{
+    int dev = 0;
+    cfs_status st = cfs::check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != CFS_OK) return st;
+    if (dev < 0 || dev >= 64) return cfs::fail(CFS_ERR_UNSUPPORTED, "device index out of range");
+    SwDevInfo& d = g_sw_info[dev];
+    if (d.ready) return CFS_OK;
+    st = cfs::check_cuda(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev), "SMs");
+    for (int N = 32; N <= 1024 && st == CFS_OK; N *= 2) {
+        const int groups = SW_THREADS / (N / SW_E);
+        const size_t bytes = sw_smem_bytes(N, groups);
+        const void* f = sw_kernel_of(N);
+        st = cfs::check_cuda(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes),
+                        "cudaFuncSetAttribute(sw_kernel)");
+        int n = 0;
+        if (st == CFS_OK)
+            st = cfs::check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, SW_THREADS,
+                                                                          bytes),
+                            "occupancy(sw_kernel)");
+        d.ctas[sw_log2(N) - 5] = std::max(1, n);
+    }
+    if (st == CFS_OK) d.ready = true;
+    return st;
+}
+
+// launches the SW kernel for N points per system (a power of two, 32..1024);
+// sw_init() must have run on this device
 void sw_launch(const float* X, const float* T, const float* phi, int P, int N, int n_sys,
                float scale, float* loss, float* dX, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)n_sys * (unsigned)((P + SW_PJ - 1) / SW_PJ);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const SwDevInfo& d = g_sw_info[dev >= 0 && dev < 64 ? dev : 0];
+    const int G = N / SW_E;
+    // groups per CTA: enough for the projections, whole warps
+    int groups = std::min(SW_THREADS / G, P);
+    const int per_warp = std::max(1, 32 / G);
+    groups = std::min(SW_THREADS / G, (groups + per_warp - 1) / per_warp * per_warp);
+    // sorts per group: shortest makespan over the resident CTAs, a CTA
+    // costing its sorts plus about 0.3 of a sort for staging the points and
+    // adding its gradient sums to dX
+    const long slots = (long)std::max(1, d.sms) * std::max(1, d.ctas[sw_log2(N) - 5]);
+    int best_pg = 1;
+    double best = -1.0;
+    for (int pg = 1; pg <= 16; ++pg) {
+        const long ctas = (long)n_sys * ((P + groups * pg - 1) / (groups * pg));
+        const double span = (double)((ctas + slots - 1) / slots) * (pg + 0.3);
+        if (best < 0.0 || span < best) { best = span; best_pg = pg; }
+        if (groups * pg >= P) break;
+    }
+    const int pc = groups * best_pg;
+    const unsigned grid = (unsigned)n_sys * (unsigned)((P + pc - 1) / pc);
+    const unsigned threads = (unsigned)(groups * G);
+    const size_t bytes = sw_smem_bytes(N, groups);
     switch (N) {
-    case 32: sw_kernel<32><<<grid, 32, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
-    case 64: sw_kernel<64><<<grid, 64, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
-    case 128: sw_kernel<128><<<grid, 128, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
-    case 256: sw_kernel<256><<<grid, 256, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
-    case 512: sw_kernel<512><<<grid, 512, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
-    default: sw_kernel<1024><<<grid, 1024, 0, st>>>(X, T, phi, P, scale, loss, dX); break;
+    case 32: sw_kernel<32><<<grid, threads, bytes, st>>>(X, T, phi, P, pc, scale, loss, dX); break;
+    case 64: sw_kernel<64><<<grid, threads, bytes, st>>>(X, T, phi, P, pc, scale, loss, dX); break;
+    case 128: sw_kernel<128><<<grid, threads, bytes, st>>>(X, T, phi, P, pc, scale, loss, dX); break;
+    case 256: sw_kernel<256><<<grid, threads, bytes, st>>>(X, T, phi, P, pc, scale, loss, dX); break;
+    case 512: sw_kernel<512><<<grid, threads, bytes, st>>>(X, T, phi, P, pc, scale, loss, dX); break;
+    default: sw_kernel<1024><<<grid, threads, bytes, st>>>(X, T, phi, P, pc, scale, loss, dX); break;
     }
 }
 
@@ -1218,7 +1460,8 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              TC_SMEM),
                         "cudaFuncSetAttribute(tc_gemm_kernel)");
-    st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
+    if (st == CFS_OK) st = sw_init();
+    if (st == CFS_OK) st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->d_step, 0, 256), "memset");
     std::vector<float> init;
@@ -1330,6 +1573,8 @@ cfs_status cfs_sw_loss(const float* X, const float* T, uint32_t n_sys, uint32_t 
         return fail(CFS_ERR_INVALID_ARG, "points per system must be a power of two in 32..1024");
     if (n_sys == 0 || n_proj == 0) return CFS_OK;
     const float scale = 1.0f / ((float)n_sys * (float)n_proj);
+    cfs_status st = sw_init();
+    if (st != CFS_OK) return st;
     sw_launch(X, T, phi, (int)n_proj, (int)n_per, (int)n_sys, scale, loss, dX,
               (cudaStream_t)stream);
     return check_cuda(cudaGetLastError(), "sw_kernel launch");

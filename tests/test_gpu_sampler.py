@@ -98,6 +98,41 @@ def test_sw_loss_matches_oracle(torch_cuda):
     assert _rel(dX.cpu().numpy(), go) < 1e-4
 
 
+@pytest.mark.parametrize("S,N,P", [(1, 32, 1), (2, 64, 5), (3, 128, 16), (2, 512, 7),
+                                   (2, 1024, 3), (4, 1024, 64)])
+def test_sw_loss_sizes_match_oracle(torch_cuda, S, N, P):
+    """Every group size of the register-blocked sort (N / 8 threads), CTAs
+    whose last run of projections is short (P not a multiple of the run),
+    one projection, and the training shape's 1024 points."""
+    torch = torch_cuda
+    from paper_2606_02226_gb300 import cfs
+    rng = np.random.default_rng(100 + N + P)
+    X = rng.normal(size=(S, N, 2)).astype(np.float32)
+    T = (rng.standard_t(3, size=(S, N, 2)) * 0.4 - 0.2).astype(np.float32)
+    phi = rng.uniform(0.0, 2 * math.pi, size=P).astype(np.float32)
+    loss, dX = cfs.sw_loss(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),
+                           torch.from_numpy(phi).cuda())
+    Lo, go = SO.sw_loss_grad(X, T, phi.astype(np.float64))
+    assert abs(float(loss.item()) - Lo) < 1e-5 * Lo
+    assert _rel(dX.cpu().numpy(), go) < 1e-4
+
+
+def test_sw_loss_sorted_sets_give_zero(torch_cuda):
+    """Equal predicted and target sets: every rank matches itself, so the
+    loss and the gradient vanish exactly (the sort and the rank search must
+    pair each key with its own copy)."""
+    torch = torch_cuda
+    from paper_2606_02226_gb300 import cfs
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(2, 1024, 2)).astype(np.float32)
+    T = X[:, rng.permutation(1024), :].copy()
+    phi = rng.uniform(0.0, 2 * math.pi, size=9).astype(np.float32)
+    loss, dX = cfs.sw_loss(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),
+                           torch.from_numpy(phi).cuda())
+    assert float(loss.item()) == 0.0
+    assert not dX.abs().max().item()
+
+
 def test_adam_matches_oracle(torch_cuda):
     torch = torch_cuda
     cfs, s, params, _, _ = _setup(torch, 64)

@@ -186,6 +186,32 @@ static void emit_scribble_chain(std::ostringstream& s, const ProgramSpec& sp)
     s << "    ox = qx; oy = qy; oz = qz;\n    return alive;\n}\n\n";
 }
 
+// index of the op chain's first duplication op (-1: none or a scribble chain)
+static int first_stars_op(const ProgramSpec& sp)
+{
+    if (!sp.scribble.empty()) return -1;
+    for (int o = 0; o < sp.n_ops; ++o)
+        if (sp.op_kind[o] == CFS_OP_STARS) return o;
+    return -1;
+}
+
+// per-CTA setup of the chain, run by every kernel before its first barrier:
+// the first duplication op's star table
+static void emit_chain_prologue(std::ostringstream& s, const ProgramSpec& sp)
+{
+    s << "__device__ __forceinline__ void cfs_chain_prologue(const cfs_launch_args& a, CfsSmem& sm)"
+         "\n{\n    (void)a; (void)sm;\n";
+    const int o = first_stars_op(sp);
+    if (o >= 0) {
+        s << "    const u32 n_ = min(__float_as_uint(" << P(o, 0) << "), (u32)CFS_STARS_TAB);\n"
+          << "    for (u32 j = threadIdx.x; j < n_; j += blockDim.x)\n"
+          << "        sm.stars[j] = cfs_star_centre(a, j, " << P(o, 1) << ", " << P(o, 2) << ", "
+          << P(o, 3) << ", " << P(o, 4) << ", " << P(o, 5) << ", " << P(o, 6) << ", "
+          << P(o, 7) << ", " << P(o, 8) << ");\n";
+    }
+    s << "}\n\n";
+}
+
 static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
 {
     if (!sp.scribble.empty()) {
@@ -234,9 +260,18 @@ static void emit_chain(std::ostringstream& s, const ProgramSpec& sp)
             s << "alive = cfs_inversion(" << Plist(o, 4) << "qx, qy, qz) && alive;\n";
             break;
         case CFS_OP_STARS:
-            s << "cfs_stars(a, __float_as_uint(" << P(o, 0) << "), " << P(o, 1) << ", "
-              << P(o, 2) << ", " << P(o, 3) << ", " << P(o, 4) << ", " << P(o, 5) << ", "
-              << P(o, 6) << ", " << P(o, 7) << ", " << P(o, 8) << ", aux, qx, qy, qz);\n";
+            if (o == first_stars_op(sp)) {
+                // the table of cfs_chain_prologue when it holds every star
+                s << "{ const u32 n_ = __float_as_uint(" << P(o, 0) << "); const u32 j_ = "
+                  << "__umulhi(aux, n_); cfs_star_place(n_ <= CFS_STARS_TAB ? sm.stars[j_] : "
+                  << "cfs_star_centre(a, j_, " << P(o, 1) << ", " << P(o, 2)
+                  << ", " << P(o, 3) << ", " << P(o, 4) << ", " << P(o, 5) << ", " << P(o, 6)
+                  << ", " << P(o, 7) << ", " << P(o, 8) << "), qx, qy, qz); }\n";
+            } else {
+                s << "cfs_stars(a, __float_as_uint(" << P(o, 0) << "), " << P(o, 1) << ", "
+                  << P(o, 2) << ", " << P(o, 3) << ", " << P(o, 4) << ", " << P(o, 5) << ", "
+                  << P(o, 6) << ", " << P(o, 7) << ", " << P(o, 8) << ", aux, qx, qy, qz);\n";
+            }
             break;
         case CFS_OP_HEMISPHERE:
             s << "cfs_hemisphere(" << P(o, 0) << ", qx, qy, qz);\n";
@@ -306,11 +341,13 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_DEPTH_TEST " << sp.depth_test << "\n";
     s << "#define CFS_BLOCK " << sp.block << "\n";
     s << "#define CFS_MINB " << sp.min_blocks << "\n";
+    s << "#define CFS_STARS_TAB " << (first_stars_op(sp) >= 0 ? 512 : 0) << "\n";
     s << "#include \"cfs_device.cuh\"\n";
     // generator parameters with constant indices come straight from the
     // argument block (the constant bank); only the table path uses smem
     s << "#define a_sys_prm(j, k) (a.sys.prm[j][k])\n\n";
     emit_gen_map(s, sp);
+    emit_chain_prologue(s, sp);
     emit_chain(s, sp);
     s << "#include \"cfs_kernels.cuh\"\n";
     return s.str();

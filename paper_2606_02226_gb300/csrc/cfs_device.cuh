@@ -52,10 +52,19 @@ __device__ __forceinline__ u32 cfs_word(uint4 r, u32 s)
 }
 
 /* ---- shared-memory copy of the per-launch tables ---------------------- */
+#ifndef CFS_STARS_TAB
+#define CFS_STARS_TAB 0
+#endif
 struct CfsSmem {
     float2 prm2[6][CFS_A_MAX_MAPS];           /* map params, pairs (0,1) (2,3) ... */
     float4 pal[CFS_A_MAX_TARGETS][CFS_A_MAX_MAPS];
     u32 pal8[CFS_A_MAX_TARGETS][CFS_A_MAX_MAPS];
+#if CFS_STARS_TAB
+    /* centre and size of the chain's first duplication op's stars (up to
+     * CFS_STARS_TAB of them), filled once per CTA: the per-step lookup
+     * replaces a Philox block per point-step with the same values */
+    float4 stars[CFS_STARS_TAB];
+#endif
 };
 
 __device__ __forceinline__ void cfs_load_smem(const cfs_launch_args& a, CfsSmem& sm)
@@ -351,19 +360,30 @@ __device__ __forceinline__ bool cfs_inversion(float cx, float cy, float cz, floa
  * of n, whose centre and size come from Philox block (j, 0, 0, 7):
  * q' = centre + size q.  Parameters: n (integer bits), x0, x1 - x0, y0,
  * y1 - y0, z0, z1 - z0, s0, s1 - s0. */
+__device__ __forceinline__ float4 cfs_star_centre(const cfs_launch_args& a, u32 j, float x0,
+                                                  float dx, float y0, float dy, float z0,
+                                                  float dz, float s0, float ds)
+{
+    const uint4 r = cfs_philox(a, j, 0u, 0u, 7u);
+    return make_float4(fmaf(dx, (float)(r.x >> 8) * CFS_INV_2_24, x0),
+                       fmaf(dy, (float)(r.y >> 8) * CFS_INV_2_24, y0),
+                       fmaf(dz, (float)(r.z >> 8) * CFS_INV_2_24, z0),
+                       fmaf(ds, (float)(r.w >> 8) * CFS_INV_2_24, s0));
+}
+
+__device__ __forceinline__ void cfs_star_place(float4 c, float& x, float& y, float& z)
+{
+    x = fmaf(c.w, x, c.x);
+    y = fmaf(c.w, y, c.y);
+    z = fmaf(c.w, z, c.z);
+}
+
 __device__ __forceinline__ void cfs_stars(const cfs_launch_args& a, u32 n, float x0, float dx,
                                           float y0, float dy, float z0, float dz, float s0,
                                           float ds, u32 aux, float& x, float& y, float& z)
 {
     const u32 j = __umulhi(aux, n);
-    const uint4 r = cfs_philox(a, j, 0u, 0u, 7u);
-    const float cx = fmaf(dx, (float)(r.x >> 8) * CFS_INV_2_24, x0);
-    const float cy = fmaf(dy, (float)(r.y >> 8) * CFS_INV_2_24, y0);
-    const float cz = fmaf(dz, (float)(r.z >> 8) * CFS_INV_2_24, z0);
-    const float sz = fmaf(ds, (float)(r.w >> 8) * CFS_INV_2_24, s0);
-    x = fmaf(sz, x, cx);
-    y = fmaf(sz, y, cy);
-    z = fmaf(sz, z, cz);
+    cfs_star_place(cfs_star_centre(a, j, x0, dx, y0, dy, z0, dz, s0, ds), x, y, z);
 }
 
 /* The unit disk as the front (z <= 0) half of a sphere of radius R. */

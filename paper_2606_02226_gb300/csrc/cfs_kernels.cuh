@@ -198,6 +198,7 @@ extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
 cfs_cloud_kernel(const __grid_constant__ cfs_launch_args a)
 {
     __shared__ CfsSmem sm;
+    cfs_chain_prologue(a, sm);   /* per-CTA tables of the chain (before the first barrier) */
     cfs_load_smem(a, sm);
     __syncthreads();
     const CfsChooseConst choose{a};
@@ -259,6 +260,7 @@ extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
 cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
 {
     __shared__ CfsSmem sm;
+    cfs_chain_prologue(a, sm);   /* per-CTA tables of the chain (before the first barrier) */
     cfs_load_smem(a, sm);
     __syncthreads();
     u32 disc[CFS_NT_ARR];
@@ -300,6 +302,7 @@ extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
 cfs_render_kernel(const __grid_constant__ cfs_launch_args a)
 {
     __shared__ CfsSmem sm;
+    cfs_chain_prologue(a, sm);   /* per-CTA tables of the chain (before the first barrier) */
     cfs_load_smem(a, sm);
     __syncthreads();
     u32 disc[CFS_NT_ARR];
@@ -322,6 +325,7 @@ extern "C" __global__ void __launch_bounds__(CFS_BLOCK)
 cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
 {
     __shared__ CfsSmem sm;
+    cfs_chain_prologue(a, sm);   /* per-CTA tables of the chain (before the first barrier) */
     cfs_load_smem(a, sm);
     __syncthreads();
     const u32 j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -399,6 +403,7 @@ extern "C" __global__ void __launch_bounds__(CFS_BLOCK)
 cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
 {
     __shared__ CfsSmem sm;
+    cfs_chain_prologue(a, sm);   /* per-CTA tables of the chain (before the first barrier) */
     __shared__ u32 s_T[CFS_A_MAX_MAPS];
     __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
     __shared__ int s_box[4];
@@ -492,6 +497,7 @@ extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
 cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
 {
     __shared__ CfsSmem sm;
+    cfs_chain_prologue(a, sm);   /* per-CTA tables of the chain (before the first barrier) */
     __shared__ u32 s_T[CFS_A_MAX_MAPS];
     __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
     __shared__ u32 s_item, s_frame, s_npts, s_pbeg, s_sid, s_ibeg, s_chunk;

@@ -105,12 +105,23 @@ def test_space_full_size_sampled(torch_cuda):
     assert _worst(gg, oo) <= POS_TOL * 20
 
 
-def test_stars_in_a_batch_are_bit_exact(torch_cuda):
+def _stars(n):
+    return W.Op("stars", (float(n), -4.0, 4.0, -4.0, 4.0, 0.0, 1.0, 0.2, 0.5))
+
+
+@pytest.mark.parametrize("chain_ops", [
+    # the first duplication op reads the per-CTA table of its stars
+    [_stars(7), W.Op("bands", (1.0, 2.0, 0.25, 3.0, 0.0)), W.Op("splat", (0,))],
+    # more stars than the table holds: the Philox block per step
+    [_stars(700), W.Op("bands", (1.0, 2.0, 0.25, 3.0, 0.0)), W.Op("splat", (0,))],
+    # a second duplication op in the chain: the table is the first op's only
+    [_stars(5), W.Op("splat", (0,)), W.Op("reset"), _stars(9),
+     W.Op("bands", (0.0, 1.0, 0.0, 2.0, 1.0)), W.Op("splat", (0,))],
+], ids=["table", "over-512", "two-ops"])
+def test_stars_in_a_batch_are_bit_exact(torch_cuda, chain_ops):
     from paper_2606_02226_gb300 import cfs
     torch = torch_cuda
     frames = W.animation_frames(n_frames=6, seed=5, min_log2=9, max_log2=11, resolutions=(64,))
-    chain_ops = [W.Op("stars", (7.0, -4.0, 4.0, -4.0, 4.0, 0.0, 1.0, 0.2, 0.5)),
-                 W.Op("bands", (1.0, 2.0, 0.25, 3.0, 0.0)), W.Op("splat", (0,))]
     chain = cfs.Chain(chain_ops, 2)
     items, descs, tens = [], [], []
     begin = 0

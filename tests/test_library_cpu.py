@@ -168,8 +168,17 @@ def test_new_op_validation_and_codegen():
     wl = W.space_render(n_points=64, iters=24, W=64, H=36)
     src, log = cfs.codegen_check(cfs.System(wl.jobs[0].system), cfs.Chain(wl.chain, 2),
                                  wl.targets)
-    assert "#define CFS_AUX 1" in src and "cfs_stars(" in src and "cfs_hemisphere(" in src
+    assert "#define CFS_AUX 1" in src and "cfs_hemisphere(" in src
+    # the first duplication op reads its per-CTA star table, with the Philox
+    # block as the fallback for more stars than the table holds
+    assert "#define CFS_STARS_TAB 512" in src and "cfs_chain_prologue" in src
+    assert "sm.stars[j_]" in src and "cfs_star_centre(a, j_" in src
     assert "0 bytes spill stores" in log
+    two = [W.Op("stars", (8.0, -1.0, 1.0, -1.0, 1.0, 2.0, 3.0, 0.1, 0.2)), W.Op("reset"),
+           W.Op("stars", (4.0, -1.0, 1.0, -1.0, 1.0, 2.0, 3.0, 0.1, 0.2)), W.Op("splat", (0,))]
+    src3, _ = cfs.codegen_check(cfs.System(W.square_system()), cfs.Chain(two, 2),
+                                [W.Target("depth_u64", 8, 8, 1)])
+    assert src3.count("sm.stars[j_]") == 1 and "cfs_stars(a, " in src3   # second op: Philox
     src2, _ = cfs.codegen_check(cfs.System(W.square_system()), ok, [W.Target("hist_u32", 8, 8, 4)])
     assert "#define CFS_AUX 1" in src2
 

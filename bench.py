@@ -74,6 +74,23 @@ def measure_atomic_peaks(torch, cfs, dev, rgba_bytes: int, depth_bytes: int, rep
     return out
 
 
+def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
+    """Gop/s of u32 adds at uniformly random addresses in each CTA's shared
+    memory (an 8192-word footprint like a privatized window), full GPU."""
+    buf = torch.zeros(8192, dtype=torch.int32, device=dev)
+    blocks, iters = 152 * 6, 4096
+    cfs.atomic_bench(4, buf, 8192, blocks, iters, seed=1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(reps):
+        cfs.atomic_bench(4, buf, 8192, blocks, iters, seed=r + 2)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return blocks * 256 * iters / (ms * 1e-3) / 1e9
+
+
 # DRAM bytes per render launch of the composed scene (mean of the two
 # objects' launches: dram__bytes_read.sum + dram__bytes_write.sum from a
 # full-size one-pass ncu capture).  Valid only for the kernel it was taken
@@ -505,7 +522,12 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             "target_bytes": bytes_targets, "items": info["n_items"], "chunk": info["chunk"],
             "grid": info["grid"], "gpu_launches_per_batch": 1, "display": display,
             "autotuned": tuning, "ms_per_batch_default_plan": ms_default,
-            "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3)}
+            "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3),
+            "context_peaks_gops": {"smem_red_u32": measure_smem_atomic_peak(torch, cfs, dev),
+                                   "note": "shared-memory u32 adds at random addresses over "
+                                           "8192 words per CTA, the window splats' operation; "
+                                           "the batch kernel is bound by its integer ALU work "
+                                           "(Philox, map choice), not by these"}}
 
 
 def bench_space(torch, cfs, dev, stream, reps: int = 5):

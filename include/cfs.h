@@ -537,8 +537,11 @@ cfs_status cfs_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, u
  * uniformly random element indices of `buf` (device, n_elems elements, a
  * power of two): kind 0 = red.add.u32 (4-byte elements), 1 =
  * red.add.v4.f32 (16-byte), 2 = red.min.u64 (8-byte), 3 = strong u64 load
- * then red.min.u64 when it lowers the value seen (the depth test).  The
- * caller times it on `stream`; contents of buf are overwritten. */
+ * then red.min.u64 when it lowers the value seen (the depth test), 4 = u32
+ * add into each CTA's shared memory over n_elems <= 8192 words (the
+ * privatized windows of batches; each CTA adds its counts to buf at the
+ * end).  The caller times it on `stream`; contents of buf are overwritten
+ * (kind 4: accumulated into). */
 cfs_status cfs_atomic_bench(int kind, void* buf, uint64_t n_elems, uint32_t blocks,
                             uint32_t iters, uint32_t seed, void* stream);
 

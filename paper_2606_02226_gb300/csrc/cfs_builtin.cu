@@ -29,15 +29,34 @@ __global__ void __launch_bounds__(256) philox_kernel(const u32* __restrict__ ctr
 
 /* Uniformly random reductions over a power-of-two footprint: kind 0 u32
  * add, 1 v4.f32 add (16-byte elements), 2 u64 min, 3 strong u64 load + u64
- * min only when it lowers the value seen (the depth test of the splat path).
- * Addresses come from a per-thread xorshift32 stream, so the kernel spends
- * little besides the memory operation. */
+ * min only when it lowers the value seen (the depth test of the splat path),
+ * 4 u32 add into the CTA's shared memory (the privatized windows; footprint
+ * at most kSmemBenchWords, the sums land in buf once per CTA).  Addresses
+ * come from a per-thread xorshift32 stream, so the kernel spends little
+ * besides the memory operation. */
+constexpr u32 kSmemBenchWords = 8192;
+
 __global__ void __launch_bounds__(256) atomic_bench_kernel(int kind, void* buf, u32 mask,
                                                            u32 iters, u32 seed)
 {
     u32 h = (blockIdx.x * blockDim.x + threadIdx.x) * 0x9E3779B1u + seed;
     h |= 1u;
     u32 acc = 0;
+    if (kind == 4) {
+        __shared__ u32 s_cnt[kSmemBenchWords];
+        for (u32 e = threadIdx.x; e < kSmemBenchWords; e += blockDim.x) s_cnt[e] = 0u;
+        __syncthreads();
+        for (u32 j = 0; j < iters; ++j) {
+            h ^= h << 13;
+            h ^= h >> 17;
+            h ^= h << 5;
+            atomicAdd(&s_cnt[h & mask], 1u);
+        }
+        __syncthreads();
+        for (u32 e = threadIdx.x; e <= mask; e += blockDim.x)
+            if (s_cnt[e]) atomicAdd(reinterpret_cast<u32*>(buf) + e, s_cnt[e]);
+        return;
+    }
     for (u32 j = 0; j < iters; ++j) {
         h ^= h << 13;
         h ^= h >> 17;
@@ -67,9 +86,11 @@ extern "C" cfs_status cfs_atomic_bench(int kind, void* buf, uint64_t n_elems, ui
                                        uint32_t iters, uint32_t seed, void* stream)
 {
     cfs::clear_error();
-    if (kind < 0 || kind > 3) return cfs::fail(CFS_ERR_INVALID_ARG, "kind must be 0..3");
+    if (kind < 0 || kind > 4) return cfs::fail(CFS_ERR_INVALID_ARG, "kind must be 0..4");
     if (!buf || n_elems == 0 || (n_elems & (n_elems - 1)) != 0 || n_elems > (1ull << 32))
         return cfs::fail(CFS_ERR_INVALID_ARG, "n_elems must be a power of two <= 2^32");
+    if (kind == 4 && n_elems > kSmemBenchWords)
+        return cfs::fail(CFS_ERR_INVALID_ARG, "shared-memory footprint is at most 8192 words");
     if (((uintptr_t)buf) % 16 != 0) return cfs::fail(CFS_ERR_INVALID_ARG, "buf not aligned");
     if (blocks == 0) return CFS_OK;
     atomic_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(

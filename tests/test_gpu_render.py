@@ -45,6 +45,40 @@ def _cfs():
 # ---------------------------------------------------------------------------
 # Philox
 # ---------------------------------------------------------------------------
+def test_philox_matches_curand(torch_cuda, tmp_path):
+    """The library's Philox4x32-10 and the oracle's against CUDA's own
+    (curand_Philox4x32_10 of the curand device headers, compiled here into a
+    small program) on 10^6 random counters and keys, plus the counter
+    patterns the renderer uses (small point, step and system numbers)."""
+    import shutil
+    import subprocess
+    torch = torch_cuda
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "philox_curand")
+    src = os.path.join(os.path.dirname(__file__), "philox_curand.cu")
+    r = subprocess.run([nvcc, "-O2", "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    a = rng.integers(0, 2**32, size=(n, 6), dtype=np.uint64).astype(np.uint32)
+    a[:4096, 0] = np.arange(4096)             # point ids
+    a[:4096, 1] = np.arange(4096) % 125       # step blocks
+    a[:4096, 2] = np.arange(4096) % 7         # systems
+    a[:4096, 3] = np.arange(4096) % 11        # tags
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    a.tofile(fin)
+    r = subprocess.run([exe, fin, fout], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    ref = np.fromfile(fout, dtype=np.uint32).reshape(n, 4)
+    ctr = torch.from_numpy(a[:, 0:4].view(np.int32).copy()).cuda()
+    key = torch.from_numpy(a[:, 4:6].view(np.int32).copy()).cuda()
+    out = _cfs().philox(ctr, key).cpu().numpy().view(np.uint32)
+    assert np.array_equal(out, ref)
+    for j in list(range(0, 64)) + list(range(4096, n, 65521)):
+        assert np.array_equal(O.philox(a[j, 0:4], a[j, 4:6]), ref[j])
+
+
 def test_philox_known_answers_gpu(torch_cuda):
     torch = torch_cuda
     rows = []
@@ -359,3 +393,33 @@ def test_chain_trigonometry_accuracy(torch_cuda, trig):
         bound = 1.5 if trig == "poly" else 2.0
         assert err[small].max() <= bound, (name, err[small].max())
         assert err[~small].max() <= 2.0, (name, err[~small].max())
+
+
+# ---------------------------------------------------------------------------
+# the atomic microbenchmark behind the rooflines does the operations it
+# claims: every reduction lands (counts add up) and stays inside the footprint
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,esz,n", [(0, 4, 1 << 16), (1, 16, 1 << 12), (4, 4, 8192),
+                                        (4, 4, 1024)])
+def test_atomic_bench_counts(torch_cuda, kind, esz, n):
+    torch = torch_cuda
+    cfs = _cfs()
+    blocks, iters = 19, 64
+    buf = torch.zeros(n * esz // 4 + 64, dtype=torch.int32, device="cuda")
+    cfs.atomic_bench(kind, buf, n, blocks, iters, seed=3)
+    torch.cuda.synchronize()
+    h = buf.cpu().numpy()
+    assert not h[n * esz // 4:].any()               # nothing past the footprint
+    if kind == 1:   # v4.f32 adds of (1, 0.5, 0, 1)
+        v = h[:4 * n].view(np.float32).reshape(n, 4)
+        assert v[:, 0].sum() == blocks * 256 * iters and v[:, 2].sum() == 0.0
+    else:
+        assert int(h[:n].astype(np.int64).sum()) == blocks * 256 * iters
+
+
+def test_atomic_bench_rejects_large_shared_footprint(torch_cuda):
+    torch = torch_cuda
+    cfs = _cfs()
+    buf = torch.zeros(1 << 14, dtype=torch.int32, device="cuda")
+    with pytest.raises(cfs.CfsError):
+        cfs.atomic_bench(4, buf, 1 << 14, 1, 1)

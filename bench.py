@@ -99,8 +99,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16265856          # (26720768 + 5810944) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "e9dad3d8a3fc0ffaade1a36ec973fee085a53a3f"
+RENDER_TRAFFIC_BYTES = 16209536          # (26710784 + 5708288) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "9f73ebcf0a01f296166f0215de2e447457c6595a"
 
 
 def _code_only(text: str) -> str:

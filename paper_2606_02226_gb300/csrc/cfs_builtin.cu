@@ -36,27 +36,33 @@ __global__ void __launch_bounds__(256) philox_kernel(const u32* __restrict__ ctr
  * besides the memory operation. */
 constexpr u32 kSmemBenchWords = 8192;
 
+// kind 4, a kernel of its own: the global kinds keep zero shared memory (and
+// so their full occupancy)
+__global__ void __launch_bounds__(256) smem_atomic_bench_kernel(void* buf, u32 mask, u32 iters,
+                                                                u32 seed)
+{
+    __shared__ u32 s_cnt[kSmemBenchWords];
+    u32 h = (blockIdx.x * blockDim.x + threadIdx.x) * 0x9E3779B1u + seed;
+    h |= 1u;
+    for (u32 e = threadIdx.x; e < kSmemBenchWords; e += blockDim.x) s_cnt[e] = 0u;
+    __syncthreads();
+    for (u32 j = 0; j < iters; ++j) {
+        h ^= h << 13;
+        h ^= h >> 17;
+        h ^= h << 5;
+        atomicAdd(&s_cnt[h & mask], 1u);
+    }
+    __syncthreads();
+    for (u32 e = threadIdx.x; e <= mask; e += blockDim.x)
+        if (s_cnt[e]) atomicAdd(reinterpret_cast<u32*>(buf) + e, s_cnt[e]);
+}
+
 __global__ void __launch_bounds__(256) atomic_bench_kernel(int kind, void* buf, u32 mask,
                                                            u32 iters, u32 seed)
 {
     u32 h = (blockIdx.x * blockDim.x + threadIdx.x) * 0x9E3779B1u + seed;
     h |= 1u;
     u32 acc = 0;
-    if (kind == 4) {
-        __shared__ u32 s_cnt[kSmemBenchWords];
-        for (u32 e = threadIdx.x; e < kSmemBenchWords; e += blockDim.x) s_cnt[e] = 0u;
-        __syncthreads();
-        for (u32 j = 0; j < iters; ++j) {
-            h ^= h << 13;
-            h ^= h >> 17;
-            h ^= h << 5;
-            atomicAdd(&s_cnt[h & mask], 1u);
-        }
-        __syncthreads();
-        for (u32 e = threadIdx.x; e <= mask; e += blockDim.x)
-            if (s_cnt[e]) atomicAdd(reinterpret_cast<u32*>(buf) + e, s_cnt[e]);
-        return;
-    }
     for (u32 j = 0; j < iters; ++j) {
         h ^= h << 13;
         h ^= h >> 17;
@@ -93,8 +99,12 @@ extern "C" cfs_status cfs_atomic_bench(int kind, void* buf, uint64_t n_elems, ui
         return cfs::fail(CFS_ERR_INVALID_ARG, "shared-memory footprint is at most 8192 words");
     if (((uintptr_t)buf) % 16 != 0) return cfs::fail(CFS_ERR_INVALID_ARG, "buf not aligned");
     if (blocks == 0) return CFS_OK;
-    atomic_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
-        kind, buf, (u32)(n_elems - 1), iters, seed);
+    if (kind == 4)
+        smem_atomic_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+            buf, (u32)(n_elems - 1), iters, seed);
+    else
+        atomic_bench_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+            kind, buf, (u32)(n_elems - 1), iters, seed);
     return cfs::check_cuda(cudaGetLastError(), "atomic_bench_kernel launch");
 }
 

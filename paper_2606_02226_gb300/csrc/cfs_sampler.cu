@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -83,11 +84,24 @@ enum Epi { EPI_SILU = 1, EPI_SILU_GRAD = 2, EPI_ATOMIC = 3 };
 constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 256;
 constexpr int TC_NV = 128 * 8 / TC_THREADS;   // 16-byte vectors per thread per operand tile
 constexpr int TC_TILE_BYTES = 128 * TC_K * 2;             // 16 KB: 128 rows x 64 K
-constexpr int TC_SMEM = 4 * TC_TILE_BYTES + 1024 + 1024;  // 2 stages x (A, B), barriers, align
+// dynamic shared memory of the kernel with ST stages of (A, B) chunks, plus
+// barriers and alignment; one stage is padded to 50 KB so that at most four
+// CTAs share an SM (four times 128 TMEM columns fill its 512)
+template <int ST>
+constexpr int tc_smem_bytes()
+{
+    return ST == 1 ? 50 * 1024 : 2 * ST * TC_TILE_BYTES + 1024 + 1024;
+}
 constexpr u32 TC_WAIT_LIMIT = 1u << 24;
 constexpr int TC_COPIES = 16;   // copies of the bias-gradient sums (spread the atomics)
 
 __device__ unsigned int g_tc_error = 0;
+// chunk stages of the GEMM kernel: 0 = by the chunks a CTA runs (one stage
+// for at most two: four CTAs per SM then take all 512 row tiles of a
+// 65536-row GEMM in one wave, 0.48 vs 0.52 ms per training step; two
+// stages for the K-split weight gradients, whose CTAs run four chunks).
+// CFS_TC_STAGES = 1 or 2 forces one for sweeps.
+int g_tc_stages = 0;
 
 struct TcArgs {
     int M, N, K;                 // N in {64, 128}
@@ -301,22 +315,26 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs& g, int row, int c0, co
     }
 }
 
+template <int ST>
 __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_constant__ TcArgs g)
 {
     extern __shared__ unsigned char tc_smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
     // stage s: A at sm + 2 s TILE, B right after it
-    u64* bars = reinterpret_cast<u64*>(sm + 4 * TC_TILE_BYTES);
-    u32* s_tmem = reinterpret_cast<u32*>(sm + 4 * TC_TILE_BYTES + 64);
-    float* s_col = reinterpret_cast<float*>(sm + 4 * TC_TILE_BYTES + 128);   // [128]
+    u64* bars = reinterpret_cast<u64*>(sm + 2 * ST * TC_TILE_BYTES);
+    u32* s_tmem = reinterpret_cast<u32*>(sm + 2 * ST * TC_TILE_BYTES + 64);
+    float* s_col = reinterpret_cast<float*>(sm + 2 * ST * TC_TILE_BYTES + 128);   // [128]
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * TC_M;
     const int kb = blockIdx.z * g.k_split;
     const int ke = min(g.K, kb + g.k_split);
     const int n_chunks = ke > kb ? (ke - kb + TC_K - 1) / TC_K : 0;
     const u32 ncols = g.N <= 64 ? 64u : 128u;
-    const u32 bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    // stage s's barrier completes once per chunk c = s, s + ST, ...: chunk c
+    // is its (c / ST)-th phase
+    auto bar = [&](int c) { return smem_addr(&bars[c % ST]); };
+    auto phase = [](int c) { return (u32)(c / ST) & 1u; };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -327,8 +345,8 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
     }
     if (tid < 128) s_col[tid] = 0.0f;
     if (tid == 0) {
-        mbar_init(bar0, 1u);
-        mbar_init(bar1, 1u);
+#pragma unroll
+        for (int q = 0; q < ST; ++q) mbar_init(smem_addr(&bars[q]), 1u);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -339,9 +357,9 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
 
     bool ok = true;
     for (int c = 0; c < n_chunks; ++c) {
-        const int s = c & 1;
-        // the stage's previous chunk (c - 2) must have left the tensor core
-        if (c >= 2) ok = mbar_wait(s ? bar1 : bar0, (u32)((c - 2) >> 1) & 1u);
+        const int s = c % ST;
+        // the stage's previous chunk (c - ST) must have left the tensor core
+        if (c >= ST) ok = mbar_wait(bar(c - ST), phase(c - ST));
         if (!__syncthreads_and(ok)) { ok = false; break; }
         const int k0 = kb + c * TC_K;
         const u32 sA = smem_addr(sm + 2 * s * TC_TILE_BYTES), sB = sA + TC_TILE_BYTES;
@@ -361,7 +379,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
             for (int kk = 0; kk < TC_K / 16; ++kk)
                 tc_mma(tmem, tc_desc(sA + kk * 256), tc_desc(sB + kk * 256), idesc,
                        (c > 0 || kk > 0) ? 1u : 0u);
-            tc_commit(s ? bar1 : bar0);
+            tc_commit(bar(c));
         }
     }
     // epilogue split: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows)
@@ -373,7 +391,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
     tc_load_z(g, row, c_begin, z_next);   // independent of the MMAs: overlaps them
     if (ok && n_chunks > 0) {
         const int last = n_chunks - 1;
-        ok = mbar_wait((last & 1) ? bar1 : bar0, (u32)(last >> 1) & 1u);
+        ok = mbar_wait(bar(last), phase(last));
     }
     ok = __syncthreads_and(ok) != 0;
     tc_fence_after();
@@ -393,7 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
         // give in-flight MMAs a bounded chance to drain before TMEM is freed
         if (n_chunks > 0) {
             const int last = n_chunks - 1;
-            mbar_wait((last & 1) ? bar1 : bar0, (u32)(last >> 1) & 1u);
+            mbar_wait(bar(last), phase(last));
         }
     }
     tc_fence_before();
@@ -441,15 +459,31 @@ __global__ void __launch_bounds__(256) out_forward_kernel(const bf16r* __restric
     Y[2 * r + 1] = y1 + w[OFF_B4 + 1];
 }
 
-// bias gradients b2 (copies part[0]) and b1 (part[1]): sum the copies the
-// GEMM epilogues accumulated into, add to grads
-__global__ void __launch_bounds__(2 * HID) bias_reduce_kernel(const float* __restrict__ part,
-                                                              float* grads)
+// gradient partial sums gathered in TC_COPIES copies to spread the atomics:
+// [2][TC_COPIES][HID] bias gradients b2 and b1 (GEMM epilogues), then
+// [TC_COPIES][OB_PART] of the output layer's backward: W4 rows 0 and 1
+// (2 x HID), b3 (HID), b4 (2), padding
+constexpr int OB_PART = 3 * HID + 4;
+constexpr int PART_FLOATS = TC_COPIES * (2 * HID + OB_PART);
+
+// sums the copies and adds them to grads
+__global__ void __launch_bounds__(512) part_reduce_kernel(const float* __restrict__ part,
+                                                          float* grads)
 {
-    const int l = threadIdx.x / HID, c = threadIdx.x % HID;
-    float s = 0.0f;
-    for (int k = 0; k < TC_COPIES; ++k) s += part[((size_t)l * TC_COPIES + k) * HID + c];
-    grads[(l == 0 ? OFF_B2 : OFF_B1) + c] += s;
+    for (int e = threadIdx.x; e < 2 * HID + 3 * HID + 2; e += blockDim.x) {
+        float s = 0.0f;
+        if (e < 2 * HID) {
+            const int l = e / HID, c = e % HID;
+            for (int k = 0; k < TC_COPIES; ++k) s += part[((size_t)l * TC_COPIES + k) * HID + c];
+            grads[(l == 0 ? OFF_B2 : OFF_B1) + c] += s;
+        } else {
+            const int q = e - 2 * HID;
+            const float* ob = part + (size_t)2 * TC_COPIES * HID;
+            for (int k = 0; k < TC_COPIES; ++k) s += ob[(size_t)k * OB_PART + q];
+            grads[q < 2 * HID ? OFF_W4 + q : (q < 3 * HID ? OFF_B3 + q - 2 * HID
+                                                          : OFF_B4 + q - 3 * HID)] += s;
+        }
+    }
 }
 
 // U [rows][D_IN] -> UT [D_IN][ldt] (the K-major operand of dW1)
@@ -481,7 +515,7 @@ __global__ void __launch_bounds__(HID) out_backward_kernel(const float* __restri
                                                            const bf16r* __restrict__ H3,
                                                            const float* __restrict__ Z3, int B,
                                                            bf16r* dZ3, bf16r* dZ3T, int ldt,
-                                                           float* grads)
+                                                           float* part)
 {
     __shared__ bf16r tT[HID][OB_ROWS + 2];   // the block's dZ3 tile, transposed
     const int n = threadIdx.x;
@@ -510,12 +544,15 @@ __global__ void __launch_bounds__(HID) out_backward_kernel(const float* __restri
         const int u = e / OB_ROWS, j = e % OB_ROWS;
         if (r0 + j < r1) dZ3T[(size_t)u * ldt + r0 + j] = tT[u][j];
     }
-    atomicAdd(grads + OFF_B3 + n, db3);
-    atomicAdd(grads + OFF_W4 + n, dw0);
-    atomicAdd(grads + OFF_W4 + HID + n, dw1);
+    // this block's sums into copy blockIdx.x % TC_COPIES (part_reduce_kernel
+    // adds the copies to the gradients)
+    float* c = part + (size_t)(blockIdx.x % TC_COPIES) * OB_PART;
+    atomicAdd(c + n, dw0);
+    atomicAdd(c + HID + n, dw1);
+    atomicAdd(c + 2 * HID + n, db3);
     if (n == 0) {
-        atomicAdd(grads + OFF_B4, db40);
-        atomicAdd(grads + OFF_B4 + 1, db41);
+        atomicAdd(c + 3 * HID, db40);
+        atomicAdd(c + 3 * HID + 1, db41);
     }
 }
 
@@ -1240,7 +1277,7 @@ struct cfs_sampler {
     float* v = nullptr;
     bf16r* wb = nullptr;     // bf16 copies
     bf16r* wbT = nullptr;    // bf16 W2^T, W3^T ([2][in][out]) for the backward GEMMs
-    float* bias_part = nullptr;   // [2][TC_COPIES][HID] bias-gradient partial sums
+    float* bias_part = nullptr;   // PART_FLOATS gradient partial sums (part_reduce_kernel)
     u32* d_step = nullptr;   // Adam step counter (device)
     u32 step = 0;            // host mirror (checkpoints)
     // inference workspace for n frames (grown on demand): records, c1,
@@ -1318,7 +1355,11 @@ cfs_status tc_gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda
     g.mode = mode; g.bias = bias; g.C = C; g.ldc = ldc; g.H = H; g.ldh = ldh;
     g.HT = HT; g.ldt = ldt; g.Zin = Zin; g.ldz = ldz; g.colsum = colsum;
     dim3 grid((M + TC_M - 1) / TC_M, 1, (K + g.k_split - 1) / g.k_split);
-    tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(g);
+    const int stages = g_tc_stages ? g_tc_stages : (g.k_split / TC_K <= 2 ? 1 : 2);
+    if (stages == 1)
+        tc_gemm_kernel<1><<<grid, TC_THREADS, tc_smem_bytes<1>(), st>>>(g);
+    else
+        tc_gemm_kernel<2><<<grid, TC_THREADS, tc_smem_bytes<2>(), st>>>(g);
     return CFS_OK;
 }
 
@@ -1344,11 +1385,12 @@ cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, floa
                     cudaStream_t st)
 {
     const bf16r* wb = s->wb;
+    // gradient sums of the output layer and of the biases gather in copies
+    // (bias_part) first: fewer atomics on the same address
+    cudaMemsetAsync(s->bias_part, 0, sizeof(float) * PART_FLOATS, st);
     out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, HID, 0, st>>>(
-        dY, wb, s->H3, s->Z3, B, s->dZ3, s->dZ3T, s->ldt, grads);
-    // dZ2 = (dZ3 W3) * silu'(Z2): the K-major B operand is W3^T; the bias
-    // gradients gather in copies (bias_part) first
-    cudaMemsetAsync(s->bias_part, 0, sizeof(float) * 2 * TC_COPIES * HID, st);
+        dY, wb, s->H3, s->Z3, B, s->dZ3, s->dZ3T, s->ldt, s->bias_part + 2 * TC_COPIES * HID);
+    // dZ2 = (dZ3 W3) * silu'(Z2): the K-major B operand is W3^T
     cfs_status r = tc_gemm(st, B, HID, HID, s->dZ3, HID, s->wbT + HID * HID, HID, EPI_SILU_GRAD,
                            nullptr, nullptr, 0, s->dZ2, HID, s->dZ2T, s->ldt, s->Z2, HID,
                            s->bias_part);
@@ -1356,7 +1398,7 @@ cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, floa
         r = tc_gemm(st, B, HID, HID, s->dZ2, HID, s->wbT, HID, EPI_SILU_GRAD, nullptr, nullptr,
                     0, nullptr, 0, s->dZ1T, s->ldt, s->Z1, HID, s->bias_part + TC_COPIES * HID);
     if (r != CFS_OK) return r;
-    bias_reduce_kernel<<<1, 2 * HID, 0, st>>>(s->bias_part, grads);
+    part_reduce_kernel<<<1, 512, 0, st>>>(s->bias_part, grads);
     transpose_in_kernel<<<(B + 31) / 32, 256, 0, st>>>(U, B, s->UT, s->ldt);
     // weight gradients dW = dZ^T A: K = the rows, split over CTAs, atomic
     const int splits = std::max(1, std::min(256, B / 256));
@@ -1446,7 +1488,7 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
     const size_t off_wb = (sizeof(float) * N_PARAMS * 3 + 255) & ~(size_t)255;
     const size_t off_wbT = off_wb + ((sizeof(bf16r) * N_PARAMS + 255) & ~(size_t)255);
     const size_t off_part = off_wbT + sizeof(bf16r) * 2 * HID * HID;
-    cfs_status st = check_cuda(cudaMalloc(&s->w, off_part + sizeof(float) * 2 * TC_COPIES * HID),
+    cfs_status st = check_cuda(cudaMalloc(&s->w, off_part + sizeof(float) * PART_FLOATS),
                                "cudaMalloc(sampler params)");
     if (st != CFS_OK) { delete s; return st; }
     s->m = s->w + N_PARAMS;
@@ -1454,12 +1496,18 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
     s->wb = reinterpret_cast<bf16r*>(reinterpret_cast<unsigned char*>(s->w) + off_wb);
     s->wbT = reinterpret_cast<bf16r*>(reinterpret_cast<unsigned char*>(s->w) + off_wbT);
     s->bias_part = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(s->w) + off_part);
-    // the tensor-core GEMM stages two 32 KB chunk pairs in dynamic shared memory
+    // the tensor-core GEMM stages its chunk pairs in dynamic shared memory
     if (st == CFS_OK)
-        st = check_cuda(cudaFuncSetAttribute(tc_gemm_kernel,
+        st = check_cuda(cudaFuncSetAttribute(tc_gemm_kernel<1>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             TC_SMEM),
+                                             tc_smem_bytes<1>()),
                         "cudaFuncSetAttribute(tc_gemm_kernel)");
+    if (st == CFS_OK)
+        st = check_cuda(cudaFuncSetAttribute(tc_gemm_kernel<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tc_smem_bytes<2>()),
+                        "cudaFuncSetAttribute(tc_gemm_kernel)");
+    if (const char* e = std::getenv("CFS_TC_STAGES")) g_tc_stages = std::atoi(e) == 1 ? 1 : 2;
     if (st == CFS_OK) st = sw_init();
     if (st == CFS_OK) st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");

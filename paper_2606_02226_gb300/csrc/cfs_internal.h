@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "cfs.h"
@@ -97,6 +98,10 @@ cfs_status launch(const Kernel& k, unsigned grid, const void* args, size_t args_
                   cudaStream_t stream);
 cfs_status check_cuda(cudaError_t e, const char* what);
 int device_sm_count();
+// 2D tensor map (TMA) of a BF16 matrix [rows][cols], row stride ld elements,
+// box_rows x box_cols boxes, no swizzle, zeros outside (cfs_runtime.cpp)
+cfs_status make_tmap_2d_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
+                             uint64_t ld, uint32_t box_cols, uint32_t box_rows);
 
 // Expands poem `poem` of a scribble program into a chain body; splat(N)
 // calls become CFS_SCRIBBLE_SPLAT_i() with their slots in splat_slots.

@@ -56,6 +56,11 @@ typedef CUresult (*PFN_LaunchKernel)(CUfunction, unsigned, unsigned, unsigned, u
 typedef CUresult (*PFN_Occupancy)(int*, CUfunction, int, size_t);
 typedef CUresult (*PFN_GetErrorString)(CUresult, const char**);
 typedef CUresult (*PFN_FuncSetAttribute)(CUfunction, CUfunction_attribute, int);
+typedef CUresult (*PFN_TensorMapEncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                             const cuuint64_t*, const cuuint64_t*,
+                                             const cuuint32_t*, const cuuint32_t*,
+                                             CUtensorMapInterleave, CUtensorMapSwizzle,
+                                             CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 struct Driver {
     PFN_ModuleLoadData module_load = nullptr;
@@ -64,6 +69,7 @@ struct Driver {
     PFN_Occupancy occupancy = nullptr;
     PFN_GetErrorString error_string = nullptr;
     PFN_FuncSetAttribute set_attribute = nullptr;
+    PFN_TensorMapEncodeTiled encode_tiled = nullptr;
     bool ok = false;
     std::string why;
 };
@@ -83,7 +89,8 @@ Driver& driver()
                   get("cuLaunchKernel", (void**)&d.launch) &&
                   get("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void**)&d.occupancy) &&
                   get("cuGetErrorString", (void**)&d.error_string) &&
-                  get("cuFuncSetAttribute", (void**)&d.set_attribute);
+                  get("cuFuncSetAttribute", (void**)&d.set_attribute) &&
+                  get("cuTensorMapEncodeTiled", (void**)&d.encode_tiled);
         d.ok = ok;
         if (!ok) d.why = "CUDA driver entry points unavailable (no GPU driver?)";
     });
@@ -144,6 +151,27 @@ cfs_status compile(const std::string& src, std::vector<char>* cubin, std::string
     return CFS_OK;
 }
 }  // namespace
+
+// 2D tensor map of a BF16 matrix [rows][cols] (row stride ld elements), boxes
+// of box_rows x box_cols elements, no swizzle, zero fill outside the matrix
+cfs_status make_tmap_2d_bf16(CUtensorMap* map, const void* base, uint64_t cols, uint64_t rows,
+                             uint64_t ld, uint32_t box_cols, uint32_t box_rows)
+{
+    Driver& d = driver();
+    if (!d.ok) return fail(CFS_ERR_CUDA, d.why);
+    if (((uintptr_t)base & 15u) || ((ld * 2) & 15u) || ((box_cols * 2) & 15u))
+        return fail(CFS_ERR_INVALID_ARG, "tensor map: base, row stride and box width must be "
+                                         "multiples of 16 bytes");
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {box_cols, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return check_cu(d.encode_tiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE),
+                    "cuTensorMapEncodeTiled");
+}
 
 int spill_bytes(const std::string& log)
 {

@@ -262,8 +262,31 @@ __device__ __forceinline__ void tc_load_z(const TcArgs& g, int row, int c0, floa
     }
 }
 
+// sums of 16 values over the warp's 32 lanes by halving exchanges (16
+// shuffles instead of 80): on return lanes 2c and 2c + 1 hold the sum of
+// value c
+__device__ __forceinline__ float warp_colsum16(float (&h)[16])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+        // this lane keeps values [0, w) or [w, 2w) of the current 2w and
+        // adds the partner's copy of the same ones; the bit that decides is
+        // lane bit log2(w) + 1 (16, 8, 4, 2 for w = 8, 4, 2, 1)
+        const bool upper = (lane & (2 * w)) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = upper ? h[k] : h[k + w];
+            const float keep = upper ? h[k + w] : h[k];
+            h[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * w);
+        }
+    }
+    return h[0] + __shfl_xor_sync(0xffffffffu, h[0], 1);
+}
+
 __device__ __forceinline__ void tc_epilogue(const TcArgs& g, int row, int c0, const float (&v)[16],
-                                            const float (&zi)[16], float* s_col)
+                                            const float (&zi)[16], float* s_col,
+                                            const float* bias)
 {
     const bool in = row < g.M;
     if (g.mode == EPI_ATOMIC) {
@@ -281,7 +304,7 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs& g, int row, int c0, co
         float z[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            z[j] = v[j] + g.bias[c0 + j];
+            z[j] = v[j] + bias[c0 + j];
             h[j] = silu_f(z[j]);
         }
         if (in) {
@@ -293,13 +316,12 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs& g, int row, int c0, co
 #pragma unroll
         for (int j = 0; j < 16; ++j) h[j] = in ? v[j] * silu_grad_f(zi[j]) : 0.0f;
         // bias gradient: column sums over the warp's 32 rows, one atomic per column
+        float hs[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            float s = h[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if ((threadIdx.x & 31) == 0 && s != 0.0f) atomicAdd(s_col + c0 + j, s);
-        }
+        for (int j = 0; j < 16; ++j) hs[j] = h[j];
+        const float s = warp_colsum16(hs);
+        const int lane = threadIdx.x & 31;
+        if (!(lane & 1) && s != 0.0f) atomicAdd(s_col + c0 + (lane >> 1), s);
     }
     if (in && g.H) {
         uint4* hp = reinterpret_cast<uint4*>(g.H + (size_t)row * g.ldh + c0);
@@ -404,7 +426,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
             if (c0 + 16 < c_end) tc_load_z(g, row, c0 + 16, z_next);
             float v[16];
             tc_ld16(lane_base + (u32)c0, v);
-            tc_epilogue(g, row, c0, v, z, s_col);
+            tc_epilogue(g, row, c0, v, z, s_col, g.bias);
         }
     } else if (!ok && tid == 0) {
         atomicExch(&g_tc_error, 1u);
@@ -426,6 +448,196 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
                      :
                      : "r"(tmem), "r"(ncols)
                      : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The row GEMMs of training and inference, D[rows][128] = A[rows][K] W^T
+// (K = 64 or 128) with the SILU / SILU_GRAD epilogues, as one persistent
+// warp-specialized kernel per GEMM (one CTA per SM, row tiles of 128 strided
+// over the CTAs):
+//   warp 0  -- TMA: the weights once, then each tile's A into a ring of
+//              TR_STAGES shared-memory slots (2D tensor maps, boxes of 128
+//              rows x 8 K elements, i.e. one 16-byte column of core
+//              matrices: K-adjacent cores 2048 B apart, 8-row groups 128 B);
+//   warp 1  -- TMEM owner; one thread issues the tile's tcgen05.mma into one
+//              of two 128-column accumulators and commits it to the slot's
+//              "empty" barrier and the accumulator's "full" barrier;
+//   warps 2..17 -- the epilogue of tile i (warp w reads TMEM lanes
+//              32 (w % 4) .. + 31 and a quarter of the columns) while tile
+//              i + 1 is loaded and multiplied; each warp then arrives on the
+//              accumulator's "empty" barrier.
+// Every wait is bounded; a time-out sets g_tc_error and the role stops.
+// ---------------------------------------------------------------------------
+constexpr int TR_EPI_WARPS = 16;
+constexpr int TR_THREADS = 32 * (2 + TR_EPI_WARPS);
+constexpr int TR_STAGES = 3;
+constexpr int TR_TILE = 128 * 128 * 2;   // one A tile or the weights at K = 128
+constexpr int TR_SMEM = 1024 + TR_TILE + TR_STAGES * TR_TILE + 256 + 4 * 128;
+
+__device__ __forceinline__ u64 tc_desc_kn(u32 saddr, u32 lbo, u32 sbo)
+{
+    return (u64)((saddr >> 4) & 0x3FFFu) | ((u64)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((u64)((sbo >> 4) & 0x3FFFu) << 32) | ((u64)1 << 46);
+}
+
+__device__ __forceinline__ void mbar_expect_tx(u32 bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(u32 bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// one box of a 2D tensor map at element coordinates (x = K, y = row)
+__device__ __forceinline__ void tma_load_2d(u32 dst, const CUtensorMap* map, int x, int y, u32 bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<u64>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ TcArgs g)
+{
+    extern __shared__ unsigned char tr_smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tr_smem_raw) + 1023) & ~(uintptr_t)1023);
+    const u32 sB = smem_addr(sm), sA = sB + TR_TILE;
+    u64* bars = reinterpret_cast<u64*>(sm + TR_TILE + TR_STAGES * TR_TILE);
+    // barriers: full[s], empty[s] (s < TR_STAGES), wfull, tfull[2], tempty[2]
+    auto full = [&](int s) { return smem_addr(&bars[s]); };
+    auto empty = [&](int s) { return smem_addr(&bars[TR_STAGES + s]); };
+    const u32 wfull = smem_addr(&bars[2 * TR_STAGES]);
+    auto tfull = [&](int b) { return smem_addr(&bars[2 * TR_STAGES + 1 + b]); };
+    auto tempty = [&](int b) { return smem_addr(&bars[2 * TR_STAGES + 3 + b]); };
+    u32* s_tmem = reinterpret_cast<u32*>(bars + 16);
+    __shared__ int s_err;
+    float* s_col = reinterpret_cast<float*>(bars + 32);   // [128]
+    __shared__ float s_bias[128];                        // SILU: the layer's bias
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_tiles = (g.M + TC_M - 1) / TC_M;
+    const int kch = g.K / 8;                  // 16-byte K columns of a tile
+    const u32 tile_bytes = (u32)(TC_M * g.K * 2);
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+                     :
+                     : "r"(smem_addr(s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x < 128) {
+        s_col[threadIdx.x] = 0.0f;
+        s_bias[threadIdx.x] = g.mode == EPI_SILU ? g.bias[threadIdx.x] : 0.0f;
+    }
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < TR_STAGES; ++s) {
+            mbar_init(full(s), 1u);
+            mbar_init(empty(s), 1u);
+        }
+        mbar_init(wfull, 1u);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull(b), 1u);
+            mbar_init(tempty(b), (u32)TR_EPI_WARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const u32 tmem = *s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(wfull, tile_bytes);
+            for (int kc = 0; kc < kch; ++kc) tma_load_2d(sB + kc * 2048, &tmB, kc * 8, 0, wfull);
+            int i = 0, issued = 0;
+            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+                const int s = i % TR_STAGES;
+                if (i >= TR_STAGES && !mbar_wait(empty(s), (u32)(i / TR_STAGES - 1) & 1u)) {
+                    atomicExch(&s_err, 1);
+                    break;
+                }
+                mbar_expect_tx(full(s), tile_bytes);
+                for (int kc = 0; kc < kch; ++kc)
+                    tma_load_2d(sA + s * TR_TILE + kc * 2048, &tmA, kc * 8, tile * TC_M, full(s));
+                issued = i + 1;
+            }
+            // every load issued has landed before the CTA may leave
+            for (int j = (issued > TR_STAGES ? issued - TR_STAGES : 0); j < issued; ++j)
+                mbar_wait(full(j % TR_STAGES), (u32)(j / TR_STAGES) & 1u);
+            mbar_wait(wfull, 0u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const u32 idesc = tc_idesc(128);
+            bool ok = mbar_wait(wfull, 0u);
+            int i = 0, committed = 0;
+            for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++i) {
+                const int s = i % TR_STAGES, b = i & 1;
+                if (!mbar_wait(full(s), (u32)(i / TR_STAGES) & 1u)) { ok = false; break; }
+                if (i >= 2 && !mbar_wait(tempty(b), (u32)(i / 2 - 1) & 1u)) { ok = false; break; }
+                tc_fence_after();
+                for (int kk = 0; kk < g.K / 16; ++kk)
+                    tc_mma(tmem + (u32)(b * 128),
+                           tc_desc_kn(sA + s * TR_TILE + kk * 4096, 2048u, 128u),
+                           tc_desc_kn(sB + kk * 4096, 2048u, 128u), idesc, kk > 0 ? 1u : 0u);
+                tc_commit(empty(s));
+                tc_commit(tfull(b));
+                committed = i + 1;
+            }
+            if (!ok) atomicExch(&s_err, 1);
+            // the last accumulator's MMAs complete before TMEM is freed
+            if (committed > 0) {
+                const int j = committed - 1;
+                mbar_wait(tfull(j & 1), (u32)(j / 2) & 1u);
+            }
+        }
+    } else {
+        const int ew = warp - 2, quad = warp & 3;
+        const int c_begin = (ew >> 2) * 32, c_end = c_begin + 32;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            const int row = tile * TC_M + quad * 32 + lane;
+            float z_next[16];
+            tc_load_z(g, row, c_begin, z_next);   // overlaps the wait
+            if (!mbar_wait(tfull(b), (u32)(i / 2) & 1u)) {
+                atomicExch(&s_err, 1);
+                break;
+            }
+            tc_fence_after();
+            const u32 base = tmem + ((u32)(quad * 32) << 16) + (u32)(b * 128);
+            for (int c0 = c_begin; c0 < c_end; c0 += 16) {
+                float z[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) z[j] = z_next[j];
+                if (c0 + 16 < c_end) tc_load_z(g, row, c0 + 16, z_next);
+                float v[16];
+                tc_ld16(base + (u32)c0, v);
+                tc_epilogue(g, row, c0, v, z, s_col, s_bias);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(b));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (g.mode == EPI_SILU_GRAD && !s_err && threadIdx.x < 128 && s_col[threadIdx.x] != 0.0f)
+        atomicAdd(g.colsum + (blockIdx.x % TC_COPIES) * 128 + threadIdx.x, s_col[threadIdx.x]);
+    if (threadIdx.x == 0 && s_err) atomicExch(&g_tc_error, 1u);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -1363,18 +1575,57 @@ cfs_status tc_gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda
     return CFS_OK;
 }
 
+// row GEMM D[M][128] = A[M][K] W^T (K = 64 or 128) with the SILU or
+// SILU_GRAD epilogue on the persistent TMA kernel; CFS_TC_ROWS=0 runs it on
+// tc_gemm_kernel instead (the same epilogue; for comparison)
+int g_tc_rows = -1;
+
+cfs_status tc_rows(cudaStream_t st, int M, int K, const bf16r* A, int lda, const bf16r* W, int ldw,
+                   int mode, const float* bias, float* C, int ldc, bf16r* H, int ldh, bf16r* HT,
+                   int ldt, const float* Zin, int ldz, float* colsum)
+{
+    if (g_tc_rows < 0) {
+        const char* e = std::getenv("CFS_TC_ROWS");
+        g_tc_rows = (e && std::atoi(e) == 0) ? 0 : 1;
+    }
+    if (!g_tc_rows || M < 1)
+        return tc_gemm(st, M, HID, K, A, lda, W, ldw, mode, bias, C, ldc, H, ldh, HT, ldt, Zin,
+                       ldz, colsum);
+    const bool aligned =
+        (K == 64 || K == 128) && lda % 8 == 0 && ldw % 8 == 0 &&
+        (!C || ((uintptr_t)C % 16 == 0 && ldc % 4 == 0)) &&
+        (!H || ((uintptr_t)H % 16 == 0 && ldh % 8 == 0)) &&
+        (!Zin || ((uintptr_t)Zin % 16 == 0 && ldz % 4 == 0));
+    if (!aligned) return fail(CFS_ERR_INVALID_ARG, "row GEMM operands not aligned");
+    CUtensorMap ta, tb;
+    cfs_status r = make_tmap_2d_bf16(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, 8u, 128u);
+    if (r == CFS_OK) r = make_tmap_2d_bf16(&tb, W, (uint64_t)K, 128u, (uint64_t)ldw, 8u, 128u);
+    if (r != CFS_OK) return r;
+    TcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = M; g.N = HID; g.K = K;
+    g.A = A; g.lda = lda; g.B = W; g.ldb = ldw;
+    g.k_split = K;
+    g.mode = mode; g.bias = bias; g.C = C; g.ldc = ldc; g.H = H; g.ldh = ldh;
+    g.HT = HT; g.ldt = ldt; g.Zin = Zin; g.ldz = ldz; g.colsum = colsum;
+    const int tiles = (M + TC_M - 1) / TC_M;
+    const int sms = std::max(1, device_sm_count());
+    tc_rows_kernel<<<std::min(tiles, sms), TR_THREADS, TR_SMEM, st>>>(ta, tb, g);
+    return CFS_OK;
+}
+
 // forward of B rows of U: Z1..Z3 (fp32), H1..H3 (bf16), H1^T, H2^T, Y (fp32 [B][2])
 cfs_status forward(cfs_sampler* s, const bf16r* U, int B, cudaStream_t st)
 {
     const bf16r* wb = s->wb;
-    cfs_status r = tc_gemm(st, B, HID, D_IN, U, D_IN, wb + OFF_W1, D_IN, EPI_SILU, s->w + OFF_B1,
+    cfs_status r = tc_rows(st, B, D_IN, U, D_IN, wb + OFF_W1, D_IN, EPI_SILU, s->w + OFF_B1,
                            s->Z1, HID, s->H1, HID, s->H1T, s->ldt, nullptr, 0, nullptr);
     if (r == CFS_OK)
-        r = tc_gemm(st, B, HID, HID, s->H1, HID, wb + OFF_W2, HID, EPI_SILU, s->w + OFF_B2,
-                    s->Z2, HID, s->H2, HID, s->H2T, s->ldt, nullptr, 0, nullptr);
+        r = tc_rows(st, B, HID, s->H1, HID, wb + OFF_W2, HID, EPI_SILU, s->w + OFF_B2, s->Z2, HID,
+                    s->H2, HID, s->H2T, s->ldt, nullptr, 0, nullptr);
     if (r == CFS_OK)
-        r = tc_gemm(st, B, HID, HID, s->H2, HID, wb + OFF_W3, HID, EPI_SILU, s->w + OFF_B3,
-                    s->Z3, HID, s->H3, HID, nullptr, 0, nullptr, 0, nullptr);
+        r = tc_rows(st, B, HID, s->H2, HID, wb + OFF_W3, HID, EPI_SILU, s->w + OFF_B3, s->Z3, HID,
+                    s->H3, HID, nullptr, 0, nullptr, 0, nullptr);
     if (r != CFS_OK) return r;
     out_forward_kernel<<<(B + 255) / 256, 256, 0, st>>>(s->H3, wb, s->w, B, s->Y);
     return CFS_OK;
@@ -1391,12 +1642,12 @@ cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, floa
     out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, HID, 0, st>>>(
         dY, wb, s->H3, s->Z3, B, s->dZ3, s->dZ3T, s->ldt, s->bias_part + 2 * TC_COPIES * HID);
     // dZ2 = (dZ3 W3) * silu'(Z2): the K-major B operand is W3^T
-    cfs_status r = tc_gemm(st, B, HID, HID, s->dZ3, HID, s->wbT + HID * HID, HID, EPI_SILU_GRAD,
+    cfs_status r = tc_rows(st, B, HID, s->dZ3, HID, s->wbT + HID * HID, HID, EPI_SILU_GRAD,
                            nullptr, nullptr, 0, s->dZ2, HID, s->dZ2T, s->ldt, s->Z2, HID,
                            s->bias_part);
     if (r == CFS_OK)
-        r = tc_gemm(st, B, HID, HID, s->dZ2, HID, s->wbT, HID, EPI_SILU_GRAD, nullptr, nullptr,
-                    0, nullptr, 0, s->dZ1T, s->ldt, s->Z1, HID, s->bias_part + TC_COPIES * HID);
+        r = tc_rows(st, B, HID, s->dZ2, HID, s->wbT, HID, EPI_SILU_GRAD, nullptr, nullptr, 0,
+                    nullptr, 0, s->dZ1T, s->ldt, s->Z1, HID, s->bias_part + TC_COPIES * HID);
     if (r != CFS_OK) return r;
     part_reduce_kernel<<<1, 512, 0, st>>>(s->bias_part, grads);
     transpose_in_kernel<<<(B + 31) / 32, 256, 0, st>>>(U, B, s->UT, s->ldt);
@@ -1508,6 +1759,10 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
                                              tc_smem_bytes<2>()),
                         "cudaFuncSetAttribute(tc_gemm_kernel)");
     if (const char* e = std::getenv("CFS_TC_STAGES")) g_tc_stages = std::atoi(e) == 1 ? 1 : 2;
+    if (st == CFS_OK)
+        st = check_cuda(cudaFuncSetAttribute(tc_rows_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM),
+                        "cudaFuncSetAttribute(tc_rows_kernel)");
     if (st == CFS_OK) st = sw_init();
     if (st == CFS_OK) st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");

@@ -715,57 +715,89 @@ __global__ void __launch_bounds__(256) transpose_in_kernel(const bf16r* __restri
     }
 }
 
-// ---------------------------------------------------------------------------
-// output layer backward: dH3 = dY W4, dZ3 = dH3 * silu'(Z3) (bf16 out),
-// db3 += sum dZ3, dW4 += dY^T H3, db4 += sum dY.  One thread per hidden
-// unit, 64 rows per block.
-// ---------------------------------------------------------------------------
-constexpr int OB_ROWS = 32;
+// output layer backward: dH3 = dY W4 (N = 2, not a tensor-core shape), dZ3 =
+// dH3 * silu'(Z3) written as dZ3 and its transpose dZ3^T; dW4 = dY^T H3,
+// db3 = sum dZ3, db4 = sum dY.  A block takes OB_ROWS rows, a warp one row
+// at a time, lane l the four units 4l .. 4l+3 (16-byte loads of Z3, 8-byte
+// loads of H3); the block's dZ3 tile is transposed in shared memory, and its
+// sums combine across warps there before one atomic per value into copy
+// blockIdx.x % TC_COPIES of `part`.
+constexpr int OB_ROWS = 64;
+constexpr int OB_THREADS = 256;
 
-__global__ void __launch_bounds__(HID) out_backward_kernel(const float* __restrict__ dY,
-                                                           const bf16r* __restrict__ wb,
-                                                           const bf16r* __restrict__ H3,
-                                                           const float* __restrict__ Z3, int B,
-                                                           bf16r* dZ3, bf16r* dZ3T, int ldt,
-                                                           float* part)
+__global__ void __launch_bounds__(OB_THREADS) out_backward_kernel(const float* __restrict__ dY,
+                                                                  const bf16r* __restrict__ wb,
+                                                                  const bf16r* __restrict__ H3,
+                                                                  const float* __restrict__ Z3,
+                                                                  int B, bf16r* dZ3, bf16r* dZ3T,
+                                                                  int ldt, float* part)
 {
-    __shared__ bf16r tT[HID][OB_ROWS + 2];   // the block's dZ3 tile, transposed
-    const int n = threadIdx.x;
-    const float w0 = from_bf16(wb[OFF_W4 + n]), w1 = from_bf16(wb[OFF_W4 + HID + n]);
-    float db3 = 0.0f, dw0 = 0.0f, dw1 = 0.0f, db40 = 0.0f, db41 = 0.0f;
+    __shared__ bf16r tT[HID][OB_ROWS + 1];   // the block's dZ3 tile, transposed
+    __shared__ float s_sum[3 * HID + 2];     // W4 rows 0 and 1, b3, b4
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = 4 * lane;
+    float w0[4], w1[4], a0[4], a1[4], ab[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        w0[j] = from_bf16(wb[OFF_W4 + c + j]);
+        w1[j] = from_bf16(wb[OFF_W4 + HID + c + j]);
+        a0[j] = a1[j] = ab[j] = 0.0f;
+    }
+    float b40 = 0.0f, b41 = 0.0f;
+    for (int e = threadIdx.x; e < 3 * HID + 2; e += OB_THREADS) s_sum[e] = 0.0f;
     const int r0 = blockIdx.x * OB_ROWS;
-    const int r1 = min(B, r0 + OB_ROWS);
-#pragma unroll 4
-    for (int r = r0; r < r1; ++r) {
+#pragma unroll 2
+    for (int k = warp; k < OB_ROWS; k += OB_THREADS / 32) {
+        const int r = r0 + k;
+        if (r >= B) break;
         const float y0 = dY[2 * r], y1 = dY[2 * r + 1];
-        const float dh = fmaf(y0, w0, y1 * w1);
-        const float d = dh * silu_grad_f(Z3[(size_t)r * HID + n]);
-        const bf16r db = to_bf16(d);
-        dZ3[(size_t)r * HID + n] = db;
-        tT[n][r - r0] = db;
-        db3 += d;
-        const float h = from_bf16(H3[(size_t)r * HID + n]);
-        dw0 = fmaf(y0, h, dw0);
-        dw1 = fmaf(y1, h, dw1);
-        db40 += y0;
-        db41 += y1;
+        const float4 z = *reinterpret_cast<const float4*>(Z3 + (size_t)r * HID + c);
+        const uint2 hv = *reinterpret_cast<const uint2*>(H3 + (size_t)r * HID + c);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+        const float h[4] = {__uint_as_float(hv.x << 16), __uint_as_float(hv.x & 0xFFFF0000u),
+                            __uint_as_float(hv.y << 16), __uint_as_float(hv.y & 0xFFFF0000u)};
+        bf16r db[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float dh = fmaf(y0, w0[j], y1 * w1[j]);
+            const float d = dh * silu_grad_f(zz[j]);
+            db[j] = to_bf16(d);
+            tT[c + j][k] = db[j];
+            ab[j] += d;
+            a0[j] = fmaf(y0, h[j], a0[j]);
+            a1[j] = fmaf(y1, h[j], a1[j]);
+        }
+        *reinterpret_cast<uint2*>(dZ3 + (size_t)r * HID + c) =
+            make_uint2((u32)db[0] | ((u32)db[1] << 16), (u32)db[2] | ((u32)db[3] << 16));
+        b40 += y0;
+        b41 += y1;
     }
-    __syncthreads();
-    // dZ3^T rows: consecutive threads write consecutive rows of a unit
-    for (int e = threadIdx.x; e < HID * OB_ROWS; e += blockDim.x) {
-        const int u = e / OB_ROWS, j = e % OB_ROWS;
-        if (r0 + j < r1) dZ3T[(size_t)u * ldt + r0 + j] = tT[u][j];
+    __syncthreads();   // tT complete, s_sum zeroed
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        atomicAdd(&s_sum[c + j], a0[j]);
+        atomicAdd(&s_sum[HID + c + j], a1[j]);
+        atomicAdd(&s_sum[2 * HID + c + j], ab[j]);
     }
-    // this block's sums into copy blockIdx.x % TC_COPIES (part_reduce_kernel
-    // adds the copies to the gradients)
-    float* c = part + (size_t)(blockIdx.x % TC_COPIES) * OB_PART;
-    atomicAdd(c + n, dw0);
-    atomicAdd(c + HID + n, dw1);
-    atomicAdd(c + 2 * HID + n, db3);
-    if (n == 0) {
-        atomicAdd(c + 3 * HID, db40);
-        atomicAdd(c + 3 * HID + 1, db41);
+    if (lane == 0) {
+        atomicAdd(&s_sum[3 * HID], b40);
+        atomicAdd(&s_sum[3 * HID + 1], b41);
     }
+    // dZ3^T rows: a warp writes 64 consecutive rows of one unit as 32 words
+    for (int e = threadIdx.x; e < HID * (OB_ROWS / 2); e += OB_THREADS) {
+        const int u = e / (OB_ROWS / 2), jp = 2 * (e % (OB_ROWS / 2));
+        const int r = r0 + jp;
+        if (r + 1 < B) {
+            *reinterpret_cast<u32*>(dZ3T + (size_t)u * ldt + r) =
+                (u32)tT[u][jp] | ((u32)tT[u][jp + 1] << 16);
+        } else if (r < B) {
+            dZ3T[(size_t)u * ldt + r] = tT[u][jp];
+        }
+    }
+    __syncthreads();   // s_sum complete
+    float* cp = part + (size_t)(blockIdx.x % TC_COPIES) * OB_PART;
+    for (int e = threadIdx.x; e < 3 * HID + 2; e += OB_THREADS)
+        if (s_sum[e] != 0.0f) atomicAdd(cp + e, s_sum[e]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1639,7 +1671,7 @@ cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, floa
     // gradient sums of the output layer and of the biases gather in copies
     // (bias_part) first: fewer atomics on the same address
     cudaMemsetAsync(s->bias_part, 0, sizeof(float) * PART_FLOATS, st);
-    out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, HID, 0, st>>>(
+    out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, OB_THREADS, 0, st>>>(
         dY, wb, s->H3, s->Z3, B, s->dZ3, s->dZ3T, s->ldt, s->bias_part + 2 * TC_COPIES * HID);
     // dZ2 = (dZ3 W3) * silu'(Z2): the K-major B operand is W3^T
     cfs_status r = tc_rows(st, B, HID, s->dZ3, HID, s->wbT + HID * HID, HID, EPI_SILU_GRAD,

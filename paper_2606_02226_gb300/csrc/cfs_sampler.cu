@@ -821,7 +821,8 @@ __global__ void __launch_bounds__(OB_THREADS) out_backward_kernel(const float* _
 //
 // After the sort, thread t holds ranks 8t .. 8t+7.  A point's rank is then
 // found by binary search of its own key (recomputed bit for bit) among the
-// sorted predicted keys, so the network carries no indices.  Gradients of the
+// sorted predicted keys, stored in the search's breadth-first order, so the
+// network carries no indices.  Gradients of the
 // group's projections are summed per point in shared memory (each point
 // belongs to one thread of the group), then over the groups, then added to
 // dX with one atomic per coordinate and CTA.  Keys must be finite.
@@ -993,8 +994,14 @@ __global__ void __launch_bounds__(SW_THREADS, 3) sw_kernel(const float* __restri
         // projection's search makes that safe), so every choice is static
         int par = 0;
         sw_merges<N, 1>(x, y, tt, gg, bufs + (size_t)gg * 2 * N, par);
-        // ranks 8t .. 8t+7: squared differences; the sorted keys and each
-        // rank's gradient go to the buffer the last move did not read
+        // ranks 8t .. 8t+7: squared differences; each rank's gradient
+        // (linear order) and the sorted keys go to the buffer the last move
+        // did not read.  The keys are stored as the binary search visits
+        // them (breadth-first, Eytzinger order: the pivot of rank r = (2m +
+        // 1) h - 1 at node N / 2h + m, node 1 the root), so the first six
+        // levels of every search read at most 32 consecutive words: no bank
+        // conflicts there, where the sorted order put every pivot of a level
+        // in one bank
         float* sk = reinterpret_cast<float*>(bufs + ((size_t)gg * 2 + par) * N);
         float* sgr = sk + N;
         float d[SW_E];
@@ -1003,9 +1010,12 @@ __global__ void __launch_bounds__(SW_THREADS, 3) sw_kernel(const float* __restri
             d[e] = x[e] - y[e];
             lacc = fmaf(d[e], d[e], lacc);
             d[e] = 2.0f * d[e] / (float)N;
+            const int q = tt * SW_E + e + 1;            // rank + 1
+            if (q < N) {
+                const int tz = __ffs(q) - 1;             // h = 2^tz
+                sk[((N / 2) >> tz) + ((q >> tz) >> 1)] = x[e];
+            }
         }
-        reinterpret_cast<float4*>(sk)[2 * tt] = make_float4(x[0], x[1], x[2], x[3]);
-        reinterpret_cast<float4*>(sk)[2 * tt + 1] = make_float4(x[4], x[5], x[6], x[7]);
         reinterpret_cast<float4*>(sgr)[2 * tt] = make_float4(d[0], d[1], d[2], d[3]);
         reinterpret_cast<float4*>(sgr)[2 * tt + 1] = make_float4(d[4], d[5], d[6], d[7]);
         sw_group_sync<G>(gg);
@@ -1014,10 +1024,10 @@ __global__ void __launch_bounds__(SW_THREADS, 3) sw_kernel(const float* __restri
             const int i = tt * SW_E + e;
             const float4 q = pts[e * G + tt];
             const float kx = sw_key(q.x, q.y, c, sn);
-            int r = 0;
+            int k = 1;
 #pragma unroll
-            for (int h = N / 2; h >= 1; h >>= 1) r += sk[r + h - 1] < kx ? h : 0;
-            const float gv = sgr[r];
+            for (int h = N / 2; h >= 1; h >>= 1) k = 2 * k + (sk[k] < kx ? 1 : 0);
+            const float gv = sgr[k - N];
             float2 a = gacc[(size_t)gg * N + sw_swz(i)];
             a.x = fmaf(gv, c, a.x);
             a.y = fmaf(gv, sn, a.y);

@@ -641,6 +641,129 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradients dW[M = 128][N] += A[128][K] B[N][K]^T (A = dZ^T, B = H^T or
+// U^T, both K-major over the rows, N = 128 or 64) split over K: CTA b takes
+// a run of 64-row K chunks.  Warp 0 loads each chunk's A and B with TMA into
+// a ring of SK_STAGES slots, one thread of warp 1 accumulates the chunks into
+// one TMEM accumulator, and warps 2..5 add it to dW with vector reductions at
+// the end.  Every wait is bounded, as in tc_rows_kernel.
+// ---------------------------------------------------------------------------
+constexpr int SK_STAGES = 4;
+constexpr int SK_THREADS = 32 * 6;
+constexpr int SK_SLOT = 2 * 128 * TC_K * 2;   // A and B chunk (64 K) of 128 rows each
+constexpr int SK_SMEM = 1024 + SK_STAGES * SK_SLOT + 256;
+
+__global__ void __launch_bounds__(SK_THREADS, 1) tc_splitk_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ TcArgs g)
+{
+    extern __shared__ unsigned char sk_smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(sk_smem_raw) + 1023) & ~(uintptr_t)1023);
+    const u32 s0 = smem_addr(sm);
+    u64* bars = reinterpret_cast<u64*>(sm + SK_STAGES * SK_SLOT);
+    auto full = [&](int s) { return smem_addr(&bars[s]); };
+    auto empty = [&](int s) { return smem_addr(&bars[SK_STAGES + s]); };
+    const u32 tdone = smem_addr(&bars[2 * SK_STAGES]);
+    u32* s_tmem = reinterpret_cast<u32*>(bars + 16);
+    __shared__ int s_err;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_chunks = (g.K + TC_K - 1) / TC_K;
+    const int per = (n_chunks + gridDim.x - 1) / gridDim.x;
+    const int c_first = blockIdx.x * per, c_last = min(n_chunks, c_first + per);
+    const u32 chunk_bytes = (u32)((128 + g.N) * TC_K * 2);
+    const u32 ncols = g.N <= 64 ? 64u : 128u;
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"(smem_addr(s_tmem)), "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < SK_STAGES; ++s) {
+            mbar_init(full(s), 1u);
+            mbar_init(empty(s), 1u);
+        }
+        mbar_init(tdone, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const u32 tmem = *s_tmem;
+    // slot s: A at s0 + s SLOT ([8 K columns][128 rows][16 B]), B after 16 KB
+    if (warp == 0) {
+        if (lane == 0) {
+            int i = 0, issued = 0;
+            for (int c = c_first; c < c_last; ++c, ++i) {
+                const int s = i % SK_STAGES;
+                if (i >= SK_STAGES && !mbar_wait(empty(s), (u32)(i / SK_STAGES - 1) & 1u)) {
+                    atomicExch(&s_err, 1);
+                    break;
+                }
+                mbar_expect_tx(full(s), chunk_bytes);
+                const u32 a = s0 + (u32)(s * SK_SLOT), b = a + 128 * TC_K * 2;
+                for (int kc = 0; kc < TC_K / 8; ++kc) {
+                    tma_load_2d(a + kc * 2048, &tmA, c * TC_K + kc * 8, 0, full(s));
+                    tma_load_2d(b + kc * (u32)(g.N * 16), &tmB, c * TC_K + kc * 8, 0, full(s));
+                }
+                issued = i + 1;
+            }
+            for (int j = (issued > SK_STAGES ? issued - SK_STAGES : 0); j < issued; ++j)
+                mbar_wait(full(j % SK_STAGES), (u32)(j / SK_STAGES) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const u32 idesc = tc_idesc(g.N);
+            bool ok = true;
+            int i = 0;
+            for (int c = c_first; c < c_last; ++c, ++i) {
+                const int s = i % SK_STAGES;
+                if (!mbar_wait(full(s), (u32)(i / SK_STAGES) & 1u)) { ok = false; break; }
+                tc_fence_after();
+                const u32 a = s0 + (u32)(s * SK_SLOT), b = a + 128 * TC_K * 2;
+#pragma unroll
+                for (int kk = 0; kk < TC_K / 16; ++kk)
+                    tc_mma(tmem, tc_desc_kn(a + kk * 4096, 2048u, 128u),
+                           tc_desc_kn(b + kk * (u32)(g.N * 32), (u32)(g.N * 16), 128u), idesc,
+                           (i > 0 || kk > 0) ? 1u : 0u);
+                tc_commit(empty(s));
+            }
+            if (!ok) atomicExch(&s_err, 1);
+            tc_commit(tdone);   // every MMA issued above (none: arrives at once)
+        }
+    } else {
+        const int quad = warp & 3;
+        const bool any = c_last > c_first;
+        if (!mbar_wait(tdone, 0u)) {
+            atomicExch(&s_err, 1);
+        } else if (any && !s_err) {
+            tc_fence_after();
+            const int row = quad * 32 + lane;
+            const u32 base = tmem + ((u32)(quad * 32) << 16);
+            const float zi[16] = {};
+            for (int c0 = 0; c0 < g.N; c0 += 16) {
+                float v[16];
+                tc_ld16(base + (u32)c0, v);
+                tc_epilogue(g, row, c0, v, zi, nullptr, nullptr);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_err) atomicExch(&g_tc_error, 1u);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ncols)
+                     : "memory");
+    }
+}
+
 // output layer forward Y = H3 W4^T + b4 (N = 2: a dot product per output,
 // not a tensor-core shape): one thread per row
 __global__ void __launch_bounds__(256) out_forward_kernel(const bf16r* __restrict__ H3,
@@ -1656,6 +1779,42 @@ cfs_status tc_rows(cudaStream_t st, int M, int K, const bf16r* A, int lda, const
     return CFS_OK;
 }
 
+// weight gradient C[128][N] += A[128][K] B[N][K]^T on the split-K TMA kernel
+// (N = 128 or 64); CFS_TC_SPLITK=0 runs it on tc_gemm_kernel instead
+int g_tc_splitk = -1;
+
+cfs_status tc_splitk(cudaStream_t st, int N, int K, const bf16r* A, int lda, const bf16r* Bm,
+                     int ldb, float* C, int ldc)
+{
+    if (g_tc_splitk < 0) {
+        const char* e = std::getenv("CFS_TC_SPLITK");
+        g_tc_splitk = (e && std::atoi(e) == 0) ? 0 : 1;
+    }
+    if (!g_tc_splitk) {
+        const int splits = std::max(1, std::min(256, K / 256));
+        return tc_gemm(st, HID, N, K, A, lda, Bm, ldb, EPI_ATOMIC, nullptr, C, ldc, nullptr, 0,
+                       nullptr, 0, nullptr, 0, nullptr, splits);
+    }
+    if (K < 1) return CFS_OK;
+    if (!(N == 64 || N == 128) || lda % 8 || ldb % 8 || (uintptr_t)C % 16 || ldc % 4)
+        return fail(CFS_ERR_INVALID_ARG, "weight-gradient GEMM operands not aligned");
+    CUtensorMap ta, tb;
+    cfs_status r = make_tmap_2d_bf16(&ta, A, (uint64_t)K, 128u, (uint64_t)lda, 8u, 128u);
+    if (r == CFS_OK)
+        r = make_tmap_2d_bf16(&tb, Bm, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, 8u, (uint32_t)N);
+    if (r != CFS_OK) return r;
+    TcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = HID; g.N = N; g.K = K;
+    g.A = A; g.lda = lda; g.B = Bm; g.ldb = ldb;
+    g.k_split = K;
+    g.mode = EPI_ATOMIC; g.C = C; g.ldc = ldc;
+    const int chunks = (K + TC_K - 1) / TC_K;
+    const int sms = std::max(1, device_sm_count());
+    tc_splitk_kernel<<<std::min(chunks, sms), SK_THREADS, SK_SMEM, st>>>(ta, tb, g);
+    return CFS_OK;
+}
+
 // forward of B rows of U: Z1..Z3 (fp32), H1..H3 (bf16), H1^T, H2^T, Y (fp32 [B][2])
 cfs_status forward(cfs_sampler* s, const bf16r* U, int B, cudaStream_t st)
 {
@@ -1694,15 +1853,11 @@ cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, floa
     part_reduce_kernel<<<1, 512, 0, st>>>(s->bias_part, grads);
     transpose_in_kernel<<<(B + 31) / 32, 256, 0, st>>>(U, B, s->UT, s->ldt);
     // weight gradients dW = dZ^T A: K = the rows, split over CTAs, atomic
-    const int splits = std::max(1, std::min(256, B / 256));
-    r = tc_gemm(st, HID, HID, B, s->dZ3T, s->ldt, s->H2T, s->ldt, EPI_ATOMIC, nullptr,
-                grads + OFF_W3, HID, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, splits);
+    r = tc_splitk(st, HID, B, s->dZ3T, s->ldt, s->H2T, s->ldt, grads + OFF_W3, HID);
     if (r == CFS_OK)
-        r = tc_gemm(st, HID, HID, B, s->dZ2T, s->ldt, s->H1T, s->ldt, EPI_ATOMIC, nullptr,
-                    grads + OFF_W2, HID, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, splits);
+        r = tc_splitk(st, HID, B, s->dZ2T, s->ldt, s->H1T, s->ldt, grads + OFF_W2, HID);
     if (r == CFS_OK)
-        r = tc_gemm(st, HID, D_IN, B, s->dZ1T, s->ldt, s->UT, s->ldt, EPI_ATOMIC, nullptr,
-                    grads + OFF_W1, D_IN, nullptr, 0, nullptr, 0, nullptr, 0, nullptr, splits);
+        r = tc_splitk(st, D_IN, B, s->dZ1T, s->ldt, s->UT, s->ldt, grads + OFF_W1, D_IN);
     return r;
 }
 
@@ -1805,6 +1960,10 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
         st = check_cuda(cudaFuncSetAttribute(tc_rows_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM),
                         "cudaFuncSetAttribute(tc_rows_kernel)");
+    if (st == CFS_OK)
+        st = check_cuda(cudaFuncSetAttribute(tc_splitk_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SK_SMEM),
+                        "cudaFuncSetAttribute(tc_splitk_kernel)");
     if (st == CFS_OK) st = sw_init();
     if (st == CFS_OK) st = check_cuda(cudaMalloc(&s->d_step, 256), "cudaMalloc(step)");
     if (st == CFS_OK) st = check_cuda(cudaMemset(s->m, 0, sizeof(float) * N_PARAMS * 2), "memset");

@@ -182,6 +182,19 @@ __device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane, without the wait
+// (the caller issues tcgen05.wait::ld before using them)
+__device__ __forceinline__ void tc_ld16_nowait(u32 taddr, u32 (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
 // 16 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tc_ld16(u32 taddr, float (&v)[16])
 {
@@ -465,8 +478,9 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
 //              "empty" barrier and the accumulator's "full" barrier;
 //   warps 2..17 -- the epilogue of tile i (warp w reads TMEM lanes
 //              32 (w % 4) .. + 31 and a quarter of the columns) while tile
-//              i + 1 is loaded and multiplied; each warp then arrives on the
-//              accumulator's "empty" barrier.
+//              i + 1 is loaded and multiplied; each warp arrives on the
+//              accumulator's "empty" barrier as soon as its columns are in
+//              registers.
 // Every wait is bounded; a time-out sets g_tc_error and the role stops.
 // ---------------------------------------------------------------------------
 constexpr int TR_EPI_WARPS = 16;
@@ -616,18 +630,32 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
             }
             tc_fence_after();
             const u32 base = tmem + ((u32)(quad * 32) << 16) + (u32)(b * 128);
-            for (int c0 = c_begin; c0 < c_end; c0 += 16) {
-                float z[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) z[j] = z_next[j];
-                if (c0 + 16 < c_end) tc_load_z(g, row, c0 + 16, z_next);
-                float v[16];
-                tc_ld16(base + (u32)c0, v);
-                tc_epilogue(g, row, c0, v, z, s_col, s_bias);
-            }
+            // both 16-column loads in flight before the one wait
+            u32 r0[16], r1[16];
+            tc_ld16_nowait(base + (u32)c_begin, r0);
+            tc_ld16_nowait(base + (u32)(c_begin + 16), r1);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // the accumulator is read: release it to the MMA thread before the
+            // arithmetic and the stores
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty(b));
+            {
+                float v[16], z[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    v[j] = __uint_as_float(r0[j]);
+                    z[j] = z_next[j];
+                }
+                tc_load_z(g, row, c_begin + 16, z_next);
+                tc_epilogue(g, row, c_begin, v, z, s_col, s_bias);
+            }
+            {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r1[j]);
+                tc_epilogue(g, row, c_begin + 16, v, z_next, s_col, s_bias);
+            }
         }
     }
     tc_fence_before();

@@ -1396,17 +1396,66 @@ __global__ void prep_kernel(const u32* step, u64 seed, int n_sys, int S, u32* se
     if (j < P) phi[j] = ((float)j + u) * (6.28318530717958647692f / (float)P);
 }
 
-// chaos-game points of the batch's systems: row r = s * N + j starts
-// uniform and runs `steps` steps (enough to reach the attractor)
+// network inputs of row r: Gaussian noise (Box-Muller on a Philox block),
+// the conditioning vector of its system and t, written as eight 16-byte
+// vectors
+__device__ __forceinline__ void write_inputs_row(const SysRec& q, int r, u32 st, u64 seed,
+                                                 bf16r* U)
+{
+    const uint4 w = philox_key(seed, (u32)r, st, 0u, TAG_NOISE);
+    const float u1 = ((float)(w.x >> 8) + 0.5f) * CFS_INV_2_24;
+    const float u2 = (float)(w.y >> 8) * CFS_INV_2_24;
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float sn, c;
+    sincosf(6.28318530717958647692f * u2, &sn, &c);
+    u32 w32[D_IN / 2];
+    w32[0] = (u32)to_bf16(rad * c) | ((u32)to_bf16(rad * sn) << 16);
+#pragma unroll
+    for (int j = 0; j < COND / 2; ++j)
+        w32[1 + j] = (u32)to_bf16(q.cond[2 * j]) | ((u32)to_bf16(q.cond[2 * j + 1]) << 16);
+    w32[1 + COND / 2] = (u32)to_bf16(q.t);
+#pragma unroll
+    for (int j = 2 + COND / 2; j < D_IN / 2; ++j) w32[j] = 0u;
+    uint4* row = reinterpret_cast<uint4*>(U + (size_t)r * D_IN);
+#pragma unroll
+    for (int v = 0; v < D_IN / 8; ++v)
+        row[v] = make_uint4(w32[4 * v], w32[4 * v + 1], w32[4 * v + 2], w32[4 * v + 3]);
+}
+
+// the records of the systems that rows r0 .. r0 + blockDim.x - 1 belong to
+// (row r: system sel[r / N]; at most 8 with N >= 32) into shared memory
+__device__ __forceinline__ int stage_systems(const SysRec* __restrict__ sys,
+                                            const u32* __restrict__ sel, int N, int rows,
+                                            SysRec* s_sys)
+{
+    const int r0 = blockIdx.x * blockDim.x;
+    const int first = r0 / N;
+    const int last = min(r0 + (int)blockDim.x - 1, rows - 1) / N;
+    constexpr int W = (int)(sizeof(SysRec) / 4);
+    for (int e = threadIdx.x; e < (last - first + 1) * W; e += blockDim.x) {
+        const int q = e / W, w = e % W;
+        reinterpret_cast<u32*>(&s_sys[q])[w] =
+            reinterpret_cast<const u32*>(&sys[sel ? sel[first + q] : 0])[w];
+    }
+    __syncthreads();
+    return first;
+}
+
+// training rows of one step: row r = s * N + j gets the chaos-game point of
+// its system after `steps` steps from a uniform start (the target) and, when
+// U is given, its network inputs
 __global__ void __launch_bounds__(256) data_kernel(const SysRec* __restrict__ sys,
                                                    const u32* __restrict__ sel, const u32* step,
                                                    u64 seed, int N, int rows, int steps,
-                                                   float* out)
+                                                   float* out, bf16r* U)
 {
+    __shared__ SysRec s_sys[256 / 32];
+    const int first = stage_systems(sys, sel, N, rows, s_sys);
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    const SysRec& q = sys[sel[r / N]];
+    const SysRec& q = s_sys[r / N - first];
     const u32 st = *step;
+    if (U) write_inputs_row(q, r, st, seed, U);
     const uint4 s0 = philox_key(seed, (u32)r, st, 0u, TAG_DATA_INIT);
     float x = (float)(s0.x >> 8) * CFS_INV_2_24, y = (float)(s0.y >> 8) * CFS_INV_2_24;
     for (int n = 0; n < steps; n += 4) {
@@ -1424,39 +1473,6 @@ __global__ void __launch_bounds__(256) data_kernel(const SysRec* __restrict__ sy
     }
     out[2 * r] = x;
     out[2 * r + 1] = y;
-}
-
-// network inputs: row r = s * N + j gets Gaussian noise (Box-Muller on a
-// Philox block), the conditioning vector of its system and t
-__global__ void __launch_bounds__(256) inputs_kernel(const SysRec* __restrict__ sys,
-                                                     const u32* __restrict__ sel,
-                                                     const u32* step, u32 step_explicit,
-                                                     u64 seed, int N, int rows, bf16r* U)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    const SysRec& q = sys[sel ? sel[r / N] : 0];
-    const u32 st = step ? *step : step_explicit;
-    const uint4 w = philox_key(seed, (u32)r, st, 0u, TAG_NOISE);
-    const float u1 = ((float)(w.x >> 8) + 0.5f) * CFS_INV_2_24;
-    const float u2 = (float)(w.y >> 8) * CFS_INV_2_24;
-    const float rad = sqrtf(-2.0f * logf(u1));
-    float sn, c;
-    sincosf(6.28318530717958647692f * u2, &sn, &c);
-    // the row [noise (2), conditioning (48), t, zeros] packed in registers,
-    // written as eight 16-byte vectors
-    u32 w32[D_IN / 2];
-    w32[0] = (u32)to_bf16(rad * c) | ((u32)to_bf16(rad * sn) << 16);
-#pragma unroll
-    for (int j = 0; j < COND / 2; ++j)
-        w32[1 + j] = (u32)to_bf16(q.cond[2 * j]) | ((u32)to_bf16(q.cond[2 * j + 1]) << 16);
-    w32[1 + COND / 2] = (u32)to_bf16(q.t);
-#pragma unroll
-    for (int j = 2 + COND / 2; j < D_IN / 2; ++j) w32[j] = 0u;
-    uint4* row = reinterpret_cast<uint4*>(U + (size_t)r * D_IN);
-#pragma unroll
-    for (int v = 0; v < D_IN / 8; ++v)
-        row[v] = make_uint4(w32[4 * v], w32[4 * v + 1], w32[4 * v + 2], w32[4 * v + 3]);
 }
 
 __global__ void step_inc_kernel(u32* step) { *step += 1u; }
@@ -2184,8 +2200,8 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
         cudaMemsetAsync(d_dY, 0, sizeof(float) * (size_t)B * 2, cap);
         cudaMemsetAsync(d_loss, 0, 4, cap);
         prep_kernel<<<1, 1024, 0, cap>>>(s->d_step, seed, n_systems, S, d_sel, d_phi, (int)n_proj);
-        data_kernel<<<(B + 255) / 256, 256, 0, cap>>>(d_sys, d_sel, s->d_step, seed, N, B, 40, d_T);
-        inputs_kernel<<<(B + 255) / 256, 256, 0, cap>>>(d_sys, d_sel, s->d_step, 0u, seed, N, B, d_U);
+        data_kernel<<<(B + 255) / 256, 256, 0, cap>>>(d_sys, d_sel, s->d_step, seed, N, B, 40, d_T,
+                                                      d_U);
         cfs_status fst = forward(s, d_U, B, cap);
         sw_launch(s->Y, d_T, d_phi, (int)n_proj, N, S, 1.0f / ((float)S * (float)n_proj),
                   d_loss, d_dY, cap);

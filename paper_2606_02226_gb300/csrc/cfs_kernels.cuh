@@ -55,6 +55,44 @@ struct CfsChooseTab {
     }
 };
 
+#if CFS_BATCH
+/* Map choice of a batch frame through a bucket table: the top 12 bits of the
+ * word pick one of 4096 buckets of 2^20 words; a bucket without a threshold
+ * inside gives every word in it the same k (the table holds it), the at most
+ * n_cmp buckets with one fall back to the comparisons.  Same k as
+ * CfsChooseTab for every word. */
+#define CFS_KTAB_BITS 12
+struct CfsChooseKtab {
+    const u32* T;               /* shared memory */
+    const unsigned char* kt;    /* shared memory, 2^CFS_KTAB_BITS entries; 0xFF: compare */
+    int n_cmp;
+    __device__ __forceinline__ int operator()(u32 w) const
+    {
+        const u32 e = kt[w >> (32 - CFS_KTAB_BITS)];
+        if (e != 0xFFu) return (int)e;
+        int k = 0;
+#pragma unroll
+        for (int j = 0; j < CFS_NCMP; ++j) k += (j < n_cmp && w >= T[j]) ? 1 : 0;
+        return k;
+    }
+};
+
+/* the frame's bucket table from its thresholds (all threads; the caller
+ * synchronizes before and after) */
+__device__ __forceinline__ void cfs_build_ktab(const u32* T, int n_cmp, unsigned char* kt)
+{
+    for (u32 b = threadIdx.x; b < (1u << CFS_KTAB_BITS); b += blockDim.x) {
+        const u32 w0 = b << (32 - CFS_KTAB_BITS), w1 = w0 | ((1u << (32 - CFS_KTAB_BITS)) - 1u);
+        int k0 = 0, k1 = 0;
+        for (int j = 0; j < n_cmp; ++j) {
+            k0 += w0 >= T[j] ? 1 : 0;
+            k1 += w1 >= T[j] ? 1 : 0;
+        }
+        kt[b] = k0 == k1 ? (unsigned char)k0 : (unsigned char)0xFFu;
+    }
+}
+#endif
+
 /* start point: Philox block (i, 0, s, 1), coordinates (word >> 8) * 2^-24,
  * or the caller's SoA start array (index j of this launch) */
 __device__ __forceinline__ void cfs_start(const cfs_launch_args& a, u32 i, u32 sid, u32 j,
@@ -504,6 +542,7 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ const float* s_start;
     __shared__ u32 s_scount;
     __shared__ int s_ncmp;
+    __shared__ unsigned char s_kt[1u << CFS_KTAB_BITS];   /* the frame's bucket table */
 #if CFS_TILE
     extern __shared__ u32 s_cnt[];
     for (u32 e = threadIdx.x; e < a.tile_cap; e += blockDim.x) s_cnt[e] = 0u;
@@ -560,9 +599,11 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
             tile = cfs_frame_window(a, f, s_cnt);
 #endif
             __syncthreads();
+            cfs_build_ktab(s_T, s_ncmp, s_kt);
+            __syncthreads();
             cur = f;
         }
-        const CfsChooseTab choose{s_T, s_ncmp};
+        const CfsChooseKtab choose{s_T, s_kt, s_ncmp};
         const u32 sid = s_sid, pbeg = s_pbeg;
         const u32 j0 = (item - s_ibeg) * s_chunk;
         const u32 j1 = min(j0 + s_chunk, s_npts);

@@ -1797,7 +1797,9 @@ cfs_status tc_rows(cudaStream_t st, int M, int K, const bf16r* A, int lda, const
         const char* e = std::getenv("CFS_TC_ROWS");
         g_tc_rows = (e && std::atoi(e) == 0) ? 0 : 1;
     }
-    if (!g_tc_rows || M < 1)
+    // fewer rows than one tile: the register-staged kernel (no tensor map with
+    // an extent below its box)
+    if (!g_tc_rows || M < TC_M)
         return tc_gemm(st, M, HID, K, A, lda, W, ldw, mode, bias, C, ldc, H, ldh, HT, ldt, Zin,
                        ldz, colsum);
     const bool aligned =
@@ -1834,7 +1836,8 @@ cfs_status tc_splitk(cudaStream_t st, int N, int K, const bf16r* A, int lda, con
         const char* e = std::getenv("CFS_TC_SPLITK");
         g_tc_splitk = (e && std::atoi(e) == 0) ? 0 : 1;
     }
-    if (!g_tc_splitk) {
+    // fewer rows than one chunk: the register-staged kernel (as in tc_rows)
+    if (!g_tc_splitk || (K > 0 && K < TC_K)) {
         const int splits = std::max(1, std::min(256, K / 256));
         return tc_gemm(st, HID, N, K, A, lda, Bm, ldb, EPI_ATOMIC, nullptr, C, ldc, nullptr, 0,
                        nullptr, 0, nullptr, 0, nullptr, splits);

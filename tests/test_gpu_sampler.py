@@ -60,14 +60,16 @@ def test_param_count_and_roundtrip(torch_cuda):
     assert np.array_equal(w, _flat(params)) and not m.any() and not v.any() and st == 0
 
 
-def test_forward_matches_oracle(torch_cuda):
-    cfs, s, params, Ub, Ut = _setup(torch_cuda, 1000)      # ragged: not a multiple of 64
+@pytest.mark.parametrize("B", [37, 129, 1000])
+def test_forward_matches_oracle(torch_cuda, B):
+    # 37: fewer rows than one tile; 129 and 1000: a ragged last tile
+    cfs, s, params, Ub, Ut = _setup(torch_cuda, B)
     Y = s.forward(Ut).cpu().numpy()
     Yo, _ = SO.forward(params, Ub, bf16=True)
     assert _rel(Y, Yo) < 1e-2, _rel(Y, Yo)
 
 
-@pytest.mark.parametrize("B", [777, 4096])
+@pytest.mark.parametrize("B", [37, 129, 777, 4096])
 def test_backward_matches_oracle(torch_cuda, B):
     # 777 rows: a ragged last row tile and a ragged K range in the weight
     # gradients; 4096 rows: the weight gradients split over 16 CTAs

@@ -99,8 +99,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16209536          # (26710784 + 5708288) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "9f73ebcf0a01f296166f0215de2e447457c6595a"
+RENDER_TRAFFIC_BYTES = 16389120          # (26827264 + 5950976) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "0b247ae60d5c849f18035c226504c4a9506aaef1"
 
 
 def _code_only(text: str) -> str:

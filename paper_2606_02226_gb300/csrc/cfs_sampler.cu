@@ -116,6 +116,7 @@ struct TcArgs {
     const float* Zin; int ldz;   // SILU_GRAD: pre-activation of the layer
     float* colsum;               // SILU_GRAD: bias gradient partials, [TC_COPIES][N]; CTA b
                                  // adds its column sums into copy b % TC_COPIES
+    int K2;                      // tc_rows_kernel<true>: K of the recomputed pre-activation
 };
 
 __device__ __forceinline__ u32 smem_addr(const void* p)
@@ -320,7 +321,7 @@ __device__ __forceinline__ void tc_epilogue(const TcArgs& g, int row, int c0, co
             z[j] = v[j] + bias[c0 + j];
             h[j] = silu_f(z[j]);
         }
-        if (in) {
+        if (in && g.C) {
             float4* zc = reinterpret_cast<float4*>(g.C + (size_t)row * g.ldc + c0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) zc[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
@@ -485,9 +486,18 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
 // ---------------------------------------------------------------------------
 constexpr int TR_EPI_WARPS = 16;
 constexpr int TR_THREADS = 32 * (2 + TR_EPI_WARPS);
-constexpr int TR_STAGES = 3;
 constexpr int TR_TILE = 128 * 128 * 2;   // one A tile or the weights at K = 128
-constexpr int TR_SMEM = 1024 + TR_TILE + TR_STAGES * TR_TILE + 256 + 4 * 128;
+
+// shapes of the two variants: RC also recomputes the pre-activation Z of
+// the layer below (second operand pair, second accumulator)
+template <bool RC>
+struct TrCfg {
+    static constexpr int STAGES = RC ? 2 : 3;
+    static constexpr int SLOT = RC ? 2 * TR_TILE : TR_TILE;      // A (and A2) of a tile
+    static constexpr int WEIGHTS = RC ? 2 * TR_TILE : TR_TILE;   // W (and W2)
+    static constexpr int SMEM = 1024 + WEIGHTS + STAGES * SLOT + 256 + 4 * 128;
+    static constexpr int ACC = RC ? 256 : 128;                   // TMEM columns per buffer
+};
 
 __device__ __forceinline__ u64 tc_desc_kn(u32 saddr, u32 lbo, u32 sbo)
 {
@@ -516,44 +526,51 @@ __device__ __forceinline__ void tma_load_2d(u32 dst, const CUtensorMap* map, int
         : "memory");
 }
 
+template <bool RC>
 __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
     const __grid_constant__ TcArgs g)
 {
+    using Cf = TrCfg<RC>;
+    constexpr int ST = Cf::STAGES;
     extern __shared__ unsigned char tr_smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(tr_smem_raw) + 1023) & ~(uintptr_t)1023);
-    const u32 sB = smem_addr(sm), sA = sB + TR_TILE;
-    u64* bars = reinterpret_cast<u64*>(sm + TR_TILE + TR_STAGES * TR_TILE);
-    // barriers: full[s], empty[s] (s < TR_STAGES), wfull, tfull[2], tempty[2]
+    // W at sm (W2 after it), then ST slots of A (A2 after it in the slot)
+    const u32 sB = smem_addr(sm), sB2 = sB + TR_TILE, sA = sB + Cf::WEIGHTS;
+    u64* bars = reinterpret_cast<u64*>(sm + Cf::WEIGHTS + ST * Cf::SLOT);
+    // barriers: full[s], empty[s] (s < ST), wfull, tfull[2], tempty[2]
     auto full = [&](int s) { return smem_addr(&bars[s]); };
-    auto empty = [&](int s) { return smem_addr(&bars[TR_STAGES + s]); };
-    const u32 wfull = smem_addr(&bars[2 * TR_STAGES]);
-    auto tfull = [&](int b) { return smem_addr(&bars[2 * TR_STAGES + 1 + b]); };
-    auto tempty = [&](int b) { return smem_addr(&bars[2 * TR_STAGES + 3 + b]); };
+    auto empty = [&](int s) { return smem_addr(&bars[ST + s]); };
+    const u32 wfull = smem_addr(&bars[2 * ST]);
+    auto tfull = [&](int b) { return smem_addr(&bars[2 * ST + 1 + b]); };
+    auto tempty = [&](int b) { return smem_addr(&bars[2 * ST + 3 + b]); };
     u32* s_tmem = reinterpret_cast<u32*>(bars + 16);
     __shared__ int s_err;
     float* s_col = reinterpret_cast<float*>(bars + 32);   // [128]
-    __shared__ float s_bias[128];                        // SILU: the layer's bias
+    // SILU: the layer's bias; RC: the bias of the recomputed pre-activation
+    __shared__ float s_bias[128];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_tiles = (g.M + TC_M - 1) / TC_M;
-    const int kch = g.K / 8;                  // 16-byte K columns of a tile
-    const u32 tile_bytes = (u32)(TC_M * g.K * 2);
+    const int kch = g.K / 8, kch2 = RC ? g.K2 / 8 : 0;   // 16-byte K columns
+    const u32 tile_bytes = (u32)(TC_M * (g.K + (RC ? g.K2 : 0)) * 2);
+    const u32 w_bytes = tile_bytes;                     // W rows = tile rows = 128
 
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :
-                     : "r"(smem_addr(s_tmem))
+                     : "r"(smem_addr(s_tmem)), "r"(2u * (u32)Cf::ACC)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x < 128) {
         s_col[threadIdx.x] = 0.0f;
-        s_bias[threadIdx.x] = g.mode == EPI_SILU ? g.bias[threadIdx.x] : 0.0f;
+        s_bias[threadIdx.x] = (g.mode == EPI_SILU || RC) ? g.bias[threadIdx.x] : 0.0f;
     }
     if (threadIdx.x == 0) {
         s_err = 0;
-        for (int s = 0; s < TR_STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(full(s), 1u);
             mbar_init(empty(s), 1u);
         }
@@ -571,23 +588,27 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
 
     if (warp == 0) {
         if (lane == 0) {
-            mbar_expect_tx(wfull, tile_bytes);
+            mbar_expect_tx(wfull, w_bytes);
             for (int kc = 0; kc < kch; ++kc) tma_load_2d(sB + kc * 2048, &tmB, kc * 8, 0, wfull);
+            for (int kc = 0; kc < kch2; ++kc) tma_load_2d(sB2 + kc * 2048, &tmB2, kc * 8, 0, wfull);
             int i = 0, issued = 0;
             for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
-                const int s = i % TR_STAGES;
-                if (i >= TR_STAGES && !mbar_wait(empty(s), (u32)(i / TR_STAGES - 1) & 1u)) {
+                const int s = i % ST;
+                if (i >= ST && !mbar_wait(empty(s), (u32)(i / ST - 1) & 1u)) {
                     atomicExch(&s_err, 1);
                     break;
                 }
                 mbar_expect_tx(full(s), tile_bytes);
+                const u32 a = sA + (u32)(s * Cf::SLOT);
                 for (int kc = 0; kc < kch; ++kc)
-                    tma_load_2d(sA + s * TR_TILE + kc * 2048, &tmA, kc * 8, tile * TC_M, full(s));
+                    tma_load_2d(a + kc * 2048, &tmA, kc * 8, tile * TC_M, full(s));
+                for (int kc = 0; kc < kch2; ++kc)
+                    tma_load_2d(a + TR_TILE + kc * 2048, &tmA2, kc * 8, tile * TC_M, full(s));
                 issued = i + 1;
             }
             // every load issued has landed before the CTA may leave
-            for (int j = (issued > TR_STAGES ? issued - TR_STAGES : 0); j < issued; ++j)
-                mbar_wait(full(j % TR_STAGES), (u32)(j / TR_STAGES) & 1u);
+            for (int j = (issued > ST ? issued - ST : 0); j < issued; ++j)
+                mbar_wait(full(j % ST), (u32)(j / ST) & 1u);
             mbar_wait(wfull, 0u);
         }
     } else if (warp == 1) {
@@ -596,14 +617,19 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
             bool ok = mbar_wait(wfull, 0u);
             int i = 0, committed = 0;
             for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++i) {
-                const int s = i % TR_STAGES, b = i & 1;
-                if (!mbar_wait(full(s), (u32)(i / TR_STAGES) & 1u)) { ok = false; break; }
+                const int s = i % ST, b = i & 1;
+                if (!mbar_wait(full(s), (u32)(i / ST) & 1u)) { ok = false; break; }
                 if (i >= 2 && !mbar_wait(tempty(b), (u32)(i / 2 - 1) & 1u)) { ok = false; break; }
                 tc_fence_after();
+                const u32 a = sA + (u32)(s * Cf::SLOT), d = tmem + (u32)(b * Cf::ACC);
                 for (int kk = 0; kk < g.K / 16; ++kk)
-                    tc_mma(tmem + (u32)(b * 128),
-                           tc_desc_kn(sA + s * TR_TILE + kk * 4096, 2048u, 128u),
+                    tc_mma(d, tc_desc_kn(a + kk * 4096, 2048u, 128u),
                            tc_desc_kn(sB + kk * 4096, 2048u, 128u), idesc, kk > 0 ? 1u : 0u);
+                // the layer below's pre-activation: the forward's MMAs on the
+                // same operands in the same order, so the same bits
+                for (int kk = 0; kk < kch2 / 2; ++kk)
+                    tc_mma(d + 128u, tc_desc_kn(a + TR_TILE + kk * 4096, 2048u, 128u),
+                           tc_desc_kn(sB2 + kk * 4096, 2048u, 128u), idesc, kk > 0 ? 1u : 0u);
                 tc_commit(empty(s));
                 tc_commit(tfull(b));
                 committed = i + 1;
@@ -617,44 +643,68 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
         }
     } else {
         const int ew = warp - 2, quad = warp & 3;
-        const int c_begin = (ew >> 2) * 32, c_end = c_begin + 32;
+        const int c_begin = (ew >> 2) * 32;
         int i = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
             const int b = i & 1;
             const int row = tile * TC_M + quad * 32 + lane;
             float z_next[16];
-            tc_load_z(g, row, c_begin, z_next);   // overlaps the wait
+            if (!RC) tc_load_z(g, row, c_begin, z_next);   // overlaps the wait
             if (!mbar_wait(tfull(b), (u32)(i / 2) & 1u)) {
                 atomicExch(&s_err, 1);
                 break;
             }
             tc_fence_after();
-            const u32 base = tmem + ((u32)(quad * 32) << 16) + (u32)(b * 128);
-            // both 16-column loads in flight before the one wait
-            u32 r0[16], r1[16];
-            tc_ld16_nowait(base + (u32)c_begin, r0);
-            tc_ld16_nowait(base + (u32)(c_begin + 16), r1);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            // the accumulator is read: release it to the MMA thread before the
-            // arithmetic and the stores
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty(b));
-            {
-                float v[16], z[16];
+            const u32 base = tmem + ((u32)(quad * 32) << 16) + (u32)(b * Cf::ACC);
+            if constexpr (RC) {
+                // per 16 columns: the product and the recomputed pre-activation
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    v[j] = __uint_as_float(r0[j]);
-                    z[j] = z_next[j];
+                for (int h = 0; h < 2; ++h) {
+                    const int c0 = c_begin + 16 * h;
+                    u32 r[16], q[16];
+                    tc_ld16_nowait(base + (u32)c0, r);
+                    tc_ld16_nowait(base + 128u + (u32)c0, q);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (h == 1) {   // the accumulators are read: release them
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(tempty(b));
+                    }
+                    float v[16], z[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = __uint_as_float(r[j]);
+                        z[j] = __uint_as_float(q[j]) + s_bias[c0 + j];
+                    }
+                    tc_epilogue(g, row, c0, v, z, s_col, s_bias);
                 }
-                tc_load_z(g, row, c_begin + 16, z_next);
-                tc_epilogue(g, row, c_begin, v, z, s_col, s_bias);
-            }
-            {
-                float v[16];
+            } else {
+                // both 16-column loads in flight before the one wait
+                u32 r0[16], r1[16];
+                tc_ld16_nowait(base + (u32)c_begin, r0);
+                tc_ld16_nowait(base + (u32)(c_begin + 16), r1);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // the accumulator is read: release it to the MMA thread before
+                // the arithmetic and the stores
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty(b));
+                {
+                    float v[16], z[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r1[j]);
-                tc_epilogue(g, row, c_begin + 16, v, z_next, s_col, s_bias);
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = __uint_as_float(r0[j]);
+                        z[j] = z_next[j];
+                    }
+                    tc_load_z(g, row, c_begin + 16, z_next);
+                    tc_epilogue(g, row, c_begin, v, z, s_col, s_bias);
+                }
+                {
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r1[j]);
+                    tc_epilogue(g, row, c_begin + 16, v, z_next, s_col, s_bias);
+                }
             }
         }
     }
@@ -665,7 +715,9 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
     if (threadIdx.x == 0 && s_err) atomicExch(&g_tc_error, 1u);
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2u * (u32)Cf::ACC)
+                     : "memory");
     }
 }
 
@@ -1789,39 +1841,63 @@ cfs_status tc_gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda
 // tc_gemm_kernel instead (the same epilogue; for comparison)
 int g_tc_rows = -1;
 
-cfs_status tc_rows(cudaStream_t st, int M, int K, const bf16r* A, int lda, const bf16r* W, int ldw,
-                   int mode, const float* bias, float* C, int ldc, bf16r* H, int ldh, bf16r* HT,
-                   int ldt, const float* Zin, int ldz, float* colsum)
+// whether row GEMMs of M rows run on tc_rows_kernel: then the backward
+// recomputes the pre-activations Z1 and Z2 and the forward need not store them
+bool rows_on_tma(int M)
 {
     if (g_tc_rows < 0) {
         const char* e = std::getenv("CFS_TC_ROWS");
         g_tc_rows = (e && std::atoi(e) == 0) ? 0 : 1;
     }
+    return g_tc_rows && M >= TC_M;
+}
+
+// A2, W2 (K2 = 64 or 128), bias2: SILU_GRAD with the pre-activation of the
+// layer below recomputed as A2 W2^T + bias2 instead of read from Zin (only
+// where rows_on_tma(M); elsewhere Zin is read)
+cfs_status tc_rows(cudaStream_t st, int M, int K, const bf16r* A, int lda, const bf16r* W, int ldw,
+                   int mode, const float* bias, float* C, int ldc, bf16r* H, int ldh, bf16r* HT,
+                   int ldt, const float* Zin, int ldz, float* colsum,
+                   const bf16r* A2 = nullptr, int lda2 = 0, const bf16r* W2 = nullptr,
+                   int ldw2 = 0, int K2 = 0, const float* bias2 = nullptr)
+{
     // fewer rows than one tile: the register-staged kernel (no tensor map with
     // an extent below its box)
-    if (!g_tc_rows || M < TC_M)
+    if (!rows_on_tma(M))
         return tc_gemm(st, M, HID, K, A, lda, W, ldw, mode, bias, C, ldc, H, ldh, HT, ldt, Zin,
                        ldz, colsum);
+    const bool rc = A2 != nullptr;
     const bool aligned =
         (K == 64 || K == 128) && lda % 8 == 0 && ldw % 8 == 0 &&
         (!C || ((uintptr_t)C % 16 == 0 && ldc % 4 == 0)) &&
         (!H || ((uintptr_t)H % 16 == 0 && ldh % 8 == 0)) &&
-        (!Zin || ((uintptr_t)Zin % 16 == 0 && ldz % 4 == 0));
+        (!Zin || ((uintptr_t)Zin % 16 == 0 && ldz % 4 == 0)) &&
+        (!rc || ((K2 == 64 || K2 == 128) && lda2 % 8 == 0 && ldw2 % 8 == 0 && W2 && bias2 &&
+                 mode == EPI_SILU_GRAD));
     if (!aligned) return fail(CFS_ERR_INVALID_ARG, "row GEMM operands not aligned");
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, ta2, tb2;
     cfs_status r = make_tmap_2d_bf16(&ta, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, 8u, 128u);
     if (r == CFS_OK) r = make_tmap_2d_bf16(&tb, W, (uint64_t)K, 128u, (uint64_t)ldw, 8u, 128u);
+    if (r == CFS_OK && rc)
+        r = make_tmap_2d_bf16(&ta2, A2, (uint64_t)K2, (uint64_t)M, (uint64_t)lda2, 8u, 128u);
+    if (r == CFS_OK && rc)
+        r = make_tmap_2d_bf16(&tb2, W2, (uint64_t)K2, 128u, (uint64_t)ldw2, 8u, 128u);
     if (r != CFS_OK) return r;
+    if (!rc) { ta2 = ta; tb2 = tb; }   // unused
     TcArgs g;
     std::memset(&g, 0, sizeof(g));
     g.M = M; g.N = HID; g.K = K;
     g.A = A; g.lda = lda; g.B = W; g.ldb = ldw;
     g.k_split = K;
-    g.mode = mode; g.bias = bias; g.C = C; g.ldc = ldc; g.H = H; g.ldh = ldh;
-    g.HT = HT; g.ldt = ldt; g.Zin = Zin; g.ldz = ldz; g.colsum = colsum;
+    g.mode = mode; g.bias = rc ? bias2 : bias; g.C = C; g.ldc = ldc; g.H = H; g.ldh = ldh;
+    g.HT = HT; g.ldt = ldt; g.Zin = rc ? nullptr : Zin; g.ldz = ldz; g.colsum = colsum;
+    g.K2 = rc ? K2 : 0;
     const int tiles = (M + TC_M - 1) / TC_M;
-    const int sms = std::max(1, device_sm_count());
-    tc_rows_kernel<<<std::min(tiles, sms), TR_THREADS, TR_SMEM, st>>>(ta, tb, g);
+    const int grid = std::min(tiles, std::max(1, device_sm_count()));
+    if (rc)
+        tc_rows_kernel<true><<<grid, TR_THREADS, TrCfg<true>::SMEM, st>>>(ta, tb, ta2, tb2, g);
+    else
+        tc_rows_kernel<false><<<grid, TR_THREADS, TrCfg<false>::SMEM, st>>>(ta, tb, ta2, tb2, g);
     return CFS_OK;
 }
 
@@ -1866,11 +1942,16 @@ cfs_status tc_splitk(cudaStream_t st, int N, int K, const bf16r* A, int lda, con
 cfs_status forward(cfs_sampler* s, const bf16r* U, int B, cudaStream_t st)
 {
     const bf16r* wb = s->wb;
+    // Z1 and Z2 only where the backward reads them (it recomputes them on
+    // tc_rows_kernel); Z3 always (the output layer's backward reads it)
+    const bool keep_z = !rows_on_tma(B);
     cfs_status r = tc_rows(st, B, D_IN, U, D_IN, wb + OFF_W1, D_IN, EPI_SILU, s->w + OFF_B1,
-                           s->Z1, HID, s->H1, HID, s->H1T, s->ldt, nullptr, 0, nullptr);
+                           keep_z ? s->Z1 : nullptr, HID, s->H1, HID, s->H1T, s->ldt, nullptr, 0,
+                           nullptr);
     if (r == CFS_OK)
-        r = tc_rows(st, B, HID, s->H1, HID, wb + OFF_W2, HID, EPI_SILU, s->w + OFF_B2, s->Z2, HID,
-                    s->H2, HID, s->H2T, s->ldt, nullptr, 0, nullptr);
+        r = tc_rows(st, B, HID, s->H1, HID, wb + OFF_W2, HID, EPI_SILU, s->w + OFF_B2,
+                    keep_z ? s->Z2 : nullptr, HID, s->H2, HID, s->H2T, s->ldt, nullptr, 0,
+                    nullptr);
     if (r == CFS_OK)
         r = tc_rows(st, B, HID, s->H2, HID, wb + OFF_W3, HID, EPI_SILU, s->w + OFF_B3, s->Z3, HID,
                     s->H3, HID, nullptr, 0, nullptr, 0, nullptr);
@@ -1890,12 +1971,15 @@ cfs_status backward(cfs_sampler* s, const bf16r* U, int B, const float* dY, floa
     out_backward_kernel<<<(B + OB_ROWS - 1) / OB_ROWS, OB_THREADS, 0, st>>>(
         dY, wb, s->H3, s->Z3, B, s->dZ3, s->dZ3T, s->ldt, s->bias_part + 2 * TC_COPIES * HID);
     // dZ2 = (dZ3 W3) * silu'(Z2): the K-major B operand is W3^T
+    // (on tc_rows_kernel the pre-activations Z2 = H1 W2^T + b2 and Z1 = U W1^T
+    // + b1 are recomputed, bit for bit, instead of read)
     cfs_status r = tc_rows(st, B, HID, s->dZ3, HID, s->wbT + HID * HID, HID, EPI_SILU_GRAD,
                            nullptr, nullptr, 0, s->dZ2, HID, s->dZ2T, s->ldt, s->Z2, HID,
-                           s->bias_part);
+                           s->bias_part, s->H1, HID, wb + OFF_W2, HID, HID, s->w + OFF_B2);
     if (r == CFS_OK)
         r = tc_rows(st, B, HID, s->dZ2, HID, s->wbT, HID, EPI_SILU_GRAD, nullptr, nullptr, 0,
-                    nullptr, 0, s->dZ1T, s->ldt, s->Z1, HID, s->bias_part + TC_COPIES * HID);
+                    nullptr, 0, s->dZ1T, s->ldt, s->Z1, HID, s->bias_part + TC_COPIES * HID, U,
+                    D_IN, wb + OFF_W1, D_IN, D_IN, s->w + OFF_B1);
     if (r != CFS_OK) return r;
     part_reduce_kernel<<<1, 512, 0, st>>>(s->bias_part, grads);
     transpose_in_kernel<<<(B + 31) / 32, 256, 0, st>>>(U, B, s->UT, s->ldt);
@@ -2004,8 +2088,14 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
                         "cudaFuncSetAttribute(tc_gemm_kernel)");
     if (const char* e = std::getenv("CFS_TC_STAGES")) g_tc_stages = std::atoi(e) == 1 ? 1 : 2;
     if (st == CFS_OK)
-        st = check_cuda(cudaFuncSetAttribute(tc_rows_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TR_SMEM),
+        st = check_cuda(cudaFuncSetAttribute(tc_rows_kernel<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TrCfg<false>::SMEM),
+                        "cudaFuncSetAttribute(tc_rows_kernel)");
+    if (st == CFS_OK)
+        st = check_cuda(cudaFuncSetAttribute(tc_rows_kernel<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TrCfg<true>::SMEM),
                         "cudaFuncSetAttribute(tc_rows_kernel)");
     if (st == CFS_OK)
         st = check_cuda(cudaFuncSetAttribute(tc_splitk_kernel,

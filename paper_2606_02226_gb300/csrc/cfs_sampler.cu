@@ -482,6 +482,10 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
 //              i + 1 is loaded and multiplied; each warp arrives on the
 //              accumulator's "empty" barrier as soon as its columns are in
 //              registers.
+// tc_rows_kernel<true> (SILU_GRAD of the input gradients) also loads the
+// layer below's activations A2 and weights W2 and multiplies them into a
+// second accumulator: its pre-activation Z = A2 W2^T + b, the same MMAs the
+// forward ran, so the SiLU derivative needs no stored Z.
 // Every wait is bounded; a time-out sets g_tc_error and the role stops.
 // ---------------------------------------------------------------------------
 constexpr int TR_EPI_WARPS = 16;

@@ -471,11 +471,11 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
 // warp-specialized kernel per GEMM (one CTA per SM, row tiles of 128 strided
 // over the CTAs):
 //   warp 0  -- TMA: the weights once, then each tile's A into a ring of
-//              TR_STAGES shared-memory slots (2D tensor maps, boxes of 128
+//              TrCfg::STAGES shared-memory slots (2D tensor maps, boxes of 128
 //              rows x 8 K elements, i.e. one 16-byte column of core
 //              matrices: K-adjacent cores 2048 B apart, 8-row groups 128 B);
 //   warp 1  -- TMEM owner; one thread issues the tile's tcgen05.mma into one
-//              of two 128-column accumulators and commits it to the slot's
+//              of two accumulator buffers and commits it to the slot's
 //              "empty" barrier and the accumulator's "full" barrier;
 //   warps 2..17 -- the epilogue of tile i (warp w reads TMEM lanes
 //              32 (w % 4) .. + 31 and a quarter of the columns) while tile

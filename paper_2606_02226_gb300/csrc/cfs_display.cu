@@ -164,7 +164,7 @@ __device__ __forceinline__ u32 map_pixel(const float4 s, float l_max, const Disp
     return quant8(r) | (quant8(g) << 8) | (quant8(b) << 16) | (quant8(v) << 24);
 }
 
-__global__ void __launch_bounds__(kThreads) display_map_kernel(const __grid_constant__ DispArgs a)
+__global__ void __launch_bounds__(kThreads, 4) display_map_kernel(const __grid_constant__ DispArgs a)
 {
     __shared__ __align__(16) DisplayLayer sL;
     for (u32 item = blockIdx.x; item < a.n_items; item += gridDim.x) {
@@ -197,6 +197,49 @@ __global__ void __launch_bounds__(kThreads) display_map_kernel(const __grid_cons
             const float am = a.a_max_fixed > 0.0f ? a.a_max_fixed : a.a_max[li];
             const float l_max = am > 0.0f ? logf(__fadd_rn(1.0f, am)) : 1.0f;
             const bool planes_ok = sL.kind != CFS_TARGET_HIST_U32 || (sL.n_px & 3u) == 0;
+            if (sL.kind == CFS_TARGET_HIST_U32 && sL.C <= 4 && planes_ok) {
+                // histograms of up to 4 channels (whole quads: n_px % 4 == 0):
+                // the next quad's planes are in flight while this quad maps
+                const u32* h = reinterpret_cast<const u32*>(sL.data);
+                const int C = sL.C;
+                auto load = [&](u32 q, uint4 (&v)[4]) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        v[c] = c < C ? __ldcs(reinterpret_cast<const uint4*>(
+                                           h + (size_t)c * sL.n_px + q))
+                                     : make_uint4(0u, 0u, 0u, 0u);
+                };
+                uint4 cur[4], nxt[4];
+                u32 p = p0 + 4 * threadIdx.x;
+                if (p < p1) load(p, cur);
+                for (; p < p1; p += 4 * kThreads) {
+                    if (p + 4 * kThreads < p1) load(p + 4 * kThreads, nxt);
+                    // s = s + n_c * palette[c], channel by channel (as sums4)
+                    float4 sq[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sq[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (c >= C) break;
+                        const u32 n[4] = {cur[c].x, cur[c].y, cur[c].z, cur[c].w};
+                        const float* pc = sL.pal[c];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float f = (float)n[j];
+                            sq[j].x = __fadd_rn(sq[j].x, __fmul_rn(f, pc[0]));
+                            sq[j].y = __fadd_rn(sq[j].y, __fmul_rn(f, pc[1]));
+                            sq[j].z = __fadd_rn(sq[j].z, __fmul_rn(f, pc[2]));
+                            sq[j].w = __fadd_rn(sq[j].w, __fmul_rn(f, pc[3]));
+                        }
+                    }
+                    u32 cq[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cq[j] = map_pixel(sq[j], l_max, a);
+                    __stcs(reinterpret_cast<uint4*>(out + p), make_uint4(cq[0], cq[1], cq[2], cq[3]));
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cur[c] = nxt[c];
+                }
+            } else
             for (u32 p = p0 + 4 * threadIdx.x; p < p1; p += 4 * kThreads) {
                 const bool full = p + 4 <= sL.n_px;
                 float4 s[4];

@@ -1,0 +1,41 @@
+"""The benchmark's CPU-side pieces, no GPU needed: the reference arm (the
+oracle timed on the host cores) prints one JSON line that keeps the contract
+of the main arm's line, and the comment stripping behind the render program's
+hash ignores comments only."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["value"] > 0
+    assert d["config"]["workload"] and d["config"]["points"] == 1 << 22
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["value"] == d["value"] and cb["unit"] == bench.UNIT
+    e2e = d["e2e"]
+    assert e2e["value"] == d["value"] and e2e["unit"] == bench.UNIT
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_code_only_strips_comments_not_code():
+    src = "int a = 1; // one\n/* block\n comment */\n\nint b = a / 2; /* half */\n"
+    assert bench._code_only(src) == "int a = 1;\nint b = a / 2;"
+    assert bench._code_only("x = y;\n// only\n") == bench._code_only("x = y;\n")
+    assert bench._code_only("x = y;") != bench._code_only("x = z;")

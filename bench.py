@@ -437,16 +437,20 @@ def run_cfs(args, wl):
                                         "(uniform random addresses, same footprints)",
                          "peaks_gops": peaks},
             "e2e": e2e, "gpu_launches": len(jobs) * K, "clocks": clk}
-    if args.batch:
+    # the subsidiary workloads and the CPU baseline are single-GPU figures: the
+    # N = 1 line carries them; at N > 1 the line is the main metric alone, so
+    # the other GPUs are not held while rank 0 measures them
+    single = world == 1
+    if args.batch and single:
         line["batch"] = bench_batch(torch, cfs, dev, stream, n_frames=args.batch_frames)
-    if args.sampler:
+    if args.sampler and single:
         line["sampler"] = bench_sampler(torch, cfs, dev, stream, train_steps=args.sampler_steps)
-    if args.space:
+    if args.space and single:
         line["space"] = bench_space(torch, cfs, dev, stream)
-    if args.cloud:
+    if args.cloud and single:
         line["cloud"] = bench_cloud(torch, cfs, dev, stream, n_frames=args.cloud_frames,
                                     n=args.cloud_points, fast_trig=args.fast_trig)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and single:
         line["cpu_baseline"] = cpu_baseline(wl, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if world > 1:

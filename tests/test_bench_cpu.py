@@ -39,3 +39,12 @@ def test_code_only_strips_comments_not_code():
     assert bench._code_only(src) == "int a = 1;\nint b = a / 2;"
     assert bench._code_only("x = y;\n// only\n") == bench._code_only("x = y;\n")
     assert bench._code_only("x = y;") != bench._code_only("x = z;")
+
+
+def test_reference_arm_other_ranks_do_nothing():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True,
+                       timeout=300, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [l for l in r.stdout.splitlines() if l.startswith("{")]

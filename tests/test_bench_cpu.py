@@ -48,3 +48,34 @@ def test_reference_arm_other_ranks_do_nothing():
                        timeout=300, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_clock_samples_summary():
+    """The clocks object from nvidia-smi samples: median SM clock, maximum,
+    the throttle reasons seen active ("Not Active" is not), malformed lines
+    skipped."""
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+        def kill(self):
+            pass
+
+    cs = bench.ClockSampler(0)
+    cs.proc = _Proc()
+    cs.lines = [
+        "0, 2070, 2070, 905.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1800, 2070, 1391.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2055, 2070, 1200.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "not a sample",
+    ]
+    r = cs.stop()
+    assert r["sm_mhz"] == 2055.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"] and r["samples"] == 3
+    cs2 = bench.ClockSampler(0)
+    cs2.proc = _Proc()
+    cs2.lines = ["0, 1500, 2070, 700, 0x8, Active, Not Active, Active, Not Active"]
+    assert cs2.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]

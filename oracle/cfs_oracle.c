@@ -204,6 +204,9 @@ typedef struct {
     uint64_t seed;   /* Philox key of the render */
     uint32_t aux;    /* word n & 3 of block (i, n >> 2, system, 2) */
     int* k;          /* colour index of the branch (BANDS changes it) */
+    float band_eps;  /* tolerance of a band op's coordinate (0: not tracked) */
+    int* k_unsure;   /* set when a band op's coordinate lies within band_eps
+                        of a band edge: another platform may pick the other band */
 } orc_opctx;
 
 static float unit24(uint32_t w) { return (float)(w >> 8) * 0x1.0p-24f; }
@@ -246,6 +249,11 @@ static int apply_op(int op, const float* v, float* q, const orc_opctx* cx)
         if (isfinite(t) && fabsf(t) < 1.0e9f) {
             long b = (long)floorf(t);
             m = (int)(((b % nb) + nb) % nb);
+            if (cx->band_eps > 0.0f && v[1] != 0.0f) {
+                /* the band the coordinate reaches when it moves by band_eps */
+                double e = fabs((double)v[1]) * (double)cx->band_eps;
+                if (floor((double)t - e) != floor((double)t + e)) *cx->k_unsure = 1;
+            }
         }
         *cx->k = base + m;
         return 1;
@@ -349,20 +357,54 @@ static int bin_of_px(double upx, int n)
     return b;
 }
 
-static void splat(orc_target* t, const float* q, int alive, int k)
+/* Near-edge bookkeeping of one candidate splat (depth z, packed colour col)
+ * at pixel pix, for the depth-parity bounds: zlo = lowest depth of any
+ * candidate (sure or near-edge), zhi = lowest depth of a sure splat, klo =
+ * lowest key (depth bits << 32 | colour, the buffer's own order) of any
+ * candidate, zalt = lowest depth of a candidate whose colour differs from
+ * klo's or is unsure (a band edge within tolerance).  zalt follows from the
+ * rule that klo's depth is the smallest depth seen: when a new lowest key of
+ * another colour arrives, the old lowest depth becomes the lowest depth of
+ * another colour. */
+static void note_candidate(orc_target* t, size_t pix, float z, uint32_t col, int sure,
+                           int unsure)
+{
+    if (t->zlo && z < t->zlo[pix]) t->zlo[pix] = z;
+    if (sure && t->zhi && z < t->zhi[pix]) t->zhi[pix] = z;
+    if (t->klo && t->zalt) {
+        uint64_t key = ((uint64_t)fbits(z) << 32) | (uint64_t)col;
+        uint64_t cur = t->klo[pix];
+        if (key < cur) {
+            if (cur != ~(uint64_t)0 && (uint32_t)cur != col) {
+                uint32_t zb = (uint32_t)(cur >> 32);
+                float zc;
+                memcpy(&zc, &zb, 4);
+                t->zalt[pix] = zc;
+            }
+            t->klo[pix] = key;
+            if (unsure) t->zalt[pix] = z;
+        } else if (((uint32_t)cur != col || unsure) && z < t->zalt[pix]) {
+            t->zalt[pix] = z;
+        }
+    }
+}
+
+static void splat(orc_target* t, const float* q, int alive, int k, int unsure)
 {
     if (!alive) { t->n_discard++; return; }
     float sx = (float)t->W / (t->x1 - t->x0);
     float sy = (float)t->H / (t->y1 - t->y0);
     int ix = bin_of(q[0], t->x0, t->x1, sx, t->W);
     int iy = bin_of(q[1], t->y0, t->y1, sy, t->H);
+    uint32_t col = t->kind == ORC_TGT_DEPTH_U64 ? t->palette8[k] : 0u;
 
     int ambiguous = 0;
     if (t->amb && t->margin_px > 0.0f && isfinite(q[0]) && isfinite(q[1])) {
         /* Near-edge accounting for the parity bound: the bins the point could
          * reach if its pixel coordinate (computed as the bin rule computes it)
-         * moved by up to margin_px.  Every such bin gets one unit of slack and
-         * the point's depth as a lower bound. */
+         * moved by up to margin_px (< 1 px, so at most one neighbour per
+         * axis).  Every such bin inside the view gets one unit of slack and
+         * the point as a possible (not sure) depth candidate. */
         double ux = (double)((q[0] - t->x0) * sx), uy = (double)((q[1] - t->y0) * sy);
         double m = t->margin_px;
         int xs[2] = {bin_of_px(ux - m, t->W), bin_of_px(ux + m, t->W)};
@@ -377,7 +419,7 @@ static void splat(orc_target* t, const float* q, int alive, int k)
                     if (xs[a] < 0 || ys[b] < 0) continue;
                     size_t pix = (size_t)ys[b] * t->W + xs[a];
                     t->amb[pix] += 1;
-                    if (t->zlo && q[2] < t->zlo[pix]) t->zlo[pix] = q[2];
+                    note_candidate(t, pix, q[2], col, 0, unsure);
                 }
             }
         }
@@ -385,8 +427,9 @@ static void splat(orc_target* t, const float* q, int alive, int k)
     if (ix < 0 || iy < 0) { t->n_discard++; return; }
     size_t pix = (size_t)iy * t->W + ix;
     if (!ambiguous) {
-        if (t->zhi && q[2] < t->zhi[pix]) t->zhi[pix] = q[2];
-        if (t->zlo && q[2] < t->zlo[pix]) t->zlo[pix] = q[2];
+        note_candidate(t, pix, q[2], col, 1, unsure);
+        /* a splat of unsure colour may land in another channel of its bin */
+        if (unsure && t->amb) t->amb[pix] += 1;
     }
     t->n_splat++;
     if (t->kind == ORC_TGT_HIST_U32) {
@@ -415,7 +458,8 @@ static int run_chain(const orc_chain* ch, const float* p, float* q_out, orc_targ
     float q[3] = {p[0], p[1], p[2]};
     int alive = 1, n_rec = 0;
     int kc = k;   /* the branch's colour index */
-    orc_opctx cx = {seed, aux, &kc};
+    int unsure = 0;
+    orc_opctx cx = {seed, aux, &kc, ch->band_eps, &unsure};
     for (int o = 0; o < ch->n_ops; ++o) {
         int op = ch->op[o];
         const float* v = ch->prm + 16 * o;
@@ -423,6 +467,7 @@ static int run_chain(const orc_chain* ch, const float* p, float* q_out, orc_targ
             q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
             alive = 1;
             kc = k;
+            unsure = 0;
         } else if (op == ORC_OP_SPLAT) {
             int ti = (int)v[0];
             if (rec) {
@@ -430,7 +475,7 @@ static int run_chain(const orc_chain* ch, const float* p, float* q_out, orc_targ
                 rec[4 * n_rec + 2] = q[2]; rec[4 * n_rec + 3] = (float)alive;
             }
             n_rec++;
-            if (do_splat && ti >= 0 && ti < n_tg) splat(&tg[ti], q, alive, kc);
+            if (do_splat && ti >= 0 && ti < n_tg) splat(&tg[ti], q, alive, kc, unsure);
         } else if (alive) {
             alive = apply_op(op, v, q, &cx);
         }

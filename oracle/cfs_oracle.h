@@ -50,6 +50,8 @@ typedef struct {
     int n_ops;
     const int* op;       /* [n_ops] */
     const float* prm;    /* [n_ops][16] */
+    float band_eps;      /* parity bookkeeping: a BANDS coordinate within band_eps
+                            of a band edge makes the splat's colour unsure (0 = off) */
 } orc_chain;
 
 typedef struct {
@@ -63,6 +65,10 @@ typedef struct {
     uint32_t* amb;              /* optional [H][W] near-edge slack */
     float* zlo;                 /* optional [H][W] lowest depth that may land here */
     float* zhi;                 /* optional [H][W] lowest depth that surely lands here */
+    uint64_t* klo;              /* optional [H][W] lowest key (depth bits << 32 | colour)
+                                   of any splat that may land here (init all ones) */
+    float* zalt;                /* optional [H][W] lowest depth of a splat that may land
+                                   here with another colour than klo's (init +inf) */
     uint64_t n_splat;           /* out */
     uint64_t n_discard;         /* out */
     uint64_t n_amb;             /* out: near-edge splats */

@@ -46,7 +46,7 @@ class _System(ctypes.Structure):
 
 class _Chain(ctypes.Structure):
     _fields_ = [("n_ops", ctypes.c_int), ("op", ctypes.POINTER(ctypes.c_int)),
-                ("prm", ctypes.POINTER(ctypes.c_float))]
+                ("prm", ctypes.POINTER(ctypes.c_float)), ("band_eps", ctypes.c_float)]
 
 
 class _Target(ctypes.Structure):
@@ -60,6 +60,8 @@ class _Target(ctypes.Structure):
                 ("amb", ctypes.POINTER(ctypes.c_uint32)),
                 ("zlo", ctypes.POINTER(ctypes.c_float)),
                 ("zhi", ctypes.POINTER(ctypes.c_float)),
+                ("klo", ctypes.POINTER(ctypes.c_uint64)),
+                ("zalt", ctypes.POINTER(ctypes.c_float)),
                 ("n_splat", ctypes.c_uint64), ("n_discard", ctypes.c_uint64),
                 ("n_amb", ctypes.c_uint64)]
 
@@ -151,13 +153,13 @@ def _system(sys, keep):
                    _ptr(prob, ctypes.c_double))
 
 
-def _chain(chain, keep):
+def _chain(chain, keep, band_eps=0.0):
     n = len(chain)
     op = keep(np.array([OP_KINDS[o.kind] for o in chain] or [0], dtype=np.int32))
     prm = keep(np.zeros((max(n, 1), 16), dtype=np.float32))
     for j, o in enumerate(chain):
         prm[j, :len(o.params)] = np.asarray(o.params, dtype=np.float32)
-    return _Chain(n, _ptr(op, ctypes.c_int), _ptr(prm, ctypes.c_float))
+    return _Chain(n, _ptr(op, ctypes.c_int), _ptr(prm, ctypes.c_float), float(band_eps))
 
 
 def alloc_target_buffer(t):
@@ -172,14 +174,21 @@ def alloc_target_buffer(t):
 
 
 class TargetResult:
-    def __init__(self, buf, amb, zlo, zhi):
+    """A target's buffer, counters and (when tracked) the near-edge records:
+    ``amb`` slack per pixel; for depth layers ``zlo`` (lowest depth that may
+    land), ``zhi`` (lowest depth that surely lands), ``klo`` (lowest key of
+    any splat that may land) and ``zalt`` (lowest depth that may land with a
+    colour other than ``klo``'s)."""
+
+    def __init__(self, buf, amb, zlo, zhi, klo=None, zalt=None):
         self.buf, self.amb, self.zlo, self.zhi = buf, amb, zlo, zhi
+        self.klo, self.zalt = klo, zalt
         self.n_splat = 0
         self.n_discard = 0
         self.n_amb = 0
 
 
-def _target(t, keep, buf, margin_px, track):
+def _target(t, keep, buf, margin_px, track, prev=None):
     pal = keep(np.zeros((MAX_MAPS, 4), dtype=np.float32))
     if getattr(t, "palette", None) is not None:
         p = np.asarray(t.palette, dtype=np.float32)
@@ -188,12 +197,16 @@ def _target(t, keep, buf, margin_px, track):
     if getattr(t, "palette8", None) is not None:
         p8 = np.asarray(t.palette8, dtype=np.uint32)
         pal8[:p8.shape[0]] = p8
-    amb = zlo = zhi = None
-    if track:
+    amb = zlo = zhi = klo = zalt = None
+    if track and prev is not None:
+        amb, zlo, zhi, klo, zalt = prev.amb, prev.zlo, prev.zhi, prev.klo, prev.zalt
+    elif track:
         amb = np.zeros((t.H, t.W), dtype=np.uint32)
         if t.kind == "depth_u64":
             zlo = np.full((t.H, t.W), np.inf, dtype=np.float32)
             zhi = np.full((t.H, t.W), np.inf, dtype=np.float32)
+            klo = np.full((t.H, t.W), np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+            zalt = np.full((t.H, t.W), np.inf, dtype=np.float32)
     x0, x1, y0, y1 = t.view
     s = _Target(TARGET_KINDS[t.kind], t.W, t.H, getattr(t, "C", 1) or 1,
                 x0, x1, y0, y1, buf.ctypes.data,
@@ -201,8 +214,11 @@ def _target(t, keep, buf, margin_px, track):
                 float(margin_px),
                 _ptr(amb, ctypes.c_uint32) if amb is not None else None,
                 _ptr(zlo, ctypes.c_float) if zlo is not None else None,
-                _ptr(zhi, ctypes.c_float) if zhi is not None else None, 0, 0, 0)
-    return s, TargetResult(buf, amb, zlo, zhi)
+                _ptr(zhi, ctypes.c_float) if zhi is not None else None,
+                _ptr(klo, ctypes.c_uint64) if klo is not None else None,
+                _ptr(zalt, ctypes.c_float) if zalt is not None else None,
+                *((prev.n_splat, prev.n_discard, prev.n_amb) if prev is not None else (0, 0, 0)))
+    return s, TargetResult(buf, amb, zlo, zhi, klo, zalt)
 
 
 def _run(seed, system_id, point_begin, n_points, step_begin, iters, burn_in, reuse, start, keep):
@@ -245,24 +261,28 @@ def choose(w, T, n_maps):
 
 def render(system, chain, targets, *, n_points, iters, burn_in, seed=0, system_id=0,
            point_begin=0, step_begin=0, reuse=False, start=None, margin_px=0.0,
-           track=False, bufs=None):
+           track=False, bufs=None, prev=None, band_eps=0.0):
     """Runs the chaos game for points point_begin .. point_begin + n_points - 1.
 
     ``system``: ``.dim``, ``.maps`` (each ``.kind``, ``.params``), ``.probs``.
     ``chain``: list of ops (``.kind``, ``.params``).  ``targets``: list with
     ``.kind``, ``.W``, ``.H``, ``.C``, ``.view`` = (x0, x1, y0, y1),
     ``.palette`` (RGBA), ``.palette8`` (depth).  ``bufs`` lets a caller
-    accumulate into existing host buffers.  Returns one ``TargetResult`` per
-    target.
+    accumulate into existing host buffers; ``prev`` (the results of an earlier
+    call with ``track``) continues its near-edge records and counters;
+    ``band_eps`` (with ``track``) marks splats whose band op's coordinate lies
+    within that distance of a band edge as of unsure colour.  Returns one
+    ``TargetResult`` per target.
     """
     keep = _Keep()
     s = _system(system, keep)
-    c = _chain(chain, keep)
+    c = _chain(chain, keep, band_eps if track else 0.0)
     results = []
     arr = (_Target * max(len(targets), 1))()
     for j, t in enumerate(targets):
-        buf = bufs[j] if bufs is not None else alloc_target_buffer(t)
-        ts, tr = _target(t, keep, buf, margin_px, track)
+        buf = prev[j].buf if prev is not None else (
+            bufs[j] if bufs is not None else alloc_target_buffer(t))
+        ts, tr = _target(t, keep, buf, margin_px, track, prev[j] if prev is not None else None)
         arr[j] = ts
         results.append(tr)
     r = _run(seed, system_id, point_begin, n_points, step_begin, iters, burn_in, reuse,
@@ -310,16 +330,21 @@ def pointcloud_generate(system, n, iters, *, seed=0, system_id=0):
     return xyz, fn
 
 
-def render_points(xyz, fn, chain, targets, *, margin_px=0.0, track=False, bufs=None):
+def render_points(xyz, fn, chain, targets, *, margin_px=0.0, track=False, bufs=None, prev=None,
+                  band_eps=0.0):
+    """Streams stored points (xyz [n][3], colour index fn [n]) once through the
+    chain; targets, ``bufs``, ``track``, ``prev`` and ``band_eps`` as in
+    ``render``."""
     keep = _Keep()
-    c = _chain(chain, keep)
+    c = _chain(chain, keep, band_eps if track else 0.0)
     xyz = keep(np.ascontiguousarray(xyz, dtype=np.float32))
     fn = keep(np.ascontiguousarray(fn, dtype=np.uint8))
     results = []
     arr = (_Target * max(len(targets), 1))()
     for j, t in enumerate(targets):
-        buf = bufs[j] if bufs is not None else alloc_target_buffer(t)
-        ts, tr = _target(t, keep, buf, margin_px, track)
+        buf = prev[j].buf if prev is not None else (
+            bufs[j] if bufs is not None else alloc_target_buffer(t))
+        ts, tr = _target(t, keep, buf, margin_px, track, prev[j] if prev is not None else None)
         arr[j] = ts
         results.append(tr)
     lib().orc_render_points(_ptr(xyz, ctypes.c_float), _ptr(fn, ctypes.c_uint8),

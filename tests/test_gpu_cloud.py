@@ -7,7 +7,9 @@ import pytest
 from oracle import oracle as O
 from paper_2606_02226_gb300 import workloads as W
 
-from _parity import EMPTY, check_depth_close, depth_of
+from _parity import EMPTY, check_depth_close, depth_of, fixed_margin
+
+POS_TOL = 1e-5
 
 pytestmark = pytest.mark.gpu
 
@@ -50,15 +52,11 @@ def _stream_parity(frame, n, W_, fast_trig=False):
     cfs.render_points(cfs.Chain(chain, 3, fast_trig=fast_trig), xyz, fn, [t], [ten], discards=disc)
     torch.cuda.synchronize()
     g = ten.cpu().numpy().view(np.uint64)
-    # margin from the chain's FP32 differences in pixels (the [-1, 1] view
-    # has W/2 pixels per unit): 2e-6 for precise trigonometry, the 1e-5
-    # position bar for the reduced-argument hardware sine/cosine; plus the
-    # bin rule's own rounding
-    pos = 1e-5 if fast_trig else 2e-6
-    margin = pos * W_ / 2 * 2 + 1e-4
-    o = O.render_points(ox, ofn, chain, [t], margin_px=margin, track=True)[0]
-    frac = check_depth_close(g, o.buf, o.zlo, o.zhi)
-    assert frac >= 0.999
+    # margin: the position tolerance in pixels (the [-1, 1] view has W/2
+    # pixels per unit)
+    o = O.render_points(ox, ofn, chain, [t], margin_px=fixed_margin([t], POS_TOL),
+                        track=True)[0]
+    check_depth_close(g, o)
     d = int(disc.item())
     assert abs(d - o.n_discard) <= o.n_amb
     assert int((g != EMPTY).sum()) > 0
@@ -104,7 +102,7 @@ def test_cloud_full_size_sampled(torch_cuda):
     assert np.array_equal(sx, p[:, -1, :]) and np.array_equal(sfn, k[:, -1])
     # each sampled point's depth bounds the layer's depth at the pixel it
     # surely lands in (relative 1e-5 for the chain's FP32 differences)
-    r = O.render_points(sx, sfn, chain, [t], margin_px=2e-6 * 8192 + 1e-4, track=True)[0]
+    r = O.render_points(sx, sfn, chain, [t], margin_px=fixed_margin([t], POS_TOL), track=True)[0]
     layer = ten.cpu().numpy().view(np.uint64)
     sure = np.isfinite(r.zhi)
     assert sure.sum() > 100

@@ -415,7 +415,8 @@ cfs_status cfs_sampler_destroy(cfs_sampler* s);
 /* Host copies of the parameters, Adam moments and step (any may be NULL):
  * a checkpoint.  Synchronizes the device.  Returns CFS_ERR_TIMEOUT (once) if
  * a tensor-core GEMM of earlier work gave up waiting on its pipeline barrier
- * (bounded waits; the affected results are then incomplete). */
+ * (bounded waits; the affected results are then incomplete): it reads and
+ * clears the device error word as cfs_stream_status does. */
 cfs_status cfs_sampler_get_params(const cfs_sampler* s, float* params, float* adam_m,
                                   float* adam_v, uint32_t* step);
 /* Restores a checkpoint (moments may be NULL: left as they are). */
@@ -463,18 +464,19 @@ cfs_status cfs_sampler_start_points(cfs_sampler* s, const cfs_system* sys, float
 
 /* ---- batched histograms without allocation --------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
- * cannot allocate device memory while rendering -- an application that
- * records its frame loop into a larger CUDA graph and owns every allocation
- * up front, a real-time or embedded host whose memory budget is fixed
- * after start-up, a process whose GPU memory belongs to another allocator.
+ * cannot allocate device memory while rendering -- a real-time or embedded
+ * host whose memory budget is fixed after start-up (an allocation there can
+ * fail or stall a frame), a process whose GPU memory belongs to another
+ * allocator that has taken the device's free memory.
  * It renders the same histograms as cfs_render_batch with a chain that only
  * splats (CFS_OP_SPLAT into slot 0), but keeps its workspace (frame
  * descriptors, work counter, discard counters) in one fixed device array
  * compiled into the library instead of calling cudaMalloc.  It calls no
  * allocating routine.
  *  - At most CFS_NOALLOC_MAX_FRAMES frames per call (else
- *    CFS_ERR_INVALID_ARG); each frame: a 2D system of affine maps and
- *    targets[0] a u32 histogram; other targets are ignored.
+ *    CFS_ERR_INVALID_ARG); each frame: a 2D system of affine maps, at most
+ *    2^32 - 1024 points, and targets[0] a u32 histogram; other targets are
+ *    ignored.
  *  - The array (about 140 KB) exists on every GPU that loads the library,
  *    until the process exits, and every call shares it: calls whose GPU
  *    work overlaps (other streams, other threads) race and corrupt each
@@ -544,6 +546,29 @@ cfs_status cfs_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, u
  * (kind 4: accumulated into). */
 cfs_status cfs_atomic_bench(int kind, void* buf, uint64_t n_elems, uint32_t blocks,
                             uint32_t iters, uint32_t seed, void* stream);
+
+/* ---- device-side errors (the asynchronous half of the error reporting:
+ *      argument errors return at the call, kernel-side failures here) ----- */
+/* Bits of the current device's error word, set by kernels of this library:
+ * a tensor-core GEMM of the sampler whose bounded mbarrier wait (a TMA
+ * arrival, an MMA commit, an epilogue hand-off) ran out skips its output,
+ * frees its tensor memory and sets CFS_DEVICE_ERR_TC_TIMEOUT. */
+#define CFS_DEVICE_ERR_TC_TIMEOUT 1u
+#define CFS_DEVICE_ERR_ALL 1u
+/* Waits for the work enqueued on `stream` (NULL: the legacy default stream),
+ * then reports, in this order: CFS_ERR_CUDA if that work failed (the CUDA
+ * error in cfs_last_error(); a sticky error leaves the context unusable),
+ * CFS_ERR_TIMEOUT if a kernel set CFS_DEVICE_ERR_TC_TIMEOUT since the last
+ * report, else CFS_OK.  The device's error word is read and cleared, so each
+ * device-side error is reported once (by this call or by
+ * cfs_sampler_get_params, which reads the same word).  The word is per
+ * device, not per stream: a flag set by work on another stream of the same
+ * device is reported here too. */
+cfs_status cfs_stream_status(void* stream);
+/* Testing aid for the reporting path: ORs `flags` (CFS_DEVICE_ERR_* bits)
+ * into the current device's error word from the host, as a kernel would,
+ * without launching anything.  CFS_ERR_INVALID_ARG for other bits. */
+cfs_status cfs_debug_raise_device_error(uint32_t flags);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* cfs_last_error(void);

@@ -132,6 +132,8 @@ _SIGNATURES = {
                                          ctypes.POINTER(cfs_target), ctypes.c_int, _P, _P]),
     "cfs_pointcloud_reorder": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int, _P, _P,
                                               _P, _P]),
+    "cfs_stream_status": (ctypes.c_int, [_P]),
+    "cfs_debug_raise_device_error": (ctypes.c_int, [ctypes.c_uint32]),
     "cfs_sampler_param_count": (ctypes.c_uint32, []),
     "cfs_sampler_create": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
     "cfs_sampler_destroy": (ctypes.c_int, [_P]),
@@ -739,6 +741,21 @@ def codegen_check(system: System, chain: Chain, target_descs, mode: int = 0,
     if st != 0:
         raise CfsError(st, lib().cfs_last_error().decode(errors="replace"))
     return src.value.decode(), log.value.decode()
+
+
+DEVICE_ERR_TC_TIMEOUT = 1
+
+
+def stream_status(stream=None):
+    """Waits for the stream's work; raises CfsError (CUDA or TIMEOUT) for a
+    failure of that work or a device-side error flag set since the last
+    report (cfs_stream_status)."""
+    _check(lib().cfs_stream_status(_stream_handle(stream)))
+
+
+def debug_raise_device_error(flags: int = DEVICE_ERR_TC_TIMEOUT):
+    """Sets device error flags from the host, as a timed-out kernel would."""
+    _check(lib().cfs_debug_raise_device_error(flags))
 
 
 def version() -> str:

@@ -321,6 +321,30 @@ const char* cfs_last_error(void) { return cfs::last_error(); }
 
 const char* cfs_version(void) { return "cfs-gb300 0.1 (sm_103a)"; }
 
+cfs_status cfs_stream_status(void* stream)
+{
+    clear_error();
+    cfs_status st = check_cuda(cudaStreamSynchronize((cudaStream_t)stream),
+                               "work on the stream failed");
+    if (st != CFS_OK) return st;
+    unsigned int flags = 0;
+    st = take_device_flags(&flags);
+    if (st != CFS_OK) return st;
+    if (flags & CFS_DEVICE_ERR_TC_TIMEOUT)
+        return fail(CFS_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its mbarrier; "
+                                     "its output is incomplete");
+    if (flags) return fail(CFS_ERR_CUDA, "unknown device error flags");
+    return CFS_OK;
+}
+
+cfs_status cfs_debug_raise_device_error(uint32_t flags)
+{
+    clear_error();
+    if (flags == 0 || (flags & ~(uint32_t)CFS_DEVICE_ERR_ALL))
+        return fail(CFS_ERR_INVALID_ARG, "flags must name CFS_DEVICE_ERR_* bits");
+    return raise_device_flags(flags);
+}
+
 cfs_status cfs_system_create(int dim, int n_maps, const cfs_map* maps, const double* probs,
                              cfs_system** out)
 {

@@ -138,6 +138,13 @@ cfs_status display_enqueue(const DisplayLayer* one, const DisplayLayer* layers, 
                            uint32_t n_items, bool any_density, float* a_max,
                            const cfs_display_params& p, cudaStream_t stream);
 
+// ---- device-side error flags (cfs_sampler.cu) ----------------------------
+// Bits of the current device's error word, set by kernels whose bounded
+// waits ran out (CFS_DEVICE_ERR_* in cfs.h).  take_: reads and clears it;
+// raise_: ORs bits into it (tests of the reporting path).
+cfs_status take_device_flags(unsigned int* flags);
+cfs_status raise_device_flags(unsigned int flags);
+
 // ---- host-side tables ---------------------------------------------------
 void philox_round_keys(uint64_t seed, unsigned int rk[10][2]);
 // per-op constants the kernels read (rotations turned into affine params, ...)

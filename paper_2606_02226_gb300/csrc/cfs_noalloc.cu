@@ -1,14 +1,14 @@
 // cfs_noalloc.cu -- batched histogram rendering that allocates nothing.
 //
-// Some callers cannot allocate device memory while they render: a frame
-// loop recorded into a larger CUDA graph by an application that owns every
-// allocation up front, a real-time or embedded host whose memory budget is
-// fixed after start-up, or a process whose GPU memory is handed out by a
-// foreign allocator.  cfs_render_batch needs a per-batch workspace (frame
-// descriptors, a work counter, discard counters) and gets it with
-// cudaMalloc; this variant keeps that workspace in one file-scope device
-// array instead, sized for at most CFS_NOALLOC_MAX_FRAMES frames.  The
-// caller still passes every input and output (systems, targets).
+// Some callers cannot allocate device memory while they render: a
+// real-time or embedded host whose memory budget is fixed after start-up
+// (an allocation can fail or stall a frame), or a process whose GPU memory
+// is handed out by another allocator that owns the device's free memory.
+// cfs_render_batch needs a per-batch workspace (frame descriptors, a work
+// counter, discard counters) and gets it with cudaMalloc; this variant keeps
+// that workspace in one file-scope device array instead, sized for at most
+// CFS_NOALLOC_MAX_FRAMES frames.  The caller still passes every input and
+// output (systems, targets).
 //
 // The array lives as long as the library is loaded, on every GPU that
 // loads it, and all calls share it: calls whose GPU work overlaps (two
@@ -38,7 +38,8 @@ struct NaTarget {
 
 struct NaFrame {
     u32 T[16];
-    int n_cmp, n_points, point_begin, system_id;
+    int n_cmp;
+    u32 n_points, point_begin, system_id;
     u32 item_begin, pad0, pad1, pad2;
     float prm[6][16];               // a b c d e f of every map, SoA
     NaTarget tg;
@@ -99,10 +100,11 @@ __global__ void __launch_bounds__(kBlock) noalloc_batch_kernel(const NaArgs a)
             __syncthreads();
             cur = f;
         }
+        // n_points <= 2^32 - kChunk (checked on the host): no wrap here
         const u32 j0 = (item - fr.item_begin) * kChunk;
-        const u32 j1 = min(j0 + kChunk, (u32)fr.n_points);
+        const u32 j1 = min(j0 + kChunk, fr.n_points);
         for (u32 j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            const u32 i = (u32)fr.point_begin + j, sid = (u32)fr.system_id;
+            const u32 i = fr.point_begin + j, sid = fr.system_id;
             const uint4 r0 = cfs_philox_rk(a.rk, i, 0u, sid, 1u);
             float x = (float)(r0.x >> 8) * CFS_INV_2_24;
             float y = (float)(r0.y >> 8) * CFS_INV_2_24;
@@ -209,6 +211,8 @@ extern "C" cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_fr
             return fail(CFS_ERR_INVALID_ARG, "every frame needs one u32 histogram target");
         if ((uint64_t)fr.point_begin + fr.n_points > (1ull << 32))
             return fail(CFS_ERR_INVALID_ARG, "point indices exceed 2^32");
+        if ((uint64_t)fr.n_points > (1ull << 32) - kChunk)
+            return fail(CFS_ERR_INVALID_ARG, "a frame may hold at most 2^32 - 1024 points");
         if (fr.start)
             return fail(CFS_ERR_UNSUPPORTED,
                         "the no-allocation batch starts every point from Philox");
@@ -222,6 +226,13 @@ extern "C" cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_fr
     cudaStream_t s = (cudaStream_t)stream_;
     if (burn_in > iters) burn_in = iters;
 
+    // work items, counted in 64 bits: the persistent CTAs draw item numbers
+    // from a 32-bit counter that runs up to n_items + grid
+    uint64_t n_items = 0;
+    for (int f = 0; f < n_frames; ++f) n_items += ((uint64_t)frames[f].n_points + kChunk - 1) / kChunk;
+    if (n_items + (uint64_t)ds->grid >= (1ull << 32))
+        return fail(CFS_ERR_INVALID_ARG, "too many points in one call");
+
     // frame descriptors go up one at a time from a stack buffer: a copy
     // from pageable memory has read its source when cudaMemcpyAsync returns
     uint32_t item = 0;
@@ -233,9 +244,9 @@ extern "C" cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_fr
         std::memset(&d, 0, sizeof(d));
         for (int j = 0; j < sy.n_cmp; ++j) d.T[j] = sy.T[j];
         d.n_cmp = sy.n_cmp;
-        d.n_points = (int)fr.n_points;
-        d.point_begin = (int)fr.point_begin;
-        d.system_id = (int)fr.system_id;
+        d.n_points = fr.n_points;
+        d.point_begin = fr.point_begin;
+        d.system_id = fr.system_id;
         d.item_begin = item;
         for (int k = 0; k < sy.n_maps; ++k)
             for (int j = 0; j < 6; ++j) d.prm[j][k] = sy.maps[k].params[j];
@@ -250,7 +261,7 @@ extern "C" cfs_status cfs_render_batch_noalloc(const cfs_frame* frames, int n_fr
                                         cudaMemcpyHostToDevice, s),
                         "cudaMemcpyAsync(frame)");
         if (st != CFS_OK) return st;
-        item += (fr.n_points + kChunk - 1) / kChunk;
+        item += (uint32_t)(((uint64_t)fr.n_points + kChunk - 1) / kChunk);
         if (clear) {
             st = check_cuda(cudaMemsetAsync(t.data, 0,
                                             (size_t)t.width * t.height * 4 * (size_t)t.channels,

@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(const __grid_consta
             tc_epilogue(g, row, c0, v, z, s_col, g.bias);
         }
     } else if (!ok && tid == 0) {
-        atomicExch(&g_tc_error, 1u);
+        atomicOr(&g_tc_error, (unsigned)CFS_DEVICE_ERR_TC_TIMEOUT);
         // give in-flight MMAs a bounded chance to drain before TMEM is freed
         if (n_chunks > 0) {
             const int last = n_chunks - 1;
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(TR_THREADS, 1) tc_rows_kernel(
     __syncthreads();
     if (g.mode == EPI_SILU_GRAD && !s_err && threadIdx.x < 128 && s_col[threadIdx.x] != 0.0f)
         atomicAdd(g.colsum + (blockIdx.x % TC_COPIES) * 128 + threadIdx.x, s_col[threadIdx.x]);
-    if (threadIdx.x == 0 && s_err) atomicExch(&g_tc_error, 1u);
+    if (threadIdx.x == 0 && s_err) atomicOr(&g_tc_error, (unsigned)CFS_DEVICE_ERR_TC_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -839,7 +839,7 @@ __global__ void __launch_bounds__(SK_THREADS, 1) tc_splitk_kernel(
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && s_err) atomicExch(&g_tc_error, 1u);
+    if (threadIdx.x == 0 && s_err) atomicOr(&g_tc_error, (unsigned)CFS_DEVICE_ERR_TC_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -2044,6 +2044,33 @@ void pack_system(const cfs_system* sys, float t, SysRec* r)
     r->t = t;
 }
 
+}  // namespace
+
+namespace cfs {
+cfs_status take_device_flags(unsigned int* flags)
+{
+    unsigned int v = 0;
+    cfs_status st = check_cuda(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(v)), "error flags");
+    if (st == CFS_OK && v) {
+        const unsigned int zero = 0;
+        st = check_cuda(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero)), "error flags");
+    }
+    *flags = v;
+    return st;
+}
+
+cfs_status raise_device_flags(unsigned int flags)
+{
+    unsigned int v = 0;
+    cfs_status st = check_cuda(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(v)), "error flags");
+    v |= flags;
+    if (st == CFS_OK)
+        st = check_cuda(cudaMemcpyToSymbol(g_tc_error, &v, sizeof(v)), "error flags");
+    return st;
+}
+}  // namespace cfs
+
+namespace {
 cfs_status check_sampler_system(const cfs_system* sys)
 {
     if (!sys) return fail(CFS_ERR_INVALID_ARG, "NULL system");
@@ -2149,14 +2176,10 @@ cfs_status cfs_sampler_get_params(const cfs_sampler* s, float* params, float* ad
         st = check_cuda(cudaMemcpy(step, s->d_step, 4, cudaMemcpyDeviceToHost), "step");
     // a tensor-core GEMM whose barrier wait ran out of time skipped its
     // output: report it once
-    unsigned int tc_err = 0;
-    if (st == CFS_OK)
-        st = check_cuda(cudaMemcpyFromSymbol(&tc_err, g_tc_error, sizeof(tc_err)), "error flag");
-    if (st == CFS_OK && tc_err) {
-        const unsigned int zero = 0;
-        cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero));
+    unsigned int flags = 0;
+    if (st == CFS_OK) st = take_device_flags(&flags);
+    if (st == CFS_OK && (flags & CFS_DEVICE_ERR_TC_TIMEOUT))
         return fail(CFS_ERR_TIMEOUT, "a tensor-core GEMM timed out waiting for its mbarrier");
-    }
     return st;
 }
 

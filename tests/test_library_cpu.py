@@ -39,6 +39,12 @@ def test_version_string():
     assert "sm_103a" in cfs.version()
 
 
+def test_device_error_injection_rejects_unknown_bits():
+    # validated before any device access
+    assert _err(lambda: cfs.debug_raise_device_error(0)) == 1
+    assert _err(lambda: cfs.debug_raise_device_error(1 << 7)) == 1
+
+
 def _err(fn):
     with pytest.raises(cfs.CfsError) as e:
         fn()

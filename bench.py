@@ -441,6 +441,8 @@ def run_cfs(args, wl):
     # N = 1 line carries them; at N > 1 the line is the main metric alone, so
     # the other GPUs are not held while rank 0 measures them
     single = world == 1
+    if args.square and single:
+        line["square"] = bench_square(torch, cfs, dev, stream)
     if args.batch and single:
         line["batch"] = bench_batch(torch, cfs, dev, stream, n_frames=args.batch_frames)
     if args.sampler and single:
@@ -455,6 +457,84 @@ def run_cfs(args, wl):
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def measure_u32_red_peak(torch, cfs, dev, nbytes: int, reps: int = 3):
+    """Gop/s of red.add.u32 at uniformly random addresses over nbytes (the
+    histogram splat's L2 operation), full GPU."""
+    n = 1 << (int(nbytes // 4).bit_length() - 1)
+    buf = torch.zeros(n, dtype=torch.int32, device=dev)
+    blocks, iters = 152 * 8, 512
+    cfs.atomic_bench(0, buf, n, blocks, iters, seed=1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for r in range(reps):
+        cfs.atomic_bench(0, buf, n, blocks, iters, seed=r + 2)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del buf
+    return blocks * 256 * iters / (ms * 1e-3) / 1e9
+
+
+def bench_square(torch, cfs, dev, stream, reps: int = 20):
+    """The square primitive (Section 1): four half-scale maps toward the
+    corners of the unit square, p = 1/4 each; 2^16 points x 200 steps,
+    burn-in 20, into a 512^2 four-channel u32 histogram (4 MiB, L2-resident).
+    One frame = clear + one render launch.  Only 2^16 threads for 152 SMs
+    (a fifth of one resident wave), each 200 dependent steps long: the frame
+    is latency- and launch-bound, reported as it is."""
+    wl = W.square_render()
+    job = wl.jobs[0]
+    t = wl.targets[0]
+    sysh = cfs.System(job.system)
+    chain = cfs.Chain(wl.chain, 2)
+    layer = cfs.alloc_target(t, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    cfs.prepare(sysh, chain, [t], [layer])
+
+    def frame():
+        cfs.target_clear([t], [layer], stream)
+        cfs.render(sysh, chain, [t], [layer], n_points=job.n_points, iters=wl.iters,
+                   burn_in=wl.burn_in, seed=wl.seed, stream=stream)
+
+    for _ in range(3):
+        frame()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(k & 0xFF)                            # L2 flush, outside the timed frame
+        a, b, c = ev[k]
+        a.record(stream)
+        cfs.target_clear([t], [layer], stream)
+        b.record(stream)
+        cfs.render(sysh, chain, [t], [layer], n_points=job.n_points, iters=wl.iters,
+                   burn_in=wl.burn_in, seed=wl.seed, stream=stream)
+        c.record(stream)
+    torch.cuda.synchronize()
+    del flush
+    frame_ms = statistics.median(a.elapsed_time(c) for a, b, c in ev)
+    kern_ms = statistics.median(b.elapsed_time(c) for a, b, c in ev)
+    total = int(layer.view(torch.int32).sum().item())
+    splats = job.n_points * (wl.iters - wl.burn_in)
+    peak = measure_u32_red_peak(torch, cfs, dev, 4 * t.C * t.W * t.H)
+    achieved = splats / (kern_ms * 1e-3) / 1e9
+    return {"workload": "square primitive (4 maps x 1/4): 2^16 points x 200 steps, burn-in 20, "
+                        "512^2 x 4ch u32 histogram",
+            "ms_per_frame": frame_ms, "render_ms": kern_ms, "frames_per_s": 1e3 / frame_ms,
+            "point_steps_per_s": job.n_points * wl.iters / (frame_ms * 1e-3),
+            "splats_per_s": splats / (frame_ms * 1e-3), "gpu_launches_per_frame": 1,
+            "total_exact": total == splats,
+            "roofline": {"bound": "l2_atomic", "kernel": "cfs_render_kernel",
+                         "achieved": achieved, "peak": peak, "unit": "Gop/s",
+                         "frac": achieved / peak,
+                         "peak_source": "measured live: library red.add.u32 microbenchmark "
+                                        "over the 4 MiB footprint",
+                         "note": "2^16 threads, 200 dependent steps each: latency-bound, "
+                                 "not enough parallelism to reach the L2 reduction rate"},
+            "timing": f"median of {reps} frames, L2 flushed (256 MiB write) before each"}
 
 
 def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
@@ -518,6 +598,14 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
                             "bytes": "36 B per pixel: two 16-byte reads of the 4 channels, "
                                      "one 4-byte write"}}
     del outs
+    # roofline: every splat is one u32 increment; outside a frame's
+    # privatized window it is an L2 reduction.  Peak: red.add.u32 at random
+    # addresses over the largest frame's histogram (2048^2 x 4 ch, 64 MiB),
+    # the footprint live while a frame renders.  Small frames keep their
+    # splats in shared memory and are bound by integer issue instead (Philox
+    # rounds, map choice), so the fraction can exceed what L2 alone allows.
+    red_peak = measure_u32_red_peak(torch, cfs, dev, 4 * 4 * 2048 * 2048)
+    splat_gops = n_pts * 280 / (ms * 1e-3) / 1e9
     return {"workload": f"{n_frames} animation frames, 2-8 affine maps, 2^16..2^22 points, "
                         "256^2..2048^2 x 4ch u32, 300 steps, burn-in 20",
             "ms_per_batch": ms, "frames_per_s": n_frames / (ms * 1e-3),
@@ -527,6 +615,14 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             "grid": info["grid"], "gpu_launches_per_batch": 1, "display": display,
             "autotuned": tuning, "ms_per_batch_default_plan": ms_default,
             "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3),
+            "roofline": {"bound": "l2_atomic", "kernel": "cfs_batch_kernel",
+                         "achieved": splat_gops, "peak": red_peak, "unit": "Gop/s",
+                         "frac": splat_gops / red_peak,
+                         "peak_source": "measured live: library red.add.u32 microbenchmark "
+                                        "over a 64 MiB footprint (the largest frame)",
+                         "bytes": "1 u32 increment per splat (280 splat steps per point)",
+                         "issue": "integer-issue bound on small frames: "
+                                  "profiles/cfs_batch_kernel_animation.md"},
             "context_peaks_gops": {"smem_red_u32": measure_smem_atomic_peak(torch, cfs, dev),
                                    "note": "shared-memory u32 adds at random addresses over "
                                            "8192 words per CTA, the window splats' operation; "
@@ -671,21 +767,27 @@ def _l1(torch, h, ref):
 
 def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames: int = 16,
                   n_eval: int = 1 << 20, batch_frames: int = 256,
-                  unique_options=(4096, 16384, 65536)):
+                  unique_options=(4096, 65536, 0), pairs: int = 12):
     """Learned warm start (form 4) against plain burn-in at equal L1 error.
 
     Training: 4096 systems of the animation family (seed 1, disjoint from the
     benchmark frames), batches of 64 systems x 1024 chaos-game points, 64
-    sliced-Wasserstein projections, Adam lr 1e-3.  Equal-L1 search on unseen
-    frames of the benchmark animation (seed 0): a frame's 1024^2 histogram
-    after 280 splat steps, L1 against an independent full-burn-in render
-    (seed A), minus the noise floor (a second independent full-burn-in
-    render, seed B).  The plain method starts uniform and burns in b steps;
-    the warm start draws m network samples per frame (every point starts at
-    sample j mod m) and runs k cleanup steps; both use seed B for their own
-    steps.  For each m, the smallest b and k with a mean excess <= 1e-3 over
-    the evaluation frames set the two configurations whose batched frames/s
-    are compared on all the animation frames (network inference included)."""
+    sliced-Wasserstein projections, Adam lr 1e-3, ``train_steps`` steps.
+    Equal-L1 search on unseen frames of the benchmark animation (seed 0): a
+    frame's 1024^2 histogram after 280 splat steps, L1 against an independent
+    full-burn-in render (seed A), minus the noise floor (a second independent
+    full-burn-in render, seed B).  The plain method starts uniform and burns
+    in b steps; the warm start draws m network samples per frame (every point
+    starts at sample j mod m; m = 0 means one sample per point) and runs k
+    cleanup steps; both use seed B for their own steps.  For each m, the
+    smallest b and k with a mean excess <= 1e-3 over the evaluation frames set
+    the configurations compared on all the animation frames (network
+    inference included).
+
+    Timing: the sample count is chosen on a selection run (two launches of
+    each arm), then plain and warm batches are timed on ``pairs`` interleaved
+    pairs; the line reports the median ratio with its quartiles and range,
+    and a win only when the lower quartile of the ratio exceeds 1."""
     B_IN, ITERS = 20, 300
     fam = W.animation_frames(n_frames=4096, seed=1)
     systems = [cfs.System(f.system) for f in fam]
@@ -727,7 +829,8 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
         for b in bs:
             ex_b[b].append(_l1(torch, hist_of(sysh, 2002, B_IN - b), ref) - floor)
         for m in unique_options:
-            st = smp.start_points(sysh, fr.t, min(m, n_eval), seed=3003 + f, stream=stream)
+            st = smp.start_points(sysh, fr.t, min(m, n_eval) if m else n_eval, seed=3003 + f,
+                                  stream=stream)
             for k in ks:
                 ex_k[m][k].append(_l1(torch, hist_of(sysh, 2002, B_IN - k, start=st), ref) -
                                   floor)
@@ -750,53 +853,87 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
                       [cfs.alloc_target(t, device=dev)]))
         begin += fr.n_points
 
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
+    def timed_once(fn):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(reps):
-            fn()
+        fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return e0.elapsed_time(e1)
 
     plain = cfs.Batch(chain, items, iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - b_min)
     plain.tune(trial_iters=80, stream=stream)          # both sides autotuned
-    ms_plain = timed(lambda: plain.launch(clear=True, stream=stream))
-    out.update({"batch_frames": len(frames), "plain_ms": ms_plain,
-                "plain_frames_per_s": len(frames) / (ms_plain * 1e-3)})
+
+    def run_plain():
+        plain.launch(clear=True, stream=stream)
+
+    run_plain()
+    ms_plain_sel = min(timed_once(run_plain) for _ in range(2))
     frame_systems = [it[0] for it in items]
     frame_t = [fr.t for fr in frames]
     frame_seeds = list(range(len(frames)))
-    best = None
+    arms = {}
+    # selection run: each arm with a k_min, two launches
     for m in unique_options:
         mk = {k: float(np.mean(v)) for k, v in ex_k[m].items()}
         k_min = next((k for k in ks if mk[k] <= 1e-3), None)
-        rec = {"excess_l1_warm_start_k": mk, "k_min": k_min}
-        if k_min is not None:
-            starts = [torch.empty((2, min(m, it[1])), dtype=torch.float32, device=dev)
-                      for it in items]
-            warm = cfs.Batch(chain, [it + (starts[fi],) for fi, it in enumerate(items)],
-                             iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - k_min)
-            warm.tune(trial_iters=80, stream=stream)
+        rec = {"excess_l1_warm_start_k": mk, "k_min": k_min,
+               "samples": "one per point" if not m else f"{m} per frame (point j: j mod m)"}
+        key = str(m) if m else "per_point"
+        out["warm"][key] = rec
+        if k_min is None:
+            continue
+        starts = [torch.empty((2, min(m, it[1]) if m else it[1]), dtype=torch.float32,
+                              device=dev) for it in items]
+        warm = cfs.Batch(chain, [it + (starts[fi],) for fi, it in enumerate(items)],
+                         iters=ITERS, burn_in=B_IN, seed=0, step_begin=B_IN - k_min)
+        warm.tune(trial_iters=80, stream=stream)
 
-            def run_warm():
-                smp.start_points_batch(frame_systems, frame_t, starts, frame_seeds,
-                                       stream=stream)
-                warm.launch(clear=True, stream=stream)
+        def infer(starts=starts):
+            smp.start_points_batch(frame_systems, frame_t, starts, frame_seeds, stream=stream)
 
-            ms_warm = timed(run_warm)
-            rec.update({"warm_ms": ms_warm, "warm_frames_per_s": len(frames) / (ms_warm * 1e-3),
-                        "warm_over_plain": ms_plain / ms_warm})
-            if best is None or rec["warm_over_plain"] > out["warm"][best]["warm_over_plain"]:
-                best = m
-            del warm, starts
-        out["warm"][m] = rec
-    out["best_unique_starts"] = best
-    if best is not None:
-        out["warm_over_plain"] = out["warm"][best]["warm_over_plain"]
+        def run_warm(infer=infer, warm=warm):
+            infer()
+            warm.launch(clear=True, stream=stream)
+
+        run_warm()
+        rec["selection_warm_ms"] = min(timed_once(run_warm) for _ in range(2))
+        rec["selection_infer_ms"] = min(timed_once(infer) for _ in range(2))
+        rec["selection_ratio"] = ms_plain_sel / rec["selection_warm_ms"]
+        arms[key] = (run_warm, infer, warm, starts)
+    if not arms:
+        return out
+    best = max(arms, key=lambda a: out["warm"][a]["selection_ratio"])
+    for a in list(arms):
+        if a != best:
+            del arms[a]
+    run_warm, infer, _, _ = arms[best]
+    # measured run: interleaved pairs, the order alternating within pairs
+    p_ms, w_ms = [], []
+    for i in range(pairs):
+        if i % 2 == 0:
+            p_ms.append(timed_once(run_plain))
+            w_ms.append(timed_once(run_warm))
+        else:
+            w_ms.append(timed_once(run_warm))
+            p_ms.append(timed_once(run_plain))
+    inf_ms = statistics.median(timed_once(infer) for _ in range(5))
+    ratios = sorted(p / w for p, w in zip(p_ms, w_ms))
+    q = np.percentile(ratios, [25, 50, 75])
+    nf = len(frames)
+    out.update({"batch_frames": nf, "chosen_samples": best,
+                "chosen_k_min": out["warm"][best]["k_min"],
+                "pairs": pairs, "plain_ms_median": statistics.median(p_ms),
+                "warm_ms_median": statistics.median(w_ms),
+                "infer_ms_median": inf_ms,
+                "plain_frames_per_s": nf / (statistics.median(p_ms) * 1e-3),
+                "warm_frames_per_s": nf / (statistics.median(w_ms) * 1e-3),
+                "warm_over_plain": float(q[1]),
+                "warm_over_plain_quartiles": [float(q[0]), float(q[2])],
+                "warm_over_plain_range": [ratios[0], ratios[-1]],
+                "win": bool(q[0] > 1.0),
+                "gain_bound": (b_min - out["warm"][best]["k_min"]) / (b_min + ITERS - B_IN)})
     return out
 
 
@@ -835,6 +972,8 @@ def main():
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--no-batch", dest="batch", action="store_false",
                     help="skip the batched-animation measurement")
+    ap.add_argument("--no-square", dest="square", action="store_false",
+                    help="skip the square-primitive measurement")
     ap.add_argument("--no-cloud", dest="cloud", action="store_false",
                     help="skip the stored-cloud measurement")
     ap.add_argument("--fast-trig", action="store_true",
@@ -843,7 +982,7 @@ def main():
                     help="skip the many-objects scene measurement")
     ap.add_argument("--no-sampler", dest="sampler", action="store_false",
                     help="skip the learned warm-start measurement")
-    ap.add_argument("--sampler-steps", type=int, default=4000)
+    ap.add_argument("--sampler-steps", type=int, default=20000)
     ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--cloud-frames", type=int, default=64)
     ap.add_argument("--cloud-points", type=int, default=1 << 26)

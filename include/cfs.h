@@ -191,14 +191,6 @@ cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chai
  *  |x| < 2^16 instead of about 1 ulp; several times fewer instructions.
  *  The generator maps are not affected. */
 #define CFS_COMPOSE_FAST_TRIG 1u
-/*  CFS_COMPOSE_POLY_TRIG -- the chain's sines and cosines reduce their
- *  argument to [-pi/4, pi/4] (Cody-Waite with pi/2 split in three parts) and
- *  evaluate minimax polynomials: within 1.5 ulp for |x| <= 32 (CUDA's
- *  sincosf beyond).  An implementation independent of CUDA's math library;
- *  measured slower than CUDA's sinf/cosf on GB300 (20.4 vs 18.9 ms per frame
- *  of the composed scene), so not the default.  Ignored when
- *  CFS_COMPOSE_FAST_TRIG is set. */
-#define CFS_COMPOSE_POLY_TRIG 2u
 cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint32_t flags,
                           cfs_chain** out);
 cfs_status cfs_chain_destroy(cfs_chain* chain);
@@ -227,7 +219,7 @@ cfs_status cfs_chain_destroy(cfs_chain* chain);
  * listed above; splat(SLOT) (a literal slot 0..3) splats into that target.
  * Expansion and argument errors are reported here (CFS_ERR_INVALID_ARG);
  * compile errors of the bodies at the first render (CFS_ERR_COMPILE, NVRTC
- * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG, CFS_COMPOSE_POLY_TRIG or 0. */
+ * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG or 0. */
 cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem,
                                 uint32_t flags, cfs_chain** out);
 /* Input dimension, op count (0 for a scribble chain) and splat count (the
@@ -326,25 +318,73 @@ cfs_status cfs_batch_launch(cfs_batch* batch, int clear, void* stream);
 /* Discarded splats of the last launch, host u64 [n_frames][n_targets];
  * waits for that launch. */
 cfs_status cfs_batch_discards(cfs_batch* batch, uint64_t* out);
-/* Work items, points per item, persistent grid size. */
+/* Work items, points per item (the plan's default), persistent grid size. */
 cfs_status cfs_batch_info(const cfs_batch* batch, uint32_t* n_items, uint32_t* chunk,
                           uint32_t* grid);
-/* Autotuner: times the batch's own frames under each candidate plan --
- * privatized window on/off (when the chain splats once into a histogram),
- * one or two trajectories per thread, 2048/4096/8192/16384 points per work item --
- * running the first `trial_iters` steps (all when 0), two trials each, and
- * keeps the fastest; the next cfs_batch_launch uses it.  Synchronous; the
- * frames' targets hold trial output afterwards (launch with clear = 1).
- * `out` (may be NULL) receives the choice and its trial time. */
+
+/* Launch plan of a batch (its tuning knobs: points per thread, privatized
+ * tile size and atomic strategy, work-item size).  The first
+ * four fields shape the compiled program; chunk is the default work-item
+ * size of every frame.  cfs_batch_create starts from the measured default
+ * plan (ilp 2, window on when the chain splats once into a histogram, 53248
+ * words, warp aggregation off, 4096 points per item). */
 typedef struct {
-    int ilp;           /* trajectories per thread */
-    int tile;          /* privatized shared-memory window */
-    uint32_t chunk;    /* points per work item */
-    float trial_ms;    /* time of the chosen plan's trial */
-    int trials;        /* plans timed */
+    int ilp;                /* trajectories stepped together per thread: 1 or 2 */
+    int window;             /* privatized shared-memory window for the chain's histogram
+                               splat: 0 off, 1 on (ignored unless the chain splats once,
+                               into a histogram, and is not a scribble) */
+    uint32_t window_words;  /* window capacity in u32 counters: 1024..53248, multiple of 256 */
+    int warp_agg;           /* window adds aggregated across a warp (match.any): 0 or 1 */
+    uint32_t chunk;         /* points per work item: a multiple of 32 in 32..2^20 */
+} cfs_batch_plan;
+cfs_status cfs_batch_get_plan(const cfs_batch* batch, cfs_batch_plan* out);
+/* Replaces the plan (compiling the program if needed; waits for the batch's
+ * last launch) and clears per-class choices of an earlier cfs_batch_tune:
+ * every frame then uses plan->chunk and the window setting. */
+cfs_status cfs_batch_set_plan(cfs_batch* batch, const cfs_batch_plan* plan);
+
+/* Autotuner.  Two stages, each timing the batch's own frames for the first
+ * `trial_iters` steps (all when 0), best of two trials per candidate:
+ *  1. the program, on the whole batch, one knob at a time from the current
+ *     plan: trajectories per thread (1, 2), window on/off, window size
+ *     (13312, 26624, 53248 words), warp aggregation, then the item size
+ *     (2048..16384 points);
+ *  2. per shape class -- frames grouped by point count (log2 rounded down
+ *     to even: 2^16-2^17, 2^18-2^19, ...) and target size (width x height of
+ *     target 0) -- the item size and whether the frame uses the window, timed
+ *     on that class's frames alone.
+ * The choices are kept in the library's tuning cache under keys made of the
+ * device (name, SM count), the program's structure and the classes; a later
+ * cfs_batch_tune whose keys are all cached applies them without trials
+ * unless `flags` has CFS_TUNE_RETUNE.  Synchronous; the frames' targets hold
+ * trial output afterwards (launch with clear = 1).  `out` (may be NULL)
+ * receives the result. */
+#define CFS_TUNE_RETUNE 1u
+typedef struct {
+    int ilp;                /* chosen program */
+    int tile;               /* window on */
+    uint32_t chunk;         /* default item size */
+    float trial_ms;         /* whole-batch trial time of the chosen program */
+    int trials;             /* candidates timed (0 when every choice came from the cache) */
+    uint32_t window_words;
+    int warp_agg;
+    int n_classes;          /* shape classes */
+    int classes_windowed;   /* classes that use the window */
+    int from_cache;         /* 1 when the cache supplied every choice */
 } cfs_batch_tuning;
-cfs_status cfs_batch_tune(cfs_batch* batch, uint32_t trial_iters, void* stream,
+cfs_status cfs_batch_tune(cfs_batch* batch, uint32_t trial_iters, uint32_t flags, void* stream,
                           cfs_batch_tuning* out);
+
+/* The tuning cache (library-wide, in memory; thread-safe).  Load merges the
+ * entries of a text file written by save (one "key value" line each; a
+ * missing file loads nothing and returns CFS_OK; a malformed line is
+ * CFS_ERR_INVALID_ARG).  Save writes every entry.  Clear empties it. */
+cfs_status cfs_tune_cache_load(const char* path);
+cfs_status cfs_tune_cache_save(const char* path);
+cfs_status cfs_tune_cache_clear(void);
+/* Number of cached entries. */
+uint32_t cfs_tune_cache_size(void);
+
 /* Waits for the batch's last launch, then frees it. */
 cfs_status cfs_batch_destroy(cfs_batch* batch);
 /* One-shot: create, launch, destroy.  Returns after the frames are rendered

@@ -76,7 +76,16 @@ class cfs_frame(ctypes.Structure):
 
 class cfs_batch_tuning(ctypes.Structure):
     _fields_ = [("ilp", ctypes.c_int), ("tile", ctypes.c_int), ("chunk", ctypes.c_uint32),
-                ("trial_ms", ctypes.c_float), ("trials", ctypes.c_int)]
+                ("trial_ms", ctypes.c_float), ("trials", ctypes.c_int),
+                ("window_words", ctypes.c_uint32), ("warp_agg", ctypes.c_int),
+                ("n_classes", ctypes.c_int), ("classes_windowed", ctypes.c_int),
+                ("from_cache", ctypes.c_int)]
+
+
+class cfs_batch_plan(ctypes.Structure):
+    _fields_ = [("ilp", ctypes.c_int), ("window", ctypes.c_int),
+                ("window_words", ctypes.c_uint32), ("warp_agg", ctypes.c_int),
+                ("chunk", ctypes.c_uint32)]
 
 
 class cfs_display_params(ctypes.Structure):
@@ -122,7 +131,14 @@ _SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.POINTER(ctypes.c_uint32)]),
     "cfs_batch_destroy": (ctypes.c_int, [_P]),
-    "cfs_batch_tune": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.POINTER(cfs_batch_tuning)]),
+    "cfs_batch_tune": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, _P,
+                                      ctypes.POINTER(cfs_batch_tuning)]),
+    "cfs_batch_get_plan": (ctypes.c_int, [_P, ctypes.POINTER(cfs_batch_plan)]),
+    "cfs_batch_set_plan": (ctypes.c_int, [_P, ctypes.POINTER(cfs_batch_plan)]),
+    "cfs_tune_cache_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "cfs_tune_cache_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "cfs_tune_cache_clear": (ctypes.c_int, []),
+    "cfs_tune_cache_size": (ctypes.c_uint32, []),
     "cfs_render_batch": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cfs_frame),
                                         ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                         ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, _P]),
@@ -243,10 +259,10 @@ class Chain:
     """A composed transform chain (Section 3, Fig. 2B) for points of
     dimension ``dim_in``; ``ops`` are ``.kind`` / ``.params`` records."""
 
-    def __init__(self, ops, dim_in: int, fast_trig: bool = False, poly_trig: bool = False):
+    def __init__(self, ops, dim_in: int, fast_trig: bool = False):
         arr, n = _transforms(ops)
         h = _P()
-        flags = (1 if fast_trig else 0) | (2 if poly_trig else 0)
+        flags = 1 if fast_trig else 0
         _check(lib().cfs_compose_ex(dim_in, arr, n, flags, ctypes.byref(h)))
         self.fast_trig = fast_trig
         self.handle = h
@@ -526,14 +542,34 @@ class Batch:
                                     ctypes.byref(c)))
         return {"n_items": a.value, "chunk": b.value, "grid": c.value}
 
-    def tune(self, trial_iters: int = 0, stream=None):
-        """Times the candidate plans on these frames and keeps the fastest
+    def tune(self, trial_iters: int = 0, stream=None, retune: bool = False):
+        """Times the candidate plans on these frames (program, then per shape
+        class) and keeps the fastest, or takes them from the tuning cache
         (the targets hold trial output afterwards); returns the choice."""
         t = cfs_batch_tuning()
-        _check(lib().cfs_batch_tune(self.handle, int(trial_iters), _stream_handle(stream),
-                                    ctypes.byref(t)))
+        _check(lib().cfs_batch_tune(self.handle, int(trial_iters), 1 if retune else 0,
+                                    _stream_handle(stream), ctypes.byref(t)))
         return {"ilp": t.ilp, "tile": t.tile, "chunk": t.chunk, "trial_ms": t.trial_ms,
-                "trials": t.trials}
+                "trials": t.trials, "window_words": t.window_words, "warp_agg": t.warp_agg,
+                "n_classes": t.n_classes, "classes_windowed": t.classes_windowed,
+                "from_cache": bool(t.from_cache)}
+
+    def plan(self) -> dict:
+        p = cfs_batch_plan()
+        _check(lib().cfs_batch_get_plan(self.handle, ctypes.byref(p)))
+        return {"ilp": p.ilp, "window": p.window, "window_words": p.window_words,
+                "warp_agg": p.warp_agg, "chunk": p.chunk}
+
+    def set_plan(self, **kw):
+        """Replaces plan fields (ilp, window, window_words, warp_agg, chunk)."""
+        cur = self.plan()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown plan fields {sorted(unknown)}")
+        cur.update(kw)
+        p = cfs_batch_plan(int(cur["ilp"]), int(cur["window"]), int(cur["window_words"]),
+                           int(cur["warp_agg"]), int(cur["chunk"]))
+        _check(lib().cfs_batch_set_plan(self.handle, ctypes.byref(p)))
 
     def display(self, outs, *, slot: int = 0, gamma: float = 2.2, brightness: float = 1.0,
                 a_max: float = 0.0, background: int = 0, a_max_out=None, stream=None):
@@ -741,6 +777,22 @@ def codegen_check(system: System, chain: Chain, target_descs, mode: int = 0,
     if st != 0:
         raise CfsError(st, lib().cfs_last_error().decode(errors="replace"))
     return src.value.decode(), log.value.decode()
+
+
+def tune_cache_load(path: str):
+    _check(lib().cfs_tune_cache_load(os.fsencode(path)))
+
+
+def tune_cache_save(path: str):
+    _check(lib().cfs_tune_cache_save(os.fsencode(path)))
+
+
+def tune_cache_clear():
+    _check(lib().cfs_tune_cache_clear())
+
+
+def tune_cache_size() -> int:
+    return int(lib().cfs_tune_cache_size())
 
 
 DEVICE_ERR_TC_TIMEOUT = 1

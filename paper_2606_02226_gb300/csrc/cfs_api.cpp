@@ -221,18 +221,6 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     // copies of the step code than with four (instruction-cache misses); the
     // composed scene's 10 ops ran 2.5% faster with four
     sp.unroll = ch->n_ops > 12 ? 2 : 4;
-    // launch-shape knobs for tuning sweeps (all variants compute the same)
-    if (const char* e = std::getenv("CFS_BLOCK")) sp.block = std::atoi(e);
-    if (const char* e = std::getenv("CFS_MINB")) sp.min_blocks = std::atoi(e);
-    if (const char* e = std::getenv("CFS_DEPTH_TEST")) sp.depth_test = std::atoi(e);
-    if (const char* e = std::getenv("CFS_SPILL_ALLOW")) sp.spill_allowance = std::atoi(e);
-    if (const char* e = std::getenv("CFS_UNROLL")) {
-        const int u = std::atoi(e);
-        if (u == 1 || u == 2 || u == 4) sp.unroll = u;
-    }
-    if (sp.block != 128 && sp.block != 256 && sp.block != 512) sp.block = 256;
-    if (sp.min_blocks < 1 || sp.min_blocks > 16) sp.min_blocks = 4;
-    sp.depth_test = sp.depth_test ? 1 : 0;
     return sp;
 }
 
@@ -410,7 +398,7 @@ cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint3
                           cfs_chain** out)
 {
     clear_error();
-    if (flags & ~(uint32_t)(CFS_COMPOSE_FAST_TRIG | CFS_COMPOSE_POLY_TRIG)) {
+    if (flags & ~(uint32_t)CFS_COMPOSE_FAST_TRIG) {
         if (out) *out = nullptr;
         return fail(CFS_ERR_INVALID_ARG, "unknown compose flags");
     }
@@ -488,7 +476,7 @@ cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem
     *out = nullptr;
     if (dim_in != 2 && dim_in != 3) return fail(CFS_ERR_INVALID_ARG, "dim_in must be 2 or 3");
     if (!source || !poem) return fail(CFS_ERR_INVALID_ARG, "NULL source or poem name");
-    if ((flags & ~(CFS_COMPOSE_FAST_TRIG | CFS_COMPOSE_POLY_TRIG)) != 0)
+    if ((flags & ~(uint32_t)CFS_COMPOSE_FAST_TRIG) != 0)
         return fail(CFS_ERR_INVALID_ARG, "unknown flags");
     std::string body;
     std::vector<int> slots;

@@ -29,9 +29,10 @@ typedef struct {
 } cfs_dev_system;
 
 /* one frame of a batch (device copy, read by the persistent batch kernel) */
+#define CFS_FRAME_NO_WINDOW 1   /* flags: the frame's splats skip the privatized window */
 typedef struct {
     unsigned int T[CFS_A_MAX_MAPS];
-    int n_maps, n_cmp, dim, pad;
+    int n_maps, n_cmp, dim, flags;
     float prm[12][CFS_A_MAX_MAPS];
     unsigned int n_points, point_begin, system_id, item_begin;   /* first work item */
     unsigned int chunk, start_count;                             /* points per item */

@@ -9,9 +9,14 @@
 // clears of every frame's targets, the persistent kernel -- is captured into
 // a CUDA graph that each cfs_batch_launch replays on the caller's stream.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
 #include <sstream>
+#include <string>
 #include <vector>
 
 #include "cfs_internal.h"
@@ -32,6 +37,8 @@ struct cfs_batch {
     std::vector<cfs_frame> frames;        // host copy (targets by value)
     std::vector<cfs_system> systems;      // host copies
     std::vector<uint32_t> chunks;         // points per item, per frame
+    std::vector<uint8_t> nowin;           // per frame: skip the privatized window
+    cfs_batch_plan plan;                  // program knobs and default item size
     cfs::ProgramSpec spec;
     cfs::Kernel kernel;
     cfs::Kernel bbox_kernel;              // pre-pass of the privatized window
@@ -60,13 +67,14 @@ namespace {
 using namespace cfs;
 
 void pack_frame(cfs_dev_frame* d, const cfs_system& s, const cfs_frame& f, int n_targets,
-                uint32_t item_begin, uint32_t chunk)
+                uint32_t item_begin, uint32_t chunk, bool nowin)
 {
     std::memset(d, 0, sizeof(*d));
     for (int j = 0; j < s.n_cmp; ++j) d->T[j] = s.T[j];
     d->n_maps = s.n_maps;
     d->n_cmp = s.n_cmp;
     d->dim = s.dim;
+    d->flags = nowin ? CFS_FRAME_NO_WINDOW : 0;
     for (int k = 0; k < s.n_maps; ++k)
         for (int j = 0; j < 12; ++j) d->prm[j][k] = s.maps[k].params[j];
     d->n_points = f.n_points;
@@ -158,80 +166,109 @@ cfs_status capture(cfs_batch* b, int clear)
 
 namespace cfs {
 // Launch shape of the persistent batch program (also used by the compile-only
-// check); returns the privatized window's capacity in u32 counters.
+// check): the default plan's program knobs; returns the privatized window's
+// capacity in u32 counters (0 when the chain cannot use one).
 uint32_t batch_spec_defaults(ProgramSpec& sp)
 {
     // measured on GB300: one 1024-thread CTA per SM sharing a ~208 KB
     // privatized window beats smaller CTAs with smaller windows (the flush
     // volume and the global-atomic share both shrink)
     sp.block = 1024;
-    if (const char* e = std::getenv("CFS_BATCH_BLOCK")) {
-        const int v = std::atoi(e);
-        if (v == 128 || v == 256 || v == 512 || v == 1024) sp.block = v;
-    }
-    sp.min_blocks = std::max(1, 2048 / sp.block);
+    sp.min_blocks = 2;
     sp.spill_allowance = 64;
     sp.depth_test = 1;
+    sp.tile_reps = 1;
     // privatized window: when the chain splats once, into a histogram
-    sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32) ? 1 : 0;
+    sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32 &&
+               sp.scribble.empty()) ? 1 : 0;
     // warp-level aggregation of equal window addresses (match.any) measured
     // slower than plain shared atomics on the animation batch: off
     sp.warp_agg = 0;
-    uint32_t tile_cap = sp.block >= 1024 ? 53248 : 8192;
-    if (const char* e = std::getenv("CFS_TILE")) sp.tile = sp.tile && std::atoi(e) != 0;
-    if (const char* e = std::getenv("CFS_WARP_AGG")) sp.warp_agg = std::atoi(e) != 0;
-    // copies of small windows (one per warp) measured slower on the animation
-    // batch (the flush grows with the copies); kept as a knob
-    sp.tile_reps = 1;
-    if (const char* e = std::getenv("CFS_TILE_REPS")) sp.tile_reps = std::max(1, std::atoi(e));
     // two trajectories per thread: 755 vs 764 ms for the 256-frame batch
     sp.ilp = 2;
-    if (const char* e = std::getenv("CFS_BATCH_ILP")) sp.ilp = std::atoi(e) == 2 ? 2 : 1;
-    if (const char* e = std::getenv("CFS_TILE_CAP")) {
-        const int c = std::atoi(e);
-        if (c >= 256 && c <= 53248) tile_cap = (uint32_t)c;
-    }
-    if (!sp.tile) { sp.warp_agg = 0; tile_cap = 0; }
+    const uint32_t tile_cap = sp.tile ? 53248u : 0u;
     sp.dyn_smem = (int)(tile_cap * sizeof(uint32_t));
     // a window above half of the SM's shared memory leaves room for one CTA
     // per SM: asking for two would only cap the registers (and spill)
     if (sp.dyn_smem > 112 * 1024) sp.min_blocks = 1;
-    if (const char* e = std::getenv("CFS_BATCH_MINB")) sp.min_blocks = std::max(1, std::atoi(e));
     return tile_cap;
 }
 }  // namespace cfs
 
 namespace {
-// Cuts every frame into items of `chunk` points (whole warps), numbers the
-// items frame by frame, repacks the staged frame descriptors and sets the
-// persistent grid (resident CTAs, at most one per item).
-cfs_status plan_items(cfs_batch* b, uint32_t chunk)
+// Cuts every frame into items of its own chunk of points (whole warps),
+// numbers the items frame by frame, repacks the staged frame descriptors and
+// sets the persistent grid (resident CTAs, at most one per item).  Frames
+// outside `active` (when given) get no items: an autotuner trial of one
+// shape class.
+cfs_status plan_items(cfs_batch* b, const std::vector<uint8_t>* active = nullptr)
 {
-    b->chunk = chunk;
     b->grid = (uint32_t)std::max(1, b->kernel.max_blocks_per_sm * std::max(1, b->kernel.num_sms));
     uint64_t total = 0;
-    b->chunks.assign(b->n_frames, chunk);
-    for (int f = 0; f < b->n_frames; ++f)
-        total += ((uint64_t)b->frames[f].n_points + chunk - 1) / chunk;
-    if (total >= (1ull << 31)) return fail(CFS_ERR_INVALID_ARG, "too many work items");
+    std::vector<uint32_t> begin(b->n_frames);
+    for (int f = 0; f < b->n_frames; ++f) {
+        begin[f] = (uint32_t)total;
+        if (active && !(*active)[f]) continue;
+        total += ((uint64_t)b->frames[f].n_points + b->chunks[f] - 1) / b->chunks[f];
+        if (total >= (1ull << 31)) return fail(CFS_ERR_INVALID_ARG, "too many work items");
+    }
     b->n_items = (uint32_t)total;
     if (b->grid > b->n_items && b->n_items > 0) b->grid = b->n_items;
     if (b->h_frames) {
-        uint32_t item = 0;
         for (int f = 0; f < b->n_frames; ++f) {
-            pack_frame(&b->h_frames[f], b->systems[f], b->frames[f], b->n_targets, item, chunk);
-            item += (b->frames[f].n_points + chunk - 1) / chunk;
+            const uint32_t np = (active && !(*active)[f]) ? 0u : b->frames[f].n_points;
+            cfs_frame fr = b->frames[f];
+            fr.n_points = np;
+            pack_frame(&b->h_frames[f], b->systems[f], fr, b->n_targets, begin[f], b->chunks[f],
+                       b->nowin[f] != 0);
         }
     }
+    b->chunk = b->plan.chunk;
     b->args.n_items = b->n_items;
-    b->args.chunk = chunk;
+    b->args.chunk = b->plan.chunk;
     return CFS_OK;
 }
 
+bool window_allowed(const ProgramSpec& sp)
+{
+    return sp.scribble.empty() && sp.splats.size() == 1 &&
+           sp.splats[0].kind == CFS_TARGET_HIST_U32;
+}
+
+cfs_status check_plan(const cfs_batch_plan& p)
+{
+    if (p.ilp != 1 && p.ilp != 2) return fail(CFS_ERR_INVALID_ARG, "plan: ilp must be 1 or 2");
+    if (p.window != 0 && p.window != 1) return fail(CFS_ERR_INVALID_ARG, "plan: window 0 or 1");
+    if (p.window_words < 1024 || p.window_words > 53248 || p.window_words % 256)
+        return fail(CFS_ERR_INVALID_ARG,
+                    "plan: window_words must be a multiple of 256 in 1024..53248");
+    if (p.warp_agg != 0 && p.warp_agg != 1)
+        return fail(CFS_ERR_INVALID_ARG, "plan: warp_agg 0 or 1");
+    if (p.chunk < 32 || p.chunk > (1u << 20) || p.chunk % 32)
+        return fail(CFS_ERR_INVALID_ARG, "plan: chunk must be a multiple of 32 in 32..2^20");
+    return CFS_OK;
+}
+
+// Sets the program knobs of the spec from the plan (window only where the
+// chain allows one) and the window capacity of the launch.
+void spec_from_plan(cfs_batch* b)
+{
+    ProgramSpec& sp = b->spec;
+    sp.ilp = b->plan.ilp;
+    sp.tile = (b->plan.window && window_allowed(sp)) ? 1 : 0;
+    sp.warp_agg = sp.tile ? b->plan.warp_agg : 0;
+    b->tile_cap = sp.tile ? b->plan.window_words : 0u;
+    sp.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
+    // a window above half of the SM's shared memory leaves room for one CTA
+    // per SM: asking for two would only cap the registers (and spill)
+    sp.min_blocks = sp.dyn_smem > 112 * 1024 ? 1 : 2;
+}
+
 // Compiles the batch program (and the window pre-pass when tiled) for the
-// spec's current knobs.
+// plan's knobs.
 cfs_status build_program(cfs_batch* b)
 {
+    spec_from_plan(b);
     cfs_status st = get_kernel(b->spec, "cfs_batch_kernel", &b->kernel);
     if (st != CFS_OK) return st;
     if (b->spec.tile) {
@@ -272,6 +309,107 @@ cfs_status run_direct(cfs_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t 
         st = launch(b->kernel, b->grid, &b->args, sizeof(b->args), s);
     if (st == CFS_OK) st = check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
     return st;
+}
+// ---- the tuning cache ------------------------------------------------------
+// Keys hold no spaces (the file format is "key value" per line).
+std::map<std::string, std::string> g_cache;
+std::mutex g_cache_mu;
+
+bool cache_get(const std::string& k, std::string* v)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    auto it = g_cache.find(k);
+    if (it == g_cache.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+void cache_put(const std::string& k, const std::string& v)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    g_cache[k] = v;
+}
+
+std::string no_spaces(std::string t)
+{
+    for (char& c : t)
+        if (c == ' ' || c == '\t' || c == '\n' || c == '\r') c = '_';
+    return t;
+}
+
+cfs_status device_key(int dev, std::string* out)
+{
+    cudaDeviceProp p;
+    cfs_status st = check_cuda(cudaGetDeviceProperties(&p, dev), "cudaGetDeviceProperties");
+    if (st != CFS_OK) return st;
+    std::ostringstream o;
+    o << no_spaces(p.name) << ".sm" << p.multiProcessorCount << ".cc" << p.major << p.minor;
+    *out = o.str();
+    return CFS_OK;
+}
+
+// the program's structure without the knobs the tuner sets
+std::string structure_key(const ProgramSpec& sp)
+{
+    ProgramSpec k = sp;
+    k.ilp = 0;
+    k.tile = 0;
+    k.warp_agg = 0;
+    k.min_blocks = 0;
+    k.dyn_smem = 0;
+    return no_spaces(k.key());
+}
+
+// point-count bucket (log2 rounded down to even) and target 0's size
+std::string frame_class(const cfs_frame& f, int n_targets)
+{
+    int lg = 0;
+    while (lg < 32 && (1ull << (lg + 1)) <= (uint64_t)std::max(1u, f.n_points)) ++lg;
+    std::ostringstream o;
+    o << "p" << (lg & ~1);
+    if (n_targets > 0) o << ".w" << f.targets[0].width << "x" << f.targets[0].height;
+    return o.str();
+}
+
+std::string format_plan(const cfs_batch_plan& p)
+{
+    std::ostringstream o;
+    o << "ilp=" << p.ilp << ",win=" << p.window << ",words=" << p.window_words
+      << ",agg=" << p.warp_agg << ",chunk=" << p.chunk;
+    return o.str();
+}
+
+bool parse_plan(const std::string& v, cfs_batch_plan* p)
+{
+    unsigned words = 0, chunk = 0;
+    int ilp = 0, win = 0, agg = 0;
+    if (std::sscanf(v.c_str(), "ilp=%d,win=%d,words=%u,agg=%d,chunk=%u", &ilp, &win, &words,
+                    &agg, &chunk) != 5)
+        return false;
+    p->ilp = ilp;
+    p->window = win;
+    p->window_words = words;
+    p->warp_agg = agg;
+    p->chunk = chunk;
+    return true;
+}
+
+std::string format_class(uint32_t chunk, uint8_t nowin)
+{
+    std::ostringstream o;
+    o << "chunk=" << chunk << ",nowin=" << (int)nowin;
+    return o.str();
+}
+
+bool parse_class(const std::string& v, uint32_t* chunk, uint8_t* nowin)
+{
+    unsigned c = 0;
+    int nw = 0;
+    if (std::sscanf(v.c_str(), "chunk=%u,nowin=%d", &c, &nw) != 2) return false;
+    if (c < 32 || c > (1u << 20) || c % 32 || (nw != 0 && nw != 1)) return false;
+    *chunk = c;
+    *nowin = (uint8_t)nw;
+    return true;
 }
 }  // namespace
 
@@ -363,27 +501,23 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
         ss.channels = ss.kind == CFS_TARGET_HIST_U32 ? frames[0].targets[slot].channels : 1;
         sp.splats.push_back(ss);
     }
-    b->tile_cap = batch_spec_defaults(sp);
-    if (!sp.scribble.empty() && sp.tile) {
-        // the privatized window needs the splat's code shape of an op chain
-        sp.tile = 0;
-        sp.warp_agg = 0;
-        b->tile_cap = 0;
-        sp.dyn_smem = 0;
-    }
+    batch_spec_defaults(sp);
+    // the default plan; cfs_batch_set_plan and cfs_batch_tune change it
+    b->plan.ilp = sp.ilp;
+    b->plan.window = 1;
+    b->plan.window_words = 53248;
+    b->plan.warp_agg = 0;
+    b->plan.chunk = 4096;
     st = build_program(b);
     if (st != CFS_OK) { delete b; return st; }
 
-    // Items: every frame is cut into items of `chunk` points (whole warps);
-    // all CTAs work on one or two frames at a time, so the live layers stay
-    // in L2.  cfs_batch_tune picks the chunk (and the program's knobs) by
-    // measurement.
-    uint32_t chunk = 4096;
-    if (const char* e = std::getenv("CFS_BATCH_CHUNK")) {
-        const int c = std::atoi(e);
-        if (c >= 32 && c % 32 == 0) chunk = (uint32_t)c;
-    }
-    st = plan_items(b, chunk);
+    // Items: every frame is cut into items of its chunk of points (whole
+    // warps); all CTAs work on one or two frames at a time, so the live
+    // layers stay in L2.  cfs_batch_tune picks the chunks (and the program's
+    // knobs) by measurement.
+    b->chunks.assign(n_frames, b->plan.chunk);
+    b->nowin.assign(n_frames, 0);
+    st = plan_items(b);
     if (st != CFS_OK) { delete b; return st; }
 
     // workspace: frames | bbox (int4 per frame) | counter (u32, padded to
@@ -410,7 +544,7 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     b->d_disc = reinterpret_cast<unsigned long long*>(b->d_work + off_disc);
 
     fill_args_common(&b->args, chain, seed, iters, burn_in);
-    st = plan_items(b, b->chunk);        // now that the staging buffer exists
+    st = plan_items(b);                  // now that the staging buffer exists
     if (st != CFS_OK) { release(b); delete b; return st; }
     b->args.step_begin = step_begin;
     b->args.frames = (unsigned long long)(uintptr_t)b->d_frames;
@@ -442,7 +576,7 @@ cfs_status cfs_batch_set_system(cfs_batch* b, int frame, const cfs_system* sys)
     b->systems[frame] = *sys;
     const uint32_t item_begin = b->h_frames[frame].item_begin;
     pack_frame(&b->h_frames[frame], b->systems[frame], b->frames[frame], b->n_targets, item_begin,
-               b->chunks[frame]);
+               b->chunks[frame], b->nowin[frame] != 0);
     return CFS_OK;
 }
 
@@ -548,11 +682,43 @@ cfs_status cfs_batch_display(cfs_batch* b, int slot, const cfs_display_params* p
     return check_cuda(cudaEventRecord(b->disp_done, (cudaStream_t)stream), "cudaEventRecord");
 }
 
-cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, void* stream,
+cfs_status cfs_batch_get_plan(const cfs_batch* b, cfs_batch_plan* out)
+{
+    clear_error();
+    if (!b || !out) return fail(CFS_ERR_INVALID_ARG, "NULL batch or out");
+    *out = b->plan;
+    return CFS_OK;
+}
+
+cfs_status cfs_batch_set_plan(cfs_batch* b, const cfs_batch_plan* plan)
+{
+    clear_error();
+    if (!b || !plan) return fail(CFS_ERR_INVALID_ARG, "NULL batch or plan");
+    cfs_status st = check_plan(*plan);
+    if (st != CFS_OK) return st;
+    if (b->launched) st = check_cuda(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+    if (st != CFS_OK) return st;
+    const cfs_batch_plan old = b->plan;
+    b->plan = *plan;
+    st = build_program(b);
+    if (st != CFS_OK) {
+        b->plan = old;
+        build_program(b);
+        return st;
+    }
+    std::fill(b->chunks.begin(), b->chunks.end(), b->plan.chunk);
+    std::fill(b->nowin.begin(), b->nowin.end(), (uint8_t)0);
+    st = plan_items(b);
+    drop_graphs(b);                     // the next launch captures the new plan
+    return st;
+}
+
+cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, uint32_t flags, void* stream,
                           cfs_batch_tuning* out)
 {
     clear_error();
     if (!b) return fail(CFS_ERR_INVALID_ARG, "NULL batch");
+    if (flags & ~CFS_TUNE_RETUNE) return fail(CFS_ERR_INVALID_ARG, "unknown tuning flags");
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != b->device) return fail(CFS_ERR_INVALID_ARG, "batch belongs to another device");
@@ -561,6 +727,9 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, void* stream,
     if (b->launched) st = check_cuda(cudaEventSynchronize(b->done), "cudaEventSynchronize");
     if (b->disp_launched && st == CFS_OK)
         st = check_cuda(cudaEventSynchronize(b->disp_done), "cudaEventSynchronize");
+    if (st != CFS_OK) return st;
+    std::string devkey;
+    st = device_key(b->device, &devkey);
     if (st != CFS_OK) return st;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     st = check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
@@ -573,53 +742,133 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, void* stream,
     const uint32_t full_iters = b->args.iters;
     if (trial_iters > 0)
         b->args.iters = std::min(full_iters, b->args.step_begin + std::max(trial_iters, 1u));
-    const ProgramSpec base = b->spec;
-    const bool tile_ok = base.scribble.empty() && base.splats.size() == 1 &&
-                         base.splats[0].kind == CFS_TARGET_HIST_U32;
-    const uint32_t base_cap = b->tile_cap ? b->tile_cap : (base.block >= 1024 ? 53248u : 8192u);
-    struct Cand { int ilp, tile; uint32_t chunk; float ms; };
-    std::vector<Cand> tried;
-    Cand best{base.ilp, base.tile, b->chunk, 1e30f};
-    const uint32_t chunks[] = {2048, 4096, 8192, 16384};
-    for (int tile = tile_ok ? 1 : 0; tile >= 0 && st == CFS_OK; --tile) {
-        for (int ilp = 1; ilp <= 2 && st == CFS_OK; ++ilp) {
-            b->spec = base;
-            b->spec.ilp = ilp;
-            b->spec.tile = tile;
-            b->spec.warp_agg = 0;
-            b->tile_cap = tile ? base_cap : 0;
-            b->spec.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
+    const bool retune = (flags & CFS_TUNE_RETUNE) != 0;
+    const bool win_ok = window_allowed(b->spec);
+    int trials = 0;
+    bool all_cached = true;
+
+    // shape classes: point-count bucket and target size
+    std::vector<std::string> cls(b->n_frames);
+    std::map<std::string, int> counts;
+    for (int f = 0; f < b->n_frames; ++f) {
+        cls[f] = frame_class(b->frames[f], b->n_targets);
+        counts[cls[f]]++;
+    }
+    std::ostringstream mix;
+    for (const auto& kv : counts) mix << kv.first << ":" << kv.second << ";";
+    const std::string skey = structure_key(b->spec);
+
+    // one timed trial of the current program and item plan (best of two)
+    auto trial = [&](const std::vector<uint8_t>* active, float* ms) -> cfs_status {
+        cfs_status r = plan_items(b, active);
+        float best = 1e30f;
+        for (int rep = 0; rep < 2 && r == CFS_OK; ++rep) {
+            r = run_direct(b, s, e0, e1);
+            if (r == CFS_OK) r = check_cuda(cudaEventSynchronize(e1), "trial");
+            float t = 0.0f;
+            if (r == CFS_OK) r = check_cuda(cudaEventElapsedTime(&t, e0, e1), "time");
+            best = std::min(best, t);
+        }
+        ++trials;
+        *ms = best;
+        return r;
+    };
+    auto set_all = [&](uint32_t chunk, uint8_t nowin) {
+        std::fill(b->chunks.begin(), b->chunks.end(), chunk);
+        std::fill(b->nowin.begin(), b->nowin.end(), nowin);
+    };
+
+    // ---- stage 1: the program, on the whole batch ------------------------
+    const std::string gkey = "batch|" + devkey + "|" + skey + "|" + mix.str();
+    cfs_batch_plan best = b->plan;
+    float best_ms = 0.0f;
+    std::string cached;
+    if (!retune && cache_get(gkey, &cached) && parse_plan(cached, &best) &&
+        check_plan(best) == CFS_OK) {
+        b->plan = best;
+        st = build_program(b);
+        set_all(best.chunk, 0);
+    } else {
+        all_cached = false;
+        set_all(best.chunk, 0);
+        st = build_program(b);
+        if (st == CFS_OK) st = trial(nullptr, &best_ms);
+        // one knob at a time, keeping each improvement
+        auto consider = [&](cfs_batch_plan cand) {
+            if (st != CFS_OK) return;
+            b->plan = cand;
             st = build_program(b);
-            for (uint32_t c : chunks) {
-                if (st != CFS_OK) break;
-                st = plan_items(b, c);
-                float ms = 1e30f;
-                for (int rep = 0; rep < 2 && st == CFS_OK; ++rep) {
-                    st = run_direct(b, s, e0, e1);
-                    if (st == CFS_OK) st = check_cuda(cudaEventSynchronize(e1), "trial");
-                    float t = 0.0f;
-                    if (st == CFS_OK) st = check_cuda(cudaEventElapsedTime(&t, e0, e1), "time");
-                    ms = std::min(ms, t);
-                }
-                if (st != CFS_OK) break;
-                tried.push_back({ilp, tile, c, ms});
-                if (ms < best.ms) best = {ilp, tile, c, ms};
+            set_all(cand.chunk, 0);
+            float ms = 0.0f;
+            if (st == CFS_OK) st = trial(nullptr, &ms);
+            if (st == CFS_OK && ms < best_ms) { best = cand; best_ms = ms; }
+        };
+        for (int ilp = 1; ilp <= 2; ++ilp)
+            if (ilp != best.ilp) { cfs_batch_plan c = best; c.ilp = ilp; consider(c); }
+        if (win_ok) {
+            { cfs_batch_plan c = best; c.window = 1 - best.window; consider(c); }
+            if (best.window) {
+                for (uint32_t w : {13312u, 26624u, 53248u})
+                    if (w != best.window_words) {
+                        cfs_batch_plan c = best; c.window_words = w; consider(c);
+                    }
+                { cfs_batch_plan c = best; c.warp_agg = 1 - best.warp_agg; consider(c); }
             }
         }
+        for (uint32_t c0 : {2048u, 4096u, 8192u, 16384u})
+            if (c0 != best.chunk) { cfs_batch_plan c = best; c.chunk = c0; consider(c); }
+        if (st == CFS_OK) {
+            cache_put(gkey, format_plan(best));
+            b->plan = best;
+            st = build_program(b);
+            set_all(best.chunk, 0);
+        }
     }
-    // keep the winner (or restore the starting point after an error)
-    b->spec = base;
+
+    // ---- stage 2: item size and window per shape class -------------------
+    int n_win = 0;
     if (st == CFS_OK) {
-        b->spec.ilp = best.ilp;
-        b->spec.tile = best.tile;
-        b->spec.warp_agg = 0;
-        b->tile_cap = best.tile ? base_cap : 0;
-        b->spec.dyn_smem = (int)(b->tile_cap * sizeof(uint32_t));
-    } else {
-        b->tile_cap = base.tile ? base_cap : 0;
+        cfs_batch_plan prog = b->plan;
+        prog.chunk = 0;                 // the program's knobs only
+        const std::string pkey = format_plan(prog);
+        std::vector<uint8_t> active(b->n_frames);
+        for (const auto& kv : counts) {
+            if (st != CFS_OK) break;
+            const std::string ckey = "class|" + devkey + "|" + skey + "|" + pkey + "|" + kv.first;
+            uint32_t c_best = b->plan.chunk;
+            uint8_t nw_best = 0;
+            std::string v;
+            if (!retune && cache_get(ckey, &v) && parse_class(v, &c_best, &nw_best)) {
+                // cached
+            } else {
+                all_cached = false;
+                for (int f = 0; f < b->n_frames; ++f) active[f] = cls[f] == kv.first;
+                float cls_best = 1e30f;
+                const int n_nw = (win_ok && b->plan.window) ? 2 : 1;
+                for (int nw = 0; nw < n_nw && st == CFS_OK; ++nw)
+                    for (uint32_t c0 : {2048u, 4096u, 8192u, 16384u}) {
+                        for (int f = 0; f < b->n_frames; ++f)
+                            if (active[f]) { b->chunks[f] = c0; b->nowin[f] = (uint8_t)nw; }
+                        float ms = 0.0f;
+                        st = trial(&active, &ms);
+                        if (st != CFS_OK) break;
+                        if (ms < cls_best) { cls_best = ms; c_best = c0; nw_best = (uint8_t)nw; }
+                    }
+                if (st == CFS_OK) cache_put(ckey, format_class(c_best, nw_best));
+            }
+            for (int f = 0; f < b->n_frames; ++f)
+                if (cls[f] == kv.first) { b->chunks[f] = c_best; b->nowin[f] = nw_best; }
+            if (!nw_best && b->spec.tile) ++n_win;
+        }
     }
-    cfs_status st2 = build_program(b);
-    if (st2 == CFS_OK) st2 = plan_items(b, st == CFS_OK ? best.chunk : 4096u);
+
+    // keep the result (or restore a consistent plan after an error)
+    if (st != CFS_OK) {
+        b->plan = best;
+        build_program(b);
+        set_all(b->plan.chunk, 0);
+    }
+    cfs_status st2 = plan_items(b);
     b->args.iters = full_iters;
     drop_graphs(b);                     // the next launch captures the new plan
     cudaEventDestroy(e0);
@@ -627,13 +876,66 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, void* stream,
     if (st != CFS_OK) return st;
     if (st2 != CFS_OK) return st2;
     if (out) {
-        out->ilp = best.ilp;
-        out->tile = best.tile;
-        out->chunk = best.chunk;
-        out->trial_ms = best.ms;
-        out->trials = (int)tried.size();
+        std::memset(out, 0, sizeof(*out));
+        out->ilp = b->plan.ilp;
+        out->tile = b->spec.tile;
+        out->chunk = b->plan.chunk;
+        out->trial_ms = best_ms;
+        out->trials = trials;
+        out->window_words = b->spec.tile ? b->plan.window_words : 0u;
+        out->warp_agg = b->spec.warp_agg;
+        out->n_classes = (int)counts.size();
+        out->classes_windowed = n_win;
+        out->from_cache = all_cached ? 1 : 0;
     }
     return CFS_OK;
+}
+
+cfs_status cfs_tune_cache_load(const char* path)
+{
+    clear_error();
+    if (!path) return fail(CFS_ERR_INVALID_ARG, "NULL path");
+    std::ifstream in(path);
+    if (!in) return CFS_OK;
+    std::map<std::string, std::string> got;
+    std::string line;
+    while (std::getline(in, line)) {
+        if (line.empty()) continue;
+        const size_t sp = line.rfind(' ');
+        if (sp == std::string::npos || sp == 0 || sp + 1 >= line.size())
+            return fail(CFS_ERR_INVALID_ARG, "malformed tuning-cache line: " + line);
+        got[line.substr(0, sp)] = line.substr(sp + 1);
+    }
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    for (auto& kv : got) g_cache[kv.first] = kv.second;
+    return CFS_OK;
+}
+
+cfs_status cfs_tune_cache_save(const char* path)
+{
+    clear_error();
+    if (!path) return fail(CFS_ERR_INVALID_ARG, "NULL path");
+    std::ofstream o(path, std::ios::trunc);
+    if (!o) return fail(CFS_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    for (const auto& kv : g_cache) o << kv.first << " " << kv.second << "\n";
+    o.flush();
+    if (!o) return fail(CFS_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    return CFS_OK;
+}
+
+cfs_status cfs_tune_cache_clear(void)
+{
+    clear_error();
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    g_cache.clear();
+    return CFS_OK;
+}
+
+uint32_t cfs_tune_cache_size(void)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    return (uint32_t)g_cache.size();
 }
 
 cfs_status cfs_batch_destroy(cfs_batch* b)

@@ -16,15 +16,7 @@
 
 namespace cfs {
 
-int trig_mode(uint32_t flags)
-{
-    int m = (flags & CFS_COMPOSE_FAST_TRIG) ? 1 : ((flags & CFS_COMPOSE_POLY_TRIG) ? 2 : 0);
-    if (const char* e = std::getenv("CFS_TRIG")) {
-        const int v = std::atoi(e);
-        if (v >= 0 && v <= 2) m = v;
-    }
-    return m;
-}
+int trig_mode(uint32_t flags) { return (flags & CFS_COMPOSE_FAST_TRIG) ? 1 : 0; }
 
 std::string ProgramSpec::key() const
 {

@@ -185,14 +185,7 @@ __device__ __forceinline__ void cfs_circle(float fid, float& x, float& y)
  *     Elementary Functions, 1980): k = rint(x / 2 pi), r = x - k C1 - k C2 -
  *     k C3 with 2 pi = C1 + C2 + C3 split so that k C1 is exact (C1 = 6.28125
  *     has 8 significant bits), then the hardware sine/cosine (__sinf,
- *     __cosf); absolute error about 4e-7 for |x| < 2^16;
- *  2: reduced to [-pi/4, pi/4] the same way with pi/2 = A + B + C (A and B
- *     with 12 significant bits, so j A and j B are exact for |j| < 2^12,
- *     C the float nearest the rest), then minimax polynomials (sin r = r +
- *     r^3 P(r^2), cos r = 1 - r^2/2 + r^4 Q(r^2), P and Q of degree 2, fitted
- *     here by weighted least squares iterated to equal ripple on [0, pi/4]:
- *     relative error 3.8e-9 and 1.2e-10) and the quadrant's signs; within
- *     1.5 ulp of the exact values for |x| <= 32, CUDA's sincosf beyond. */
+ *     __cosf); absolute error about 4e-7 for |x| < 2^16. */
 #ifndef CFS_FAST_TRIG
 #define CFS_FAST_TRIG 0
 #endif
@@ -205,40 +198,10 @@ __device__ __forceinline__ float cfs_reduce_2pi(float x)
     return r;
 }
 
-__device__ __forceinline__ void cfs_sincos_poly(float x, float* s, float* c)
-{
-    if (!(fabsf(x) <= 32.0f)) {       /* large or not finite */
-        sincosf(x, s, c);
-        return;
-    }
-    const float j = rintf(x * 0.63661974668502808f);      /* x / (pi / 2) */
-    float r = fmaf(-j, 1.5703125f, x);                      /* A */
-    r = fmaf(-j, 4.837512969970703e-4f, r);                 /* B */
-    r = fmaf(-j, 7.549790126404332e-8f, r);                 /* C */
-    const float r2 = r * r;
-    float p = fmaf(r2, -1.9515285384841263e-4f, 8.332161232829094e-3f);
-    p = fmaf(r2, p, -0.16666655242443085f);
-    const float sn = fmaf(r2 * r, p, r);
-    float q = fmaf(r2, 2.4433158614556305e-5f, -1.3887316454201937e-3f);
-    q = fmaf(r2, q, 4.166664555668831e-2f);
-    const float cs = fmaf(r2 * r2, q, fmaf(-0.5f * r, r, 1.0f));
-    const int quad = (int)j & 3;
-    float so = (quad & 1) ? cs : sn;
-    float co = (quad & 1) ? sn : cs;
-    if (quad & 2) so = -so;
-    if ((quad + 1) & 2) co = -co;
-    *s = so;
-    *c = co;
-}
-
 __device__ __forceinline__ float cfs_sin(float x)
 {
 #if CFS_FAST_TRIG == 1
     return __sinf(cfs_reduce_2pi(x));
-#elif CFS_FAST_TRIG == 2
-    float s, c;
-    cfs_sincos_poly(x, &s, &c);
-    return s;
 #else
     return sinf(x);
 #endif
@@ -248,10 +211,6 @@ __device__ __forceinline__ float cfs_cos(float x)
 {
 #if CFS_FAST_TRIG == 1
     return __cosf(cfs_reduce_2pi(x));
-#elif CFS_FAST_TRIG == 2
-    float s, c;
-    cfs_sincos_poly(x, &s, &c);
-    return c;
 #else
     return cosf(x);
 #endif
@@ -263,8 +222,6 @@ __device__ __forceinline__ void cfs_sincos(float x, float* s, float* c)
     const float r = cfs_reduce_2pi(x);
     *s = __sinf(r);
     *c = __cosf(r);
-#elif CFS_FAST_TRIG == 2
-    cfs_sincos_poly(x, s, c);
 #else
     sincosf(x, s, c);
 #endif

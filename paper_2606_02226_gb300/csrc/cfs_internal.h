@@ -66,7 +66,7 @@ struct ProgramSpec {
     int tile = 0;              // batch: privatized shared window for the first splat
     int warp_agg = 0;          // warp-aggregated shared atomics in that window
     int tile_reps = 1;         // at most this many copies of a small window
-    int fast_trig = 0;         // chain trigonometry: 0 libm, 1 hardware, 2 polynomial
+    int fast_trig = 0;         // chain trigonometry: 0 libm, 1 reduced argument + hardware
     int unroll = 4;            // copies of the step code in the step loop (4, 2, 1)
     int ilp = 1;               // batch: trajectories stepped together per thread (1, 2)
     int dyn_smem = 0;          // dynamic shared memory per CTA (bytes)
@@ -76,7 +76,7 @@ struct ProgramSpec {
 };
 
 std::string generate_source(const ProgramSpec& spec);
-// chain trigonometry of compose flags: 0 CUDA libm, 1 hardware, 2 polynomial
+// chain trigonometry of compose flags: 0 CUDA libm, 1 reduced argument + hardware
 int trig_mode(uint32_t flags);
 
 // ---- runtime: driver entry points, NVRTC, module cache ---------------------
@@ -108,9 +108,9 @@ cfs_status make_tmap_2d_bf16(CUtensorMap* map, const void* base, uint64_t cols, 
 cfs_status scribble_expand(const std::string& source, const std::string& poem, std::string* body,
                            std::vector<int>* splat_slots);
 
-// Launch shape of the persistent batch program (block, occupancy, privatized
-// window, warp aggregation, ILP; environment knobs); returns the window's
-// capacity in u32 counters and sets dyn_smem.
+// Launch shape of the persistent batch program under the default plan
+// (block, occupancy, privatized window, warp aggregation, ILP); returns the
+// window's capacity in u32 counters and sets dyn_smem.
 uint32_t batch_spec_defaults(ProgramSpec& sp);
 
 // ---- density-estimation display (cfs_display.cu) ---------------------------

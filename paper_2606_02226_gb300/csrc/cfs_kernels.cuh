@@ -497,6 +497,8 @@ __device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, in
     CfsTile tl{cnt, 0, 0, 0, 0, 1, 0, 0};
     const int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
     if (b.z < b.x || b.w < b.y || a.tile_cap < (u32)CFS_TILE_C) return tl;
+    /* the autotuner's choice for the frame's shape class: no window */
+    if (reinterpret_cast<const cfs_dev_frame*>(a.frames)[f].flags & CFS_FRAME_NO_WINDOW) return tl;
     const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* pixels */
     int ww = bw, wh = bh;
     if ((long long)bw * bh > cap) {

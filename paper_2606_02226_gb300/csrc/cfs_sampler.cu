@@ -96,12 +96,10 @@ constexpr u32 TC_WAIT_LIMIT = 1u << 24;
 constexpr int TC_COPIES = 16;   // copies of the bias-gradient sums (spread the atomics)
 
 __device__ unsigned int g_tc_error = 0;
-// chunk stages of the GEMM kernel: 0 = by the chunks a CTA runs (one stage
-// for at most two: four CTAs per SM then take all 512 row tiles of a
-// 65536-row GEMM in one wave, 0.48 vs 0.52 ms per training step; two
-// stages for the K-split weight gradients, whose CTAs run four chunks).
-// CFS_TC_STAGES = 1 or 2 forces one for sweeps.
-int g_tc_stages = 0;
+// chunk stages of the register-staged GEMM kernel: by the chunks a CTA runs
+// (one stage for at most two: four CTAs per SM then take all row tiles of a
+// GEMM in one wave; two stages for K-split weight gradients, whose CTAs run
+// four chunks).
 
 struct TcArgs {
     int M, N, K;                 // N in {64, 128}
@@ -1832,7 +1830,7 @@ cfs_status tc_gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda
     g.mode = mode; g.bias = bias; g.C = C; g.ldc = ldc; g.H = H; g.ldh = ldh;
     g.HT = HT; g.ldt = ldt; g.Zin = Zin; g.ldz = ldz; g.colsum = colsum;
     dim3 grid((M + TC_M - 1) / TC_M, 1, (K + g.k_split - 1) / g.k_split);
-    const int stages = g_tc_stages ? g_tc_stages : (g.k_split / TC_K <= 2 ? 1 : 2);
+    const int stages = g.k_split / TC_K <= 2 ? 1 : 2;
     if (stages == 1)
         tc_gemm_kernel<1><<<grid, TC_THREADS, tc_smem_bytes<1>(), st>>>(g);
     else
@@ -1841,20 +1839,12 @@ cfs_status tc_gemm(cudaStream_t st, int M, int N, int K, const bf16r* A, int lda
 }
 
 // row GEMM D[M][128] = A[M][K] W^T (K = 64 or 128) with the SILU or
-// SILU_GRAD epilogue on the persistent TMA kernel; CFS_TC_ROWS=0 runs it on
-// tc_gemm_kernel instead (the same epilogue; for comparison)
-int g_tc_rows = -1;
+// SILU_GRAD epilogue on the persistent TMA kernel (tc_gemm_kernel for
+// fewer rows than one tile)
 
 // whether row GEMMs of M rows run on tc_rows_kernel: then the backward
 // recomputes the pre-activations Z1 and Z2 and the forward need not store them
-bool rows_on_tma(int M)
-{
-    if (g_tc_rows < 0) {
-        const char* e = std::getenv("CFS_TC_ROWS");
-        g_tc_rows = (e && std::atoi(e) == 0) ? 0 : 1;
-    }
-    return g_tc_rows && M >= TC_M;
-}
+bool rows_on_tma(int M) { return M >= TC_M; }
 
 // A2, W2 (K2 = 64 or 128), bias2: SILU_GRAD with the pre-activation of the
 // layer below recomputed as A2 W2^T + bias2 instead of read from Zin (only
@@ -1906,18 +1896,12 @@ cfs_status tc_rows(cudaStream_t st, int M, int K, const bf16r* A, int lda, const
 }
 
 // weight gradient C[128][N] += A[128][K] B[N][K]^T on the split-K TMA kernel
-// (N = 128 or 64); CFS_TC_SPLITK=0 runs it on tc_gemm_kernel instead
-int g_tc_splitk = -1;
-
+// (N = 128 or 64)
 cfs_status tc_splitk(cudaStream_t st, int N, int K, const bf16r* A, int lda, const bf16r* Bm,
                      int ldb, float* C, int ldc)
 {
-    if (g_tc_splitk < 0) {
-        const char* e = std::getenv("CFS_TC_SPLITK");
-        g_tc_splitk = (e && std::atoi(e) == 0) ? 0 : 1;
-    }
     // fewer rows than one chunk: the register-staged kernel (as in tc_rows)
-    if (!g_tc_splitk || (K > 0 && K < TC_K)) {
+    if (K > 0 && K < TC_K) {
         const int splits = std::max(1, std::min(256, K / 256));
         return tc_gemm(st, HID, N, K, A, lda, Bm, ldb, EPI_ATOMIC, nullptr, C, ldc, nullptr, 0,
                        nullptr, 0, nullptr, 0, nullptr, splits);
@@ -2117,7 +2101,6 @@ cfs_status cfs_sampler_create(const float* params, uint64_t seed, cfs_sampler** 
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              tc_smem_bytes<2>()),
                         "cudaFuncSetAttribute(tc_gemm_kernel)");
-    if (const char* e = std::getenv("CFS_TC_STAGES")) g_tc_stages = std::atoi(e) == 1 ? 1 : 2;
     if (st == CFS_OK)
         st = check_cuda(cudaFuncSetAttribute(tc_rows_kernel<false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -54,27 +54,27 @@ def _host(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-@pytest.mark.parametrize("tile_cap,warp_agg,use_tile,ilp,iters",
-                         [("8192", "1", "1", "1", 60), ("256", "1", "1", "1", 60),
-                          ("1024", "0", "1", "1", 60), ("8192", "1", "0", "1", 60),
-                          ("8192", "1", "1", "2", 60), ("256", "1", "1", "2", 63),
-                          ("8192", "1", "0", "2", 61)])
-def test_batch_matches_oracle_frame_by_frame(torch_cuda, monkeypatch, tile_cap, warp_agg,
-                                             use_tile, ilp, iters):
-    # the privatized window at its default size, at a size smaller than most
-    # attractors (splats split between shared and global memory), without
-    # warp aggregation, and switched off; one or two trajectories per thread
-    # (with step counts that cut the last Philox block)
-    monkeypatch.setenv("CFS_TILE_CAP", tile_cap)
-    monkeypatch.setenv("CFS_WARP_AGG", warp_agg)
-    monkeypatch.setenv("CFS_TILE", use_tile)
-    monkeypatch.setenv("CFS_BATCH_ILP", ilp)
+@pytest.mark.parametrize("words,warp_agg,window,ilp,iters,chunk",
+                         [(8192, 1, 1, 1, 60, 4096), (1024, 1, 1, 1, 60, 4096),
+                          (1024, 0, 1, 1, 60, 64), (8192, 1, 0, 1, 60, 4096),
+                          (8192, 1, 1, 2, 60, 2048), (1024, 1, 1, 2, 63, 96),
+                          (8192, 1, 0, 2, 61, 4096), (53248, 0, 1, 2, 62, 16384)])
+def test_batch_matches_oracle_frame_by_frame(torch_cuda, words, warp_agg, window, ilp, iters,
+                                             chunk):
+    # plans passed through the C ABI: the privatized window at its default
+    # size, at a size smaller than most attractors (splats split between
+    # shared and global memory), without warp aggregation, and switched off;
+    # one or two trajectories per thread (with step counts that cut the last
+    # Philox block); items from 64 points to more than a frame
     frames = W.animation_frames(n_frames=14, seed=2, min_log2=8, max_log2=12,
                                 resolutions=(64, 128))
     cfs, chain, items, descs, tens = _setup(frames)
     b = cfs.Batch(chain, items, iters=iters, burn_in=20, seed=4)
+    b.set_plan(ilp=ilp, window=window, window_words=words, warp_agg=warp_agg, chunk=chunk)
+    assert b.plan() == {"ilp": ilp, "window": window, "window_words": words,
+                        "warp_agg": warp_agg, "chunk": chunk}
     info = b.info()
-    assert info["n_items"] >= len(frames) and info["grid"] >= 1
+    assert info["n_items"] >= len(frames) and info["grid"] >= 1 and info["chunk"] == chunk
     b.launch(clear=True)
     torch_cuda.cuda.synchronize()
     ref, rdisc = _oracle(frames, descs, iters, 20, 4)
@@ -82,6 +82,17 @@ def test_batch_matches_oracle_frame_by_frame(torch_cuda, monkeypatch, tile_cap, 
         assert np.array_equal(_host(tens[f]), ref[f]), f
         assert int(_host(tens[f]).sum()) == frames[f].n_points * (iters - 20)
     assert list(b.discards()[:, 0]) == rdisc == [0] * len(frames)
+
+
+def test_batch_plan_validation(torch_cuda):
+    frames = W.animation_frames(n_frames=2, seed=2, min_log2=8, max_log2=9, resolutions=(32,))
+    cfs, chain, items, descs, tens = _setup(frames)
+    b = cfs.Batch(chain, items, iters=30, burn_in=10, seed=1)
+    for bad in ({"ilp": 3}, {"window": 2}, {"window_words": 1000}, {"window_words": 60000},
+                {"warp_agg": 5}, {"chunk": 33}, {"chunk": 0}):
+        with pytest.raises(cfs.CfsError):
+            b.set_plan(**bad)
+    assert b.plan()["ilp"] == 2              # unchanged by the rejected plans
 
 
 def test_batch_graph_replay_clear_and_accumulate(torch_cuda):
@@ -177,19 +188,44 @@ def test_batch_start_points_and_step_begin(torch_cuda):
         begin += fr.n_points
 
 
-def test_batch_autotuner_keeps_results_exact(torch_cuda):
-    # tuning changes the plan (window, trajectories per thread, item size),
-    # never the frames: the tuned launch is still the oracle's, bit for bit
+def test_batch_autotuner_keeps_results_exact(torch_cuda, tmp_path):
+    # tuning changes the plan (program knobs, per-class item sizes and
+    # windows), never the frames: the tuned launch is still the oracle's, bit
+    # for bit; a second tune of the same batch takes every choice from the
+    # cache, which survives a save / clear / load round trip
     frames = W.animation_frames(n_frames=9, seed=6, min_log2=8, max_log2=12,
                                 resolutions=(64, 128))
     cfs, chain, items, descs, tens = _setup(frames)
+    cfs.tune_cache_clear()
     b = cfs.Batch(chain, items, iters=44, burn_in=20, seed=3)
     choice = b.tune(trial_iters=24)
     assert choice["trials"] >= 8 and choice["chunk"] in (2048, 4096, 8192, 16384)
     assert choice["ilp"] in (1, 2) and choice["tile"] in (0, 1) and choice["trial_ms"] > 0
+    assert choice["n_classes"] >= 2 and not choice["from_cache"]
+    assert choice["window_words"] in ((13312, 26624, 53248) if choice["tile"] else (0,))
     b.launch(clear=True)
     torch_cuda.cuda.synchronize()
     ref, rdisc = _oracle(frames, descs, 44, 20, 3)
     for f in range(len(frames)):
         assert np.array_equal(_host(tens[f]), ref[f]), f
     assert list(b.discards()[:, 0]) == rdisc
+    n = cfs.tune_cache_size()
+    assert n == 1 + choice["n_classes"]
+    path = str(tmp_path / "tune.txt")
+    cfs.tune_cache_save(path)
+    cfs.tune_cache_clear()
+    assert cfs.tune_cache_size() == 0
+    cfs.tune_cache_load(path)
+    assert cfs.tune_cache_size() == n
+    b2 = cfs.Batch(chain, items, iters=44, burn_in=20, seed=3)
+    again = b2.tune(trial_iters=24)
+    assert again["from_cache"] and again["trials"] == 0
+    for k in ("ilp", "tile", "chunk", "window_words", "warp_agg", "classes_windowed"):
+        assert again[k] == choice[k], k
+    b2.launch(clear=True)
+    torch_cuda.cuda.synchronize()
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), ref[f]), f
+    forced = b2.tune(trial_iters=24, retune=True)
+    assert not forced["from_cache"] and forced["trials"] >= 8
+    cfs.tune_cache_clear()

@@ -361,12 +361,12 @@ def test_invalid_arguments_report_errors(torch_cuda):
                    [cfs.alloc_target(t)], n_points=10, iters=5, burn_in=0)
 
 
-@pytest.mark.parametrize("trig", ["poly", "libm"])
+@pytest.mark.parametrize("trig", ["libm", "fast"])
 def test_chain_trigonometry_accuracy(torch_cuda, trig):
     """sin and cos of the chain (sinusoidal gives sin x, Eq. 2's stretch with
-    y = 0 gives -cos x) against float64 on a dense sweep: within 1.5 ulp for
-    the polynomial mode on |x| <= 32 and within 2 ulp beyond (CUDA's sincosf
-    there) and for CUDA's own functions."""
+    y = 0 gives -cos x) against float64 on a dense sweep: CUDA's own
+    functions within 2 ulp; the reduced-argument hardware mode within 1e-6
+    absolute for |x| <= 4000."""
     torch = torch_cuda
     cfs = _cfs()
     xs = np.concatenate([np.linspace(-32, 32, 200001), np.linspace(-4000, 4000, 20001),
@@ -378,7 +378,7 @@ def test_chain_trigonometry_accuracy(torch_cuda, trig):
     res = {}
     for name, ops in (("sin", [W.Op("sinusoidal"), W.Op("splat", (0,))]),
                       ("cos", [W.Op("stretch"), W.Op("splat", (0,))])):
-        ch = cfs.Chain(ops, 2, poly_trig=(trig == "poly"))
+        ch = cfs.Chain(ops, 2, fast_trig=(trig == "fast"))
         _, p, q = cfs.trace(cfs.System(ident), ch, ids, iters=1,
                             start=torch.from_numpy(start).cuda())
         assert np.array_equal(p.cpu().numpy()[:, 0, 0], xs)      # the identity map
@@ -386,12 +386,12 @@ def test_chain_trigonometry_accuracy(torch_cuda, trig):
         res[name] = v if name == "sin" else -v
     x64 = xs.astype(np.float64)
     for name, ref in (("sin", np.sin(x64)), ("cos", np.cos(x64))):
+        if trig == "fast":
+            assert np.abs(res[name].astype(np.float64) - ref).max() <= 1e-6, name
+            continue
         ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
         err = np.abs(res[name].astype(np.float64) - ref) / ulp
-        small = np.abs(xs) <= 32
-        bound = 1.5 if trig == "poly" else 2.0
-        assert err[small].max() <= bound, (name, err[small].max())
-        assert err[~small].max() <= 2.0, (name, err[~small].max())
+        assert err.max() <= 2.0, (name, err.max())
 
 
 # ---------------------------------------------------------------------------

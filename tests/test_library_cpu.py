@@ -39,6 +39,25 @@ def test_version_string():
     assert "sm_103a" in cfs.version()
 
 
+def test_tune_cache_files_need_no_gpu(tmp_path):
+    cfs.tune_cache_clear()
+    assert cfs.tune_cache_size() == 0
+    cfs.tune_cache_load(str(tmp_path / "missing.txt"))       # nothing there: nothing loaded
+    good = tmp_path / "cache.txt"
+    good.write_text("class|dev|prog|p16.w64x64 chunk=2048,nowin=0\n"
+                    "batch|dev|prog|p16.w64x64:3; ilp=2,win=1,words=53248,agg=0,chunk=4096\n")
+    cfs.tune_cache_load(str(good))
+    assert cfs.tune_cache_size() == 2
+    out = tmp_path / "out.txt"
+    cfs.tune_cache_save(str(out))
+    assert sorted(out.read_text().splitlines()) == sorted(good.read_text().splitlines())
+    bad = tmp_path / "bad.txt"
+    bad.write_text("no-value-here\n")
+    assert _err(lambda: cfs.tune_cache_load(str(bad))) == 1
+    cfs.tune_cache_clear()
+    assert cfs.tune_cache_size() == 0
+
+
 def test_device_error_injection_rejects_unknown_bits():
     # validated before any device access
     assert _err(lambda: cfs.debug_raise_device_error(0)) == 1

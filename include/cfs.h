@@ -191,6 +191,14 @@ cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chai
  *  |x| < 2^16 instead of about 1 ulp; several times fewer instructions.
  *  The generator maps are not affected. */
 #define CFS_COMPOSE_FAST_TRIG 1u
+/*  CFS_COMPOSE_FOLD_LINEAR -- every run of two or more consecutive linear
+ *  ops (AFFINE2/ROTATE2 on 2D points; AFFINE3/ROTATE3/TRANSLATE3 on 3D
+ *  points) runs as one affine op whose matrix and offset are the run's
+ *  product, formed in double from the ops' FP32 constants and rounded once
+ *  to FP32.  Positions then differ from op-by-op FP32 evaluation by a few
+ *  ulps (fewer roundings); op indices (cfs_chain_set_params, cfs_chain_info)
+ *  stay those of the ops as given. */
+#define CFS_COMPOSE_FOLD_LINEAR 4u
 cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint32_t flags,
                           cfs_chain** out);
 cfs_status cfs_chain_destroy(cfs_chain* chain);
@@ -219,7 +227,8 @@ cfs_status cfs_chain_destroy(cfs_chain* chain);
  * listed above; splat(SLOT) (a literal slot 0..3) splats into that target.
  * Expansion and argument errors are reported here (CFS_ERR_INVALID_ARG);
  * compile errors of the bodies at the first render (CFS_ERR_COMPILE, NVRTC
- * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG or 0. */
+ * log in cfs_last_error()).  flags: CFS_COMPOSE_FAST_TRIG or 0 (a poem's ops are
+ * its own code, so CFS_COMPOSE_FOLD_LINEAR does not apply). */
 cfs_status cfs_compose_scribble(int dim_in, const char* source, const char* poem,
                                 uint32_t flags, cfs_chain** out);
 /* Input dimension, op count (0 for a scribble chain) and splat count (the

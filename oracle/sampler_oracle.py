@@ -162,10 +162,15 @@ def noise(seed: int, n: int, step: int = 0):
 
 def conditioning(maps, t):
     """u[2:51] of a system: a b c d e f of each map (up to 8, zero after),
-    then t."""
+    then t.  The maps go in canonical order, decreasing |det A| = |a d - b c|
+    (float64 from the FP32 parameters), ties by index: an attractor does not
+    depend on the order in which its maps are listed."""
+    prm = [np.asarray(m, dtype=np.float32).astype(np.float64)[:6] for m in maps[:8]]
+    order = sorted(range(len(prm)), key=lambda k: (-abs(prm[k][0] * prm[k][3] -
+                                                        prm[k][1] * prm[k][2]), k))
     c = np.zeros(49)
-    for k, m in enumerate(maps[:8]):
-        c[6 * k:6 * k + 6] = np.asarray(m, dtype=np.float64)[:6]
+    for q, k in enumerate(order):
+        c[6 * q:6 * q + 6] = prm[k]
     c[48] = t
     return c
 

@@ -259,10 +259,10 @@ class Chain:
     """A composed transform chain (Section 3, Fig. 2B) for points of
     dimension ``dim_in``; ``ops`` are ``.kind`` / ``.params`` records."""
 
-    def __init__(self, ops, dim_in: int, fast_trig: bool = False):
+    def __init__(self, ops, dim_in: int, fast_trig: bool = False, fold_linear: bool = False):
         arr, n = _transforms(ops)
         h = _P()
-        flags = 1 if fast_trig else 0
+        flags = (1 if fast_trig else 0) | (4 if fold_linear else 0)
         _check(lib().cfs_compose_ex(dim_in, arr, n, flags, ctypes.byref(h)))
         self.fast_trig = fast_trig
         self.handle = h

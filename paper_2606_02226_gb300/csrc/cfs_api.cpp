@@ -77,6 +77,79 @@ void derive_op_params(const cfs_transform& op, float out[CFS_OP_PARAMS])
 }
 
 namespace {
+bool linear2(int k) { return k == CFS_OP_AFFINE2 || k == CFS_OP_ROTATE2; }
+bool linear3(int k)
+{
+    return k == CFS_OP_AFFINE3 || k == CFS_OP_ROTATE3 || k == CFS_OP_TRANSLATE3;
+}
+
+// x -> M x + t of a linear op (3D form; 2D ops act on x, y and keep z), from
+// the FP32 constants the kernels would use
+void op_matrix(const cfs_transform& op, double M[9], double t[3])
+{
+    float d[CFS_OP_PARAMS];
+    derive_op_params(op, d);
+    for (int j = 0; j < 9; ++j) M[j] = 0.0;
+    t[0] = t[1] = t[2] = 0.0;
+    if (linear2(op.kind)) {
+        const float* v = op.kind == CFS_OP_AFFINE2 ? op.params : d;
+        M[0] = v[0]; M[1] = v[1]; M[3] = v[2]; M[4] = v[3]; M[8] = 1.0;
+        if (op.kind == CFS_OP_AFFINE2) { t[0] = v[4]; t[1] = v[5]; }
+    } else {
+        const float* v = op.kind == CFS_OP_AFFINE3 ? op.params : d;
+        for (int j = 0; j < 9; ++j) M[j] = v[j];
+        for (int j = 0; j < 3; ++j) t[j] = v[9 + j];
+    }
+}
+}  // namespace
+
+void refresh_exec_ops(cfs_chain* c)
+{
+    c->n_xops = 0;
+    for (int o = 0; o < c->n_ops;) {
+        const int k = c->ops[o].kind;
+        int e = o + 1;
+        if (c->flags & CFS_COMPOSE_FOLD_LINEAR) {
+            while (e < c->n_ops && ((linear2(k) && linear2(c->ops[e].kind)) ||
+                                    (linear3(k) && linear3(c->ops[e].kind))))
+                ++e;
+        }
+        if (e - o < 2) {
+            c->xops[c->n_xops++] = c->ops[o];
+            o = e;
+            continue;
+        }
+        // compose in double: after op j, x -> M_j (...) + t_j
+        double M[9], t[3];
+        op_matrix(c->ops[o], M, t);
+        for (int j = o + 1; j < e; ++j) {
+            double N[9], u[3], P[9], w[3];
+            op_matrix(c->ops[j], N, u);
+            for (int r = 0; r < 3; ++r) {
+                for (int q = 0; q < 3; ++q)
+                    P[3 * r + q] = N[3 * r] * M[q] + N[3 * r + 1] * M[3 + q] + N[3 * r + 2] * M[6 + q];
+                w[r] = N[3 * r] * t[0] + N[3 * r + 1] * t[1] + N[3 * r + 2] * t[2] + u[r];
+            }
+            std::memcpy(M, P, sizeof(M));
+            std::memcpy(t, w, sizeof(t));
+        }
+        cfs_transform f;
+        std::memset(&f, 0, sizeof(f));
+        if (linear2(k)) {
+            f.kind = CFS_OP_AFFINE2;
+            const double v[6] = {M[0], M[1], M[3], M[4], t[0], t[1]};
+            for (int j = 0; j < 6; ++j) f.params[j] = (float)v[j];
+        } else {
+            f.kind = CFS_OP_AFFINE3;
+            for (int j = 0; j < 9; ++j) f.params[j] = (float)M[j];
+            for (int j = 0; j < 3; ++j) f.params[9 + j] = (float)t[j];
+        }
+        c->xops[c->n_xops++] = f;
+        o = e;
+    }
+}
+
+namespace {
 
 bool finite_all(const float* v, int n)
 {
@@ -188,15 +261,15 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     for (int j = 0; j < sys->n_maps; ++j) sp.map_kind[j] = sys->maps[j].kind;
     sp.n_cmp = sys->n_cmp;
     sp.reuse = reuse;
-    sp.n_ops = ch->n_ops;
+    sp.n_ops = ch->n_xops;
     sp.n_targets = n_tg;
     sp.fast_trig = trig_mode(ch->flags);
-    for (int o = 0; o < ch->n_ops; ++o) {
-        sp.op_kind[o] = ch->ops[o].kind;
-        if (ch->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)ch->ops[o].params[1];
-        if (ch->ops[o].kind == CFS_OP_BANDS) sp.op_axis[o] = (int)ch->ops[o].params[0];
-        if (ch->ops[o].kind == CFS_OP_SPLAT) {
-            const int slot = (int)ch->ops[o].params[0];
+    for (int o = 0; o < ch->n_xops; ++o) {
+        sp.op_kind[o] = ch->xops[o].kind;
+        if (ch->xops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)ch->xops[o].params[1];
+        if (ch->xops[o].kind == CFS_OP_BANDS) sp.op_axis[o] = (int)ch->xops[o].params[0];
+        if (ch->xops[o].kind == CFS_OP_SPLAT) {
+            const int slot = (int)ch->xops[o].params[0];
             SplatSpec s;
             s.slot = slot;
             s.kind = tg ? tg[slot].kind : CFS_TARGET_HIST_U32;
@@ -220,7 +293,7 @@ ProgramSpec make_spec(Mode mode, const cfs_system* sys, const cfs_chain* ch,
     // long chains (three objects from one point, 19 ops) ran 5% faster with two
     // copies of the step code than with four (instruction-cache misses); the
     // composed scene's 10 ops ran 2.5% faster with four
-    sp.unroll = ch->n_ops > 12 ? 2 : 4;
+    sp.unroll = ch->n_xops > 12 ? 2 : 4;
     return sp;
 }
 
@@ -234,7 +307,7 @@ void fill_args(cfs_launch_args* a, const cfs_system* sys, const cfs_chain* ch,
     a->sys.dim = sys->dim;
     for (int k = 0; k < sys->n_maps; ++k)
         for (int j = 0; j < 12; ++j) a->sys.prm[j][k] = sys->maps[k].params[j];
-    for (int o = 0; o < ch->n_ops; ++o) derive_op_params(ch->ops[o], a->op[o]);
+    for (int o = 0; o < ch->n_xops; ++o) derive_op_params(ch->xops[o], a->op[o]);
     for (int t = 0; t < n_tg; ++t) {
         const cfs_target& g = tg[t];
         cfs_dev_target& d = a->tg[t];
@@ -294,7 +367,7 @@ void fill_args_common(cfs_launch_args* a, const cfs_chain* ch, uint64_t seed, ui
                       uint32_t burn_in)
 {
     std::memset(a, 0, sizeof(*a));
-    for (int o = 0; o < ch->n_ops; ++o) derive_op_params(ch->ops[o], a->op[o]);
+    for (int o = 0; o < ch->n_xops; ++o) derive_op_params(ch->xops[o], a->op[o]);
     philox_round_keys(seed, a->rk);
     a->iters = iters;
     a->burn_in = burn_in;
@@ -398,7 +471,7 @@ cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint3
                           cfs_chain** out)
 {
     clear_error();
-    if (flags & ~(uint32_t)CFS_COMPOSE_FAST_TRIG) {
+    if (flags & ~(uint32_t)(CFS_COMPOSE_FAST_TRIG | CFS_COMPOSE_FOLD_LINEAR)) {
         if (out) *out = nullptr;
         return fail(CFS_ERR_INVALID_ARG, "unknown compose flags");
     }
@@ -448,6 +521,7 @@ cfs_status cfs_compose_ex(int dim_in, const cfs_transform* ops, int n_ops, uint3
     c->flags = flags;
     for (int o = 0; o < n_ops; ++o) c->ops[o] = ops[o];
     c->n_splat = n_splat;
+    refresh_exec_ops(c);
     *out = c;
     return CFS_OK;
 }
@@ -520,6 +594,7 @@ cfs_status cfs_chain_set_params(cfs_chain* chain, int index, const float* params
         if (!op_params_ok(t, dim, &why)) return fail(CFS_ERR_INVALID_ARG, why);
     }
     chain->ops[index] = t;
+    refresh_exec_ops(chain);
     return CFS_OK;
 }
 

@@ -477,15 +477,15 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     sp.n_maps = CFS_MAX_MAPS;
     for (int j = 0; j < CFS_MAX_MAPS; ++j) sp.map_kind[j] = s0->maps[0].kind;
     sp.n_cmp = max_cmp;
-    sp.n_ops = chain->n_ops;
+    sp.n_ops = chain->n_xops;
     sp.n_targets = n_targets;
     sp.fast_trig = trig_mode(chain->flags);
-    for (int o = 0; o < chain->n_ops; ++o) {
-        sp.op_kind[o] = chain->ops[o].kind;
-        if (chain->ops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)chain->ops[o].params[1];
-        if (chain->ops[o].kind == CFS_OP_BANDS) sp.op_axis[o] = (int)chain->ops[o].params[0];
-        if (chain->ops[o].kind == CFS_OP_SPLAT) {
-            const int slot = (int)chain->ops[o].params[0];
+    for (int o = 0; o < chain->n_xops; ++o) {
+        sp.op_kind[o] = chain->xops[o].kind;
+        if (chain->xops[o].kind == CFS_OP_ROTATE3) sp.op_axis[o] = (int)chain->xops[o].params[1];
+        if (chain->xops[o].kind == CFS_OP_BANDS) sp.op_axis[o] = (int)chain->xops[o].params[0];
+        if (chain->xops[o].kind == CFS_OP_SPLAT) {
+            const int slot = (int)chain->xops[o].params[0];
             SplatSpec ss;
             ss.slot = slot;
             ss.kind = frames[0].targets[slot].kind;

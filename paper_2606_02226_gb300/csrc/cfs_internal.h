@@ -25,6 +25,10 @@ struct cfs_chain {
     int n_ops = 0;
     uint32_t flags = 0;         // CFS_COMPOSE_*
     cfs_transform ops[CFS_MAX_OPS];
+    // the ops the kernels run: `ops`, or with CFS_COMPOSE_FOLD_LINEAR every
+    // run of consecutive linear ops folded into one affine op
+    int n_xops = 0;
+    cfs_transform xops[CFS_MAX_OPS];
     int n_splat = 0;
     // a chain written as a scribble poem (cfs_compose_scribble): the expanded
     // body with CFS_SCRIBBLE_SPLAT_i() for the i-th splat call, and its slots
@@ -144,6 +148,9 @@ cfs_status display_enqueue(const DisplayLayer* one, const DisplayLayer* layers, 
 // raise_: ORs bits into it (tests of the reporting path).
 cfs_status take_device_flags(unsigned int* flags);
 cfs_status raise_device_flags(unsigned int flags);
+
+// Recomputes chain->xops from chain->ops (after compose and set_params).
+void refresh_exec_ops(cfs_chain* chain);
 
 // ---- host-side tables ---------------------------------------------------
 void philox_round_keys(uint64_t seed, unsigned int rk[10][2]);

@@ -1583,7 +1583,17 @@ __device__ __forceinline__ u32 pack2(float lo, float hi)
     return (u32)to_bf16(lo) | ((u32)to_bf16(hi) << 16);
 }
 
-__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// SiLU for inference: z sigma(z) = z (1 + tanh(z / 2)) / 2 with the hardware
+// tanh (one special-function operation instead of an exponential and a
+// reciprocal; relative error about 2^-11, below the BF16 rounding of the
+// activation that follows)
+__device__ __forceinline__ float silu_fast(float z)
+{
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * z));
+    const float h = 0.5f * z;
+    return fmaf(h, t, h);
+}
 
 // c1 = W1[:, 2:51] u_cond + b1 with the BF16-rounded operands (one block
 // per frame)
@@ -2014,17 +2024,29 @@ cfs_status upload_params(cfs_sampler* s, const float* host)
     return check_cuda(cudaDeviceSynchronize(), "sampler params");
 }
 
+// The system's record: thresholds and maps in their own order (the chaos
+// game that makes training targets), and the conditioning vector with the
+// maps in canonical order -- decreasing |det A| = |a d - b c| (in double
+// from the FP32 parameters), ties by index -- because the attractor does
+// not depend on the order in which the maps are listed.
 void pack_system(const cfs_system* sys, float t, SysRec* r)
 {
     std::memset(r, 0, sizeof(*r));
     for (int j = 0; j < sys->n_cmp; ++j) r->T[j] = sys->T[j];
     r->n_cmp = sys->n_cmp;
     r->n_maps = sys->n_maps;
-    for (int k = 0; k < sys->n_maps && k < MAX_SYS_MAPS; ++k)
-        for (int j = 0; j < 6; ++j) {
-            r->prm[k][j] = sys->maps[k].params[j];
-            r->cond[6 * k + j] = sys->maps[k].params[j];
-        }
+    const int n = std::min(sys->n_maps, MAX_SYS_MAPS);
+    int order[MAX_SYS_MAPS];
+    double adet[MAX_SYS_MAPS];
+    for (int k = 0; k < n; ++k) {
+        const float* v = sys->maps[k].params;
+        order[k] = k;
+        adet[k] = std::fabs((double)v[0] * (double)v[3] - (double)v[1] * (double)v[2]);
+        for (int j = 0; j < 6; ++j) r->prm[k][j] = v[j];
+    }
+    std::stable_sort(order, order + n, [&](int a, int b) { return adet[a] > adet[b]; });
+    for (int q = 0; q < n; ++q)
+        for (int j = 0; j < 6; ++j) r->cond[6 * q + j] = sys->maps[order[q]].params[j];
     r->t = t;
 }
 

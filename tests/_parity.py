@@ -123,3 +123,81 @@ def check_depth_close(g, o, rel=1e-5, min_decided=0.2):
     return n_dec
 
 
+
+
+def merge_tracked(parts):
+    """Combines tracked oracle results of disjoint point ranges (lists of
+    TargetResult, one list per part) into the result of the whole range:
+    counts and sums add, depth keys and depth bounds take the minimum, and
+    the lowest depth of another colour follows from each part's lowest key
+    (every candidate of a part is at least as deep as that part's lowest)."""
+    out = []
+    for j in range(len(parts[0])):
+        rs = [p[j] for p in parts]
+        r = O.TargetResult(rs[0].buf.copy(), None if rs[0].amb is None else rs[0].amb.copy(),
+                           None if rs[0].zlo is None else rs[0].zlo.copy(),
+                           None if rs[0].zhi is None else rs[0].zhi.copy(),
+                           None if rs[0].klo is None else rs[0].klo.copy(),
+                           None if rs[0].zalt is None else rs[0].zalt.copy())
+        r.n_splat, r.n_discard, r.n_amb = rs[0].n_splat, rs[0].n_discard, rs[0].n_amb
+        for b in rs[1:]:
+            if r.buf.dtype == np.uint64:
+                np.minimum(r.buf, b.buf, out=r.buf)
+            else:
+                r.buf += b.buf
+            r.n_splat += b.n_splat
+            r.n_discard += b.n_discard
+            r.n_amb += b.n_amb
+            if r.amb is not None:
+                r.amb += b.amb
+            if r.zlo is not None:
+                np.minimum(r.zlo, b.zlo, out=r.zlo)
+                np.minimum(r.zhi, b.zhi, out=r.zhi)
+                ka, kb = r.klo, b.klo
+                col = np.uint64(0xFFFFFFFF)
+                same = (ka & col) == (kb & col)
+                da = np.where(ka == EMPTY, np.inf, depth_of(ka)).astype(np.float32)
+                db = np.where(kb == EMPTY, np.inf, depth_of(kb)).astype(np.float32)
+                alt = np.where(same, np.minimum(r.zalt, b.zalt),
+                               np.where(ka < kb, np.minimum(r.zalt, db),
+                                        np.minimum(b.zalt, da)))
+                alt = np.where(kb == EMPTY, r.zalt, np.where(ka == EMPTY, b.zalt, alt))
+                r.zalt = alt.astype(np.float32)
+                r.klo = np.minimum(ka, kb)
+        out.append(r)
+    return out
+
+
+def _oracle_worker(args):
+    wl, jobs, margin_px, track, band_eps = args
+    res = None
+    for job in jobs:
+        res = O.render(job.system, wl.chain, wl.targets, n_points=job.n_points, iters=wl.iters,
+                       burn_in=wl.burn_in, seed=wl.seed, system_id=job.system_id,
+                       point_begin=job.point_begin, margin_px=margin_px, track=track,
+                       prev=res, band_eps=band_eps)
+    return res
+
+
+def split_jobs(wl, parts):
+    """The workload's jobs cut into `parts` lists of disjoint point ranges."""
+    out = [[] for _ in range(parts)]
+    for job in wl.jobs:
+        per = -(-job.n_points // parts)
+        for p in range(parts):
+            b = p * per
+            n = min(per, job.n_points - b)
+            if n > 0:
+                out[p].append(W.RenderJob(job.system, job.point_begin + b, n, job.system_id))
+    return [o for o in out if o]
+
+
+def oracle_render_parallel(wl, workers, margin_px=0.0, track=False, band_eps=0.0):
+    """The oracle's render of ``wl`` on ``workers`` spawned processes over
+    disjoint point ranges, merged (spawn: a forked child of a process that
+    holds a GPU context can hang)."""
+    import multiprocessing as mp
+    chunks = split_jobs(wl, workers)
+    with mp.get_context("spawn").Pool(len(chunks)) as pool:
+        parts = pool.map(_oracle_worker, [(wl, c, margin_px, track, band_eps) for c in chunks])
+    return merge_tracked(parts)

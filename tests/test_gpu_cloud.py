@@ -38,7 +38,7 @@ def test_cloud_generation_bit_exact(torch_cuda, n, iters):
     assert np.array_equal(fn.cpu().numpy(), ofn)
 
 
-def _stream_parity(frame, n, W_, fast_trig=False):
+def _stream_parity(frame, n, W_, fast_trig=False, fold=False):
     torch = pytest.importorskip("torch")
     cfs = _cfs()
     sysd = W.cloud_system()
@@ -49,7 +49,8 @@ def _stream_parity(frame, n, W_, fast_trig=False):
     disc = torch.zeros(1, dtype=torch.int64, device="cuda")
     xyz = torch.from_numpy(np.ascontiguousarray(ox.T)).cuda()
     fn = torch.from_numpy(ofn).cuda()
-    cfs.render_points(cfs.Chain(chain, 3, fast_trig=fast_trig), xyz, fn, [t], [ten], discards=disc)
+    cfs.render_points(cfs.Chain(chain, 3, fast_trig=fast_trig, fold_linear=fold), xyz, fn, [t],
+                      [ten], discards=disc)
     torch.cuda.synchronize()
     g = ten.cpu().numpy().view(np.uint64)
     # margin: the position tolerance in pixels (the [-1, 1] view has W/2
@@ -63,10 +64,13 @@ def _stream_parity(frame, n, W_, fast_trig=False):
     return g, o
 
 
-@pytest.mark.parametrize("frame,fast_trig", [(0, False), (21, False), (63, False), (0, True),
-                                             (63, True)])
-def test_cloud_streaming_parity(torch_cuda, frame, fast_trig):
-    _stream_parity(frame, 1 << 15, 512, fast_trig=fast_trig)
+@pytest.mark.parametrize("frame,fast_trig,fold", [(0, False, False), (21, False, False),
+                                                  (63, False, False), (0, True, False),
+                                                  (63, True, False), (0, False, True),
+                                                  (40, True, True)])
+def test_cloud_streaming_parity(torch_cuda, frame, fast_trig, fold):
+    # fold: the four affines and the camera translation run as one affine op
+    _stream_parity(frame, 1 << 15, 512, fast_trig=fast_trig, fold=fold)
 
 
 def test_render_points_needs_multiple_of_4(torch_cuda):

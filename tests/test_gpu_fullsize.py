@@ -1,0 +1,98 @@
+"""Whole-image parity at the benchmark's sizes, against the oracle run on
+every host core (spawned processes over disjoint point ranges, records
+merged).
+
+  * Batched animation frames of 2^18-2^20 points at 1024^2 and 2048^2 (four
+    channels), rendered in one persistent launch under the plan the
+    autotuner picks for the 256-frame animation (16384-point items, the
+    53248-word privatized window, two trajectories per thread), where large
+    frames spill most of their splats past the window to L2 reductions:
+    bit-exact, frame by frame, with exact discard counts.
+  * One 2^20-point x 500-step frame of the composed scene at 2048^2 (FP32
+    RGBA and depth+colour layers): every bin within its near-edge slack,
+    L1 <= 1e-5 of the total, exact colours on decided depth pixels.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_02226_gb300 import workloads as W
+
+from _parity import (EMPTY, check_depth_close, check_rgba_close, fixed_margin, gpu_render,
+                     oracle_render_parallel)
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+WORKERS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _bench_frames():
+    """Three 1024^2 and two 2048^2 frames of the benchmark animation with
+    2^18..2^20 points each."""
+    pick, n1024, n2048 = [], 0, 0
+    for fr in W.animation_frames(n_frames=256, seed=0):
+        if not (1 << 18) <= fr.n_points <= (1 << 20):
+            continue
+        if fr.W == 1024 and n1024 < 3:
+            pick.append(fr)
+            n1024 += 1
+        elif fr.W == 2048 and n2048 < 2:
+            pick.append(fr)
+            n2048 += 1
+    assert len(pick) == 5
+    return pick
+
+
+def test_batch_at_bench_size_bit_exact(torch_cuda):
+    torch = torch_cuda
+    from paper_2606_02226_gb300 import cfs
+    frames = _bench_frames()
+    chain_ops = [W.Op("splat", (0,))]
+    chain = cfs.Chain(chain_ops, 2)
+    items, tens, jobs, begin = [], [], [], 0
+    for f, fr in enumerate(frames):
+        t = W.animation_target(fr.W)
+        ten = cfs.alloc_target(t)
+        items.append((cfs.System(fr.system), fr.n_points, begin, f, [t], [ten]))
+        tens.append(ten)
+        jobs.append(W.RenderJob(fr.system, begin, fr.n_points, f))
+        begin += fr.n_points
+    b = cfs.Batch(chain, items, iters=300, burn_in=20, seed=0)
+    b.set_plan(ilp=2, window=1, window_words=53248, warp_agg=0, chunk=16384)
+    b.launch(clear=True)
+    torch.cuda.synchronize()
+    disc = b.discards()[:, 0]
+    for f, (fr, job) in enumerate(zip(frames, jobs)):
+        wl = W.Workload("frame", [job], chain_ops, [W.animation_target(fr.W)], 300, 20, 0)
+        o = oracle_render_parallel(wl, WORKERS)[0]
+        g = tens[f].cpu().numpy().view(np.uint32)
+        assert np.array_equal(g, o.buf), f
+        assert int(disc[f]) == o.n_discard == 0, f
+        assert int(g.sum(dtype=np.uint64)) == fr.n_points * 280, f
+        print(f"frame {f}: {fr.n_points} points at {fr.W}^2, bit-exact")
+
+
+def test_composed_whole_image_2048(torch_cuda):
+    wl = W.composed_render(n_points=1 << 20, iters=500, W=2048)
+    margin = fixed_margin(wl.targets, POS_TOL)
+    g, disc = gpu_render(wl)
+    o = oracle_render_parallel(wl, WORKERS, margin_px=margin, track=True)
+    total = (1 << 20) * 480
+    assert int(round(float(g[0][..., 3].sum(dtype=np.float64)))) + disc[0] == total
+    assert o[0].n_splat + o[0].n_discard == total
+    assert abs(disc[1] - o[1].n_discard) <= o[1].n_amb
+    check_rgba_close(g[0], o[0].buf, o[0].amb, total, rel_l1=1e-5)
+    d = np.abs(g[0][..., 3].astype(np.float64) - o[0].buf[..., 3].astype(np.float64)).sum()
+    print(f"RGBA alpha L1: {d:.0f} of {total} splats ({d / total:.2e})")
+    check_depth_close(g[1], o[1])
+    assert (g[1] != EMPTY).sum() > 100000

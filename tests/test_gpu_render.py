@@ -166,6 +166,25 @@ def _check_trace(g, o, exact_p=True):
     return float(d.max()) if d.size else 0.0
 
 
+def test_folded_linear_ops_trace_parity(torch_cuda):
+    """CFS_COMPOSE_FOLD_LINEAR: the 3D branch's rotation and translation (and
+    a run of 2D affines) run as one affine op; traced positions stay within
+    the position bar of the oracle's op-by-op evaluation."""
+    cfs = _cfs()
+    wl = W.composed_render(n_points=1 << 12, iters=48, W=256)
+    chain = [W.Op("affine2", (0.9, -0.2, 0.3, 0.8, 0.05, -0.1)), W.Op("rotate2", (0.4,)),
+             W.Op("affine2", (1.1, 0.0, 0.1, 0.95, 0.0, 0.02))] + wl.chain
+    for job in wl.jobs:
+        ids = job.point_begin + np.array([0, 3, 1000, job.n_points - 1], dtype=np.uint32)
+        torch = torch_cuda
+        k, p, q = cfs.trace(cfs.System(job.system), cfs.Chain(chain, 2, fold_linear=True),
+                            torch.from_numpy(ids.view(np.int32)).cuda(), iters=wl.iters)
+        ko, po, qo = O.trace(job.system, chain, ids, iters=wl.iters)
+        worst = _check_trace((k.cpu().numpy(), p.cpu().numpy(), q.cpu().numpy()),
+                             (ko, po, qo))
+        print(f"folded chain: largest traced position difference {worst:.2e}")
+
+
 def test_composed_trace_parity(torch_cuda):
     wl = W.composed_render(n_points=1 << 12, iters=64, W=256)
     for job in wl.jobs:

@@ -58,6 +58,22 @@ def test_tune_cache_files_need_no_gpu(tmp_path):
     assert cfs.tune_cache_size() == 0
 
 
+def test_fold_linear_runs_one_affine_op():
+    # the cloud chain's four affines and camera translation become one op in
+    # the generated program; op indices for animation stay the user's
+    ops = W.cloud_chain(3)
+    t = W.cloud_target(64)
+    s = cfs.System(W.cloud_system())
+    plain, _ = cfs.codegen_check(s, cfs.Chain(ops, 3), [t], mode=4)
+    c = cfs.Chain(ops, 3, fold_linear=True)
+    folded, _ = cfs.codegen_check(s, c, [t], mode=4)
+    assert plain.count("cfs_affine3(") == 4 and folded.count("cfs_affine3(") == 1
+    assert "cfs_translate" not in folded or folded.count("cfs_translate") < plain.count("cfs_translate")
+    c.set_params(0, ops[0].params)       # twist, still op 0
+    c.set_params(5, ops[5].params)       # an affine inside the folded run
+    assert _err(lambda: c.set_params(11, (0.0,))) == 1
+
+
 def test_device_error_injection_rejects_unknown_bits():
     # validated before any device access
     assert _err(lambda: cfs.debug_raise_device_error(0)) == 1

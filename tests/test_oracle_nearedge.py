@@ -25,7 +25,8 @@ from oracle import oracle as O
 from paper_2606_02226_gb300 import workloads as W
 
 sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
-from _parity import EMPTY, check_depth_close, check_hist_close  # noqa: E402
+from _parity import (EMPTY, check_depth_close, check_hist_close, merge_tracked,  # noqa: E402
+                     oracle_render, split_jobs, _oracle_worker)
 
 M = 0.01          # margin in pixels
 SPLAT = [W.Op("splat", (0,))]
@@ -335,3 +336,23 @@ def test_hist_checker_rejects_moves_beyond_the_slack():
     g[0, free[0], free[1]] += 1          # a moved splat where no edge is near
     with pytest.raises(AssertionError):
         check_hist_close(g, r.buf, r.amb, n)
+
+
+# ---------------------------------------------------------------------------
+# records of disjoint point ranges merge into the records of the whole range
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("parts", [2, 3])
+def test_merged_records_equal_one_process(parts):
+    wl = W.composed_render(n_points=1201, iters=40, W=48)
+    m = 0.05
+    whole = oracle_render(wl, margin_px=m, track=True)
+    merged = merge_tracked([_oracle_worker((wl, c, m, True, 0.0))
+                            for c in split_jobs(wl, parts)])
+    for a, b in zip(whole, merged):
+        assert np.array_equal(a.buf, b.buf)
+        assert (a.n_splat, a.n_discard, a.n_amb) == (b.n_splat, b.n_discard, b.n_amb)
+        assert np.array_equal(a.amb, b.amb)
+        if a.zlo is not None:
+            for k in ("zlo", "zhi", "klo", "zalt"):
+                assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    assert whole[1].n_amb > 0 and np.isfinite(whole[1].zalt).sum() > 100

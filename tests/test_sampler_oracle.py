@@ -157,3 +157,16 @@ def test_noise_is_standard_gaussian():
     assert abs(z.var() - 1.0) < 5 * math.sqrt(2 / 8000)
     # the two components of a Box-Muller pair are uncorrelated
     assert abs(np.corrcoef(z[:, 0], z[:, 1])[0, 1]) < 5 / math.sqrt(4000)
+
+
+def test_conditioning_orders_maps_by_determinant():
+    # |det| 0.06, 0.25, 0.0, 0.25: canonical order 1, 3 (tie: by index), 0, 2
+    maps = [(0.2, 0.0, 0.0, 0.3, 1.0, 2.0), (0.5, 0.0, 0.0, 0.5, 3.0, 4.0),
+            (0.0, 0.0, 0.0, 0.0, 5.0, 6.0), (0.0, 0.5, -0.5, 0.0, 7.0, 8.0)]
+    c = S.conditioning(maps, 0.75)
+    f = [np.float32(m).astype(np.float64) for m in maps]      # the FP32 parameters
+    assert np.array_equal(c[0:6], f[1]) and np.array_equal(c[6:12], f[3])
+    assert np.array_equal(c[12:18], f[0]) and np.array_equal(c[18:24], f[2])
+    assert np.all(c[24:48] == 0) and c[48] == 0.75
+    # the order of listing does not change the conditioning
+    assert np.array_equal(S.conditioning([maps[2], maps[0], maps[1], maps[3]], 0.75), c)

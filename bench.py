@@ -25,6 +25,7 @@ import threading
 import time
 
 import numpy as np
+from typing import Optional
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -446,7 +447,9 @@ def run_cfs(args, wl):
     if args.batch and single:
         line["batch"] = bench_batch(torch, cfs, dev, stream, n_frames=args.batch_frames)
     if args.sampler and single:
-        line["sampler"] = bench_sampler(torch, cfs, dev, stream, train_steps=args.sampler_steps)
+        line["sampler"] = bench_sampler(torch, cfs, dev, stream, train_steps=args.sampler_steps,
+                                        lr_final=args.sampler_lr_final or None,
+                                        pairs=args.sampler_pairs)
     if args.space and single:
         line["space"] = bench_space(torch, cfs, dev, stream)
     if args.cloud and single:
@@ -767,7 +770,8 @@ def _l1(torch, h, ref):
 
 def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames: int = 16,
                   n_eval: int = 1 << 20, batch_frames: int = 256,
-                  unique_options=(4096, 65536, 0), pairs: int = 12):
+                  unique_options=(4096, 65536, 0), pairs: int = 12,
+                  lr_final: Optional[float] = None):
     """Learned warm start (form 4) against plain burn-in at equal L1 error.
 
     Training: 4096 systems of the animation family (seed 1, disjoint from the
@@ -796,7 +800,7 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hist = smp.train(systems, tvals, train_steps, systems_per_step=64, points_per_system=1024,
-                     n_proj=64, lr=1e-3, seed=1, stream=stream)
+                     n_proj=64, lr=1e-3, lr_final=lr_final, seed=1, stream=stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
 
@@ -837,6 +841,8 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
     mb = {b: float(np.mean(v)) for b, v in ex_b.items()}
     b_min = next((b for b in bs if mb[b] <= 1e-3), None)
     out = {"train_steps": train_steps, "train_s": train_s,
+           "lr": {"start": 1e-3, "final": lr_final if lr_final is not None else 1e-3,
+                  "schedule": "cosine" if lr_final is not None else "constant"},
            "train_ms_per_step": 1e3 * train_s / max(train_steps, 1),
            "loss_first": float(np.mean(hist[:20])), "loss_last": float(np.mean(hist[-20:])),
            "eval_frames": eval_frames, "eval_points": n_eval, "l1_resolution": 1024,
@@ -986,6 +992,10 @@ def main():
     ap.add_argument("--no-sampler", dest="sampler", action="store_false",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--sampler-steps", type=int, default=20000)
+    ap.add_argument("--sampler-lr-final", type=float, default=1e-5,
+                    help="cosine decay of the sampler's step size from 1e-3 to this (0: constant)")
+    ap.add_argument("--sampler-pairs", type=int, default=12,
+                    help="interleaved plain/warm batch timings")
     ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--cloud-frames", type=int, default=64)
     ap.add_argument("--cloud-points", type=int, default=1 << 26)

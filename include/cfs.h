@@ -504,6 +504,24 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
                              uint32_t systems_per_step, uint32_t points_per_system,
                              uint32_t n_proj, float lr, uint64_t seed, float* loss_history,
                              void* stream);
+/* As cfs_sampler_train, with the run's settings in a struct and a
+ * learning-rate schedule: step i of the run (0-based, of `steps`) uses
+ * lr_final + (lr - lr_final) (1 + cos(pi i / (steps - 1))) / 2, a cosine
+ * decay from lr to lr_final (lr_final == lr: constant, as cfs_sampler_train).
+ * Both rates positive and finite, else CFS_ERR_INVALID_ARG. */
+typedef struct {
+    uint32_t steps;
+    uint32_t systems_per_step;
+    uint32_t points_per_system;   /* power of two in 32..1024 */
+    uint32_t n_proj;
+    float lr;
+    float lr_final;
+    uint64_t seed;
+} cfs_train_options;
+cfs_status cfs_sampler_train_ex(cfs_sampler* s, const cfs_system* const* systems,
+                                const float* t_values, int n_systems,
+                                const cfs_train_options* options, float* loss_history,
+                                void* stream);
 /* Warm-start points for `sys` at frame time t: n network outputs on noise
  * drawn from (seed) -- Box-Muller on Philox4x32-10 blocks (row, 0, 0, 3)
  * with key (seed lo, seed hi) -- written SoA to start (device f32 [2][n]),

@@ -88,6 +88,12 @@ class cfs_batch_plan(ctypes.Structure):
                 ("chunk", ctypes.c_uint32)]
 
 
+class cfs_train_options(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("systems_per_step", ctypes.c_uint32),
+                ("points_per_system", ctypes.c_uint32), ("n_proj", ctypes.c_uint32),
+                ("lr", ctypes.c_float), ("lr_final", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 class cfs_display_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_float), ("brightness", ctypes.c_float),
                 ("a_max", ctypes.c_float), ("background", ctypes.c_uint32)]
@@ -164,6 +170,8 @@ _SIGNATURES = {
                                          ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint32, ctypes.c_float, ctypes.c_uint64, _P,
                                          _P]),
+    "cfs_sampler_train_ex": (ctypes.c_int, [_P, ctypes.POINTER(_P), _P, ctypes.c_int,
+                                            ctypes.POINTER(cfs_train_options), _P, _P]),
     "cfs_sampler_start_points": (ctypes.c_int, [_P, _P, ctypes.c_float, ctypes.c_uint32,
                                                 ctypes.c_uint64, _P, _P]),
     "cfs_render_batch_noalloc": (ctypes.c_int, [ctypes.POINTER(cfs_frame), ctypes.c_int,
@@ -692,15 +700,24 @@ class Sampler:
 
     def train(self, systems, t_values, steps: int, *, systems_per_step: int = 64,
               points_per_system: int = 1024, n_proj: int = 64, lr: float = 1e-3,
-              seed: int = 0, stream=None):
-        """systems: list of System handles; returns the loss per step."""
+              lr_final: Optional[float] = None, seed: int = 0, stream=None):
+        """systems: list of System handles; returns the loss per step.
+        ``lr_final``: cosine decay of the step size from ``lr`` to it over
+        the run (None: constant ``lr``)."""
         arr = (_P * len(systems))(*[s.handle for s in systems])
         tv = np.ascontiguousarray(t_values, np.float32)
         hist = np.zeros(max(steps, 1), np.float32)
-        _check(lib().cfs_sampler_train(self.handle, arr, _fptr(tv), len(systems), steps,
-                                       systems_per_step, points_per_system, n_proj, lr,
-                                       int(seed) & 0xFFFFFFFFFFFFFFFF, _fptr(hist),
-                                       _stream_handle(stream)))
+        if lr_final is None:
+            _check(lib().cfs_sampler_train(self.handle, arr, _fptr(tv), len(systems), steps,
+                                           systems_per_step, points_per_system, n_proj, lr,
+                                           int(seed) & 0xFFFFFFFFFFFFFFFF, _fptr(hist),
+                                           _stream_handle(stream)))
+        else:
+            o = cfs_train_options(steps, systems_per_step, points_per_system, n_proj, lr,
+                                  lr_final, int(seed) & 0xFFFFFFFFFFFFFFFF)
+            _check(lib().cfs_sampler_train_ex(self.handle, arr, _fptr(tv), len(systems),
+                                              ctypes.byref(o), _fptr(hist),
+                                              _stream_handle(stream)))
         return hist[:steps]
 
     def start_points(self, system: System, t: float, n: int, seed: int = 0, out=None,

@@ -1386,14 +1386,26 @@ __device__ __forceinline__ void store_bf16_weight(bf16r* wb, bf16r* wbT, int i, 
     }
 }
 
+// Step size of a training run of `total` steps that started at step `first`:
+// cosine decay from lr to lr_final (Loshchilov & Hutter's schedule without
+// restarts); lr_final == lr keeps it constant.
+__device__ __forceinline__ float lr_at(u32 step, u32 first, u32 total, float lr, float lr_final)
+{
+    if (lr_final == lr || total < 2) return lr;
+    const float x = fminf(1.0f, (float)(step - first) / (float)(total - 1));
+    return lr_final + 0.5f * (lr - lr_final) * (1.0f + cosf(3.14159265358979f * x));
+}
+
 __global__ void __launch_bounds__(256) adam_kernel(float* w, float* m, float* v,
                                                    const float* g, bf16r* wb, bf16r* wbT, int n,
-                                                   const u32* step, u32 t_explicit, float lr,
+                                                   const u32* step, u32 t_explicit, float lr0,
+                                                   float lr_final, u32 first, u32 total,
                                                    float b1, float b2, float eps)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const u32 t = step ? (*step + 1u) : t_explicit;
+    const float lr = step ? lr_at(*step, first, total, lr0, lr_final) : lr0;
     const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
     const float gi = g[i];
     const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
@@ -1540,49 +1552,24 @@ __global__ void gather_loss_kernel(const float* loss, const u32* step, u32 first
 }
 
 
-// warp-level BF16 fragments for the fused inference (small per-point
-// products that stay in registers): ldmatrix x4 and mma.sync m16n8k16
-__device__ __forceinline__ void ldsm_x4(u32 (&r)[4], const void* p)
-{
-    const u32 a = (u32)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const u32 (&a)[4], u32 b0, u32 b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
-        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // ---------------------------------------------------------------------------
-// fused inference: start points of one system straight from noise.
+// fused inference on the tensor cores: start points of many frames straight
+// from noise, 128 rows (points) per tile.
 // Layer 1 is a rank-2 update: only the noise varies from row to row, so
 // z1 = c1 + W1[:, 0] n0 + W1[:, 1] n1 with c1 = W1[:, 2:51] u_cond + b1 (one
-// vector per call).  Layers 2-4 run on the tensor cores (mma.sync m16n8k16
-// bf16); each warp keeps its 16 rows' activations in registers: the FP32
-// accumulator fragments of one layer, rounded to BF16, are exactly the A
-// fragments of the next.  Weights live in shared memory with rows padded to
-// 272 bytes (conflict-free ldmatrix).
+// vector per frame, cond_kernel); each thread computes its row's 128
+// activations and writes them, BF16, as the A operand of layer 2 in shared
+// memory (no-swizzle K-major core matrices: 8-column K groups 2048 B apart,
+// 8-row groups 128 B apart).  Layers 2 and 3 (128 x 128) and the output
+// layer (padded to N = 16) are one tcgen05.mma chain each (M = 128, K = 16
+// per instruction) into the group's 128 TMEM columns; the epilogue reads
+// each thread's row back (tcgen05.ld, TMEM lane = row), adds the bias,
+// applies SiLU and writes the next layer's A tile in place.
+// A CTA holds the weights once and runs IT_GROUPS independent warpgroups,
+// each on its own tiles with its own A tile, TMEM columns and mbarrier, so
+// one group's MMAs overlap the other groups' SiLU epilogues.  Every wait is
+// bounded (a time-out sets the device error flag and the group stops).
 // ---------------------------------------------------------------------------
-constexpr int IP = 136;                       // padded row length (bf16)
-constexpr int IW = 4;                         // warps per CTA
-struct InferSmem {
-    bf16r w2[HID][IP];
-    bf16r w3[HID][IP];
-    bf16r w4[8][IP];
-    float c1[HID], w10[HID], w11[HID], b2[HID], b3[HID], b4[2];
-};
-
-__device__ __forceinline__ u32 pack2(float lo, float hi)
-{
-    return (u32)to_bf16(lo) | ((u32)to_bf16(hi) << 16);
-}
-
 // SiLU for inference: z sigma(z) = z (1 + tanh(z / 2)) / 2 with the hardware
 // tanh (one special-function operation instead of an exponential and a
 // reciprocal; relative error about 2^-11, below the BF16 rounding of the
@@ -1611,38 +1598,56 @@ __global__ void cond_kernel(const bf16r* __restrict__ wb, const float* __restric
     c1[j] = acc;
 }
 
-__device__ __forceinline__ void hidden_layer(const bf16r (*W)[IP], const float* bias, u32 (&a)[8][4],
-                                             int lane)
+constexpr int IT_GROUPS = 4;
+constexpr int IT_THREADS = 128 * IT_GROUPS;
+constexpr int IT_W = HID * HID * 2;            // W2 or W3 in shared memory (bytes)
+constexpr int IT_N4 = 16;                      // output layer rows, padded
+constexpr int IT_W4 = IT_N4 * HID * 2;
+constexpr int IT_A = 128 * HID * 2;            // one group's activation tile
+constexpr int IT_SMEM = 1024 + 2 * IT_W + IT_W4 + IT_GROUPS * IT_A + 256;
+
+// byte offset of element (row r, column k) of a K-major tile whose 8-row
+// groups are 128 B apart and whose 8-column K groups are `kstride` apart
+__device__ __forceinline__ u32 it_off(int r, int k, u32 kstride)
 {
-    float acc[16][4];
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-#pragma unroll
-    for (int kt = 0; kt < 8; ++kt) {
-#pragma unroll
-        for (int nt = 0; nt < 16; nt += 2) {
-            u32 b[4];
-            ldsm_x4(b, &W[nt * 8 + (lane & 7) + ((lane >> 4) << 3)][kt * 16 + ((lane >> 3) & 1) * 8]);
-            mma_bf16(acc[nt], a[kt], b[0], b[1]);
-            mma_bf16(acc[nt + 1], a[kt], b[2], b[3]);
-        }
-    }
-    const int tq = lane & 3;
-#pragma unroll
-    for (int kt = 0; kt < 8; ++kt) {
-        const int c0 = (2 * kt) * 8 + 2 * tq, c1 = (2 * kt + 1) * 8 + 2 * tq;
-        a[kt][0] = pack2(silu_fast(acc[2 * kt][0] + bias[c0]), silu_fast(acc[2 * kt][1] + bias[c0 + 1]));
-        a[kt][1] = pack2(silu_fast(acc[2 * kt][2] + bias[c0]), silu_fast(acc[2 * kt][3] + bias[c0 + 1]));
-        a[kt][2] = pack2(silu_fast(acc[2 * kt + 1][0] + bias[c1]),
-                         silu_fast(acc[2 * kt + 1][1] + bias[c1 + 1]));
-        a[kt][3] = pack2(silu_fast(acc[2 * kt + 1][2] + bias[c1]),
-                         silu_fast(acc[2 * kt + 1][3] + bias[c1 + 1]));
-    }
+    return (u32)(k >> 3) * kstride + (u32)r * 16u + (u32)(k & 7) * 2u;
 }
 
-// frames of one inference launch: tile_begin[f] = first 16-row tile of
+__device__ __forceinline__ void it_st16(u32 addr, u32 a, u32 b, u32 c, u32 d)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void it_fence_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void it_group_sync(int g)
+{
+    asm volatile("bar.sync %0, 128;" ::"r"(g + 1) : "memory");
+}
+
+// group barrier that also ANDs a flag over the group's 128 threads: every
+// thread leaves with the same answer, so a time-out seen by one thread
+// stops the whole group together
+__device__ __forceinline__ bool it_group_all(int g, bool v)
+{
+    u32 r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((u32)v), "r"(g + 1)
+        : "memory");
+    return r != 0;
+}
+
+// frames of one inference launch: tile_begin[f] = first 128-row tile of
 // frame f (tile_begin[n_sys] = all tiles), its c1 vector, row count, seed
 // and output (SoA [2][count])
 struct InferFrames {
@@ -1654,33 +1659,111 @@ struct InferFrames {
     int n_sys;
 };
 
-__global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict__ wb,
-                                                        const float* __restrict__ w,
-                                                        const InferFrames fs)
+__global__ void __launch_bounds__(IT_THREADS, 1) infer_tc_kernel(const bf16r* __restrict__ wb,
+                                                                 const float* __restrict__ w,
+                                                                 const InferFrames fs)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    InferSmem& sm = *reinterpret_cast<InferSmem*>(smem_raw);
-    for (int e = threadIdx.x; e < HID * HID; e += blockDim.x) {
-        const int r = e / HID, c = e % HID;
-        sm.w2[r][c] = wb[OFF_W2 + e];
-        sm.w3[r][c] = wb[OFF_W3 + e];
+    extern __shared__ unsigned char it_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(it_raw) + 1023) & ~(uintptr_t)1023);
+    const u32 sW2 = smem_addr(sm), sW3 = sW2 + IT_W, sW4 = sW3 + IT_W;
+    const u32 sA0 = sW4 + IT_W4;
+    u64* bars = reinterpret_cast<u64*>(sm + 2 * IT_W + IT_W4 + IT_GROUPS * IT_A);
+    u32* s_tmem = reinterpret_cast<u32*>(bars + IT_GROUPS);
+    __shared__ float s_w10[HID], s_w11[HID], s_b2[HID], s_b3[HID], s_b4[2];
+    __shared__ int s_err;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights into the B-operand layout (rows = output features n, K = inputs)
+    for (int e = tid; e < HID * HID; e += IT_THREADS) {
+        const int n = e / HID, k = e % HID;
+        const u32 o = it_off(n, k, 2048u);
+        *reinterpret_cast<bf16r*>(sm + o) = wb[OFF_W2 + e];
+        *reinterpret_cast<bf16r*>(sm + IT_W + o) = wb[OFF_W3 + e];
     }
-    for (int e = threadIdx.x; e < 8 * HID; e += blockDim.x) {
-        const int r = e / HID, c = e % HID;
-        sm.w4[r][c] = r < D_OUT ? wb[OFF_W4 + e] : (bf16r)0;
+    for (int e = tid; e < IT_N4 * HID; e += IT_THREADS) {
+        const int n = e / HID, k = e % HID;
+        *reinterpret_cast<bf16r*>(sm + 2 * IT_W + it_off(n, k, (u32)IT_N4 * 16u)) =
+            n < D_OUT ? wb[OFF_W4 + e] : (bf16r)0;
     }
-    for (int j = threadIdx.x; j < HID; j += blockDim.x) {
-        sm.w10[j] = from_bf16(wb[OFF_W1 + j * D_IN]);
-        sm.w11[j] = from_bf16(wb[OFF_W1 + j * D_IN + 1]);
-        sm.b2[j] = w[OFF_B2 + j];
-        sm.b3[j] = w[OFF_B3 + j];
+    for (int j = tid; j < HID; j += IT_THREADS) {
+        s_w10[j] = from_bf16(wb[OFF_W1 + j * D_IN]);
+        s_w11[j] = from_bf16(wb[OFF_W1 + j * D_IN + 1]);
+        s_b2[j] = w[OFF_B2 + j];
+        s_b3[j] = w[OFF_B3 + j];
     }
-    if (threadIdx.x < 2) sm.b4[threadIdx.x] = w[OFF_B4 + threadIdx.x];
+    if (tid < 2) s_b4[tid] = w[OFF_B4 + tid];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"(smem_addr(s_tmem)), "r"(128u * IT_GROUPS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        s_err = 0;
+        for (int g = 0; g < IT_GROUPS; ++g) mbar_init(smem_addr(&bars[g]), 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    it_fence_async_smem();          // the weights, written by st.shared, feed the MMAs
+    tc_fence_before();
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gq = lane >> 2, tq = lane & 3;
+    tc_fence_after();
+
+    const int g = warp >> 2, wq = warp & 3, r = wq * 32 + lane;   // r: row in the tile
+    const u32 sA = sA0 + (u32)(g * IT_A);
+    const u32 bar = smem_addr(&bars[g]);
+    const u32 tcol = *s_tmem + (u32)(g * 128);                    // the group's columns
+    const u32 tlane = tcol + ((u32)(wq * 32) << 16);              // this warp's lanes
+    const bool issuer = wq == 0 && lane == 0;
+    const u32 idesc128 = tc_idesc(128), idesc16 = tc_idesc(IT_N4);
+    u32 phase = 0;
+    int pending = 0;               // commits issued and not yet waited for (issuer)
+    bool ok = true;
+
+    // layer k's MMAs on the A tile into the group's columns, committed to bar
+    auto mma_layer = [&](u32 sW, u32 lbo_w, u32 idesc) {
+        it_fence_async_smem();
+        tc_fence_before();
+        it_group_sync(g);
+        if (issuer) {
+            tc_fence_after();
+            for (int kk = 0; kk < HID / 16; ++kk)
+                tc_mma(tcol, tc_desc_kn(sA + (u32)kk * 4096u, 2048u, 128u),
+                       tc_desc_kn(sW + (u32)kk * 2u * lbo_w, lbo_w, 128u), idesc,
+                       kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+            pending = 1;
+        }
+    };
+    auto wait_layer = [&]() -> bool {
+        const bool done = it_group_all(g, mbar_wait(bar, phase));
+        if (done) {
+            phase ^= 1u;
+            if (issuer) pending = 0;
+        }
+        tc_fence_after();
+        return done;
+    };
+    // epilogue of a hidden layer: bias, SiLU, BF16, written as the next A tile
+    auto hidden_epilogue = [&](const float* bias) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < HID; c0 += 16) {
+            float v[16];
+            tc_ld16(tlane + (u32)c0, v);
+            u32 q[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                q[j] = pack_bf16x2(silu_fast(v[2 * j] + bias[c0 + 2 * j]),
+                                   silu_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+            it_st16(sA + it_off(r, c0, 2048u), q[0], q[1], q[2], q[3]);
+            it_st16(sA + it_off(r, c0 + 8, 2048u), q[4], q[5], q[6], q[7]);
+        }
+    };
+
     const u32 tiles = fs.tile_begin[fs.n_sys];
-    for (u32 tile = blockIdx.x * IW + warp; tile < tiles; tile += gridDim.x * IW) {
+    for (u32 tile = blockIdx.x * IT_GROUPS + (u32)g; tile < tiles;
+         tile += gridDim.x * IT_GROUPS) {
         // the frame of this tile: last f with tile_begin[f] <= tile
         int lo = 0, hi = fs.n_sys;
         while (hi - lo > 1) {
@@ -1688,65 +1771,64 @@ __global__ void __launch_bounds__(IW * 32) infer_kernel(const bf16r* __restrict_
             if (fs.tile_begin[mid] <= tile) lo = mid; else hi = mid;
         }
         const int f = lo;
-        const u32 lt = tile - fs.tile_begin[f];
-        const int n = (int)fs.count[f];
-        const u64 seed = fs.seed[f];
+        const u32 row = (tile - fs.tile_begin[f]) * 128u + (u32)r;
+        const u32 n = fs.count[f];
         const float* c1 = fs.c1 + (size_t)f * HID;
-        float* start = fs.out[f];
-        // noise of rows gq and gq + 8 (Box-Muller on Philox (row, 0, 0, 3))
-        float nz[2][2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const u32 row = lt * 16 + (u32)(gq + 8 * h);
-            const uint4 r = philox_key(seed, row, 0u, 0u, TAG_NOISE);
-            const float u1 = ((float)(r.x >> 8) + 0.5f) * CFS_INV_2_24;
-            const float u2 = (float)(r.y >> 8) * CFS_INV_2_24;
+        // noise of this row (Box-Muller on Philox (row, 0, 0, 3))
+        float n0, n1;
+        {
+            const uint4 q = philox_key(fs.seed[f], row, 0u, 0u, TAG_NOISE);
+            const float u1 = ((float)(q.x >> 8) + 0.5f) * CFS_INV_2_24;
+            const float u2 = (float)(q.y >> 8) * CFS_INV_2_24;
             const float rad = sqrtf(-2.0f * logf(u1));
             float sn, cs;
             sincosf(6.28318530717958647692f * u2, &sn, &cs);
-            nz[h][0] = from_bf16(to_bf16(rad * cs));
-            nz[h][1] = from_bf16(to_bf16(rad * sn));
+            n0 = from_bf16(to_bf16(rad * cs));
+            n1 = from_bf16(to_bf16(rad * sn));
         }
-        // layer 1 (rank-2 update), straight into the A fragments of layer 2
-        u32 a[8][4];
+        // layer 1 (rank-2 update) into the A tile
+#pragma unroll 1
+        for (int c0 = 0; c0 < HID; c0 += 8) {
+            u32 q[4];
 #pragma unroll
-        for (int kt = 0; kt < 8; ++kt) {
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int c = (2 * kt + half) * 8 + 2 * tq;
-                float v[2][2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float cc = c1[c + q];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-                        v[h][q] = silu_fast(fmaf(sm.w11[c + q], nz[h][1],
-                                                 fmaf(sm.w10[c + q], nz[h][0], cc)));
-                }
-                a[kt][2 * half + 0] = pack2(v[0][0], v[0][1]);
-                a[kt][2 * half + 1] = pack2(v[1][0], v[1][1]);
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + 2 * j;
+                q[j] = pack_bf16x2(
+                    silu_fast(fmaf(s_w11[c], n1, fmaf(s_w10[c], n0, __ldg(c1 + c)))),
+                    silu_fast(fmaf(s_w11[c + 1], n1, fmaf(s_w10[c + 1], n0, __ldg(c1 + c + 1)))));
             }
+            it_st16(sA + it_off(r, c0, 2048u), q[0], q[1], q[2], q[3]);
         }
-        hidden_layer(sm.w2, sm.b2, a, lane);
-        hidden_layer(sm.w3, sm.b3, a, lane);
-        // output layer: one 16 x 8 tile, columns 0 and 1 are the point
-        float y[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int kt = 0; kt < 8; ++kt) {
-            u32 b[4];
-            ldsm_x4(b, &sm.w4[(lane & 7)][kt * 16 + ((lane >> 3) & 1) * 8]);
-            mma_bf16(y, a[kt], b[0], b[1]);
+        mma_layer(sW2, 2048u, idesc128);
+        if (!(ok = wait_layer())) break;
+        hidden_epilogue(s_b2);
+        mma_layer(sW3, 2048u, idesc128);
+        if (!(ok = wait_layer())) break;
+        hidden_epilogue(s_b3);
+        mma_layer(sW4, (u32)IT_N4 * 16u, idesc16);
+        if (!(ok = wait_layer())) break;
+        float y[16];
+        tc_ld16(tlane, y);
+        tc_fence_before();          // TMEM read: the next tile's MMAs may overwrite it
+        if (row < n) {
+            float* out = fs.out[f];
+            out[row] = y[0] + s_b4[0];
+            out[(size_t)n + row] = y[1] + s_b4[1];
         }
-        if (tq == 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = (int)lt * 16 + gq + 8 * h;
-                if (row < n) {
-                    start[row] = y[2 * h] + sm.b4[0];
-                    start[(size_t)n + row] = y[2 * h + 1] + sm.b4[1];
-                }
-            }
-        }
+    }
+    if (!ok) {
+        atomicExch(&s_err, 1);
+        // the MMAs of an unfinished commit complete before TMEM is freed
+        if (issuer && pending) mbar_wait(bar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(&g_tc_error, (unsigned)CFS_DEVICE_ERR_TC_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem),
+                     "r"(128u * IT_GROUPS)
+                     : "memory");
     }
 }
 
@@ -2259,7 +2341,8 @@ cfs_status cfs_sampler_adam(cfs_sampler* s, const float* grads, uint32_t t, floa
     clear_error();
     if (!s || !grads || t == 0) return fail(CFS_ERR_INVALID_ARG, "bad arguments");
     adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
-        s->w, s->m, s->v, grads, s->wb, s->wbT, N_PARAMS, nullptr, t, lr, 0.9f, 0.999f, 1e-8f);
+        s->w, s->m, s->v, grads, s->wb, s->wbT, N_PARAMS, nullptr, t, lr, lr, 0u, 0u, 0.9f,
+        0.999f, 1e-8f);
     return check_cuda(cudaGetLastError(), "adam launch");
 }
 
@@ -2269,9 +2352,30 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
                              uint32_t n_proj, float lr, uint64_t seed, float* loss_history,
                              void* stream)
 {
+    cfs_train_options o;
+    o.steps = steps;
+    o.systems_per_step = systems_per_step;
+    o.points_per_system = points_per_system;
+    o.n_proj = n_proj;
+    o.lr = lr;
+    o.lr_final = lr;
+    o.seed = seed;
+    return cfs_sampler_train_ex(s, systems, t_values, n_systems, &o, loss_history, stream);
+}
+
+cfs_status cfs_sampler_train_ex(cfs_sampler* s, const cfs_system* const* systems,
+                                const float* t_values, int n_systems,
+                                const cfs_train_options* opt, float* loss_history, void* stream)
+{
     clear_error();
-    if (!s || !systems || !t_values || n_systems <= 0)
-        return fail(CFS_ERR_INVALID_ARG, "NULL sampler or systems");
+    if (!s || !systems || !t_values || n_systems <= 0 || !opt)
+        return fail(CFS_ERR_INVALID_ARG, "NULL sampler, systems or options");
+    const uint32_t steps = opt->steps, systems_per_step = opt->systems_per_step;
+    const uint32_t points_per_system = opt->points_per_system, n_proj = opt->n_proj;
+    const float lr = opt->lr, lr_final = opt->lr_final;
+    const uint64_t seed = opt->seed;
+    if (!(lr > 0.0f) || !(lr_final > 0.0f) || !std::isfinite(lr) || !std::isfinite(lr_final))
+        return fail(CFS_ERR_INVALID_ARG, "learning rates must be positive and finite");
     if (points_per_system < 32 || points_per_system > 1024 ||
         (points_per_system & (points_per_system - 1)))
         return fail(CFS_ERR_INVALID_ARG, "points per system must be a power of two in 32..1024");
@@ -2333,7 +2437,8 @@ cfs_status cfs_sampler_train(cfs_sampler* s, const cfs_system* const* systems,
         gather_loss_kernel<<<1, 1, 0, cap>>>(d_loss, s->d_step, step0, d_hist, steps);
         if (fst == CFS_OK) fst = backward(s, d_U, B, d_dY, d_g, cap);
         adam_kernel<<<(N_PARAMS + 255) / 256, 256, 0, cap>>>(s->w, s->m, s->v, d_g, s->wb, s->wbT,
-                                                             N_PARAMS, s->d_step, 0u, lr, 0.9f,
+                                                             N_PARAMS, s->d_step, 0u, lr,
+                                                             lr_final, step0, steps, 0.9f,
                                                              0.999f, 1e-8f);
         step_inc_kernel<<<1, 1, 0, cap>>>(s->d_step);
         cudaError_t e = cudaGetLastError();
@@ -2389,7 +2494,7 @@ cfs_status cfs_sampler_start_points_batch(cfs_sampler* s, int n_frames,
         if (st != CFS_OK) return st;
         if (counts[f] > (1u << 30)) return fail(CFS_ERR_INVALID_ARG, "count too large");
         if (counts[f] && !starts[f]) return fail(CFS_ERR_INVALID_ARG, "NULL output");
-        tiles += (counts[f] + 15) / 16;
+        tiles += (counts[f] + 127) / 128;
     }
     if (tiles >= (1ull << 31)) return fail(CFS_ERR_INVALID_ARG, "too many rows");
     cudaStream_t sm = (cudaStream_t)stream;
@@ -2424,7 +2529,7 @@ cfs_status cfs_sampler_start_points_batch(cfs_sampler* s, int n_frames,
     for (int f = 0; f < n_frames; ++f) {
         pack_system(systems[f], t[f], reinterpret_cast<SysRec*>(h + L.rec) + f);
         h_tiles[f] = acc;
-        acc += (counts[f] + 15) / 16;
+        acc += (counts[f] + 127) / 128;
         reinterpret_cast<u32*>(h + L.count)[f] = counts[f];
         reinterpret_cast<u64*>(h + L.seed)[f] = seeds[f];
         reinterpret_cast<float**>(h + L.out)[f] = starts[f];
@@ -2439,20 +2544,19 @@ cfs_status cfs_sampler_start_points_batch(cfs_sampler* s, int n_frames,
     cond_kernel<<<n_frames, HID, 0, sm>>>(s->wb, s->w, reinterpret_cast<const SysRec*>(d + L.rec),
                                          reinterpret_cast<float*>(d + L.c1));
     if (acc == 0) return check_cuda(cudaGetLastError(), "sampler conditioning");
-    const int smem = (int)sizeof(InferSmem);
     static int smem_set = -1;
     if (smem_set != s->device) {
-        st = check_cuda(cudaFuncSetAttribute(infer_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+        st = check_cuda(cudaFuncSetAttribute(infer_tc_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             IT_SMEM),
                         "cudaFuncSetAttribute");
         if (st != CFS_OK) return st;
         smem_set = s->device;
     }
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, infer_kernel, IW * 32, smem);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    int grid = std::max(1, per_sm) * std::max(1, sms);
-    grid = (int)std::min<uint64_t>((uint64_t)grid, (acc + IW - 1) / IW);
+    // persistent: one CTA per SM (its shared memory and 512 TMEM columns),
+    // IT_GROUPS tiles in flight per CTA
+    const int sms = std::max(1, device_sm_count());
+    const int grid = (int)std::min<uint64_t>((uint64_t)sms, (acc + IT_GROUPS - 1) / IT_GROUPS);
     InferFrames fs;
     fs.c1 = reinterpret_cast<const float*>(d + L.c1);
     fs.tile_begin = reinterpret_cast<const u32*>(d + L.tiles);
@@ -2460,7 +2564,7 @@ cfs_status cfs_sampler_start_points_batch(cfs_sampler* s, int n_frames,
     fs.seed = reinterpret_cast<const u64*>(d + L.seed);
     fs.out = reinterpret_cast<float* const*>(d + L.out);
     fs.n_sys = n_frames;
-    infer_kernel<<<grid, IW * 32, smem, sm>>>(s->wb, s->w, fs);
+    infer_tc_kernel<<<grid, IT_THREADS, IT_SMEM, sm>>>(s->wb, s->w, fs);
     return check_cuda(cudaGetLastError(), "sampler start points");
 }
 

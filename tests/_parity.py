@@ -83,6 +83,8 @@ def check_rgba_close(g, o, amb, total, rel_l1=1e-5):
     d = np.abs(g.astype(np.float64) - o.astype(np.float64))
     bad = d > amb[..., None]
     assert not bad.any(), f"{bad.sum()} RGBA values differ beyond the near-edge slack"
+    print(f"RGBA alpha L1: {d[..., 3].sum():.0f} of {total} splats "
+          f"({d[..., 3].sum() / max(total, 1):.2e}; bar {rel_l1:.0e})")
     assert d[..., 3].sum() <= rel_l1 * total, (d[..., 3].sum(), total)
 
 

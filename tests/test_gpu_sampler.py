@@ -233,3 +233,27 @@ def test_training_reduces_loss_and_beats_uniform_start(torch_cuda):
                 assert l1s < l1u, (f, k, l1s, l1u)
             wins += l1s < l1u
     assert wins >= 9
+
+
+def test_train_ex_schedule(torch_cuda):
+    """cfs_sampler_train_ex: a constant schedule is cfs_sampler_train bit for
+    bit; a cosine decay trains too (finite, falling loss) and ends at other
+    parameters."""
+    from paper_2606_02226_gb300 import cfs
+    frames = _family(8, seed=3)
+    systems = [cfs.System(f.system) for f in frames]
+    t = np.array([f.t for f in frames], np.float32)
+    a = cfs.Sampler(seed=2)
+    b = cfs.Sampler(seed=2)
+    c = cfs.Sampler(seed=2)
+    ha = a.train(systems, t, 60, systems_per_step=8, points_per_system=256, n_proj=16, seed=4)
+    hb = b.train(systems, t, 60, systems_per_step=8, points_per_system=256, n_proj=16, seed=4,
+                 lr_final=1e-3)
+    hc = c.train(systems, t, 60, systems_per_step=8, points_per_system=256, n_proj=16, seed=4,
+                 lr_final=1e-5)
+    wa, wb_, wc = a.get_params()[0], b.get_params()[0], c.get_params()[0]
+    assert np.array_equal(wa, wb_) and np.array_equal(ha, hb)
+    assert np.all(np.isfinite(hc)) and not np.array_equal(wa, wc)
+    assert hc[-10:].mean() < hc[:5].mean()
+    with pytest.raises(cfs.CfsError):
+        c.train(systems, t, 2, systems_per_step=8, points_per_system=256, lr_final=0.0)

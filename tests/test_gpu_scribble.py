@@ -110,3 +110,61 @@ def test_scribble_chain_in_a_batch(torch_cuda):
                        point_begin=begin)
         assert np.array_equal(outs[1][f].view(np.uint32), res[0].buf)
         begin += fr.n_points
+
+
+FIG3_STYLE = r"""
+// a verse whose default factor (8) every call below overrides
+__verse mult_by(v | float factor = 8.0f;) { v = v * factor; }
+// a stanza: under the index bound, sum two inputs into `out`, run the
+// injected block, add one; its keyword r is passed but never used
+__stanza sum_check(a_in, b_in, out | float r = 1.0f;) {
+    if (k < limit) {
+        out = a_in + b_in;
+        __split_stanza();
+        out = out + 1.0f;
+    }
+}
+__poem fig3() {
+    int stanza_num = STANZA;
+    int limit = 2;
+    if (stanza_num == 0) {
+        @SCALL sum_check(px, py, qx | r = 5.0f;) {
+            @VCALL mult_by(qx | factor = 2.0f;);
+        }
+        if (k < limit) {
+            @VCALL mult_by(qx | factor = 0.5f;);
+        }
+    }
+    splat(0);
+}
+"""
+
+
+@pytest.mark.parametrize("stanza", [0, 1])
+def test_scribble_fig3_semantics(torch_cuda, stanza):
+    """The composition Fig. 3 shows (Section 3.1), in this library's dialect:
+    a stanza that sums two inputs into an output, has a verse call injected
+    at its split point and adds one afterwards, all under an index bound and
+    a stanza selector, followed by a second call of the same verse.  The
+    verse's default factor 8 is overridden by 2 inside the stanza and by 0.5
+    after it; the stanza's keyword r = 5 is unused.  Inputs are the
+    generator's point (px, py), the output the copy's x, the index the map
+    k (bound 2).  Expected: qx = ((px + py) 2 + 1) 0.5 where the selector is
+    0 and k < 2, else qx = px; qy = py throughout."""
+    from paper_2606_02226_gb300 import cfs
+    torch = torch_cuda
+    ch = cfs.Chain.from_scribble(FIG3_STYLE.replace("STANZA", str(stanza)), "fig3", 2)
+    sysd = W.square_system()
+    ids = np.arange(256, dtype=np.uint32)
+    k, p, q = cfs.trace(cfs.System(sysd), ch, torch.from_numpy(ids.view(np.int32)).cuda(),
+                        iters=16)
+    k, p, q = k.cpu().numpy(), p.cpu().numpy(), q.cpu().numpy()
+    px, py = p[..., 0].astype(np.float32), p[..., 1].astype(np.float32)
+    f32 = np.float32
+    inner = ((px + py) * f32(2.0) + f32(1.0)) * f32(0.5)
+    ex = np.where((k < 2) & (stanza == 0), inner, px)
+    assert np.array_equal(q[..., 0, 0], ex)
+    assert np.array_equal(q[..., 0, 1], py)
+    assert ((k < 2).mean() > 0.3) and ((k >= 2).mean() > 0.3)   # both branches taken
+    ko, po, _ = O.trace(sysd, [W.Op("splat", (0,))], ids, iters=16)
+    assert np.array_equal(k, ko) and np.array_equal(p, po)

@@ -454,7 +454,8 @@ def run_cfs(args, wl):
         line["space"] = bench_space(torch, cfs, dev, stream)
     if args.cloud and single:
         line["cloud"] = bench_cloud(torch, cfs, dev, stream, n_frames=args.cloud_frames,
-                                    n=args.cloud_points, fast_trig=args.fast_trig)
+                                    n=args.cloud_points, fast_trig=args.fast_trig,
+                                    fold=not args.no_fold)
     if not args.no_cpu_baseline and single:
         line["cpu_baseline"] = cpu_baseline(wl, target_s=args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -683,7 +684,7 @@ def bench_space(torch, cfs, dev, stream, reps: int = 5):
 
 
 def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
-                fast_trig: bool = False):
+                fast_trig: bool = False, fold: bool = True):
     """Stored-cloud deformation: a 2^26-point cloud of a 3D IFS (8 maps)
     generated once, then 64 animation frames each streaming it through twist,
     bend, sphere inversion, sinusoidal, four affines and a perspective splat
@@ -708,7 +709,9 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
     xyz, fn = xyz_m, fn_m
     t = W.cloud_target(Wd)
     layer = cfs.alloc_target(t, device=dev)
-    chain = cfs.Chain(W.cloud_chain(0, n_frames), 3, fast_trig=fast_trig)
+    # the four affines and the camera translation run as one affine op
+    # (CFS_COMPOSE_FOLD_LINEAR; positions within a few ulps of op-by-op)
+    chain = cfs.Chain(W.cloud_chain(0, n_frames), 3, fast_trig=fast_trig, fold_linear=fold)
 
     def frame(f):
         ops = W.cloud_chain(f, n_frames)
@@ -750,6 +753,7 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
     kern_gbs = cloud_bytes / (kern_ms * 1e-3) / 1e9
     return {"workload": f"{n}-point 3D IFS cloud; twist/bend/inversion/sinusoidal/4 affines/"
                         f"perspective -> 8192^2 depth+colour u64; {n_frames} frames",
+            "fold_linear": fold,
             "generate_ms": gen_ms, "reorder_ms": reorder_ms,
             "render_points_ms_generation_order": unsorted_ms,
             "ms_per_frame": frame_ms, "frames_per_s": 1e3 / frame_ms,
@@ -918,18 +922,23 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
         if a != best:
             del arms[a]
     run_warm, infer, _, _ = arms[best]
-    # measured run: interleaved pairs, the order alternating within pairs
+    # measured run: interleaved pairs, the order alternating within pairs;
+    # each arm of a pair is the faster of two back-to-back launches
     p_ms, w_ms = [], []
     for i in range(pairs):
-        if i % 2 == 0:
-            p_ms.append(timed_once(run_plain))
-            w_ms.append(timed_once(run_warm))
-        else:
-            w_ms.append(timed_once(run_warm))
-            p_ms.append(timed_once(run_plain))
+        for arm in ((0, 1) if i % 2 == 0 else (1, 0)):
+            if arm == 0:
+                p_ms.append(min(timed_once(run_plain) for _ in range(2)))
+            else:
+                w_ms.append(min(timed_once(run_warm) for _ in range(2)))
     inf_ms = statistics.median(timed_once(infer) for _ in range(5))
     ratios = sorted(p / w for p, w in zip(p_ms, w_ms))
     q = np.percentile(ratios, [25, 50, 75])
+    # 95% bootstrap interval of the median ratio (fixed resampling seed)
+    rng = np.random.default_rng(12345)
+    boot = np.median(rng.choice(np.array(ratios), size=(4000, len(ratios)), replace=True),
+                     axis=1)
+    ci = np.percentile(boot, [2.5, 97.5])
     nf = len(frames)
     out.update({"batch_frames": nf, "chosen_samples": best,
                 "chosen_k_min": out["warm"][best]["k_min"],
@@ -941,7 +950,10 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
                 "warm_over_plain": float(q[1]),
                 "warm_over_plain_quartiles": [float(q[0]), float(q[2])],
                 "warm_over_plain_range": [ratios[0], ratios[-1]],
-                "win": bool(q[0] > 1.0),
+                "warm_over_plain_median_ci95": [float(ci[0]), float(ci[1])],
+                "win": bool(ci[0] > 1.0),
+                "win_rule": "the 95% bootstrap interval of the median per-pair ratio lies "
+                            "above 1",
                 "gain_bound": (b_min - out["warm"][best]["k_min"]) / (b_min + ITERS - B_IN)})
     return out
 
@@ -987,12 +999,14 @@ def main():
                     help="skip the stored-cloud measurement")
     ap.add_argument("--fast-trig", action="store_true",
                     help="chains use reduced-argument hardware sine/cosine")
+    ap.add_argument("--no-fold", action="store_true",
+                    help="the cloud's chain runs its linear ops one by one")
     ap.add_argument("--no-space", dest="space", action="store_false",
                     help="skip the many-objects scene measurement")
     ap.add_argument("--no-sampler", dest="sampler", action="store_false",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--sampler-steps", type=int, default=20000)
-    ap.add_argument("--sampler-lr-final", type=float, default=1e-5,
+    ap.add_argument("--sampler-lr-final", type=float, default=0.0,
                     help="cosine decay of the sampler's step size from 1e-3 to this (0: constant)")
     ap.add_argument("--sampler-pairs", type=int, default=12,
                     help="interleaved plain/warm batch timings")

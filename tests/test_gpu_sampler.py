@@ -236,9 +236,10 @@ def test_training_reduces_loss_and_beats_uniform_start(torch_cuda):
 
 
 def test_train_ex_schedule(torch_cuda):
-    """cfs_sampler_train_ex: a constant schedule is cfs_sampler_train bit for
-    bit; a cosine decay trains too (finite, falling loss) and ends at other
-    parameters."""
+    """cfs_sampler_train_ex: a constant schedule trains as cfs_sampler_train
+    does (the weight gradients are sums of FP32 atomics, so two runs agree to
+    rounding, not bit for bit); a cosine decay trains too (finite, falling
+    loss) and ends at other parameters."""
     from paper_2606_02226_gb300 import cfs
     frames = _family(8, seed=3)
     systems = [cfs.System(f.system) for f in frames]
@@ -252,8 +253,9 @@ def test_train_ex_schedule(torch_cuda):
     hc = c.train(systems, t, 60, systems_per_step=8, points_per_system=256, n_proj=16, seed=4,
                  lr_final=1e-5)
     wa, wb_, wc = a.get_params()[0], b.get_params()[0], c.get_params()[0]
-    assert np.array_equal(wa, wb_) and np.array_equal(ha, hb)
-    assert np.all(np.isfinite(hc)) and not np.array_equal(wa, wc)
+    same = np.abs(wa - wb_).max()
+    assert same < 2e-4 and np.allclose(ha, hb, rtol=1e-3, atol=1e-6), same
+    assert np.all(np.isfinite(hc)) and np.abs(wa - wc).max() > 10 * max(same, 1e-6)
     assert hc[-10:].mean() < hc[:5].mean()
     with pytest.raises(cfs.CfsError):
         c.train(systems, t, 2, systems_per_step=8, points_per_system=256, lr_final=0.0)

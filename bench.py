@@ -811,8 +811,8 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
     frames = W.animation_frames(n_frames=batch_frames, seed=0)
     tgt = W.Target("hist_u32", 1024, 1024, 1, W.ANIMATION_VIEW)
     chain = cfs.Chain([W.Op("splat", (0,))], 2)
-    bs = [0, 1, 2, 3, 4, 6, 8, 10, 12, 16]
-    ks = [0, 1, 2, 3, 4, 6, 8]
+    bs = list(range(0, 13)) + [16]
+    ks = list(range(0, 9))
     buf = cfs.alloc_target(tgt, device=dev)
 
     def hist_of(sysh, seed, step_begin, start=None):

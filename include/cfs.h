@@ -361,7 +361,8 @@ cfs_status cfs_batch_set_plan(cfs_batch* batch, const cfs_batch_plan* plan);
  *  2. per shape class -- frames grouped by point count (log2 rounded down
  *     to even: 2^16-2^17, 2^18-2^19, ...) and target size (width x height of
  *     target 0) -- the item size and whether the frame uses the window, timed
- *     on that class's frames alone.
+ *     on that class's frames alone; the classes' choices are then kept only
+ *     if the whole batch runs faster with them than under stage 1's plan.
  * The choices are kept in the library's tuning cache under keys made of the
  * device (name, SM count), the program's structure and the classes; a later
  * cfs_batch_tune whose keys are all cached applies them without trials
@@ -380,6 +381,8 @@ typedef struct {
     int n_classes;          /* shape classes */
     int classes_windowed;   /* classes that use the window */
     int from_cache;         /* 1 when the cache supplied every choice */
+    int classes_used;       /* 1 when the per-class choices beat the program's plan
+                               alone on the whole batch (else every frame uses it) */
 } cfs_batch_tuning;
 cfs_status cfs_batch_tune(cfs_batch* batch, uint32_t trial_iters, uint32_t flags, void* stream,
                           cfs_batch_tuning* out);

@@ -79,7 +79,7 @@ class cfs_batch_tuning(ctypes.Structure):
                 ("trial_ms", ctypes.c_float), ("trials", ctypes.c_int),
                 ("window_words", ctypes.c_uint32), ("warp_agg", ctypes.c_int),
                 ("n_classes", ctypes.c_int), ("classes_windowed", ctypes.c_int),
-                ("from_cache", ctypes.c_int)]
+                ("from_cache", ctypes.c_int), ("classes_used", ctypes.c_int)]
 
 
 class cfs_batch_plan(ctypes.Structure):
@@ -560,7 +560,7 @@ class Batch:
         return {"ilp": t.ilp, "tile": t.tile, "chunk": t.chunk, "trial_ms": t.trial_ms,
                 "trials": t.trials, "window_words": t.window_words, "warp_agg": t.warp_agg,
                 "n_classes": t.n_classes, "classes_windowed": t.classes_windowed,
-                "from_cache": bool(t.from_cache)}
+                "from_cache": bool(t.from_cache), "classes_used": bool(t.classes_used)}
 
     def plan(self) -> dict:
         p = cfs_batch_plan()

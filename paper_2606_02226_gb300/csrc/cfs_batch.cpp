@@ -827,6 +827,7 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, uint32_t flags, vo
 
     // ---- stage 2: item size and window per shape class -------------------
     int n_win = 0;
+    bool use_classes = false;
     if (st == CFS_OK) {
         cfs_batch_plan prog = b->plan;
         prog.chunk = 0;                 // the program's knobs only
@@ -860,6 +861,34 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, uint32_t flags, vo
                 if (cls[f] == kv.first) { b->chunks[f] = c_best; b->nowin[f] = nw_best; }
             if (!nw_best && b->spec.tile) ++n_win;
         }
+        // a class timed alone is not the class inside the batch (frames of
+        // other classes share the CTAs and the L2): the classes' choices are
+        // kept only when the whole batch runs faster with them than with the
+        // program's plan alone
+        if (st == CFS_OK) {
+            const std::string ukey = "classes|" + devkey + "|" + skey + "|" + pkey + "|" +
+                                     mix.str();
+            std::string v;
+            if (!retune && cache_get(ukey, &v) && (v == "1" || v == "0")) {
+                use_classes = v == "1";
+            } else {
+                all_cached = false;
+                const std::vector<uint32_t> ch = b->chunks;
+                const std::vector<uint8_t> nw = b->nowin;
+                float with_ms = 0.0f, without_ms = 0.0f;
+                st = trial(nullptr, &with_ms);
+                set_all(b->plan.chunk, 0);
+                if (st == CFS_OK) st = trial(nullptr, &without_ms);
+                use_classes = with_ms < without_ms;
+                b->chunks = ch;
+                b->nowin = nw;
+                if (st == CFS_OK) cache_put(ukey, use_classes ? "1" : "0");
+            }
+            if (!use_classes) {
+                set_all(b->plan.chunk, 0);
+                n_win = b->spec.tile ? (int)counts.size() : 0;
+            }
+        }
     }
 
     // keep the result (or restore a consistent plan after an error)
@@ -887,6 +916,7 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, uint32_t flags, vo
         out->n_classes = (int)counts.size();
         out->classes_windowed = n_win;
         out->from_cache = all_cached ? 1 : 0;
+        out->classes_used = use_classes ? 1 : 0;
     }
     return CFS_OK;
 }

@@ -210,7 +210,7 @@ def test_batch_autotuner_keeps_results_exact(torch_cuda, tmp_path):
         assert np.array_equal(_host(tens[f]), ref[f]), f
     assert list(b.discards()[:, 0]) == rdisc
     n = cfs.tune_cache_size()
-    assert n == 1 + choice["n_classes"]
+    assert n == 2 + choice["n_classes"]      # program, classes, and whether to use them
     path = str(tmp_path / "tune.txt")
     cfs.tune_cache_save(path)
     cfs.tune_cache_clear()
@@ -220,7 +220,8 @@ def test_batch_autotuner_keeps_results_exact(torch_cuda, tmp_path):
     b2 = cfs.Batch(chain, items, iters=44, burn_in=20, seed=3)
     again = b2.tune(trial_iters=24)
     assert again["from_cache"] and again["trials"] == 0
-    for k in ("ilp", "tile", "chunk", "window_words", "warp_agg", "classes_windowed"):
+    for k in ("ilp", "tile", "chunk", "window_words", "warp_agg", "classes_windowed",
+              "classes_used"):
         assert again[k] == choice[k], k
     b2.launch(clear=True)
     torch_cuda.cuda.synchronize()

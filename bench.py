@@ -774,7 +774,7 @@ def _l1(torch, h, ref):
 
 def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames: int = 16,
                   n_eval: int = 1 << 20, batch_frames: int = 256,
-                  unique_options=(4096, 65536, 0), pairs: int = 12,
+                  unique_options=(4096, 65536, 0), pairs: int = 24,
                   lr_final: Optional[float] = None):
     """Learned warm start (form 4) against plain burn-in at equal L1 error.
 
@@ -1008,7 +1008,7 @@ def main():
     ap.add_argument("--sampler-steps", type=int, default=20000)
     ap.add_argument("--sampler-lr-final", type=float, default=0.0,
                     help="cosine decay of the sampler's step size from 1e-3 to this (0: constant)")
-    ap.add_argument("--sampler-pairs", type=int, default=12,
+    ap.add_argument("--sampler-pairs", type=int, default=24,
                     help="interleaved plain/warm batch timings")
     ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--cloud-frames", type=int, default=64)

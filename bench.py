@@ -745,6 +745,16 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
     e1.record(stream)
     torch.cuda.synchronize()
     unsorted_ms = e0.elapsed_time(e1) / 8
+    # the same chain with reduced-argument hardware sine/cosine
+    # (CFS_COMPOSE_FAST_TRIG: about 4e-7 absolute per evaluation)
+    fast = cfs.Chain(W.cloud_chain(0, n_frames), 3, fast_trig=True, fold_linear=fold)
+    cfs.render_points(fast, xyz, fn, [t], [layer], stream=stream)
+    e0.record(stream)
+    for f in range(8):
+        cfs.render_points(fast, xyz, fn, [t], [layer], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fast_ms = e0.elapsed_time(e1) / 8
     # algorithmic bytes of a frame: the cloud read once (12 B of positions +
     # 1 B of map index per point) and the layer written once (clear)
     cloud_bytes = 13 * n
@@ -763,13 +773,48 @@ def bench_cloud(torch, cfs, dev, stream, n_frames: int = 64, n: int = 1 << 26,
                          "frac": kern_gbs / peaks["hbm_gbs"],
                          "peak_source": f"{src} (MEASURED_PEAKS.json copy bandwidth)",
                          "bytes": "13 B per point (cloud read once)"},
-            "frame_gbs_algorithmic": frame_gbs}
+            "frame_gbs_algorithmic": frame_gbs,
+            "fast_trig": {"render_points_ms": fast_ms,
+                          "frac_of_hbm": cloud_bytes / (fast_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                          "note": "same launch with CFS_COMPOSE_FAST_TRIG (not the default)"}}
 
 
 def _l1(torch, h, ref):
     a = h.to(torch.float64)
     b = ref.to(torch.float64)
     return float((a / a.sum() - b / b.sum()).abs().sum())
+
+
+# MLP work per row: layers 2 and 3 (128 x 128) and the output layer (2 x
+# 128) on the tensor cores, 2 FLOP per multiply-add; layer 1 is a rank-2
+# update on the CUDA cores at inference and a 64 x 128 GEMM in training
+_MLP_TC_FLOP_INFER = 2 * (128 * 128 * 2 + 2 * 128)
+_MLP_FLOP_FWD = 2 * (64 * 128 + 128 * 128 * 2 + 2 * 128)
+
+
+def _train_roofline(ms_per_step, rows=65536):
+    """One training step's tensor work (forward, input gradients of layers
+    2-3, weight gradients: three times the forward's multiply-adds) against
+    the sustained BF16 peak."""
+    pk, src = _peaks()
+    flop = 3 * _MLP_FLOP_FWD * rows
+    tf = flop / (ms_per_step * 1e-3) / 1e12
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    return {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+            "frac": tf / peak, "flop_per_step": flop,
+            "peak_source": f"{src} (sustained cuBLAS BF16)",
+            "note": "K <= 128 per row tile: the step is bound by its epilogues' traffic and "
+                    "the sort, not by the tensor pipe"}
+
+
+def _infer_roofline(samples, ms):
+    pk, src = _peaks()
+    tf = _MLP_TC_FLOP_INFER * samples / (ms * 1e-3) / 1e12
+    peak = pk.get("bf16_tflops", 1900.0)
+    return {"bound": "tensor", "kernel": "infer_tc_kernel", "achieved": tf, "peak": peak,
+            "unit": "TFLOP/s", "frac": tf / peak, "samples": samples,
+            "peak_source": f"{src} (burst cuBLAS BF16)",
+            "note": "time of the whole call (conditioning kernel and frame upload included)"}
 
 
 def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames: int = 16,
@@ -848,6 +893,7 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
            "lr": {"start": 1e-3, "final": lr_final if lr_final is not None else 1e-3,
                   "schedule": "cosine" if lr_final is not None else "constant"},
            "train_ms_per_step": 1e3 * train_s / max(train_steps, 1),
+           "train_roofline": _train_roofline(1e3 * train_s / max(train_steps, 1)),
            "loss_first": float(np.mean(hist[:20])), "loss_last": float(np.mean(hist[-20:])),
            "eval_frames": eval_frames, "eval_points": n_eval, "l1_resolution": 1024,
            "noise_floor_l1": float(np.mean(floors)), "excess_l1_plain_burn_in": mb,
@@ -945,6 +991,9 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
                 "pairs": pairs, "plain_ms_median": statistics.median(p_ms),
                 "warm_ms_median": statistics.median(w_ms),
                 "infer_ms_median": inf_ms,
+                "infer_roofline": _infer_roofline(
+                    sum((min(int(best), it[1]) if best != "per_point" else it[1])
+                        for it in items), inf_ms),
                 "plain_frames_per_s": nf / (statistics.median(p_ms) * 1e-3),
                 "warm_frames_per_s": nf / (statistics.median(w_ms) * 1e-3),
                 "warm_over_plain": float(q[1]),

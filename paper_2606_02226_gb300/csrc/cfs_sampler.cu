@@ -1613,6 +1613,14 @@ __device__ __forceinline__ u32 it_off(int r, int k, u32 kstride)
     return (u32)(k >> 3) * kstride + (u32)r * 16u + (u32)(k & 7) * 2u;
 }
 
+// two floats to packed BF16 (round to nearest even), lo in the low half
+__device__ __forceinline__ u32 it_bf16x2(float lo, float hi)
+{
+    u32 r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 __device__ __forceinline__ void it_st16(u32 addr, u32 a, u32 b, u32 c, u32 d)
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
@@ -1670,7 +1678,7 @@ __global__ void __launch_bounds__(IT_THREADS, 1) infer_tc_kernel(const bf16r* __
     const u32 sA0 = sW4 + IT_W4;
     u64* bars = reinterpret_cast<u64*>(sm + 2 * IT_W + IT_W4 + IT_GROUPS * IT_A);
     u32* s_tmem = reinterpret_cast<u32*>(bars + IT_GROUPS);
-    __shared__ float s_w10[HID], s_w11[HID], s_b2[HID], s_b3[HID], s_b4[2];
+    __shared__ __align__(16) float s_w10[HID], s_w11[HID], s_b2[HID], s_b3[HID], s_b4[4];
     __shared__ int s_err;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -1747,15 +1755,19 @@ __global__ void __launch_bounds__(IT_THREADS, 1) infer_tc_kernel(const bf16r* __
     };
     // epilogue of a hidden layer: bias, SiLU, BF16, written as the next A tile
     auto hidden_epilogue = [&](const float* bias) {
+        const float4* b4 = reinterpret_cast<const float4*>(bias);
 #pragma unroll 1
         for (int c0 = 0; c0 < HID; c0 += 16) {
             float v[16];
             tc_ld16(tlane + (u32)c0, v);
             u32 q[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                q[j] = pack_bf16x2(silu_fast(v[2 * j] + bias[c0 + 2 * j]),
-                                   silu_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+            for (int j = 0; j < 4; ++j) {
+                const float4 bb = b4[c0 / 4 + j];
+                q[2 * j] = it_bf16x2(silu_fast(v[4 * j] + bb.x), silu_fast(v[4 * j + 1] + bb.y));
+                q[2 * j + 1] = it_bf16x2(silu_fast(v[4 * j + 2] + bb.z),
+                                         silu_fast(v[4 * j + 3] + bb.w));
+            }
             it_st16(sA + it_off(r, c0, 2048u), q[0], q[1], q[2], q[3]);
             it_st16(sA + it_off(r, c0 + 8, 2048u), q[4], q[5], q[6], q[7]);
         }
@@ -1786,16 +1798,22 @@ __global__ void __launch_bounds__(IT_THREADS, 1) infer_tc_kernel(const bf16r* __
             n0 = from_bf16(to_bf16(rad * cs));
             n1 = from_bf16(to_bf16(rad * sn));
         }
-        // layer 1 (rank-2 update) into the A tile
+        // layer 1 (rank-2 update) into the A tile (16-byte loads of c1 and
+        // of the two noise columns of W1, shared by the whole group)
+        const float4* c14 = reinterpret_cast<const float4*>(c1);
+        const float4* w04 = reinterpret_cast<const float4*>(s_w10);
+        const float4* w14 = reinterpret_cast<const float4*>(s_w11);
 #pragma unroll 1
         for (int c0 = 0; c0 < HID; c0 += 8) {
             u32 q[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = c0 + 2 * j;
-                q[j] = pack_bf16x2(
-                    silu_fast(fmaf(s_w11[c], n1, fmaf(s_w10[c], n0, __ldg(c1 + c)))),
-                    silu_fast(fmaf(s_w11[c + 1], n1, fmaf(s_w10[c + 1], n0, __ldg(c1 + c + 1)))));
+            for (int h = 0; h < 2; ++h) {
+                const float4 cc = __ldg(c14 + c0 / 4 + h);
+                const float4 a0 = w04[c0 / 4 + h], a1 = w14[c0 / 4 + h];
+                q[2 * h] = it_bf16x2(silu_fast(fmaf(a1.x, n1, fmaf(a0.x, n0, cc.x))),
+                                     silu_fast(fmaf(a1.y, n1, fmaf(a0.y, n0, cc.y))));
+                q[2 * h + 1] = it_bf16x2(silu_fast(fmaf(a1.z, n1, fmaf(a0.z, n0, cc.z))),
+                                         silu_fast(fmaf(a1.w, n1, fmaf(a0.w, n0, cc.w))));
             }
             it_st16(sA + it_off(r, c0, 2048u), q[0], q[1], q[2], q[3]);
         }

@@ -11,7 +11,8 @@ from paper_2606_02226_gb300 import workloads as W
 EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 
-def gpu_render(wl, jobs=None, stream=None, discards=None, depth_test=None, fast_trig=False):
+def gpu_render(wl, jobs=None, stream=None, discards=None, depth_test=None, fast_trig=False,
+               fold_linear=False):
     """Renders every job of ``wl`` on the GPU; returns host numpy buffers and
     the per-target discard counts."""
     import torch
@@ -20,7 +21,7 @@ def gpu_render(wl, jobs=None, stream=None, discards=None, depth_test=None, fast_
     disc = torch.zeros(len(wl.targets), dtype=torch.int64, device="cuda")
     for job in (jobs or wl.jobs):
         sysh = cfs.System(job.system)
-        ch = cfs.Chain(wl.chain, job.system.dim, fast_trig=fast_trig)
+        ch = cfs.Chain(wl.chain, job.system.dim, fast_trig=fast_trig, fold_linear=fold_linear)
         cfs.render(sysh, ch, wl.targets, tensors, n_points=job.n_points, iters=wl.iters,
                    burn_in=wl.burn_in, seed=wl.seed, system_id=job.system_id,
                    point_begin=job.point_begin, discards=disc, stream=stream)

@@ -68,10 +68,12 @@ def _disk_square():
     return W.System(2, maps, [0.25] * 4)
 
 
-@pytest.mark.parametrize("W_,H_", [(320, 180), (257, 131)])
-def test_space_render_parity_small(torch_cuda, W_, H_):
+@pytest.mark.parametrize("W_,H_,fold", [(320, 180, False), (257, 131, False), (320, 180, True)])
+def test_space_render_parity_small(torch_cuda, W_, H_, fold):
     # the scene's chain on an exact generator: every difference comes from
-    # the chain's FP32 transcendentals and is covered by the near-edge slack
+    # the chain's FP32 transcendentals and is covered by the near-edge slack;
+    # fold: the planet's and the ring's rotations and translations run as
+    # one affine op each
     wl = W.space_render(n_points=3001, iters=40, W=W_, H=H_)
     wl.jobs[0].system = _disk_square()
     sysd = wl.jobs[0].system
@@ -80,7 +82,7 @@ def test_space_render_parity_small(torch_cuda, W_, H_):
     assert _worst(g, o) <= POS_TOL * 20
     # screen coordinates (after the perspective) within the position bar
     assert _worst_xy(g, o) <= POS_TOL
-    gl, disc = gpu_render(wl)
+    gl, disc = gpu_render(wl, fold_linear=fold)
     # band colours: a band op's coordinate (before the perspective) within
     # the position bar of a band edge makes the splat's colour unsure
     ol = oracle_render(wl, margin_px=fixed_margin(wl.targets, POS_TOL), track=True,

@@ -55,11 +55,21 @@ __device__ __forceinline__ float from_bf16(bf16r v)
     return __uint_as_float(((u32)v) << 16);
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
+// SiLU and its derivative in training: sigma(z) = 1 / (1 + e^-z) with the
+// hardware exponential and reciprocal (relative error a few ulps, far below
+// the BF16 rounding of the activations and gradients they feed)
+__device__ __forceinline__ float sigmoid_f(float z)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + __expf(-z)));
+    return r;
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 
 __device__ __forceinline__ float silu_grad_f(float z)
 {
-    const float s = 1.0f / (1.0f + expf(-z));
+    const float s = sigmoid_f(z);
     return s * (1.0f + z * (1.0f - s));
 }
 

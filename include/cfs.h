@@ -191,11 +191,12 @@ cfs_status cfs_compose(int dim_in, const cfs_transform* ops, int n_ops, cfs_chai
  *  |x| < 2^16 instead of about 1 ulp; several times fewer instructions.
  *  The generator maps are not affected. */
 #define CFS_COMPOSE_FAST_TRIG 1u
-/*  CFS_COMPOSE_FOLD_LINEAR -- every run of two or more consecutive linear
- *  ops (AFFINE2/ROTATE2 on 2D points; AFFINE3/ROTATE3/TRANSLATE3 on 3D
- *  points) runs as one affine op whose matrix and offset are the run's
- *  product, formed in double from the ops' FP32 constants and rounded once
- *  to FP32.  Positions then differ from op-by-op FP32 evaluation by a few
+/*  CFS_COMPOSE_FOLD_LINEAR -- a run of two or more consecutive linear ops
+ *  (AFFINE2/ROTATE2 on 2D points; AFFINE3/ROTATE3/TRANSLATE3 on 3D points)
+ *  runs as one affine op whose matrix and offset are the run's product,
+ *  formed in double from the ops' FP32 constants and rounded once to FP32,
+ *  wherever that op costs fewer multiply-adds than the run (a rotation about
+ *  an axis costs 4, a translation 3, a general 3D affine 9, a 2D one 4).  Positions then differ from op-by-op FP32 evaluation by a few
  *  ulps (fewer roundings); op indices (cfs_chain_set_params, cfs_chain_info)
  *  stay those of the ops as given. */
 #define CFS_COMPOSE_FOLD_LINEAR 4u

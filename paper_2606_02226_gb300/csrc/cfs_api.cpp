@@ -78,6 +78,19 @@ void derive_op_params(const cfs_transform& op, float out[CFS_OP_PARAMS])
 
 namespace {
 bool linear2(int k) { return k == CFS_OP_AFFINE2 || k == CFS_OP_ROTATE2; }
+
+// multiply-adds a linear op costs in the generated code (rotations about an
+// axis and translations have specialised forms)
+int linear_cost(int k)
+{
+    switch (k) {
+    case CFS_OP_AFFINE2: case CFS_OP_ROTATE2: return 4;
+    case CFS_OP_AFFINE3: return 9;
+    case CFS_OP_ROTATE3: return 4;
+    case CFS_OP_TRANSLATE3: return 3;
+    default: return 0;
+    }
+}
 bool linear3(int k)
 {
     return k == CFS_OP_AFFINE3 || k == CFS_OP_ROTATE3 || k == CFS_OP_TRANSLATE3;
@@ -114,8 +127,13 @@ void refresh_exec_ops(cfs_chain* c)
                                     (linear3(k) && linear3(c->ops[e].kind))))
                 ++e;
         }
-        if (e - o < 2) {
-            c->xops[c->n_xops++] = c->ops[o];
+        // fold only where one affine op is cheaper than the run as written
+        int run_cost = 0;
+        for (int j = o; j < e; ++j) run_cost += linear_cost(c->ops[j].kind);
+        const int folded_cost = linear2(k) ? linear_cost(CFS_OP_AFFINE2)
+                                           : linear_cost(CFS_OP_AFFINE3);
+        if (e - o < 2 || folded_cost >= run_cost) {
+            for (int j = o; j < e; ++j) c->xops[c->n_xops++] = c->ops[j];
             o = e;
             continue;
         }

@@ -1860,6 +1860,223 @@ __global__ void __launch_bounds__(IT_THREADS, 1) infer_tc_kernel(const bf16r* __
     }
 }
 
+// ---------------------------------------------------------------------------
+// The training forward pass fused per 128-row tile (the same structure as
+// infer_tc_kernel): the tile of inputs U goes from global memory into the
+// group's A tile; layer 1 (K = 64), layer 2 and layer 3 run as tcgen05.mma
+// chains into the group's TMEM columns, each epilogue adding the bias,
+// applying SiLU and writing the next A tile in place.  What the backward
+// pass reads is written on the way: H1 (row-major: the input of the
+// recomputed Z2) and its transpose, H2's transpose, H3 and Z3 (the output
+// layer's backward); the output layer itself (N = 2) runs on the CUDA cores
+// in the layer-3 epilogue.  H2 in row-major form, which only the next
+// layer's GEMM read, never leaves the chip.
+// ---------------------------------------------------------------------------
+constexpr int TF_GROUPS = 4;
+constexpr int TF_THREADS = 128 * TF_GROUPS;
+constexpr int TF_W1 = HID * D_IN * 2;          // 16 KB
+constexpr int TF_SMEM = 1024 + TF_W1 + 2 * IT_W + TF_GROUPS * IT_A + 256;
+
+struct TrainFwdArgs {
+    const bf16r* U;                // [B][D_IN]
+    int B;
+    bf16r *H1, *H1T, *H2T, *H3;    // H1, H3 [B][HID]; transposes [HID][ldt]
+    int ldt;
+    float *Z3, *Y;                 // Z3 [B][HID], Y [B][2]
+};
+
+__global__ void __launch_bounds__(TF_THREADS, 1) train_fwd_kernel(const bf16r* __restrict__ wb,
+                                                                  const float* __restrict__ w,
+                                                                  const TrainFwdArgs g)
+{
+    extern __shared__ unsigned char tf_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(tf_raw) + 1023) & ~(uintptr_t)1023);
+    const u32 sW1 = smem_addr(sm), sW2 = sW1 + TF_W1, sW3 = sW2 + IT_W;
+    const u32 sA0 = sW3 + IT_W;
+    u64* bars = reinterpret_cast<u64*>(sm + TF_W1 + 2 * IT_W + TF_GROUPS * IT_A);
+    u32* s_tmem = reinterpret_cast<u32*>(bars + TF_GROUPS);
+    __shared__ __align__(16) float s_b1[HID], s_b2[HID], s_b3[HID], s_w4[D_OUT][HID];
+    __shared__ float s_b4[2];
+    __shared__ int s_err;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights into the B-operand layout (rows = output features, K = inputs)
+    for (int e = tid; e < HID * D_IN; e += TF_THREADS) {
+        const int n = e / D_IN, k = e % D_IN;
+        *reinterpret_cast<bf16r*>(sm + it_off(n, k, 2048u)) = wb[OFF_W1 + e];
+    }
+    for (int e = tid; e < HID * HID; e += TF_THREADS) {
+        const int n = e / HID, k = e % HID;
+        const u32 o = it_off(n, k, 2048u);
+        *reinterpret_cast<bf16r*>(sm + TF_W1 + o) = wb[OFF_W2 + e];
+        *reinterpret_cast<bf16r*>(sm + TF_W1 + IT_W + o) = wb[OFF_W3 + e];
+    }
+    for (int j = tid; j < HID; j += TF_THREADS) {
+        s_b1[j] = w[OFF_B1 + j];
+        s_b2[j] = w[OFF_B2 + j];
+        s_b3[j] = w[OFF_B3 + j];
+        s_w4[0][j] = from_bf16(wb[OFF_W4 + j]);
+        s_w4[1][j] = from_bf16(wb[OFF_W4 + HID + j]);
+    }
+    if (tid < 2) s_b4[tid] = w[OFF_B4 + tid];
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"(smem_addr(s_tmem)), "r"(128u * TF_GROUPS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        s_err = 0;
+        for (int q = 0; q < TF_GROUPS; ++q) mbar_init(smem_addr(&bars[q]), 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    it_fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const int gi = warp >> 2, wq = warp & 3, r = wq * 32 + lane;
+    const u32 sA = sA0 + (u32)(gi * IT_A);
+    const u32 bar = smem_addr(&bars[gi]);
+    const u32 tcol = *s_tmem + (u32)(gi * 128);
+    const u32 tlane = tcol + ((u32)(wq * 32) << 16);
+    const bool issuer = wq == 0 && lane == 0;
+    const u32 idesc = tc_idesc(128);
+    u32 phase = 0;
+    int pending = 0;
+    bool ok = true;
+
+    auto mma_layer = [&](u32 sW, int K) {
+        it_fence_async_smem();
+        tc_fence_before();
+        it_group_sync(gi);
+        if (issuer) {
+            tc_fence_after();
+            for (int kk = 0; kk < K / 16; ++kk)
+                tc_mma(tcol, tc_desc_kn(sA + (u32)kk * 4096u, 2048u, 128u),
+                       tc_desc_kn(sW + (u32)kk * 4096u, 2048u, 128u), idesc, kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+            pending = 1;
+        }
+    };
+    auto wait_layer = [&]() -> bool {
+        const bool done = it_group_all(gi, mbar_wait(bar, phase));
+        if (done) {
+            phase ^= 1u;
+            if (issuer) pending = 0;
+        }
+        tc_fence_after();
+        return done;
+    };
+    // epilogue of layers 1 and 2: H = SiLU(acc + b) as BF16 into the next A
+    // tile, and into global memory (row-major and / or transposed)
+    auto hidden_epilogue = [&](const float* bias, int row, bool in, bf16r* H, bf16r* HT) {
+        const float4* b4 = reinterpret_cast<const float4*>(bias);
+#pragma unroll 1
+        for (int c0 = 0; c0 < HID; c0 += 16) {
+            float v[16];
+            tc_ld16(tlane + (u32)c0, v);
+            float h[16];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 bb = b4[c0 / 4 + j];
+                h[4 * j] = silu_f(v[4 * j] + bb.x);
+                h[4 * j + 1] = silu_f(v[4 * j + 1] + bb.y);
+                h[4 * j + 2] = silu_f(v[4 * j + 2] + bb.z);
+                h[4 * j + 3] = silu_f(v[4 * j + 3] + bb.w);
+            }
+            u32 q[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) q[j] = pack_bf16x2(h[2 * j], h[2 * j + 1]);
+            it_st16(sA + it_off(r, c0, 2048u), q[0], q[1], q[2], q[3]);
+            it_st16(sA + it_off(r, c0 + 8, 2048u), q[4], q[5], q[6], q[7]);
+            if (in && H) {
+                uint4* hp = reinterpret_cast<uint4*>(H + (size_t)row * HID + c0);
+                hp[0] = make_uint4(q[0], q[1], q[2], q[3]);
+                hp[1] = make_uint4(q[4], q[5], q[6], q[7]);
+            }
+            if (in && HT) {
+                // consecutive lanes hold consecutive rows: each column's stores coalesce
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    HT[(size_t)(c0 + j) * g.ldt + row] = (bf16r)(q[j >> 1] >> (16 * (j & 1)));
+            }
+        }
+    };
+
+    const int n_tiles = (g.B + 127) / 128;
+    for (int tile = blockIdx.x * TF_GROUPS + gi; tile < n_tiles; tile += gridDim.x * TF_GROUPS) {
+        const int row = tile * 128 + r;
+        const bool in = row < g.B;
+        // the tile's inputs: row r's 64 BF16 values into K groups 0..7
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(g.U + (size_t)row * D_IN);
+#pragma unroll
+            for (int kq = 0; kq < D_IN / 8; ++kq) {
+                const uint4 v = in ? __ldg(src + kq) : make_uint4(0u, 0u, 0u, 0u);
+                it_st16(sA + it_off(r, 8 * kq, 2048u), v.x, v.y, v.z, v.w);
+            }
+        }
+        mma_layer(sW1, D_IN);
+        if (!(ok = wait_layer())) break;
+        hidden_epilogue(s_b1, row, in, g.H1, g.H1T);
+        mma_layer(sW2, HID);
+        if (!(ok = wait_layer())) break;
+        hidden_epilogue(s_b2, row, in, nullptr, g.H2T);
+        mma_layer(sW3, HID);
+        if (!(ok = wait_layer())) break;
+        // layer 3: Z3 (FP32) and H3 (BF16) out, then the output layer on
+        // the BF16 activations, columns in order
+        float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < HID; c0 += 16) {
+            float v[16];
+            tc_ld16(tlane + (u32)c0, v);
+            float z[16];
+            u32 q[8];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) z[j] = v[j] + s_b3[c0 + j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) q[j] = pack_bf16x2(silu_f(z[2 * j]), silu_f(z[2 * j + 1]));
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float x = __uint_as_float((q[j >> 1] >> (16 * (j & 1))) << 16);
+                y0 = fmaf(x, s_w4[0][c0 + j], y0);
+                y1 = fmaf(x, s_w4[1][c0 + j], y1);
+            }
+            if (in) {
+                float4* zp = reinterpret_cast<float4*>(g.Z3 + (size_t)row * HID + c0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    zp[j] = make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]);
+                uint4* hp = reinterpret_cast<uint4*>(g.H3 + (size_t)row * HID + c0);
+                hp[0] = make_uint4(q[0], q[1], q[2], q[3]);
+                hp[1] = make_uint4(q[4], q[5], q[6], q[7]);
+            }
+        }
+        tc_fence_before();          // TMEM read: the next tile's MMAs may overwrite it
+        if (in) {
+            g.Y[2 * (size_t)row] = y0 + s_b4[0];
+            g.Y[2 * (size_t)row + 1] = y1 + s_b4[1];
+        }
+    }
+    if (!ok) {
+        atomicExch(&s_err, 1);
+        if (issuer && pending) mbar_wait(bar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && s_err) atomicOr(&g_tc_error, (unsigned)CFS_DEVICE_ERR_TC_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem),
+                     "r"(128u * TF_GROUPS)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -2050,6 +2267,26 @@ cfs_status tc_splitk(cudaStream_t st, int N, int K, const bf16r* A, int lda, con
 cfs_status forward(cfs_sampler* s, const bf16r* U, int B, cudaStream_t st)
 {
     const bf16r* wb = s->wb;
+    if (rows_on_tma(B) && (uintptr_t)U % 16 == 0) {
+        // the fused pass (one launch): what the backward reads, and Y
+        static int smem_dev = -1;
+        if (smem_dev != s->device) {
+            cfs_status r = check_cuda(cudaFuncSetAttribute(train_fwd_kernel,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           TF_SMEM),
+                                      "cudaFuncSetAttribute(train_fwd_kernel)");
+            if (r != CFS_OK) return r;
+            smem_dev = s->device;
+        }
+        TrainFwdArgs a;
+        a.U = U; a.B = B;
+        a.H1 = s->H1; a.H1T = s->H1T; a.H2T = s->H2T; a.H3 = s->H3;
+        a.ldt = s->ldt; a.Z3 = s->Z3; a.Y = s->Y;
+        const int tiles = (B + 127) / 128;
+        const int grid = std::max(1, std::min(device_sm_count(), (tiles + TF_GROUPS - 1) / TF_GROUPS));
+        train_fwd_kernel<<<grid, TF_THREADS, TF_SMEM, st>>>(wb, s->w, a);
+        return check_cuda(cudaGetLastError(), "train_fwd_kernel launch");
+    }
     // Z1 and Z2 only where the backward reads them (it recomputes them on
     // tc_rows_kernel); Z3 always (the output layer's backward reads it)
     const bool keep_z = !rows_on_tma(B);

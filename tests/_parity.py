@@ -204,3 +204,23 @@ def oracle_render_parallel(wl, workers, margin_px=0.0, track=False, band_eps=0.0
     with mp.get_context("spawn").Pool(len(chunks)) as pool:
         parts = pool.map(_oracle_worker, [(wl, c, margin_px, track, band_eps) for c in chunks])
     return merge_tracked(parts)
+
+
+def _points_worker(args):
+    xyz, fn, chain, targets, margin_px, track, band_eps = args
+    return O.render_points(xyz, fn, chain, targets, margin_px=margin_px, track=track,
+                           band_eps=band_eps)
+
+
+def oracle_render_points_parallel(xyz, fn, chain, targets, workers, margin_px=0.0, track=False,
+                                  band_eps=0.0):
+    """The oracle's render of stored points (xyz [n][3], fn [n]) on spawned
+    processes over disjoint point ranges, merged."""
+    import multiprocessing as mp
+    n = xyz.shape[0]
+    per = -(-n // workers)
+    parts = [(xyz[b:b + per], fn[b:b + per], chain, targets, margin_px, track, band_eps)
+             for b in range(0, n, per)]
+    with mp.get_context("spawn").Pool(len(parts)) as pool:
+        res = pool.map(_points_worker, parts)
+    return merge_tracked(res)

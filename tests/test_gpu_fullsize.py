@@ -24,7 +24,7 @@ import pytest
 from paper_2606_02226_gb300 import workloads as W
 
 from _parity import (EMPTY, check_depth_close, check_rgba_close, fixed_margin, gpu_render,
-                     oracle_render_parallel)
+                     oracle_render_parallel, oracle_render_points_parallel)
 
 pytestmark = pytest.mark.gpu
 
@@ -127,3 +127,34 @@ def test_space_whole_image_full_size(torch_cuda):
     assert abs(disc[0] - ol[0].n_discard) <= ol[0].n_amb
     check_depth_close(gl[0], ol[0])
     assert (gl[0] != EMPTY).sum() > 100000
+
+
+def test_cloud_full_size_central_crop(torch_cuda):
+    """The bench's stored cloud (2^26 points, generated on the GPU -- bit for
+    bit the oracle's generation -- and streamed through frame 40's chain
+    with the linear ops folded, as the bench runs it) into the 8192^2 depth
+    layer, compared with the oracle over the central 1024 x 1024 pixels: the
+    oracle renders every point into that crop alone (view [-1/8, 1/8]^2,
+    the same 4096 pixels per unit), so every crop pixel gets its depth
+    bounds and, where decided, its exact colour."""
+    torch = torch_cuda
+    from paper_2606_02226_gb300 import cfs
+    sysd = W.cloud_system()
+    n = 1 << 26
+    xyz, fn = cfs.pointcloud_generate(cfs.System(sysd), n, 32)
+    t = W.cloud_target(8192)
+    ten = cfs.alloc_target(t)
+    chain = W.cloud_chain(40)
+    cfs.render_points(cfs.Chain(chain, 3, fold_linear=True), xyz, fn, [t], [ten])
+    torch.cuda.synchronize()
+    crop = ten[3584:4608, 3584:4608].cpu().numpy().view(np.uint64)
+    hx = np.ascontiguousarray(xyz.cpu().numpy().T)
+    hf = fn.cpu().numpy()
+    del xyz, fn, ten
+    tc = W.cloud_target(1024)
+    tc.view = (-0.125, 0.125, -0.125, 0.125)
+    o = oracle_render_points_parallel(hx, hf, chain, [tc], WORKERS,
+                                      margin_px=fixed_margin([tc], POS_TOL), track=True)[0]
+    assert o.n_splat + o.n_discard == n
+    check_depth_close(crop, o)
+    assert (crop != EMPTY).sum() > 50000

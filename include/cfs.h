@@ -363,7 +363,8 @@ cfs_status cfs_batch_set_plan(cfs_batch* batch, const cfs_batch_plan* plan);
  *     to even: 2^16-2^17, 2^18-2^19, ...) and target size (width x height of
  *     target 0) -- the item size and whether the frame uses the window, timed
  *     on that class's frames alone; the classes' choices are then kept only
- *     if the whole batch runs faster with them than under stage 1's plan.
+ *     if the whole batch runs faster with them than under stage 1's plan
+ *     (batches of more than 32 classes skip this stage).
  * The choices are kept in the library's tuning cache under keys made of the
  * device (name, SM count), the program's structure and the classes; a later
  * cfs_batch_tune whose keys are all cached applies them without trials

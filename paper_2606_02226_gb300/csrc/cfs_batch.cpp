@@ -310,6 +310,10 @@ cfs_status run_direct(cfs_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t 
     if (st == CFS_OK) st = check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
     return st;
 }
+// the autotuner's per-class stage runs for batches of at most this many shape
+// classes
+constexpr int kMaxTunedClasses = 32;
+
 // ---- the tuning cache ------------------------------------------------------
 // Keys hold no spaces (the file format is "key value" per line).
 std::map<std::string, std::string> g_cache;
@@ -826,9 +830,12 @@ cfs_status cfs_batch_tune(cfs_batch* b, uint32_t trial_iters, uint32_t flags, vo
     }
 
     // ---- stage 2: item size and window per shape class -------------------
-    int n_win = 0;
+    // (only for a batch of at most kMaxTunedClasses classes: each class costs
+    // up to eight trials)
+    int n_win = b->spec.tile ? (int)counts.size() : 0;
     bool use_classes = false;
-    if (st == CFS_OK) {
+    if (st == CFS_OK && (int)counts.size() <= kMaxTunedClasses) {
+        n_win = 0;
         cfs_batch_plan prog = b->plan;
         prog.chunk = 0;                 // the program's knobs only
         const std::string pkey = format_plan(prog);

@@ -964,6 +964,11 @@ def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames
         rec["selection_infer_ms"] = min(timed_once(infer) for _ in range(2))
         rec["selection_ratio"] = ms_plain_sel / rec["selection_warm_ms"]
         arms[key] = (run_warm, infer, warm, starts)
+    if "per_point" in out["warm"] and "selection_infer_ms" in out["warm"]["per_point"]:
+        # the inference kernel's throughput on the largest call: one sample
+        # per point of the 256 frames
+        out["infer_roofline_per_point"] = _infer_roofline(
+            sum(it[1] for it in items), out["warm"]["per_point"]["selection_infer_ms"])
     if not arms:
         return out
     best = max(arms, key=lambda a: out["warm"][a]["selection_ratio"])

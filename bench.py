@@ -396,11 +396,13 @@ def run_cfs(args, wl):
             h.copy_(t, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / n_e2e
-    e2e = {"value": wl.point_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+    e2e = {"value": wl.point_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": len(jobs) * cfs.render_arg_bytes(),
            "d2h_bytes_per_step": d2h,
            "note": "system and chain built from host descriptions and passed through the C "
-                   "ABI each step (parameters travel in the launch); both layers read back "
-                   "to pinned host memory"}
+                   "ABI each step: the inputs travel host to device in each render launch's "
+                   "argument block (the h2d bytes); both layers read back to pinned host "
+                   "memory"}
 
     if rank != 0:
         if world > 1:
@@ -822,7 +824,7 @@ def _infer_roofline(samples, ms):
 
 def bench_sampler(torch, cfs, dev, stream, train_steps: int = 20000, eval_frames: int = 16,
                   n_eval: int = 1 << 20, batch_frames: int = 256,
-                  unique_options=(4096, 65536, 0), pairs: int = 24,
+                  unique_options=(4096, 65536, 0), pairs: int = 40,
                   lr_final: Optional[float] = None):
     """Learned warm start (form 4) against plain burn-in at equal L1 error.
 
@@ -1066,7 +1068,7 @@ def main():
     ap.add_argument("--sampler-steps", type=int, default=20000)
     ap.add_argument("--sampler-lr-final", type=float, default=0.0,
                     help="cosine decay of the sampler's step size from 1e-3 to this (0: constant)")
-    ap.add_argument("--sampler-pairs", type=int, default=24,
+    ap.add_argument("--sampler-pairs", type=int, default=40,
                     help="interleaved plain/warm batch timings")
     ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--cloud-frames", type=int, default=64)

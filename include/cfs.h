@@ -645,6 +645,11 @@ cfs_status cfs_debug_raise_device_error(uint32_t flags);
 /* Message of the last failed call on this thread ("" if none). */
 const char* cfs_last_error(void);
 
+/* Bytes of the argument block each cfs_render launch copies from the host to
+ * the device: the system, the chain's constants, the targets and the Philox
+ * round keys travel there, not in device buffers. */
+uint32_t cfs_render_arg_bytes(void);
+
 /* Library version string. */
 const char* cfs_version(void);
 

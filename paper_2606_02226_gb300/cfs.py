@@ -155,6 +155,7 @@ _SIGNATURES = {
     "cfs_pointcloud_reorder": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.c_int, _P, _P,
                                               _P, _P]),
     "cfs_stream_status": (ctypes.c_int, [_P]),
+    "cfs_render_arg_bytes": (ctypes.c_uint32, []),
     "cfs_debug_raise_device_error": (ctypes.c_int, [ctypes.c_uint32]),
     "cfs_sampler_param_count": (ctypes.c_uint32, []),
     "cfs_sampler_create": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
@@ -825,6 +826,11 @@ def stream_status(stream=None):
 def debug_raise_device_error(flags: int = DEVICE_ERR_TC_TIMEOUT):
     """Sets device error flags from the host, as a timed-out kernel would."""
     _check(lib().cfs_debug_raise_device_error(flags))
+
+
+def render_arg_bytes() -> int:
+    """Bytes of the argument block a render launch copies to the device."""
+    return int(lib().cfs_render_arg_bytes())
 
 
 def version() -> str:

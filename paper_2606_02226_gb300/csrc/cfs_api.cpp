@@ -400,6 +400,8 @@ const char* cfs_last_error(void) { return cfs::last_error(); }
 
 const char* cfs_version(void) { return "cfs-gb300 0.1 (sm_103a)"; }
 
+uint32_t cfs_render_arg_bytes(void) { return (uint32_t)sizeof(cfs_launch_args); }
+
 cfs_status cfs_stream_status(void* stream)
 {
     clear_error();

@@ -39,6 +39,12 @@ def test_version_string():
     assert "sm_103a" in cfs.version()
 
 
+def test_render_arg_bytes():
+    # system (848 B), chain constants (2048), four targets (1504), Philox
+    # round keys (80) and the launch's pointers and counts
+    assert 4400 < cfs.render_arg_bytes() <= 4 * 1024 + 1024
+
+
 def test_tune_cache_files_need_no_gpu(tmp_path):
     cfs.tune_cache_clear()
     assert cfs.tune_cache_size() == 0

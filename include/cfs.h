@@ -331,6 +331,16 @@ cfs_status cfs_batch_discards(cfs_batch* batch, uint64_t* out);
 /* Work items, points per item (the plan's default), persistent grid size. */
 cfs_status cfs_batch_info(const cfs_batch* batch, uint32_t* n_items, uint32_t* chunk,
                           uint32_t* grid);
+/* The privatized shared-memory windows of every frame in the last launch,
+ * host int32 [n_frames][C][4] (C: the channels of target 0's histogram) =
+ * (x0, y0, x1, y1): the inclusive pixel box of channel c of target 0 whose
+ * splats the launch counted in shared memory (every other splat is a
+ * global reduction); (0, 0, -1, -1) for none (window off in the plan or
+ * for the frame's shape class, or no sample of the channel landed).
+ * Measurement aid: with the frame's histogram it gives the numbers of
+ * shared-memory and global splats exactly.  Waits for the launch;
+ * CFS_ERR_INVALID_ARG before the first launch. */
+cfs_status cfs_batch_windows(cfs_batch* batch, int32_t* out);
 
 /* Launch plan of a batch (its tuning knobs: points per thread, privatized
  * tile size and atomic strategy, work-item size).  The first

@@ -133,6 +133,7 @@ _SIGNATURES = {
     "cfs_batch_set_system": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cfs_batch_launch": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "cfs_batch_discards": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "cfs_batch_windows": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "cfs_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.POINTER(ctypes.c_uint32)]),
@@ -530,6 +531,9 @@ class Batch:
         self.handle = h
         self.n_frames = len(frames)
         self.n_targets = nt
+        d0 = frames[0][4][0] if frames and nt else None
+        self.window_channels = max(1, int(d0.C)) if d0 is not None and d0.kind == "hist_u32" \
+            else 1
         self._keep = [f[0] for f in frames] + [chain]
 
     def launch(self, clear: bool = True, stream=None):
@@ -543,6 +547,15 @@ class Batch:
         out = np.zeros((self.n_frames, max(1, self.n_targets)), dtype=np.uint64)
         _check(lib().cfs_batch_discards(self.handle,
                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out
+
+    def windows(self) -> np.ndarray:
+        """Each frame's privatized windows in the last launch: int32
+        [n_frames][channels][4] = (x0, y0, x1, y1), inclusive pixels of
+        each channel of target 0; (0, 0, -1, -1) where there was none."""
+        out = np.zeros((self.n_frames, self.window_channels, 4), dtype=np.int32)
+        _check(lib().cfs_batch_windows(self.handle,
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
         return out
 
     def info(self):

@@ -524,11 +524,13 @@ cfs_status cfs_batch_create(const cfs_chain* chain, int n_targets, const cfs_fra
     st = plan_items(b);
     if (st != CFS_OK) { delete b; return st; }
 
-    // workspace: frames | bbox (int4 per frame) | counter (u32, padded to
+    // workspace: frames | window boxes (an int4 per frame and histogram
+    // channel, CFS_A_MAX_MAPS slots per frame) | counter (u32, padded to
     // 256 B) | discards (the counter and discards are reset every launch)
     const size_t fbytes = sizeof(cfs_dev_frame) * (size_t)n_frames;
     const size_t off_bbox = (fbytes + 255) & ~(size_t)255;
-    const size_t off_counter = (off_bbox + 16 * (size_t)n_frames + 255) & ~(size_t)255;
+    const size_t off_counter =
+        (off_bbox + 16 * (size_t)CFS_A_MAX_MAPS * (size_t)n_frames + 255) & ~(size_t)255;
     const size_t off_disc = off_counter + 256;
     b->work_bytes = off_disc + sizeof(unsigned long long) * (size_t)n_frames *
                                    (size_t)std::max(1, n_targets);
@@ -625,6 +627,47 @@ cfs_status cfs_batch_info(const cfs_batch* b, uint32_t* n_items, uint32_t* chunk
     if (n_items) *n_items = b->n_items;
     if (chunk) *chunk = b->chunk;
     if (grid) *grid = b->grid;
+    return CFS_OK;
+}
+
+// histogram channels of the batch's target 0 (the windowed splat's)
+static int window_channels(const cfs_batch* b)
+{
+    if (b->n_frames < 1 || b->n_targets < 1) return 1;
+    const cfs_target& g = b->frames[0].targets[0];
+    return g.kind == CFS_TARGET_HIST_U32 ? std::max(1, g.channels) : 1;
+}
+
+cfs_status cfs_batch_windows(cfs_batch* b, int32_t* out)
+{
+    clear_error();
+    if (!b || !out) return fail(CFS_ERR_INVALID_ARG, "NULL batch or out");
+    if (!b->launched) return fail(CFS_ERR_INVALID_ARG, "the batch has not been launched");
+    cfs_status st = check_cuda(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+    if (st != CFS_OK) return st;
+    const int C = window_channels(b);
+    const size_t n = 4 * (size_t)CFS_A_MAX_MAPS * (size_t)b->n_frames;
+    std::vector<int32_t> box(n, 0);
+    if (b->spec.tile) {
+        st = check_cuda(cudaMemcpy(box.data(), b->d_bbox, sizeof(int32_t) * n,
+                                   cudaMemcpyDeviceToHost),
+                        "cudaMemcpy(windows)");
+        if (st != CFS_OK) return st;
+    }
+    const long long cap = b->spec.tile ? (long long)(b->tile_cap / (uint32_t)C) : 0;
+    for (int f = 0; f < b->n_frames; ++f)
+        for (int c = 0; c < C; ++c) {
+            int32_t* o = out + 4 * ((size_t)f * (size_t)C + (size_t)c);
+            const int32_t* w = box.data() + 4 * ((size_t)f * CFS_A_MAX_MAPS + (size_t)c);
+            // the kernel's rule: no window for the frame, an empty box, or a
+            // box above the channel's counters
+            const bool none = !b->spec.tile || b->nowin[f] || w[2] < w[0] || w[3] < w[1] ||
+                              (long long)(w[2] - w[0] + 1) * (long long)(w[3] - w[1] + 1) > cap;
+            o[0] = none ? 0 : w[0];
+            o[1] = none ? 0 : w[1];
+            o[2] = none ? -1 : w[2];
+            o[3] = none ? -1 : w[3];
+        }
     return CFS_OK;
 }
 

@@ -422,20 +422,22 @@ __device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x,
     }
 }
 
-/* Privatized histogram window (batched frames): u32 counters in shared
- * memory for pixels [wx0, wx0 + ww) x [wy0, wy0 + wh) of every channel,
- * layout [ch][y][x].  ww == 0 turns it off. */
+/* The privatized window of a batch frame's u32 histogram: one pixel box
+ * per channel (a channel's splats come from its own maps, whose images are
+ * smaller copies of the attractor, so each channel's box sits over that
+ * channel's densest region), cap counters per channel in shared memory. */
 struct CfsTile {
-    u32* cnt;
-    int wx0, wy0, ww, wh;
-    int n_rep;      /* copies of the window (warp w adds to copy w % n_rep) */
-    int stride;     /* counters per copy */
-    int rep_off;    /* this warp's copy offset: (warp % n_rep) * stride */
+    u32* cnt;           /* shared counters: channel c at cnt + c * cap */
+    const int4* win;    /* shared, per channel: (x0, y0, w, h); w = 0: no window */
+    int cap;            /* counters per channel */
+    int rep_off;        /* this warp's copy: (warp % n_rep) * stride */
+    int n_rep;          /* copies of each channel's window */
+    int stride;         /* counters per copy (the largest channel window) */
 };
 
-/* u32 histogram splat that adds to the shared window when the bin lies in
- * it (one shared atomic per group of lanes hitting the same counter with
- * CFS_WARP_AGG) and to global memory otherwise. */
+/* u32 histogram splat that adds to the shared window of its channel when
+ * the bin lies in it (one shared atomic per group of lanes hitting the same
+ * counter with CFS_WARP_AGG) and to global memory otherwise. */
 __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, const CfsTile& tl,
                                                     float x, float y, bool alive, int ch,
                                                     u32& disc)
@@ -443,10 +445,11 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
     const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
     const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
     if (alive && ix >= 0 && iy >= 0) {
-        const int lx = ix - tl.wx0, ly = iy - tl.wy0;
-        if ((unsigned)lx < (unsigned)tl.ww && (unsigned)ly < (unsigned)tl.wh) {
-            const u32 idx = ((u32)ch * (u32)tl.wh + (u32)ly) * (u32)tl.ww + (u32)lx +
-                            (u32)tl.rep_off;
+        const int4 w = tl.win[ch];
+        const int lx = ix - w.x, ly = iy - w.y;
+        if ((unsigned)lx < (unsigned)w.z && (unsigned)ly < (unsigned)w.w) {
+            const u32 idx = (u32)ch * (u32)tl.cap + (u32)tl.rep_off + (u32)ly * (u32)w.z +
+                            (u32)lx;
 #if CFS_WARP_AGG
             const u32 act = __activemask();
             const u32 peers = __match_any_sync(act, idx);
@@ -464,28 +467,28 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
     }
 }
 
-/* Adds the window's nonzero counters (summed over its copies) to the
- * global histogram and zeroes them (all threads of the CTA; the caller
- * synchronizes around it). */
+/* Adds the windows' nonzero counters (summed over their copies) to the
+ * global histogram and zeroes them; every thread of the CTA takes part. */
 __device__ __forceinline__ void cfs_flush_tile(const cfs_dev_target& t, const CfsTile& tl, int C)
 {
-    if (tl.ww <= 0) return;
-    const u32 per = (u32)tl.ww * (u32)tl.wh;
-    const u32 n = (u32)C * per;
     u32* base = reinterpret_cast<u32*>(t.data);
-    for (u32 e = threadIdx.x; e < n; e += blockDim.x) {
-        u32 v = 0;
-        for (int r = 0; r < tl.n_rep; ++r) {
-            u32* c = tl.cnt + (size_t)r * tl.stride + e;
-            v += *c;
-            *c = 0u;
-        }
-        if (v) {
-            const u32 ch = e / per, r = e - ch * per;
-            const u32 ly = r / (u32)tl.ww, lx = r - ly * (u32)tl.ww;
-            const size_t off = ((size_t)ch * (size_t)t.H + (size_t)(tl.wy0 + (int)ly)) *
-                                   (size_t)t.W + (size_t)(tl.wx0 + (int)lx);
-            cfs_red_add_u32(base + off, v);
+    for (int ch = 0; ch < C; ++ch) {
+        const int4 w = tl.win[ch];
+        const u32 per = (u32)w.z * (u32)w.w;
+        u32* cc = tl.cnt + (size_t)ch * (size_t)tl.cap;
+        for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
+            u32 v = 0;
+            for (int r = 0; r < tl.n_rep; ++r) {
+                u32* c = cc + (size_t)r * (size_t)tl.stride + e;
+                v += *c;
+                *c = 0u;
+            }
+            if (v) {
+                const u32 ly = e / (u32)w.z, lx = e - ly * (u32)w.z;
+                const size_t off = ((size_t)ch * (size_t)t.H + (size_t)(w.y + (int)ly)) *
+                                       (size_t)t.W + (size_t)(w.x + (int)lx);
+                cfs_red_add_u32(base + off, v);
+            }
         }
     }
 }

@@ -318,7 +318,7 @@ cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
         float4 Z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (CFS_DIM == 3) Z = cfs_ld_stream_f4(xs + 2 * (size_t)n_pts + o, policy);
         const u32 K = cfs_ld_stream_u32(fn + o, policy);
-        const CfsTile nt{0, 0, 0, 0, 0, 1, 0, 0};
+        const CfsTile nt{0, 0, 0, 0, 1, 0};
         float qx, qy, qz;
         cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), 0u, disc, true, (float*)0, qx, qy, qz,
                   nt);
@@ -353,7 +353,7 @@ cfs_render_kernel(const __grid_constant__ cfs_launch_args a)
         float x, y, z;
         cfs_start(a, i, a.system_id, j, a.n_points, x, y, z);
         cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc,
-                      CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
+                      CfsTile{0, 0, 0, 0, 1, 0});
     }
     cfs_flush_discards(a, disc, CFS_NT);
 }
@@ -386,7 +386,7 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         float qx, qy, qz;
         const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, aux, disc, false,
                                      qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz,
-                                     CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
+                                     CfsTile{0, 0, 0, 0, 1, 0});
 #if CFS_REUSE
         if (alive) { x = qx; y = qy; z = qz; }
 #else
@@ -433,10 +433,73 @@ __device__ __forceinline__ void cfs_load_frame(const cfs_dev_frame& fr, CfsSmem&
 }
 
 #if CFS_TILE
-/* Pre-pass of the privatized window: one CTA per frame runs its first
- * blockDim points for up to 32 splat steps and records the pixel box they
- * reach in target 0 (a sample: splats outside the final window still go to
- * global memory, so the box only has to catch most of them). */
+/* The first blockDim points of a frame, run for up to 32 splat steps past
+ * the burn-in: calls visit(ix, iy, k) for every sample that lands in target
+ * 0 (k: the generator map of the step). */
+template <class Visit>
+__device__ __forceinline__ void cfs_window_samples(const cfs_launch_args& a,
+                                                   const cfs_dev_frame& fr,
+                                                   const CfsChooseTab& choose,
+                                                   const cfs_dev_target* s_tg, const CfsSmem& sm,
+                                                   Visit visit)
+{
+    const u32 j = threadIdx.x;
+    if (j >= fr.n_points) return;
+    const u32 i = fr.point_begin + j, sid = fr.system_id;
+    const uint4 r0 = cfs_philox(a, i, 0u, sid, 1u);
+    float x = (float)(r0.x >> 8) * CFS_INV_2_24;
+    float y = (float)(r0.y >> 8) * CFS_INV_2_24;
+    float z = CFS_DIM == 3 ? (float)(r0.z >> 8) * CFS_INV_2_24 : 0.0f;
+    const u32 n1 = min(a.iters, a.burn_in + 32u);
+    const cfs_dev_target& t0 = s_tg[0];
+    u32 disc[CFS_NT_ARR];
+    for (u32 n = 0; n < n1; ++n) {
+        const uint4 r = cfs_philox(a, i, n >> 2, sid, 0u);
+        const int k = choose(cfs_word(r, n & 3u));
+        cfs_gen_map(a, k, x, y, z, sm);
+        if (n < a.burn_in) continue;
+        const u32 aux = cfs_word(cfs_aux_block(a, i, n >> 2, sid), n & 3u);
+        float rec[4 * CFS_NSPLAT_ARR];
+        float qx, qy, qz;
+        cfs_chain(a, s_tg, sm, x, y, z, k, aux, disc, false, rec, qx, qy, qz,
+                  CfsTile{0, 0, 0, 0, 1, 0});
+        const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
+        const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);
+        if (rec[3] != 0.0f && ix >= 0 && iy >= 0) visit(ix, iy, k);
+    }
+}
+
+#define CFS_WG 64                        /* coarse density grid: CFS_WG x CFS_WG cells */
+#define CFS_WIN_SHAPES 5                 /* window aspect ratios 1/4, 1/2, 1, 2, 4 */
+
+/* Window shape q of the pre-pass (width / height = 2^(q - 2), q = 0..4):
+ * at most cap pixels, inside a bw x bh box, widened to the cap once the
+ * height is clamped. */
+__device__ __forceinline__ void cfs_window_shape(int q, int cap, int bw, int bh, int& ww, int& wh)
+{
+    ww = (int)sqrtf((float)cap * ldexpf(1.0f, q - 2));
+    ww = max(1, min(ww, bw));
+    wh = max(1, min(bh, cap / ww));
+    ww = max(1, min(bw, cap / wh));
+}
+
+/* Pre-pass of the privatized windows: one CTA per frame samples the frame's
+ * first blockDim trajectories (see cfs_window_samples) and writes, for each
+ * channel c of target 0, the pixel box its window covers (at most
+ * tile_cap / CFS_TILE_C pixels; empty when no sample of the channel
+ * landed) to frame_bbox[f * CFS_A_MAX_MAPS + c].  A sample's channel is
+ * its map index mod CFS_TILE_C (a chain that recolours moves splats to
+ * other channels; they then miss the window more often, nothing else).
+ * When the channel's sampled box fits its window, the window is that box.
+ * Otherwise the channel's samples are binned into a coarse grid over the
+ * box, and of the windows of the channel's capacity (five aspect ratios,
+ * positions on the grid's cell boundaries) the one holding the most
+ * samples wins: attractors are far from uniform, and the densest region is
+ * where privatizing the counters saves the most L2 reductions.  Splats
+ * outside the windows still go to global memory, so the choice changes the
+ * speed only, never the histogram.  The trajectories are run again for
+ * every pass (two per channel at most): they are cheaper than storing the
+ * samples. */
 extern "C" __global__ void __launch_bounds__(CFS_BLOCK)
 cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
 {
@@ -445,80 +508,130 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ u32 s_T[CFS_A_MAX_MAPS];
     __shared__ cfs_dev_target s_tg[CFS_NT_ARR];
     __shared__ int s_box[4];
+    __shared__ u32 s_grid[CFS_WG * CFS_WG];
+    __shared__ unsigned long long s_best;
     const int f = blockIdx.x;
     const cfs_dev_frame& fr = reinterpret_cast<const cfs_dev_frame*>(a.frames)[f];
     cfs_load_frame(fr, sm, s_T, s_tg);
-    if (threadIdx.x == 0) {
-        s_box[0] = 0x7fffffff; s_box[1] = 0x7fffffff; s_box[2] = -1; s_box[3] = -1;
-    }
-    __syncthreads();
     const CfsChooseTab choose{s_T, fr.n_cmp};
-    int bx0 = 0x7fffffff, by0 = 0x7fffffff, bx1 = -1, by1 = -1;
-    const u32 j = threadIdx.x;
-    if (j < fr.n_points) {
-        const u32 i = fr.point_begin + j, sid = fr.system_id;
-        const uint4 r0 = cfs_philox(a, i, 0u, sid, 1u);
-        float x = (float)(r0.x >> 8) * CFS_INV_2_24;
-        float y = (float)(r0.y >> 8) * CFS_INV_2_24;
-        float z = CFS_DIM == 3 ? (float)(r0.z >> 8) * CFS_INV_2_24 : 0.0f;
-        const u32 n1 = min(a.iters, a.burn_in + 32u);
-        const cfs_dev_target& t0 = s_tg[0];
-        u32 disc[CFS_NT_ARR];
-        for (u32 n = 0; n < n1; ++n) {
-            const uint4 r = cfs_philox(a, i, n >> 2, sid, 0u);
-            const int k = choose(cfs_word(r, n & 3u));
-            cfs_gen_map(a, k, x, y, z, sm);
-            if (n < a.burn_in) continue;
-            const u32 aux = cfs_word(cfs_aux_block(a, i, n >> 2, sid), n & 3u);
-            float rec[4 * CFS_NSPLAT_ARR];
-            float qx, qy, qz;
-            cfs_chain(a, s_tg, sm, x, y, z, k, aux, disc, false, rec, qx, qy, qz,
-                      CfsTile{0, 0, 0, 0, 0, 1, 0, 0});
-            const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
-            const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);
-            if (rec[3] != 0.0f && ix >= 0 && iy >= 0) {
-                bx0 = min(bx0, ix); by0 = min(by0, iy);
-                bx1 = max(bx1, ix); by1 = max(by1, iy);
-            }
+    const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* window pixels per channel */
+    int4* out = reinterpret_cast<int4*>(a.frame_bbox) + (size_t)f * CFS_A_MAX_MAPS;
+    for (int c = 0; c < CFS_TILE_C; ++c) {
+        if (threadIdx.x == 0) {
+            s_box[0] = 0x7fffffff; s_box[1] = 0x7fffffff; s_box[2] = -1; s_box[3] = -1;
+            s_best = 0ull;
         }
+        for (int e = threadIdx.x; e < CFS_WG * CFS_WG; e += blockDim.x) s_grid[e] = 0u;
+        __syncthreads();
+        int bx0 = 0x7fffffff, by0 = 0x7fffffff, bx1 = -1, by1 = -1;
+        cfs_window_samples(a, fr, choose, s_tg, sm, [&](int ix, int iy, int k) {
+            if (k % CFS_TILE_C != c) return;
+            bx0 = min(bx0, ix); by0 = min(by0, iy);
+            bx1 = max(bx1, ix); by1 = max(by1, iy);
+        });
+        atomicMin(&s_box[0], bx0); atomicMin(&s_box[1], by0);
+        atomicMax(&s_box[2], bx1); atomicMax(&s_box[3], by1);
+        __syncthreads();
+        int4 box = make_int4(s_box[0], s_box[1], s_box[2], s_box[3]);
+        const int bw = box.z - box.x + 1, bh = box.w - box.y + 1;
+        if (box.z >= box.x && box.w >= box.y && cap >= 1 && (long long)bw * bh > cap) {
+            /* the grid: cells of cw x ch pixels over the box, gx x gy of them */
+            const int cw = (bw + CFS_WG - 1) / CFS_WG, ch = (bh + CFS_WG - 1) / CFS_WG;
+            const int gx = (bw + cw - 1) / cw, gy = (bh + ch - 1) / ch;
+            cfs_window_samples(a, fr, choose, s_tg, sm, [&](int ix, int iy, int k) {
+                if (k % CFS_TILE_C == c && ix >= box.x && ix <= box.z && iy >= box.y &&
+                    iy <= box.w)
+                    atomicAdd(&s_grid[((iy - box.y) / ch) * CFS_WG + (ix - box.x) / cw], 1u);
+            });
+            __syncthreads();
+            /* summed-area table: rows, then columns */
+            for (int r = threadIdx.x; r < gy; r += blockDim.x) {
+                u32 s = 0u;
+                for (int q = 0; q < gx; ++q) s_grid[r * CFS_WG + q] = (s += s_grid[r * CFS_WG + q]);
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < gx; q += blockDim.x) {
+                u32 s = 0u;
+                for (int r = 0; r < gy; ++r) s_grid[r * CFS_WG + q] = (s += s_grid[r * CFS_WG + q]);
+            }
+            __syncthreads();
+            /* candidates: shape q, cell position (i0, j0); the window's whole
+             * cells nw x nh are counted */
+            const int per = CFS_WG * CFS_WG;
+            for (int cand = threadIdx.x; cand < CFS_WIN_SHAPES * per; cand += blockDim.x) {
+                const int q = cand / per, pos = cand - q * per;
+                const int j0 = pos / CFS_WG, i0 = pos - j0 * CFS_WG;
+                int ww, wh;
+                cfs_window_shape(q, cap, bw, bh, ww, wh);
+                const int nw = max(1, ww / cw), nh = max(1, wh / ch);
+                if (i0 + nw > gx || j0 + nh > gy) continue;
+                auto at = [&](int r, int col) -> u32 {
+                    return (r < 0 || col < 0) ? 0u : s_grid[r * CFS_WG + col];
+                };
+                const int r1 = j0 + nh - 1, c1 = i0 + nw - 1;
+                const u32 mass = at(r1, c1) - at(j0 - 1, c1) - at(r1, i0 - 1) + at(j0 - 1, i0 - 1);
+                /* most samples; ties to the lowest candidate number */
+                const unsigned long long key =
+                    ((unsigned long long)mass << 32) | (unsigned long long)(0xffffffffu - (u32)cand);
+                atomicMax(&s_best, key);
+            }
+            __syncthreads();
+            int ww, wh, x0, y0;
+            if (s_best != 0ull) {
+                const u32 cand = 0xffffffffu - (u32)(s_best & 0xffffffffull);
+                const int q = (int)(cand / (u32)per), pos = (int)(cand % (u32)per);
+                const int j0 = pos / CFS_WG, i0 = pos - j0 * CFS_WG;
+                cfs_window_shape(q, cap, bw, bh, ww, wh);
+                const int nw = max(1, ww / cw), nh = max(1, wh / ch);
+                /* centre the window on the counted cells */
+                x0 = box.x + i0 * cw + (nw * cw - ww) / 2;
+                y0 = box.y + j0 * ch + (nh * ch - wh) / 2;
+            } else {                   /* (no candidate) the square shape, centred */
+                cfs_window_shape(2, cap, bw, bh, ww, wh);
+                x0 = box.x + (bw - ww) / 2;
+                y0 = box.y + (bh - wh) / 2;
+            }
+            /* inside the box */
+            x0 = max(box.x, min(x0, box.z - ww + 1));
+            y0 = max(box.y, min(y0, box.w - wh + 1));
+            box = make_int4(x0, y0, x0 + ww - 1, y0 + wh - 1);
+        } else if (cap < 1) {
+            box = make_int4(0, 0, -1, -1);
+        }
+        if (threadIdx.x == 0) out[c] = box;
+        __syncthreads();                /* s_box, s_grid and s_best are reused */
     }
-    atomicMin(&s_box[0], bx0); atomicMin(&s_box[1], by0);
-    atomicMax(&s_box[2], bx1); atomicMax(&s_box[3], by1);
-    __syncthreads();
-    if (threadIdx.x == 0)
-        reinterpret_cast<int4*>(a.frame_bbox)[f] = make_int4(s_box[0], s_box[1], s_box[2], s_box[3]);
 }
 
-/* Window of frame f: its sampled box when it fits the tile, else the
- * largest centred square-ish window that does. */
-__device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, int f, u32* cnt)
+/* Windows of frame f into s_win (one box per channel; threads < CFS_TILE_C
+ * write them): the pre-pass's boxes (each fits its channel's counters),
+ * none when the frame's shape class runs without a window.  s_rep receives
+ * (n_rep, stride): the copies each channel window gets (small windows get
+ * one per warp, up to CFS_TILE_REPS, so that warps stop contending for the
+ * same counters) and the counters per copy. */
+__device__ __forceinline__ void cfs_frame_window(const cfs_launch_args& a, int f, int4* s_win,
+                                                 int* s_rep)
 {
-    const int4 b = reinterpret_cast<const int4*>(a.frame_bbox)[f];
-    CfsTile tl{cnt, 0, 0, 0, 0, 1, 0, 0};
-    const int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
-    if (b.z < b.x || b.w < b.y || a.tile_cap < (u32)CFS_TILE_C) return tl;
-    /* the autotuner's choice for the frame's shape class: no window */
-    if (reinterpret_cast<const cfs_dev_frame*>(a.frames)[f].flags & CFS_FRAME_NO_WINDOW) return tl;
-    const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* pixels */
-    int ww = bw, wh = bh;
-    if ((long long)bw * bh > cap) {
-        int side = (int)sqrtf((float)cap);
-        while ((side + 1) * (side + 1) <= cap) ++side;
-        while (side * side > cap) --side;
-        ww = min(bw, side);
-        wh = min(bh, cap / max(ww, 1));
-        wh = min(wh, bh);
+    const bool off = (reinterpret_cast<const cfs_dev_frame*>(a.frames)[f].flags &
+                      CFS_FRAME_NO_WINDOW) != 0 || a.tile_cap < (u32)CFS_TILE_C;
+    const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);
+    const int4* box = reinterpret_cast<const int4*>(a.frame_bbox) + (size_t)f * CFS_A_MAX_MAPS;
+    if (threadIdx.x < CFS_TILE_C) {
+        int4 b = box[threadIdx.x];
+        int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
+        if (off || b.z < b.x || b.w < b.y || (long long)bw * bh > cap) bw = bh = 0;
+        s_win[threadIdx.x] = make_int4(b.x, b.y, bw, bh);
     }
-    tl.ww = ww;
-    tl.wh = wh;
-    tl.wx0 = b.x + (bw - ww) / 2;
-    tl.wy0 = b.y + (bh - wh) / 2;
-    /* small windows get one copy per warp (up to CFS_TILE_REPS): warps then
-     * stop contending for the same shared counters */
-    tl.stride = CFS_TILE_C * ww * wh;
-    tl.n_rep = max(1, min(CFS_TILE_REPS, (int)(a.tile_cap / (u32)max(tl.stride, 1))));
-    tl.rep_off = ((int)(threadIdx.x >> 5) % tl.n_rep) * tl.stride;
-    return tl;
+    if (threadIdx.x == 0) {
+        int stride = 1;
+        for (int c = 0; c < CFS_TILE_C; ++c) {
+            const int4 b = box[c];
+            const long long n = (long long)(b.z - b.x + 1) * (long long)(b.w - b.y + 1);
+            if (!off && b.z >= b.x && b.w >= b.y && n <= cap) stride = max(stride, (int)n);
+        }
+        s_rep[0] = max(1, min(CFS_TILE_REPS, cap / stride));
+        s_rep[1] = stride;
+    }
 }
 #endif
 
@@ -531,8 +644,9 @@ __device__ __forceinline__ CfsTile cfs_frame_window(const cfs_launch_args& a, in
  * stay in L2.  A CTA loads a frame's thresholds, maps, palettes and target
  * geometry into shared memory when its next item belongs to another frame.
  * With CFS_TILE the first splat goes to a privatized shared-memory window
- * of the frame's histogram (attractors are small and dense: many splats hit
- * the same bins), flushed to global memory when the CTA leaves the frame. */
+ * of the frame's histogram, one per channel, placed by the pre-pass
+ * (attractors are small and dense: many splats hit the same bins), flushed
+ * to global memory when the CTA leaves the frame. */
 extern "C" __global__ void __launch_bounds__(CFS_BLOCK, CFS_MINB)
 cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
 {
@@ -547,10 +661,13 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ unsigned char s_kt[1u << CFS_KTAB_BITS];   /* the frame's bucket table */
 #if CFS_TILE
     extern __shared__ u32 s_cnt[];
+    __shared__ int4 s_win[CFS_TILE_C];
+    __shared__ int s_rep[2];
     for (u32 e = threadIdx.x; e < a.tile_cap; e += blockDim.x) s_cnt[e] = 0u;
-    CfsTile tile{s_cnt, 0, 0, 0, 0, 1, 0, 0};
+    if (threadIdx.x < CFS_TILE_C) s_win[threadIdx.x] = make_int4(0, 0, 0, 0);
+    CfsTile tile{s_cnt, s_win, (int)(a.tile_cap / (u32)CFS_TILE_C), 0, 1, 0};
 #else
-    const CfsTile tile{0, 0, 0, 0, 0, 1, 0, 0};
+    const CfsTile tile{0, 0, 0, 0, 1, 0};
 #endif
     const cfs_dev_frame* frames = reinterpret_cast<const cfs_dev_frame*>(a.frames);
     u32* counter = reinterpret_cast<u32*>(a.work_counter);
@@ -598,9 +715,14 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
                 s_scount = fr.start_count;
             }
 #if CFS_TILE
-            tile = cfs_frame_window(a, f, s_cnt);
+            cfs_frame_window(a, f, s_win, s_rep);
 #endif
             __syncthreads();
+#if CFS_TILE
+            tile.n_rep = s_rep[0];
+            tile.stride = s_rep[1];
+            tile.rep_off = ((int)(threadIdx.x >> 5) % tile.n_rep) * tile.stride;
+#endif
             cfs_build_ktab(s_T, s_ncmp, s_kt);
             __syncthreads();
             cur = f;

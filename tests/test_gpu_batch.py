@@ -84,6 +84,59 @@ def test_batch_matches_oracle_frame_by_frame(torch_cuda, words, warp_agg, window
     assert list(b.discards()[:, 0]) == rdisc == [0] * len(frames)
 
 
+@pytest.mark.parametrize("words", [1024, 4096, 53248])
+def test_batch_windows_lie_in_their_channels_budget(torch_cuda, words):
+    # the pre-pass places one window per histogram channel: inside the
+    # target, at most window_words / channels pixels, and, where a
+    # channel's sampled splats exceed that, over denser regions than
+    # centred windows
+    frames = W.animation_frames(n_frames=10, seed=5, min_log2=11, max_log2=13,
+                                resolutions=(128, 256))
+    cfs, chain, items, descs, tens = _setup(frames)
+    b = cfs.Batch(chain, items, iters=60, burn_in=20, seed=2)
+    with pytest.raises(cfs.CfsError):
+        b.windows()                      # before the first launch
+    b.set_plan(window=1, window_words=words, chunk=512)
+    b.launch(clear=True)
+    torch_cuda.cuda.synchronize()
+    win = b.windows()
+    C = descs[0].C
+    cap = words // C
+    assert win.shape == (len(frames), C, 4)
+    tot_inside = tot_centred = 0
+    for f, fr in enumerate(frames):
+        h = _host(tens[f]).reshape(C, fr.W, fr.W)
+        assert int(h.sum()) == fr.n_points * 40
+        for c in range(C):
+            x0, y0, x1, y1 = (int(v) for v in win[f, c])
+            if x1 < x0:
+                assert (x0, y0, x1, y1) == (0, 0, -1, -1)
+                continue
+            assert 0 <= x0 <= x1 < fr.W and 0 <= y0 <= y1 < fr.W
+            assert (x1 - x0 + 1) * (y1 - y0 + 1) <= cap
+            ys, xs = np.nonzero(h[c])
+            if len(xs) == 0:
+                continue
+            inside = int(h[c, y0:y1 + 1, x0:x1 + 1].sum())
+            # the centred window of the same shape over the channel's
+            # splats' box
+            ww, wh = x1 - x0 + 1, y1 - y0 + 1
+            cx = xs.min() + max(0, (xs.max() - xs.min() + 1 - ww) // 2)
+            cy = ys.min() + max(0, (ys.max() - ys.min() + 1 - wh) // 2)
+            centred = int(h[c, cy:cy + wh, cx:cx + ww].sum())
+            tot_inside += inside
+            tot_centred += centred
+            if (xs.max() - xs.min() + 1) * (ys.max() - ys.min() + 1) <= cap // 2:
+                # a channel whose splats fit with room to spare: the sampled
+                # box catches nearly all of them
+                assert inside >= 0.97 * h[c].sum(), (f, c)
+    # summed over the frames' channels, the sampled choice holds more splats
+    # than centred windows of the same shapes
+    print(f"window_words {words}: {tot_inside} splats in the chosen windows, "
+          f"{tot_centred} in centred ones")
+    assert tot_inside >= tot_centred
+
+
 def test_batch_plan_validation(torch_cuda):
     frames = W.animation_frames(n_frames=2, seed=2, min_log2=8, max_log2=9, resolutions=(32,))
     cfs, chain, items, descs, tens = _setup(frames)

@@ -262,7 +262,9 @@ cfs_status get_kernel(const ProgramSpec& spec, const char* name, Kernel* out)
         k.fn = (void*)fn;
         k.block = spec.block;
         k.dyn_smem = spec.dyn_smem;
-        if (spec.dyn_smem > 48 * 1024) {
+        // without the opt-in, static plus dynamic shared memory may not pass
+        // 48 KB: a window just under 48 KB would fail to launch
+        if (spec.dyn_smem > 0) {
             st = check_cu(d.set_attribute(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES,
                                           spec.dyn_smem),
                           "cuFuncSetAttribute(max dynamic shared memory)");

@@ -543,6 +543,29 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
             "timing": f"median of {reps} frames, L2 flushed (256 MiB write) before each"}
 
 
+# Warp instructions the batch kernel issues per point-step: ncu
+# smsp__inst_executed.sum of one full 256-frame launch under the tuned plan
+# (1.934e11 warp instructions for 7.78e10 point-steps, one pass).  Valid for
+# the kernel it was taken on (profiles/cfs_batch_kernel_animation.md).
+BATCH_WARP_INSTR_PER_POINT_STEP = 1.934e11 / (259390750 * 300)
+SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
+
+
+def batch_issue(point_steps: int, ms: float):
+    """The batch kernel's issue-slot use: its measured instructions per
+    point-step, at the timed launch's rate, against one warp instruction per
+    scheduler per clock at the maximum SM clock."""
+    rate = BATCH_WARP_INSTR_PER_POINT_STEP * point_steps / (ms * 1e-3)
+    peak = SM_COUNT * SCHEDULERS_PER_SM * SM_MAX_MHZ * 1e6
+    return {"bound": "alu", "achieved": rate, "peak": peak, "unit": "warp instructions/s",
+            "frac": rate / peak,
+            "instructions_per_point_step": 32 * BATCH_WARP_INSTR_PER_POINT_STEP,
+            "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock at 2070 MHz; "
+                           "instructions per point-step from an ncu count of the full batch",
+            "note": "the batch's tighter bound: integer issue (Philox rounds, map choice, "
+                    "affine map, bin, window test)"}
+
+
 def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
     """Batched animation: 256 frames of 2-8 random affine maps interpolated
     between two keyframes, 2^16..2^22 points (log-uniform) and 256^2..2048^2
@@ -650,8 +673,7 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
                          "t_min_ms": t_min_ms,
                          "bytes": "1 u32 increment per splat (280 splat steps per point): "
                                   f"{n_smem} in shared-memory windows, {n_l2} L2 reductions",
-                         "issue": "frames whose splats stay in shared memory are "
-                                  "integer-issue bound: profiles/cfs_batch_kernel_animation.md"}}
+                         "issue": batch_issue(n_pts * 300, ms)}}
 
 
 def bench_space(torch, cfs, dev, stream, reps: int = 5):

@@ -137,9 +137,24 @@ __device__ __forceinline__ void cfs_step(const cfs_launch_args& a, const CH& cho
 #endif
 }
 
+/* One step past the burn-in with copy semantics: choose, apply, splat the
+ * copy through the chain. */
+template <class CH, class TG>
+__device__ __forceinline__ void cfs_step_splat(const cfs_launch_args& a, const CH& choose,
+                                               const TG& tg, const CfsSmem& sm, u32 w, u32 aux,
+                                               float& x, float& y, float& z, u32* disc,
+                                               const CfsTile& tile)
+{
+    const int k = choose(w);
+    cfs_gen_map(a, k, x, y, z, sm);
+    float qx, qy, qz;
+    cfs_chain(a, tg, sm, x, y, z, k, aux, disc, true, (float*)0, qx, qy, qz, tile);
+}
+
 /* Runs steps step_begin .. iters-1 of point i of system sid: one Philox
  * block per four steps.  Blocks cut by step_begin or iters run their steps
- * under warp-uniform guards.  CFS_UNROLL (4, 2 or 1) is how many copies of
+ * under warp-uniform guards (when none is cut and the burn-in ends on a
+ * block boundary, a guard-free loop runs instead).  CFS_UNROLL (4, 2 or 1) is how many copies of
  * the step code the loop holds: the generated chain can be long, and
  * instruction-cache pressure trades against the scheduler's freedom to
  * overlap consecutive steps. */
@@ -154,6 +169,55 @@ __device__ __forceinline__ void cfs_run_point(const cfs_launch_args& a, const CH
 {
     const u32 b0 = a.step_begin, b1 = a.iters;
     const bool whole = ((b0 | b1) & 3u) == 0u;
+#if !CFS_REUSE && !(CFS_BATCH && CFS_ILP == 2)
+    /* (the two-trajectory batch program calls this only for a frame's odd
+     * last point: the general loop keeps its code small) */
+    if (whole && (a.burn_in & 3u) == 0u) {
+        /* every block whole and the burn-in ending on a block boundary: the
+         * burn-in blocks move the point without the chain, the rest splat
+         * every step, and no step needs a guard (the same steps, in the same
+         * order, as the general loop below) */
+        const u32 nb1 = b1 >> 2, nbs = min(max(b0, a.burn_in) >> 2, nb1);
+        u32 nb = b0 >> 2;
+#pragma unroll 1
+        for (; nb < nbs; ++nb) {
+            const uint4 r = cfs_philox(a, i, nb, sid, 0u);
+            cfs_gen_map(a, choose(r.x), x, y, z, sm);
+            cfs_gen_map(a, choose(r.y), x, y, z, sm);
+            cfs_gen_map(a, choose(r.z), x, y, z, sm);
+            cfs_gen_map(a, choose(r.w), x, y, z, sm);
+        }
+#pragma unroll 1
+        for (; nb < nb1; ++nb) {
+            const uint4 r = cfs_philox(a, i, nb, sid, 0u);
+            const uint4 ra = cfs_aux_block(a, i, nb, sid);
+#if CFS_UNROLL == 4
+            cfs_step_splat(a, choose, tg, sm, r.x, ra.x, x, y, z, disc, tile);
+            cfs_step_splat(a, choose, tg, sm, r.y, ra.y, x, y, z, disc, tile);
+            cfs_step_splat(a, choose, tg, sm, r.z, ra.z, x, y, z, disc, tile);
+            cfs_step_splat(a, choose, tg, sm, r.w, ra.w, x, y, z, disc, tile);
+#elif CFS_UNROLL == 2
+#pragma unroll 1
+            for (u32 h = 0; h < 4; h += 2) {
+                cfs_step_splat(a, choose, tg, sm, h ? r.z : r.x, h ? ra.z : ra.x, x, y, z, disc,
+                               tile);
+                cfs_step_splat(a, choose, tg, sm, h ? r.w : r.y, h ? ra.w : ra.y, x, y, z, disc,
+                               tile);
+            }
+#else
+            u32 w[4] = {r.x, r.y, r.z, r.w};
+            u32 v[4] = {ra.x, ra.y, ra.z, ra.w};
+#pragma unroll 1
+            for (u32 h = 0; h < 4; ++h) {
+                cfs_step_splat(a, choose, tg, sm, w[0], v[0], x, y, z, disc, tile);
+                w[0] = w[1]; w[1] = w[2]; w[2] = w[3];
+                v[0] = v[1]; v[1] = v[2]; v[2] = v[3];
+            }
+#endif
+        }
+        return;
+    }
+#endif
 #pragma unroll 1
     for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
         const uint4 r = cfs_philox(a, i, nb, sid, 0u);
@@ -205,6 +269,45 @@ __device__ __forceinline__ void cfs_run_point2(const cfs_launch_args& a, const C
 {
     const u32 b0 = a.step_begin, b1 = a.iters;
     const bool whole = ((b0 | b1) & 3u) == 0u;
+#if !CFS_REUSE
+    if (whole && (a.burn_in & 3u) == 0u) {
+        /* every block whole and the burn-in ending on a block boundary: the
+         * burn-in blocks move the points without the chain, the rest splat
+         * every step, and no step needs a guard (the same steps, in the same
+         * order, as the general loop below) */
+        const u32 nb1 = b1 >> 2, nbs = min(max(b0, a.burn_in) >> 2, nb1);
+        u32 nb = b0 >> 2;
+#pragma unroll 1
+        for (; nb < nbs; ++nb) {
+            const uint4 r0 = cfs_philox(a, i0, nb, sid, 0u);
+            const uint4 r1 = cfs_philox(a, i1, nb, sid, 0u);
+            const u32 w0[4] = {r0.x, r0.y, r0.z, r0.w};
+            const u32 w1[4] = {r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cfs_gen_map(a, choose(w0[q]), x0, y0, z0, sm);
+                cfs_gen_map(a, choose(w1[q]), x1, y1, z1, sm);
+            }
+        }
+#pragma unroll 1
+        for (; nb < nb1; ++nb) {
+            const uint4 r0 = cfs_philox(a, i0, nb, sid, 0u);
+            const uint4 r1 = cfs_philox(a, i1, nb, sid, 0u);
+            const uint4 a0 = cfs_aux_block(a, i0, nb, sid);
+            const uint4 a1 = cfs_aux_block(a, i1, nb, sid);
+            const u32 w0[4] = {r0.x, r0.y, r0.z, r0.w};
+            const u32 w1[4] = {r1.x, r1.y, r1.z, r1.w};
+            const u32 v0[4] = {a0.x, a0.y, a0.z, a0.w};
+            const u32 v1[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cfs_step_splat(a, choose, tg, sm, w0[q], v0[q], x0, y0, z0, disc, tile);
+                cfs_step_splat(a, choose, tg, sm, w1[q], v1[q], x1, y1, z1, disc, tile);
+            }
+        }
+        return;
+    }
+#endif
 #pragma unroll 1
     for (u32 nb = b0 >> 2; (nb << 2) < b1; ++nb) {
         const uint4 r0 = cfs_philox(a, i0, nb, sid, 0u);

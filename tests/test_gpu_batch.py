@@ -84,6 +84,24 @@ def test_batch_matches_oracle_frame_by_frame(torch_cuda, words, warp_agg, window
     assert list(b.discards()[:, 0]) == rdisc == [0] * len(frames)
 
 
+@pytest.mark.parametrize("ilp,burn_in", [(1, 18), (2, 18), (1, 0), (2, 0), (2, 60)])
+def test_batch_burn_in_on_and_off_block_boundaries(torch_cuda, ilp, burn_in):
+    # whole Philox blocks with the burn-in on a block boundary take the
+    # guard-free loop (0, 60), elsewhere (18) the general one; both must give
+    # the oracle's histograms, including a burn-in that covers every step
+    frames = W.animation_frames(n_frames=6, seed=9, min_log2=8, max_log2=11,
+                                resolutions=(64, 128))
+    cfs, chain, items, descs, tens = _setup(frames)
+    b = cfs.Batch(chain, items, iters=60, burn_in=burn_in, seed=6)
+    b.set_plan(ilp=ilp, chunk=256)
+    b.launch(clear=True)
+    torch_cuda.cuda.synchronize()
+    ref, rdisc = _oracle(frames, descs, 60, burn_in, 6)
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), ref[f]), f
+        assert int(_host(tens[f]).sum()) == frames[f].n_points * max(0, 60 - burn_in)
+
+
 @pytest.mark.parametrize("words", [1024, 4096, 53248])
 def test_batch_windows_lie_in_their_channels_budget(torch_cuda, words):
     # the pre-pass places one window per histogram channel: inside the

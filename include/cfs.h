@@ -331,7 +331,8 @@ cfs_status cfs_batch_discards(cfs_batch* batch, uint64_t* out);
 /* Work items, points per item (the plan's default), persistent grid size. */
 cfs_status cfs_batch_info(const cfs_batch* batch, uint32_t* n_items, uint32_t* chunk,
                           uint32_t* grid);
-/* The privatized shared-memory windows of every frame in the last launch,
+/* The privatized shared-memory windows of every frame in the last launch
+ * (or, after cfs_batch_tune, its last trial),
  * host int32 [n_frames][C][4] (C: the channels of target 0's histogram) =
  * (x0, y0, x1, y1): the inclusive pixel box of channel c of target 0 whose
  * splats the launch counted in shared memory (every other splat is a

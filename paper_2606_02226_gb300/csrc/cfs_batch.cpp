@@ -56,6 +56,10 @@ struct cfs_batch {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [clear]
     cudaEvent_t done = nullptr;
     bool launched = false;
+    // the window set-up of the last launch or trial (cfs_batch_windows)
+    bool last_tile = false;
+    uint32_t last_tile_cap = 0;
+    std::vector<uint8_t> last_nowin;
     // display (cfs_batch_display): layer descriptions staged in pinned memory
     cfs::DisplayLayer* h_disp = nullptr;
     unsigned char* d_disp = nullptr;      // DisplayLayer [n_frames] | float a_max [n_frames]
@@ -287,8 +291,17 @@ void drop_graphs(cfs_batch* b)
 }
 
 // the launch sequence of a batch without a graph (the autotuner's trials)
+// remembers the window set-up a launch runs with
+void note_windows(cfs_batch* b)
+{
+    b->last_tile = b->spec.tile != 0;
+    b->last_tile_cap = b->tile_cap;
+    b->last_nowin = b->nowin;
+}
+
 cfs_status run_direct(cfs_batch* b, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
 {
+    note_windows(b);
     cudaError_t e = cudaMemcpyAsync(b->d_frames, b->h_frames,
                                     sizeof(cfs_dev_frame) * (size_t)b->n_frames,
                                     cudaMemcpyHostToDevice, s);
@@ -602,6 +615,7 @@ cfs_status cfs_batch_launch(cfs_batch* b, int clear, void* stream)
                                "cudaGraphLaunch");
     if (st != CFS_OK) return st;
     b->launched = true;
+    note_windows(b);
     return check_cuda(cudaEventRecord(b->done, (cudaStream_t)stream), "cudaEventRecord");
 }
 
@@ -648,20 +662,20 @@ cfs_status cfs_batch_windows(cfs_batch* b, int32_t* out)
     const int C = window_channels(b);
     const size_t n = 4 * (size_t)CFS_A_MAX_MAPS * (size_t)b->n_frames;
     std::vector<int32_t> box(n, 0);
-    if (b->spec.tile) {
+    if (b->last_tile) {
         st = check_cuda(cudaMemcpy(box.data(), b->d_bbox, sizeof(int32_t) * n,
                                    cudaMemcpyDeviceToHost),
                         "cudaMemcpy(windows)");
         if (st != CFS_OK) return st;
     }
-    const long long cap = b->spec.tile ? (long long)(b->tile_cap / (uint32_t)C) : 0;
+    const long long cap = b->last_tile ? (long long)(b->last_tile_cap / (uint32_t)C) : 0;
     for (int f = 0; f < b->n_frames; ++f)
         for (int c = 0; c < C; ++c) {
             int32_t* o = out + 4 * ((size_t)f * (size_t)C + (size_t)c);
             const int32_t* w = box.data() + 4 * ((size_t)f * CFS_A_MAX_MAPS + (size_t)c);
             // the kernel's rule: no window for the frame, an empty box, or a
             // box above the channel's counters
-            const bool none = !b->spec.tile || b->nowin[f] || w[2] < w[0] || w[3] < w[1] ||
+            const bool none = !b->last_tile || b->last_nowin[f] || w[2] < w[0] || w[3] < w[1] ||
                               (long long)(w[2] - w[0] + 1) * (long long)(w[3] - w[1] + 1) > cap;
             o[0] = none ? 0 : w[0];
             o[1] = none ? 0 : w[1];

@@ -545,25 +545,51 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
 
 # Warp instructions the batch kernel issues per point-step: ncu
 # smsp__inst_executed.sum of one full 256-frame launch under the tuned plan
-# (1.934e11 warp instructions for 7.78e10 point-steps, one pass).  Valid for
-# the kernel it was taken on (profiles/cfs_batch_kernel_animation.md).
-BATCH_WARP_INSTR_PER_POINT_STEP = 1.934e11 / (259390750 * 300)
+# (one pass; profiles/cfs_batch_kernel_animation.md).  Valid only for the
+# program it was taken on: the bench reports it while the batch program's
+# hash (as for the render traffic) and the tuned plan's program knobs match.
+BATCH_WARP_INSTR = 1.8816e11             # per launch of the 256 frames (7.78e10 point-steps)
+BATCH_INSTR_SOURCE_SHA1 = "7f4eb2012f38f6f6f61cb21f2a59837a8c577b55"
+BATCH_INSTR_PLAN = {"ilp": 2, "tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 
 
-def batch_issue(point_steps: int, ms: float):
+def batch_program_sha1(cfs, frames):
+    """Hash of the batch program the animation compiles under the default
+    program knobs (the frame with the most maps sets the threshold count)."""
+    import hashlib
+    fr = max(frames, key=lambda f: len(f.system.maps))
+    src, _ = cfs.codegen_check(cfs.System(fr.system), cfs.Chain([W.Op("splat", (0,))], 2),
+                               [W.animation_target(fr.W)], mode=2)
+    h = hashlib.sha1(_code_only(src).encode())
+    csrc = os.path.join(ROOT, "paper_2606_02226_gb300", "csrc")
+    for name in ("cfs_args.h", "cfs_device.cuh", "cfs_kernels.cuh"):
+        with open(os.path.join(csrc, name)) as fh:
+            h.update(_code_only(fh.read()).encode())
+    return h.hexdigest()
+
+
+def batch_issue(point_steps: int, ms: float, sha1: str, tuning: dict):
     """The batch kernel's issue-slot use: its measured instructions per
-    point-step, at the timed launch's rate, against one warp instruction per
-    scheduler per clock at the maximum SM clock."""
-    rate = BATCH_WARP_INSTR_PER_POINT_STEP * point_steps / (ms * 1e-3)
+    launch, at the timed launch's rate, against one warp instruction per
+    scheduler per clock at the maximum SM clock; null when the count was
+    taken on another program."""
     peak = SM_COUNT * SCHEDULERS_PER_SM * SM_MAX_MHZ * 1e6
-    return {"bound": "alu", "achieved": rate, "peak": peak, "unit": "warp instructions/s",
-            "frac": rate / peak,
-            "instructions_per_point_step": 32 * BATCH_WARP_INSTR_PER_POINT_STEP,
-            "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock at 2070 MHz; "
-                           "instructions per point-step from an ncu count of the full batch",
-            "note": "the batch's tighter bound: integer issue (Philox rounds, map choice, "
-                    "affine map, bin, window test)"}
+    same = sha1 == BATCH_INSTR_SOURCE_SHA1 and all(tuning.get(k) == v
+                                                    for k, v in BATCH_INSTR_PLAN.items())
+    out = {"bound": "alu", "peak": peak, "unit": "warp instructions/s", "program_sha1": sha1,
+           "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock at 2070 MHz; "
+                          "instructions per launch from an ncu count of the full batch",
+           "note": "the batch's tighter bound: integer issue (Philox rounds, map choice, "
+                   "affine map, bin, window test)"}
+    if not same:
+        out.update({"achieved": None, "frac": None,
+                    "instructions_per_point_step": None})
+        return out
+    rate = BATCH_WARP_INSTR / (ms * 1e-3)
+    out.update({"achieved": rate, "frac": rate / peak,
+                "instructions_per_point_step": 32 * BATCH_WARP_INSTR / point_steps})
+    return out
 
 
 def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
@@ -581,7 +607,10 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
         begin += fr.n_points
     b = cfs.Batch(chain, items, iters=300, burn_in=20, seed=0)
 
-    def timed_batch():
+    def timed_batch(tag):
+        # (an NVTX range per plan: a profiler can pick the tuned plan's
+        # launches by name, whatever number of trials the tuner ran)
+        torch.cuda.nvtx.range_push(tag)
         b.launch(clear=True, stream=stream)               # capture + warm-up
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -591,12 +620,13 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             b.launch(clear=True, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         return e0.elapsed_time(e1) / reps
 
-    ms_default = timed_batch()
+    ms_default = timed_batch("batch_default_plan")
     # the autotuner times the candidate plans on these frames (80 steps each)
     tuning = b.tune(trial_iters=80, stream=stream)
-    ms = timed_batch()
+    ms = timed_batch("batch_tuned_plan")
     n_pts = sum(fr.n_points for fr in frames)
     bytes_targets = sum(4 * 4 * fr.W * fr.W for fr in frames)
     info = b.info()
@@ -673,7 +703,8 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
                          "t_min_ms": t_min_ms,
                          "bytes": "1 u32 increment per splat (280 splat steps per point): "
                                   f"{n_smem} in shared-memory windows, {n_l2} L2 reductions",
-                         "issue": batch_issue(n_pts * 300, ms)}}
+                         "issue": batch_issue(n_pts * 300, ms, batch_program_sha1(cfs, frames),
+                                              tuning)}}
 
 
 def bench_space(torch, cfs, dev, stream, reps: int = 5):

@@ -548,8 +548,8 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
 # (one pass; profiles/cfs_batch_kernel_animation.md).  Valid only for the
 # program it was taken on: the bench reports it while the batch program's
 # hash (as for the render traffic) and the tuned plan's program knobs match.
-BATCH_WARP_INSTR = 1.8816e11             # per launch of the 256 frames (7.78e10 point-steps)
-BATCH_INSTR_SOURCE_SHA1 = "7f4eb2012f38f6f6f61cb21f2a59837a8c577b55"
+BATCH_WARP_INSTR = 1.8171e11             # per launch of the 256 frames (7.78e10 point-steps)
+BATCH_INSTR_SOURCE_SHA1 = "17fffafa05c4c8c8475a620efe53372ed838f309"
 BATCH_INSTR_PLAN = {"ilp": 2, "tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 

@@ -668,20 +668,25 @@ cfs_status cfs_batch_windows(cfs_batch* b, int32_t* out)
                         "cudaMemcpy(windows)");
         if (st != CFS_OK) return st;
     }
-    const long long cap = b->last_tile ? (long long)(b->last_tile_cap / (uint32_t)C) : 0;
-    for (int f = 0; f < b->n_frames; ++f)
+    for (int f = 0; f < b->n_frames; ++f) {
+        // the kernel's rule: the channels' windows take consecutive counters;
+        // none for a frame without one, an empty box, or a box that would
+        // pass the last counter
+        long long used = 0;
         for (int c = 0; c < C; ++c) {
             int32_t* o = out + 4 * ((size_t)f * (size_t)C + (size_t)c);
             const int32_t* w = box.data() + 4 * ((size_t)f * CFS_A_MAX_MAPS + (size_t)c);
-            // the kernel's rule: no window for the frame, an empty box, or a
-            // box above the channel's counters
-            const bool none = !b->last_tile || b->last_nowin[f] || w[2] < w[0] || w[3] < w[1] ||
-                              (long long)(w[2] - w[0] + 1) * (long long)(w[3] - w[1] + 1) > cap;
+            const long long ww = (long long)w[2] - w[0] + 1, wh = (long long)w[3] - w[1] + 1;
+            const bool none = !b->last_tile || b->last_nowin[f] || ww < 1 || wh < 1 ||
+                              ww > 0xFFFF || wh > 0x7FFF ||
+                              used + ww * wh > (long long)b->last_tile_cap;
+            if (!none) used += ww * wh;
             o[0] = none ? 0 : w[0];
             o[1] = none ? 0 : w[1];
             o[2] = none ? -1 : w[2];
             o[3] = none ? -1 : w[3];
         }
+    }
     return CFS_OK;
 }
 

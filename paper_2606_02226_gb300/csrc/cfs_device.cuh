@@ -425,14 +425,12 @@ __device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x,
 /* The privatized window of a batch frame's u32 histogram: one pixel box
  * per channel (a channel's splats come from its own maps, whose images are
  * smaller copies of the attractor, so each channel's box sits over that
- * channel's densest region), cap counters per channel in shared memory. */
+ * channel's densest region), the channels' counters packed one after the
+ * other in shared memory. */
 struct CfsTile {
-    u32* cnt;           /* shared counters: channel c at cnt + c * cap */
-    const int4* win;    /* shared, per channel: (x0, y0, w, h); w = 0: no window */
-    int cap;            /* counters per channel */
-    int rep_off;        /* this warp's copy: (warp % n_rep) * stride */
-    int n_rep;          /* copies of each channel's window */
-    int stride;         /* counters per copy (the largest channel window) */
+    u32* cnt;           /* shared counters */
+    const int4* win;    /* shared, per channel: (x0, y0, w | h << 16, first counter);
+                           w = 0: no window */
 };
 
 /* u32 histogram splat that adds to the shared window of its channel when
@@ -445,11 +443,11 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
     const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
     const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
     if (alive && ix >= 0 && iy >= 0) {
-        const int4 w = tl.win[ch];
-        const int lx = ix - w.x, ly = iy - w.y;
-        if ((unsigned)lx < (unsigned)w.z && (unsigned)ly < (unsigned)w.w) {
-            const u32 idx = (u32)ch * (u32)tl.cap + (u32)tl.rep_off + (u32)ly * (u32)w.z +
-                            (u32)lx;
+        const int4 g = tl.win[ch];
+        const u32 lx = (u32)(ix - g.x), ly = (u32)(iy - g.y);
+        const u32 w = (u32)g.z & 0xFFFFu, h = (u32)g.z >> 16;
+        if (lx < w && ly < h) {
+            const u32 idx = (u32)g.w + ly * w + lx;
 #if CFS_WARP_AGG
             const u32 act = __activemask();
             const u32 peers = __match_any_sync(act, idx);
@@ -467,26 +465,22 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
     }
 }
 
-/* Adds the windows' nonzero counters (summed over their copies) to the
- * global histogram and zeroes them; every thread of the CTA takes part. */
+/* Adds the windows' nonzero counters to the global histogram and zeroes
+ * them; every thread of the CTA takes part. */
 __device__ __forceinline__ void cfs_flush_tile(const cfs_dev_target& t, const CfsTile& tl, int C)
 {
     u32* base = reinterpret_cast<u32*>(t.data);
     for (int ch = 0; ch < C; ++ch) {
-        const int4 w = tl.win[ch];
-        const u32 per = (u32)w.z * (u32)w.w;
-        u32* cc = tl.cnt + (size_t)ch * (size_t)tl.cap;
-        for (u32 e = threadIdx.x; e < per; e += blockDim.x) {
-            u32 v = 0;
-            for (int r = 0; r < tl.n_rep; ++r) {
-                u32* c = cc + (size_t)r * (size_t)tl.stride + e;
-                v += *c;
-                *c = 0u;
-            }
+        const int4 g = tl.win[ch];
+        const u32 w = (u32)g.z & 0xFFFFu, h = (u32)g.z >> 16;
+        u32* cc = tl.cnt + (u32)g.w;
+        for (u32 e = threadIdx.x; e < w * h; e += blockDim.x) {
+            const u32 v = cc[e];
+            cc[e] = 0u;
             if (v) {
-                const u32 ly = e / (u32)w.z, lx = e - ly * (u32)w.z;
-                const size_t off = ((size_t)ch * (size_t)t.H + (size_t)(w.y + (int)ly)) *
-                                       (size_t)t.W + (size_t)(w.x + (int)lx);
+                const u32 ly = e / w, lx = e - ly * w;
+                const size_t off = ((size_t)ch * (size_t)t.H + (size_t)(g.y + (int)ly)) *
+                                       (size_t)t.W + (size_t)(g.x + (int)lx);
                 cfs_red_add_u32(base + off, v);
             }
         }

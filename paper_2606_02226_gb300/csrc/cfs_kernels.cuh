@@ -421,7 +421,7 @@ cfs_points_kernel(const __grid_constant__ cfs_launch_args a)
         float4 Z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (CFS_DIM == 3) Z = cfs_ld_stream_f4(xs + 2 * (size_t)n_pts + o, policy);
         const u32 K = cfs_ld_stream_u32(fn + o, policy);
-        const CfsTile nt{0, 0, 0, 0, 1, 0};
+        const CfsTile nt{0, 0};
         float qx, qy, qz;
         cfs_chain(a, a.tg, sm, X.x, Y.x, Z.x, (int)(K & 0xFFu), 0u, disc, true, (float*)0, qx, qy, qz,
                   nt);
@@ -456,7 +456,7 @@ cfs_render_kernel(const __grid_constant__ cfs_launch_args a)
         float x, y, z;
         cfs_start(a, i, a.system_id, j, a.n_points, x, y, z);
         cfs_run_point(a, choose, a.tg, sm, i, a.system_id, x, y, z, disc,
-                      CfsTile{0, 0, 0, 0, 1, 0});
+                      CfsTile{0, 0});
     }
     cfs_flush_discards(a, disc, CFS_NT);
 }
@@ -489,7 +489,7 @@ cfs_trace_kernel(const __grid_constant__ cfs_launch_args a)
         float qx, qy, qz;
         const bool alive = cfs_chain(a, a.tg, sm, x, y, z, k, aux, disc, false,
                                      qout + s * (size_t)CFS_NSPLAT_ARR * 4, qx, qy, qz,
-                                     CfsTile{0, 0, 0, 0, 1, 0});
+                                     CfsTile{0, 0});
 #if CFS_REUSE
         if (alive) { x = qx; y = qy; z = qz; }
 #else
@@ -565,7 +565,7 @@ __device__ __forceinline__ void cfs_window_samples(const cfs_launch_args& a,
         float rec[4 * CFS_NSPLAT_ARR];
         float qx, qy, qz;
         cfs_chain(a, s_tg, sm, x, y, z, k, aux, disc, false, rec, qx, qy, qz,
-                  CfsTile{0, 0, 0, 0, 1, 0});
+                  CfsTile{0, 0});
         const int ix = cfs_bin(rec[0], t0.x0, t0.x1, t0.sx, t0.W);
         const int iy = cfs_bin(rec[1], t0.y0, t0.y1, t0.sy, t0.H);
         if (rec[3] != 0.0f && ix >= 0 && iy >= 0) visit(ix, iy, k);
@@ -588,9 +588,11 @@ __device__ __forceinline__ void cfs_window_shape(int q, int cap, int bw, int bh,
 
 /* Pre-pass of the privatized windows: one CTA per frame samples the frame's
  * first blockDim trajectories (see cfs_window_samples) and writes, for each
- * channel c of target 0, the pixel box its window covers (at most
- * tile_cap / CFS_TILE_C pixels; empty when no sample of the channel
- * landed) to frame_bbox[f * CFS_A_MAX_MAPS + c].  A sample's channel is
+ * channel c of target 0, the pixel box its window covers to
+ * frame_bbox[f * CFS_A_MAX_MAPS + c] (empty when no sample of the channel
+ * landed).  The channels share the tile_cap counters in proportion to
+ * their sampled splats (a channel's capacity, in pixels, is its share,
+ * rounded down, so the windows together never pass tile_cap).  A sample's channel is
  * its map index mod CFS_TILE_C (a chain that recolours moves splats to
  * other channels; they then miss the window more often, nothing else).
  * When the channel's sampled box fits its window, the window is that box.
@@ -613,13 +615,35 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
     __shared__ int s_box[4];
     __shared__ u32 s_grid[CFS_WG * CFS_WG];
     __shared__ unsigned long long s_best;
+    __shared__ u32 s_mass[CFS_TILE_C];
     const int f = blockIdx.x;
     const cfs_dev_frame& fr = reinterpret_cast<const cfs_dev_frame*>(a.frames)[f];
     cfs_load_frame(fr, sm, s_T, s_tg);
     const CfsChooseTab choose{s_T, fr.n_cmp};
-    const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);    /* window pixels per channel */
+    if (threadIdx.x < CFS_TILE_C) s_mass[threadIdx.x] = 0u;
+    __syncthreads();
+    {
+        /* the channels' sampled splats */
+        u32 m[CFS_TILE_C];
+#pragma unroll
+        for (int c = 0; c < CFS_TILE_C; ++c) m[c] = 0u;
+        cfs_window_samples(a, fr, choose, s_tg, sm, [&](int ix, int iy, int k) {
+            (void)ix; (void)iy;
+            const int ch = k % CFS_TILE_C;
+#pragma unroll
+            for (int c = 0; c < CFS_TILE_C; ++c) m[c] += ch == c ? 1u : 0u;
+        });
+#pragma unroll
+        for (int c = 0; c < CFS_TILE_C; ++c)
+            if (m[c]) atomicAdd(&s_mass[c], m[c]);
+    }
+    __syncthreads();
+    u32 total = 0;
+    for (int c = 0; c < CFS_TILE_C; ++c) total += s_mass[c];
     int4* out = reinterpret_cast<int4*>(a.frame_bbox) + (size_t)f * CFS_A_MAX_MAPS;
     for (int c = 0; c < CFS_TILE_C; ++c) {
+        /* window pixels of this channel */
+        const int cap = total ? (int)(((unsigned long long)a.tile_cap * s_mass[c]) / total) : 0;
         if (threadIdx.x == 0) {
             s_box[0] = 0x7fffffff; s_box[1] = 0x7fffffff; s_box[2] = -1; s_box[3] = -1;
             s_best = 0ull;
@@ -706,34 +730,27 @@ cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
     }
 }
 
-/* Windows of frame f into s_win (one box per channel; threads < CFS_TILE_C
- * write them): the pre-pass's boxes (each fits its channel's counters),
- * none when the frame's shape class runs without a window.  s_rep receives
- * (n_rep, stride): the copies each channel window gets (small windows get
- * one per warp, up to CFS_TILE_REPS, so that warps stop contending for the
- * same counters) and the counters per copy. */
-__device__ __forceinline__ void cfs_frame_window(const cfs_launch_args& a, int f, int4* s_win,
-                                                 int* s_rep)
+/* Windows of frame f into s_win (thread 0 writes them): the pre-pass's
+ * boxes, their counters packed one channel after the other; none when the
+ * frame's shape class runs without a window (and, as a guard, for a box
+ * that would pass the counters' end). */
+__device__ __forceinline__ void cfs_frame_window(const cfs_launch_args& a, int f, int4* s_win)
 {
+    if (threadIdx.x != 0) return;
     const bool off = (reinterpret_cast<const cfs_dev_frame*>(a.frames)[f].flags &
-                      CFS_FRAME_NO_WINDOW) != 0 || a.tile_cap < (u32)CFS_TILE_C;
-    const int cap = (int)(a.tile_cap / (u32)CFS_TILE_C);
+                      CFS_FRAME_NO_WINDOW) != 0;
     const int4* box = reinterpret_cast<const int4*>(a.frame_bbox) + (size_t)f * CFS_A_MAX_MAPS;
-    if (threadIdx.x < CFS_TILE_C) {
-        int4 b = box[threadIdx.x];
-        int bw = b.z - b.x + 1, bh = b.w - b.y + 1;
-        if (off || b.z < b.x || b.w < b.y || (long long)bw * bh > cap) bw = bh = 0;
-        s_win[threadIdx.x] = make_int4(b.x, b.y, bw, bh);
-    }
-    if (threadIdx.x == 0) {
-        int stride = 1;
-        for (int c = 0; c < CFS_TILE_C; ++c) {
-            const int4 b = box[c];
-            const long long n = (long long)(b.z - b.x + 1) * (long long)(b.w - b.y + 1);
-            if (!off && b.z >= b.x && b.w >= b.y && n <= cap) stride = max(stride, (int)n);
+    u32 used = 0;
+    for (int c = 0; c < CFS_TILE_C; ++c) {
+        const int4 b = box[c];
+        const long long w = (long long)b.z - b.x + 1, h = (long long)b.w - b.y + 1;
+        if (off || w < 1 || h < 1 || w > 0xFFFF || h > 0x7FFF ||
+            (long long)used + w * h > (long long)a.tile_cap) {
+            s_win[c] = make_int4(0, 0, 0, 0);
+            continue;
         }
-        s_rep[0] = max(1, min(CFS_TILE_REPS, cap / stride));
-        s_rep[1] = stride;
+        s_win[c] = make_int4(b.x, b.y, (int)((u32)w | ((u32)h << 16)), (int)used);
+        used += (u32)(w * h);
     }
 }
 #endif
@@ -765,12 +782,11 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
 #if CFS_TILE
     extern __shared__ u32 s_cnt[];
     __shared__ int4 s_win[CFS_TILE_C];
-    __shared__ int s_rep[2];
     for (u32 e = threadIdx.x; e < a.tile_cap; e += blockDim.x) s_cnt[e] = 0u;
     if (threadIdx.x < CFS_TILE_C) s_win[threadIdx.x] = make_int4(0, 0, 0, 0);
-    CfsTile tile{s_cnt, s_win, (int)(a.tile_cap / (u32)CFS_TILE_C), 0, 1, 0};
+    const CfsTile tile{s_cnt, s_win};
 #else
-    const CfsTile tile{0, 0, 0, 0, 1, 0};
+    const CfsTile tile{0, 0};
 #endif
     const cfs_dev_frame* frames = reinterpret_cast<const cfs_dev_frame*>(a.frames);
     u32* counter = reinterpret_cast<u32*>(a.work_counter);
@@ -818,14 +834,9 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
                 s_scount = fr.start_count;
             }
 #if CFS_TILE
-            cfs_frame_window(a, f, s_win, s_rep);
+            cfs_frame_window(a, f, s_win);
 #endif
             __syncthreads();
-#if CFS_TILE
-            tile.n_rep = s_rep[0];
-            tile.stride = s_rep[1];
-            tile.rep_off = ((int)(threadIdx.x >> 5) % tile.n_rep) * tile.stride;
-#endif
             cfs_build_ktab(s_T, s_ncmp, s_kt);
             __syncthreads();
             cur = f;

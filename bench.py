@@ -100,8 +100,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16852608          # (27631360 + 6073856) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "a15279fc3cf0c4b7bfa3f911f6aeaa127f7bcab9"
+RENDER_TRAFFIC_BYTES = 16601216          # (27364864 + 5837568) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "5e53397ca2beb69c278307ff0126f9b076eba196"
 
 
 def _code_only(text: str) -> str:

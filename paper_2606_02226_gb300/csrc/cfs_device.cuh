@@ -442,24 +442,24 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
 {
     const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
     const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
-    if (alive && ix >= 0 && iy >= 0) {
-        const int4 g = tl.win[ch];
-        const u32 lx = (u32)(ix - g.x), ly = (u32)(iy - g.y);
-        const u32 w = (u32)g.z & 0xFFFFu, h = (u32)g.z >> 16;
-        if (lx < w && ly < h) {
-            const u32 idx = (u32)g.w + ly * w + lx;
+    /* the window test first: a bin inside a window (whose corner is never
+     * negative) is a valid bin, so most splats skip the validity test */
+    const int4 g = tl.win[ch];
+    const u32 lx = (u32)(ix - g.x), ly = (u32)(iy - g.y);
+    const u32 w = (u32)g.z & 0xFFFFu, h = (u32)g.z >> 16;
+    if (alive && lx < w && ly < h) {
+        const u32 idx = (u32)g.w + ly * w + lx;
 #if CFS_WARP_AGG
-            const u32 act = __activemask();
-            const u32 peers = __match_any_sync(act, idx);
-            if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(tl.cnt + idx, __popc(peers));
+        const u32 act = __activemask();
+        const u32 peers = __match_any_sync(act, idx);
+        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(tl.cnt + idx, __popc(peers));
 #else
-            atomicAdd(tl.cnt + idx, 1u);
+        atomicAdd(tl.cnt + idx, 1u);
 #endif
-        } else {
-            u32* base = reinterpret_cast<u32*>(t.data);
-            const size_t off = ((size_t)ch * (size_t)t.H + (size_t)iy) * (size_t)t.W + (size_t)ix;
-            cfs_red_add_u32(base + off, 1u);
-        }
+    } else if (alive && ix >= 0 && iy >= 0) {
+        u32* base = reinterpret_cast<u32*>(t.data);
+        const size_t off = ((size_t)ch * (size_t)t.H + (size_t)iy) * (size_t)t.W + (size_t)ix;
+        cfs_red_add_u32(base + off, 1u);
     } else {
         disc += 1;
     }

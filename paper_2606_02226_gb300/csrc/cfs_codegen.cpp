@@ -73,7 +73,7 @@ static void emit_gen_map(std::ostringstream& s, const ProgramSpec& sp)
         else
             s << "    cfs_affine3_tab(k, x, y, z, sm);\n";
     } else if (all_circle) {
-        s << "    cfs_circle(sm.prm2[0][k].x, x, y);\n    (void)z;\n";
+        s << "    cfs_circle(sm.prm4[0][k].x, x, y);\n    (void)z;\n";
     } else {
         // maps of different kinds: the fused switch
         s << "    switch (k) {\n";

@@ -56,7 +56,7 @@ __device__ __forceinline__ u32 cfs_word(uint4 r, u32 s)
 #define CFS_STARS_TAB 0
 #endif
 struct CfsSmem {
-    float2 prm2[6][CFS_A_MAX_MAPS];           /* map params, pairs (0,1) (2,3) ... */
+    float4 prm4[3][CFS_A_MAX_MAPS];           /* map k's params 4j..4j+3 at [j][k] */
     float4 pal[CFS_A_MAX_TARGETS][CFS_A_MAX_MAPS];
     u32 pal8[CFS_A_MAX_TARGETS][CFS_A_MAX_MAPS];
 #if CFS_STARS_TAB
@@ -69,9 +69,10 @@ struct CfsSmem {
 
 __device__ __forceinline__ void cfs_load_smem(const cfs_launch_args& a, CfsSmem& sm)
 {
-    for (int t = threadIdx.x; t < 6 * CFS_A_MAX_MAPS; t += blockDim.x) {
+    for (int t = threadIdx.x; t < 3 * CFS_A_MAX_MAPS; t += blockDim.x) {
         const int j = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
-        sm.prm2[j][k] = make_float2(a.sys.prm[2 * j][k], a.sys.prm[2 * j + 1][k]);
+        sm.prm4[j][k] = make_float4(a.sys.prm[4 * j][k], a.sys.prm[4 * j + 1][k],
+                                    a.sys.prm[4 * j + 2][k], a.sys.prm[4 * j + 3][k]);
     }
     for (int t = threadIdx.x; t < CFS_A_MAX_TARGETS * CFS_A_MAX_MAPS; t += blockDim.x) {
         const int g = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
@@ -85,9 +86,11 @@ __device__ __forceinline__ void cfs_load_smem(const cfs_launch_args& a, CfsSmem&
 /* Affine 2D map k from the shared table: x' = fma(a, x, fma(b, y, e)). */
 __device__ __forceinline__ void cfs_affine2_tab(int k, float& x, float& y, const CfsSmem& sm)
 {
-    const float2 ab = sm.prm2[0][k], cd = sm.prm2[1][k], ef = sm.prm2[2][k];
-    const float nx = fmaf(ab.x, x, fmaf(ab.y, y, ef.x));
-    const float ny = fmaf(cd.x, x, fmaf(cd.y, y, ef.y));
+    /* (a, b, c, d) in one 16-byte load, (e, f) in one 8-byte load */
+    const float4 m = sm.prm4[0][k];
+    const float2 ef = *reinterpret_cast<const float2*>(&sm.prm4[1][k]);
+    const float nx = fmaf(m.x, x, fmaf(m.y, y, ef.x));
+    const float ny = fmaf(m.z, x, fmaf(m.w, y, ef.y));
     x = nx;
     y = ny;
 }
@@ -96,11 +99,10 @@ __device__ __forceinline__ void cfs_affine2_tab(int k, float& x, float& y, const
 __device__ __forceinline__ void cfs_affine3_tab(int k, float& x, float& y, float& z,
                                                 const CfsSmem& sm)
 {
-    const float2 m01 = sm.prm2[0][k], m23 = sm.prm2[1][k], m45 = sm.prm2[2][k];
-    const float2 m67 = sm.prm2[3][k], m89 = sm.prm2[4][k], mab = sm.prm2[5][k];
-    const float nx = fmaf(m01.x, x, fmaf(m01.y, y, fmaf(m23.x, z, m89.y)));
-    const float ny = fmaf(m23.y, x, fmaf(m45.x, y, fmaf(m45.y, z, mab.x)));
-    const float nz = fmaf(m67.x, x, fmaf(m67.y, y, fmaf(m89.x, z, mab.y)));
+    const float4 p0 = sm.prm4[0][k], p1 = sm.prm4[1][k], p2 = sm.prm4[2][k];
+    const float nx = fmaf(p0.x, x, fmaf(p0.y, y, fmaf(p0.z, z, p2.y)));
+    const float ny = fmaf(p0.w, x, fmaf(p1.x, y, fmaf(p1.y, z, p2.z)));
+    const float nz = fmaf(p1.z, x, fmaf(p1.w, y, fmaf(p2.x, z, p2.w)));
     x = nx;
     y = ny;
     z = nz;

@@ -521,9 +521,10 @@ __device__ __forceinline__ void cfs_flush_frame_discards(const cfs_launch_args& 
 __device__ __forceinline__ void cfs_load_frame(const cfs_dev_frame& fr, CfsSmem& sm, u32* s_T,
                                                cfs_dev_target* s_tg)
 {
-    for (int t = threadIdx.x; t < 6 * CFS_A_MAX_MAPS; t += blockDim.x) {
+    for (int t = threadIdx.x; t < 3 * CFS_A_MAX_MAPS; t += blockDim.x) {
         const int jj = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;
-        sm.prm2[jj][k] = make_float2(fr.prm[2 * jj][k], fr.prm[2 * jj + 1][k]);
+        sm.prm4[jj][k] = make_float4(fr.prm[4 * jj][k], fr.prm[4 * jj + 1][k],
+                                     fr.prm[4 * jj + 2][k], fr.prm[4 * jj + 3][k]);
     }
     for (int t = threadIdx.x; t < CFS_NT_ARR * CFS_A_MAX_MAPS; t += blockDim.x) {
         const int g = t / CFS_A_MAX_MAPS, k = t % CFS_A_MAX_MAPS;

@@ -102,6 +102,40 @@ def test_batch_burn_in_on_and_off_block_boundaries(torch_cuda, ilp, burn_in):
         assert int(_host(tens[f]).sum()) == frames[f].n_points * max(0, 60 - burn_in)
 
 
+@pytest.mark.parametrize("C,words,ilp", [(1, 1024, 2), (1, 4096, 1), (16, 1024, 2),
+                                         (16, 8192, 1), (3, 2048, 2)])
+def test_batch_windows_with_other_channel_counts(torch_cuda, C, words, ilp):
+    # one window per channel of a C-channel histogram (channel = map index
+    # mod C; with 16 channels and at most 8 maps half of them stay empty),
+    # the windows' counters packed one channel after the other: the
+    # histograms are the oracle's bit for bit
+    from paper_2606_02226_gb300 import cfs
+    frames = W.animation_frames(n_frames=8, seed=11, min_log2=9, max_log2=12,
+                                resolutions=(64, 128))
+    chain = cfs.Chain([W.Op("splat", (0,))], 2)
+    items, descs, tens, begin = [], [], [], 0
+    for f, fr in enumerate(frames):
+        t = W.Target("hist_u32", fr.W, fr.W, C, W.ANIMATION_VIEW)
+        ten = cfs.alloc_target(t)
+        items.append((cfs.System(fr.system), fr.n_points, begin, f, [t], [ten]))
+        descs.append(t)
+        tens.append(ten)
+        begin += fr.n_points
+    b = cfs.Batch(chain, items, iters=60, burn_in=20, seed=8)
+    b.set_plan(ilp=ilp, window=1, window_words=words, chunk=256)
+    b.launch(clear=True)
+    torch_cuda.cuda.synchronize()
+    win = b.windows()
+    assert win.shape == (len(frames), C, 4)
+    for f in range(len(frames)):
+        area = [(int(x1) - int(x0) + 1) * (int(y1) - int(y0) + 1)
+                for x0, y0, x1, y1 in win[f] if x1 >= x0]
+        assert 0 < sum(area) <= words, (f, area)
+    ref, rdisc = _oracle(frames, descs, 60, 20, 8)
+    for f in range(len(frames)):
+        assert np.array_equal(_host(tens[f]), ref[f]), f
+
+
 @pytest.mark.parametrize("words", [1024, 4096, 53248])
 def test_batch_windows_lie_in_the_counter_budget(torch_cuda, words):
     # the pre-pass places one window per histogram channel: inside the

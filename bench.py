@@ -100,8 +100,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16601216          # (27364864 + 5837568) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "5e53397ca2beb69c278307ff0126f9b076eba196"
+RENDER_TRAFFIC_BYTES = 16629120          # (27533056 + 5725184) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "7c5f8e7445677962711638a6c77a1bec73501b00"
 
 
 def _code_only(text: str) -> str:
@@ -378,31 +378,51 @@ def run_cfs(args, wl):
     value = world * wl.point_steps / (mean_step * 1e-3)
 
     # ---- end to end through the public API with host buffers ------------
+    # Every step builds the system and chain from host descriptions, renders
+    # and reads both layers back to pinned host memory.  Two sets of layers
+    # alternate, so that step n's read-back (on a copy stream) overlaps step
+    # n + 1's rendering; a step reuses its layers only after their previous
+    # read-back, and the timed region ends when the last read-back has.
     e2e = None
-    host = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in targets]
-    d2h = sum(h.numel() * h.element_size() for h in host)
+    layers = [targets, [torch.empty_like(t) for t in targets]]
+    hosts = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in targets]
+             for _ in range(2)]
+    d2h = sum(h.numel() * h.element_size() for h in hosts[0])
+    copy_stream = torch.cuda.Stream()
+    rendered = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [None, None]
     torch.cuda.synchronize()
     n_e2e = max(2, min(K, 5))
     t0 = time.perf_counter()
-    for _ in range(n_e2e):
+    for n in range(n_e2e):
+        buf = n % 2
+        if copied[buf] is not None:
+            stream.wait_event(copied[buf])           # its previous read-back is done
         ss = [cfs.System(j.system) for j in jobs]        # inputs handed over from the host
         ch = cfs.Chain(wl.chain, 2, fast_trig=args.fast_trig)
-        cfs.target_clear(wl.targets, targets, stream)
+        cfs.target_clear(wl.targets, layers[buf], stream)
         for s, j in zip(ss, jobs):
-            cfs.render(s, ch, wl.targets, targets, n_points=j.n_points, iters=wl.iters,
+            cfs.render(s, ch, wl.targets, layers[buf], n_points=j.n_points, iters=wl.iters,
                        burn_in=wl.burn_in, seed=wl.seed, system_id=j.system_id,
                        point_begin=j.point_begin, stream=stream)
-        for h, t in zip(host, targets):
-            h.copy_(t, non_blocking=True)
-        torch.cuda.synchronize()
+        rendered[buf].record(stream)
+        copy_stream.wait_event(rendered[buf])
+        with torch.cuda.stream(copy_stream):
+            for h, t in zip(hosts[buf], layers[buf]):
+                h.copy_(t, non_blocking=True)
+        copied[buf] = torch.cuda.Event()
+        copied[buf].record(copy_stream)
+    torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / n_e2e
+    del layers[1]
     e2e = {"value": wl.point_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": len(jobs) * cfs.render_arg_bytes(),
            "d2h_bytes_per_step": d2h,
            "note": "system and chain built from host descriptions and passed through the C "
                    "ABI each step: the inputs travel host to device in each render launch's "
                    "argument block (the h2d bytes); both layers read back to pinned host "
-                   "memory"}
+                   "memory, each step's read-back overlapping the next step's rendering "
+                   "(two sets of layers)"}
 
     if rank != 0:
         if world > 1:
@@ -543,14 +563,16 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
             "timing": f"median of {reps} frames, L2 flushed (256 MiB write) before each"}
 
 
-# Warp instructions the batch kernel issues per point-step: ncu
-# smsp__inst_executed.sum of one full 256-frame launch under the tuned plan
-# (one pass; profiles/cfs_batch_kernel_animation.md).  Valid only for the
-# program it was taken on: the bench reports it while the batch program's
-# hash (as for the render traffic) and the tuned plan's program knobs match.
-BATCH_WARP_INSTR = 1.8171e11             # per launch of the 256 frames (7.78e10 point-steps)
-BATCH_INSTR_SOURCE_SHA1 = "17fffafa05c4c8c8475a620efe53372ed838f309"
-BATCH_INSTR_PLAN = {"ilp": 2, "tile": 1, "warp_agg": 0}
+# Warp instructions the batch kernel issues per launch of the 256 frames
+# (7.78e10 point-steps), by trajectories per thread: ncu smsp__inst_executed.sum
+# of one full launch (one pass; profiles/cfs_batch_kernel_animation.md).
+# Valid only for the code they were taken on: the bench reports them while the
+# hash of the batch program under the default knobs (the same device headers
+# and generator as every plan's program) matches, and for the tuned plan's
+# trajectories per thread with the window on and no warp aggregation.
+BATCH_WARP_INSTR = {1: 1.7581e11, 2: 1.6984e11}   # (2: counted under 4096-point items)
+BATCH_INSTR_SOURCE_SHA1 = "6fe67bec03c13962750f38ec7484904db9f818e1"
+BATCH_INSTR_PLAN = {"tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 
 
@@ -575,8 +597,9 @@ def batch_issue(point_steps: int, ms: float, sha1: str, tuning: dict):
     scheduler per clock at the maximum SM clock; null when the count was
     taken on another program."""
     peak = SM_COUNT * SCHEDULERS_PER_SM * SM_MAX_MHZ * 1e6
-    same = sha1 == BATCH_INSTR_SOURCE_SHA1 and all(tuning.get(k) == v
-                                                    for k, v in BATCH_INSTR_PLAN.items())
+    count = BATCH_WARP_INSTR.get(tuning.get("ilp"))
+    same = (sha1 == BATCH_INSTR_SOURCE_SHA1 and count is not None and
+            all(tuning.get(k) == v for k, v in BATCH_INSTR_PLAN.items()))
     out = {"bound": "alu", "peak": peak, "unit": "warp instructions/s", "program_sha1": sha1,
            "peak_source": "152 SMs x 4 schedulers x 1 warp instruction per clock at 2070 MHz; "
                           "instructions per launch from an ncu count of the full batch",
@@ -586,9 +609,9 @@ def batch_issue(point_steps: int, ms: float, sha1: str, tuning: dict):
         out.update({"achieved": None, "frac": None,
                     "instructions_per_point_step": None})
         return out
-    rate = BATCH_WARP_INSTR / (ms * 1e-3)
+    rate = count / (ms * 1e-3)
     out.update({"achieved": rate, "frac": rate / peak,
-                "instructions_per_point_step": 32 * BATCH_WARP_INSTR / point_steps})
+                "instructions_per_point_step": 32 * count / point_steps})
     return out
 
 

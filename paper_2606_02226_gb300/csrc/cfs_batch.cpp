@@ -181,7 +181,6 @@ uint32_t batch_spec_defaults(ProgramSpec& sp)
     sp.min_blocks = 2;
     sp.spill_allowance = 64;
     sp.depth_test = 1;
-    sp.tile_reps = 1;
     // privatized window: when the chain splats once, into a histogram
     sp.tile = (sp.splats.size() == 1 && sp.splats[0].kind == CFS_TARGET_HIST_U32 &&
                sp.scribble.empty()) ? 1 : 0;

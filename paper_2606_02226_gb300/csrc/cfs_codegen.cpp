@@ -23,7 +23,7 @@ std::string ProgramSpec::key() const
     std::ostringstream s;
     s << "m" << int(mode) << ".d" << dim << ".n" << n_maps << ".c" << n_cmp << ".r" << reuse
       << ".t" << n_targets << ".z" << depth_test << ".b" << block << "." << min_blocks << "."
-      << spill_allowance << ".p" << tile << warp_agg << "." << tile_reps << ".f" << fast_trig
+      << spill_allowance << ".p" << tile << warp_agg << ".f" << fast_trig
       << ".u" << unroll << ".i" << ilp << ".k";
     for (int j = 0; j < n_maps; ++j) s << map_kind[j];
     s << ".o";
@@ -327,7 +327,6 @@ std::string generate_source(const ProgramSpec& sp)
     s << "#define CFS_CLOUD " << (sp.mode == Mode::Cloud ? 1 : 0) << "\n";
     s << "#define CFS_TILE " << (sp.tile ? 1 : 0) << "\n";
     s << "#define CFS_WARP_AGG " << (sp.warp_agg ? 1 : 0) << "\n";
-    s << "#define CFS_TILE_REPS " << (sp.tile_reps > 0 ? sp.tile_reps : 1) << "\n";
     s << "#define CFS_TILE_C " << (sp.splats.empty() ? 1 : sp.splats[0].channels) << "\n";
     s << "#define CFS_POINTS " << (sp.mode == Mode::Points ? 1 : 0) << "\n";
     s << "#define CFS_DEPTH_TEST " << sp.depth_test << "\n";

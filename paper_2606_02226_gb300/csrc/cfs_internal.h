@@ -69,7 +69,6 @@ struct ProgramSpec {
     int spill_allowance = 0;   // bytes of spill stores accepted at min_blocks
     int tile = 0;              // batch: privatized shared window for the first splat
     int warp_agg = 0;          // warp-aggregated shared atomics in that window
-    int tile_reps = 1;         // at most this many copies of a small window
     int fast_trig = 0;         // chain trigonometry: 0 libm, 1 reduced argument + hardware
     int unroll = 4;            // copies of the step code in the step loop (4, 2, 1)
     int ilp = 1;               // batch: trajectories stepped together per thread (1, 2)

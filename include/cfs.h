@@ -354,7 +354,9 @@ typedef struct {
     int window;             /* privatized shared-memory window for the chain's histogram
                                splat: 0 off, 1 on (ignored unless the chain splats once,
                                into a histogram, and is not a scribble) */
-    uint32_t window_words;  /* window capacity in u32 counters: 1024..53248, multiple of 256 */
+    uint32_t window_words;  /* window capacity in u32 counters: 1024..53248, multiple of 256;
+                               the histogram's channels share them in proportion to their
+                               sampled splats, one window (pixel box) per channel */
     int warp_agg;           /* window adds aggregated across a warp (match.any): 0 or 1 */
     uint32_t chunk;         /* points per work item: a multiple of 32 in 32..2^20 */
 } cfs_batch_plan;

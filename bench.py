@@ -100,8 +100,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16629120          # (27533056 + 5725184) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "7c5f8e7445677962711638a6c77a1bec73501b00"
+RENDER_TRAFFIC_BYTES = 16574848          # (27284480 + 5865216) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "b9d7fb198f0377fc6a1ac341a215bc39c2a51474"
 
 
 def _code_only(text: str) -> str:
@@ -571,7 +571,7 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
 # and generator as every plan's program) matches, and for the tuned plan's
 # trajectories per thread with the window on and no warp aggregation.
 BATCH_WARP_INSTR = {1: 1.7581e11, 2: 1.6984e11}   # (2: counted under 4096-point items)
-BATCH_INSTR_SOURCE_SHA1 = "6fe67bec03c13962750f38ec7484904db9f818e1"
+BATCH_INSTR_SOURCE_SHA1 = "efaf006004352e534b0f349b4168fb465cf11a50"
 BATCH_INSTR_PLAN = {"tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 

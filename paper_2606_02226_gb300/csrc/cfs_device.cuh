@@ -380,6 +380,16 @@ __device__ __forceinline__ int cfs_bin(float u, float lo, float hi, float scale,
     return in ? b : -1;
 }
 
+/* The same bin with its validity apart: ok is lo <= u <= hi (false for NaN),
+ * and then the bin lies in 0..n-1; the value is meaningless when !ok.  (The
+ * splats test ok instead of a -1.) */
+__device__ __forceinline__ int cfs_bin_ok(float u, float lo, float hi, float scale, int n,
+                                          bool& ok)
+{
+    ok = (u >= lo) && (u <= hi);
+    return min(__float2int_rd((u - lo) * scale), n - 1);
+}
+
 /* The splat reductions carry no "memory" clobber: nothing in a kernel reads
  * a target except the depth test, which is correct under any order (keys
  * only decrease), so the compiler may schedule them freely. */
@@ -413,9 +423,10 @@ __device__ __forceinline__ u64 cfs_ld_relaxed_u64(const u64* p)
 __device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x, float y,
                                                bool alive, int ch, u32& disc)
 {
-    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
-    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
-    if (alive && ix >= 0 && iy >= 0) {
+    bool okx, oky;
+    const int ix = cfs_bin_ok(x, t.x0, t.x1, t.sx, t.W, okx);
+    const int iy = cfs_bin_ok(y, t.y0, t.y1, t.sy, t.H, oky);
+    if (alive && okx && oky) {
         u32* base = reinterpret_cast<u32*>(t.data);
         const size_t off = ((size_t)ch * (size_t)t.H + (size_t)iy) * (size_t)t.W + (size_t)ix;
         cfs_red_add_u32(base + off, 1u);
@@ -442,14 +453,14 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
                                                     float x, float y, bool alive, int ch,
                                                     u32& disc)
 {
-    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
-    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
-    /* the window test first: a bin inside a window (whose corner is never
-     * negative) is a valid bin, so most splats skip the validity test */
+    bool okx, oky;
+    const int ix = cfs_bin_ok(x, t.x0, t.x1, t.sx, t.W, okx);
+    const int iy = cfs_bin_ok(y, t.y0, t.y1, t.sy, t.H, oky);
+    const bool ok = alive && okx && oky;
     const int4 g = tl.win[ch];
     const u32 lx = (u32)(ix - g.x), ly = (u32)(iy - g.y);
     const u32 w = (u32)g.z & 0xFFFFu, h = (u32)g.z >> 16;
-    if (alive && lx < w && ly < h) {
+    if (ok && lx < w && ly < h) {
         const u32 idx = (u32)g.w + ly * w + lx;
 #if CFS_WARP_AGG
         const u32 act = __activemask();
@@ -458,7 +469,7 @@ __device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, con
 #else
         atomicAdd(tl.cnt + idx, 1u);
 #endif
-    } else if (alive && ix >= 0 && iy >= 0) {
+    } else if (ok) {
         u32* base = reinterpret_cast<u32*>(t.data);
         const size_t off = ((size_t)ch * (size_t)t.H + (size_t)iy) * (size_t)t.W + (size_t)ix;
         cfs_red_add_u32(base + off, 1u);
@@ -493,9 +504,10 @@ __device__ __forceinline__ void cfs_flush_tile(const cfs_dev_target& t, const Cf
 __device__ __forceinline__ void cfs_splat_rgba(const cfs_dev_target& t, float x, float y,
                                                bool alive, float4 col, u32& disc)
 {
-    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
-    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
-    if (alive && ix >= 0 && iy >= 0) {
+    bool okx, oky;
+    const int ix = cfs_bin_ok(x, t.x0, t.x1, t.sx, t.W, okx);
+    const int iy = cfs_bin_ok(y, t.y0, t.y1, t.sy, t.H, oky);
+    if (alive && okx && oky) {
         float* base = reinterpret_cast<float*>(t.data);
         const size_t off = ((size_t)iy * (size_t)t.W + (size_t)ix) * 4;
         cfs_red_add_v4f32(base + off, col);
@@ -511,9 +523,10 @@ __device__ __forceinline__ void cfs_splat_rgba(const cfs_dev_target& t, float x,
 __device__ __forceinline__ void cfs_splat_depth(const cfs_dev_target& t, float x, float y,
                                                 float z, bool alive, u32 rgba8, u32& disc)
 {
-    const int ix = cfs_bin(x, t.x0, t.x1, t.sx, t.W);
-    const int iy = cfs_bin(y, t.y0, t.y1, t.sy, t.H);
-    if (alive && ix >= 0 && iy >= 0) {
+    bool okx, oky;
+    const int ix = cfs_bin_ok(x, t.x0, t.x1, t.sx, t.W, okx);
+    const int iy = cfs_bin_ok(y, t.y0, t.y1, t.sy, t.H, oky);
+    if (alive && okx && oky) {
         u64* base = reinterpret_cast<u64*>(t.data);
         u64* p = base + ((size_t)iy * (size_t)t.W + (size_t)ix);
         const u64 key = ((u64)__float_as_uint(z) << 32) | (u64)rgba8;

@@ -100,8 +100,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16574848          # (27284480 + 5865216) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "b9d7fb198f0377fc6a1ac341a215bc39c2a51474"
+RENDER_TRAFFIC_BYTES = 16717312          # (27507968 + 5926656) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "8b215813b80ddb1937f669bdb94227fea771212c"
 
 
 def _code_only(text: str) -> str:
@@ -570,8 +570,8 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
 # hash of the batch program under the default knobs (the same device headers
 # and generator as every plan's program) matches, and for the tuned plan's
 # trajectories per thread with the window on and no warp aggregation.
-BATCH_WARP_INSTR = {1: 1.7581e11, 2: 1.6984e11}   # (2: counted under 4096-point items)
-BATCH_INSTR_SOURCE_SHA1 = "efaf006004352e534b0f349b4168fb465cf11a50"
+BATCH_WARP_INSTR = {1: 1.6409e11, 2: 1.5892e11}   # (2: counted under 4096-point items)
+BATCH_INSTR_SOURCE_SHA1 = "6921f2f95e8bd8be1a55d11103107814d6738697"
 BATCH_INSTR_PLAN = {"tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 

@@ -422,7 +422,8 @@ def run_cfs(args, wl):
                    "ABI each step: the inputs travel host to device in each render launch's "
                    "argument block (the h2d bytes); both layers read back to pinned host "
                    "memory, each step's read-back overlapping the next step's rendering "
-                   "(two sets of layers)"}
+                   "(two sets of layers); unlike the device-timed value, no L2 flush "
+                   "between steps, so it can come out slightly above it"}
 
     if rank != 0:
         if world > 1:

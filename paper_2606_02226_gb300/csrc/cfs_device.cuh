@@ -435,6 +435,15 @@ __device__ __forceinline__ void cfs_splat_hist(const cfs_dev_target& t, float x,
     }
 }
 
+/* What a windowed batch splat reads of its target: the frame's values,
+ * copied to the batch kernel's locals once per frame so that they stay in
+ * registers instead of being read from shared memory on every splat. */
+struct CfsBinTarget {
+    unsigned long long data;
+    int W, H;
+    float x0, x1, sx, y0, y1, sy;
+};
+
 /* The privatized window of a batch frame's u32 histogram: one pixel box
  * per channel (a channel's splats come from its own maps, whose images are
  * smaller copies of the attractor, so each channel's box sits over that
@@ -449,9 +458,9 @@ struct CfsTile {
 /* u32 histogram splat that adds to the shared window of its channel when
  * the bin lies in it (one shared atomic per group of lanes hitting the same
  * counter with CFS_WARP_AGG) and to global memory otherwise. */
-__device__ __forceinline__ void cfs_splat_hist_tile(const cfs_dev_target& t, const CfsTile& tl,
-                                                    float x, float y, bool alive, int ch,
-                                                    u32& disc)
+template <class T>
+__device__ __forceinline__ void cfs_splat_hist_tile(const T& t, const CfsTile& tl, float x,
+                                                    float y, bool alive, int ch, u32& disc)
 {
     bool okx, oky;
     const int ix = cfs_bin_ok(x, t.x0, t.x1, t.sx, t.W, okx);

@@ -792,6 +792,14 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
     const cfs_dev_frame* frames = reinterpret_cast<const cfs_dev_frame*>(a.frames);
     u32* counter = reinterpret_cast<u32*>(a.work_counter);
     int cur = -1;
+#if CFS_TILE
+    /* the windowed chain splats once, into target 0: its bin values in
+     * registers (the flush still reads s_tg) */
+    CfsBinTarget bt[1] = {};
+#define CFS_BATCH_TG bt
+#else
+#define CFS_BATCH_TG s_tg
+#endif
     u32 disc[CFS_NT_ARR];
 #pragma unroll
     for (int t = 0; t < CFS_NT_ARR; ++t) disc[t] = 0;
@@ -840,6 +848,10 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
             __syncthreads();
             cfs_build_ktab(s_T, s_ncmp, s_kt);
             __syncthreads();
+#if CFS_TILE
+            bt[0] = CfsBinTarget{s_tg[0].data, s_tg[0].W, s_tg[0].H, s_tg[0].x0, s_tg[0].x1,
+                                 s_tg[0].sx, s_tg[0].y0, s_tg[0].y1, s_tg[0].sy};
+#endif
             cur = f;
         }
         const CfsChooseKtab choose{s_T, s_kt, s_ncmp};
@@ -875,17 +887,17 @@ cfs_batch_kernel(const __grid_constant__ cfs_launch_args a)
             if (j2 < j1) {
                 float x2, y2, z2;
                 start_of(j2, x2, y2, z2);
-                cfs_run_point2(a, choose, s_tg, sm, pbeg + j, pbeg + j2, sid, x, y, z, x2, y2,
+                cfs_run_point2(a, choose, CFS_BATCH_TG, sm, pbeg + j, pbeg + j2, sid, x, y, z, x2, y2,
                                z2, disc, tile);
             } else {
-                cfs_run_point(a, choose, s_tg, sm, pbeg + j, sid, x, y, z, disc, tile);
+                cfs_run_point(a, choose, CFS_BATCH_TG, sm, pbeg + j, sid, x, y, z, disc, tile);
             }
         }
 #else
         for (u32 j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             float x, y, z;
             start_of(j, x, y, z);
-            cfs_run_point(a, choose, s_tg, sm, pbeg + j, sid, x, y, z, disc, tile);
+            cfs_run_point(a, choose, CFS_BATCH_TG, sm, pbeg + j, sid, x, y, z, disc, tile);
         }
 #endif
         __syncthreads();

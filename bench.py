@@ -100,8 +100,8 @@ def measure_smem_atomic_peak(torch, cfs, dev, reps: int = 3):
 # GPU machine computes: the occupancy search (fewer blocks per SM while ptxas
 # spills) depends on the NVRTC build the process loads, so the generated text
 # can differ between machines.
-RENDER_TRAFFIC_BYTES = 16717312          # (27507968 + 5926656) / 2, launches 1 and 2 of a frame
-RENDER_TRAFFIC_SOURCE_SHA1 = "8b215813b80ddb1937f669bdb94227fea771212c"
+RENDER_TRAFFIC_BYTES = 16654976          # (27533056 + 5776896) / 2, launches 1 and 2 of a frame
+RENDER_TRAFFIC_SOURCE_SHA1 = "299f853b513ea714b0c2aae0b5442704db9b7803"
 
 
 def _code_only(text: str) -> str:
@@ -571,8 +571,8 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
 # hash of the batch program under the default knobs (the same device headers
 # and generator as every plan's program) matches, and for the tuned plan's
 # trajectories per thread with the window on and no warp aggregation.
-BATCH_WARP_INSTR = {1: 1.6409e11, 2: 1.5892e11}   # (2: counted under 4096-point items)
-BATCH_INSTR_SOURCE_SHA1 = "6921f2f95e8bd8be1a55d11103107814d6738697"
+BATCH_WARP_INSTR = {2: 1.5009e11}       # (one trajectory per thread: not counted)
+BATCH_INSTR_SOURCE_SHA1 = "c4bf7aee1a244ec9098f29dd029db2992597668a"
 BATCH_INSTR_PLAN = {"tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 

@@ -571,7 +571,7 @@ def bench_square(torch, cfs, dev, stream, reps: int = 20):
 # hash of the batch program under the default knobs (the same device headers
 # and generator as every plan's program) matches, and for the tuned plan's
 # trajectories per thread with the window on and no warp aggregation.
-BATCH_WARP_INSTR = {2: 1.5009e11}       # (one trajectory per thread: not counted)
+BATCH_WARP_INSTR = {1: 1.5580e11, 2: 1.5009e11}
 BATCH_INSTR_SOURCE_SHA1 = "c4bf7aee1a244ec9098f29dd029db2992597668a"
 BATCH_INSTR_PLAN = {"tile": 1, "warp_agg": 0}
 SM_COUNT, SCHEDULERS_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
@@ -650,7 +650,18 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
     ms_default = timed_batch("batch_default_plan")
     # the autotuner times the candidate plans on these frames (80 steps each)
     tuning = b.tune(trial_iters=80, stream=stream)
-    ms = timed_batch("batch_tuned_plan")
+    tuned_ilp = int(b.plan()["ilp"])
+    ms = timed_batch(f"batch_tuned_ilp{tuned_ilp}")
+    # the tuned plan with the other number of trajectories per thread, for
+    # comparison (only when the tuner kept no per-class choices, which a new
+    # plan would clear); then the tuned plan again, for the launches after
+    other_ilp, ms_other = (1 if tuned_ilp == 2 else 2), None
+    if not tuning.get("classes_used"):
+        b.set_plan(ilp=other_ilp)
+        ms_other = timed_batch(f"batch_other_ilp{other_ilp}")
+        b.set_plan(ilp=tuned_ilp)
+        b.launch(clear=True, stream=stream)
+        torch.cuda.synchronize()
     n_pts = sum(fr.n_points for fr in frames)
     bytes_targets = sum(4 * 4 * fr.W * fr.W for fr in frames)
     info = b.info()
@@ -714,6 +725,7 @@ def bench_batch(torch, cfs, dev, stream, reps: int = 3, n_frames: int = 256):
             "target_bytes": bytes_targets, "items": info["n_items"], "chunk": info["chunk"],
             "grid": info["grid"], "gpu_launches_per_batch": 2, "display": display,
             "autotuned": tuning, "ms_per_batch_default_plan": ms_default,
+            "ms_per_batch_other_ilp": {"ilp": other_ilp, "ms": ms_other},
             "frames_per_s_with_display": n_frames / ((ms + disp_ms) * 1e-3),
             "splats_in_windows": n_smem / n_splat,
             "roofline": {"bound": "atomic", "kernel": "cfs_batch_kernel",

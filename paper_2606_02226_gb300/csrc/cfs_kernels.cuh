@@ -593,9 +593,10 @@ __device__ __forceinline__ void cfs_window_shape(int q, int cap, int bw, int bh,
  * frame_bbox[f * CFS_A_MAX_MAPS + c] (empty when no sample of the channel
  * landed).  The channels share the tile_cap counters in proportion to
  * their sampled splats (a channel's capacity, in pixels, is its share,
- * rounded down, so the windows together never pass tile_cap).  A sample's channel is
- * its map index mod CFS_TILE_C (a chain that recolours moves splats to
- * other channels; they then miss the window more often, nothing else).
+ * rounded down, so the windows together never pass tile_cap).  A sample's
+ * channel is its map index mod CFS_TILE_C (a chain that recolours moves
+ * splats to other channels; they then miss the window more often, nothing
+ * else).
  * When the channel's sampled box fits its window, the window is that box.
  * Otherwise the channel's samples are binned into a coarse grid over the
  * box, and of the windows of the channel's capacity (five aspect ratios,
@@ -604,8 +605,8 @@ __device__ __forceinline__ void cfs_window_shape(int q, int cap, int bw, int bh,
  * where privatizing the counters saves the most L2 reductions.  Splats
  * outside the windows still go to global memory, so the choice changes the
  * speed only, never the histogram.  The trajectories are run again for
- * every pass (two per channel at most): they are cheaper than storing the
- * samples. */
+ * every pass (one for the channels' splat counts, then two per channel at
+ * most): that is cheaper than storing the samples. */
 extern "C" __global__ void __launch_bounds__(CFS_BLOCK)
 cfs_bbox_kernel(const __grid_constant__ cfs_launch_args a)
 {

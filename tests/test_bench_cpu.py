@@ -79,3 +79,21 @@ def test_clock_samples_summary():
     cs2.proc = _Proc()
     cs2.lines = ["0, 1500, 2070, 700, 0x8, Active, Not Active, Active, Not Active"]
     assert cs2.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_batch_issue_only_for_the_counted_program():
+    # the batch's issue figure uses instruction counts taken on one program:
+    # reported for that program's hash and a plan whose trajectories per
+    # thread were counted, null otherwise
+    steps = 259390750 * 300
+    tuned = {"ilp": 2, "tile": 1, "warp_agg": 0}
+    ok = bench.batch_issue(steps, 165.0, bench.BATCH_INSTR_SOURCE_SHA1, tuned)
+    peak = bench.SM_COUNT * bench.SCHEDULERS_PER_SM * bench.SM_MAX_MHZ * 1e6
+    assert ok["frac"] == ok["achieved"] / peak
+    assert ok["achieved"] == bench.BATCH_WARP_INSTR[2] / 0.165
+    assert abs(ok["instructions_per_point_step"] - 32 * bench.BATCH_WARP_INSTR[2] / steps) < 1e-9
+    for sha, plan in (("another program", tuned), (bench.BATCH_INSTR_SOURCE_SHA1,
+                                                   dict(tuned, warp_agg=1)),
+                      (bench.BATCH_INSTR_SOURCE_SHA1, dict(tuned, ilp=3))):
+        d = bench.batch_issue(steps, 165.0, sha, plan)
+        assert d["frac"] is None and d["achieved"] is None and d["program_sha1"] == sha

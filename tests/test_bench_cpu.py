@@ -1,7 +1,8 @@
 """The benchmark's CPU-side pieces, no GPU needed: the reference arm (the
 oracle timed on the host cores) prints one JSON line that keeps the contract
-of the main arm's line, and the comment stripping behind the render program's
-hash ignores comments only."""
+of the main arm's line, the comment stripping behind the programs' hashes
+ignores comments only, and the batch's issue figure is given only for the
+program its instruction counts were taken on."""
 import json
 import os
 import subprocess

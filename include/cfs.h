@@ -337,7 +337,9 @@ cfs_status cfs_batch_info(const cfs_batch* batch, uint32_t* n_items, uint32_t* c
  * (x0, y0, x1, y1): the inclusive pixel box of channel c of target 0 whose
  * splats the launch counted in shared memory (every other splat is a
  * global reduction); (0, 0, -1, -1) for none (window off in the plan or
- * for the frame's shape class, or no sample of the channel landed).
+ * for the frame's shape class, no sample of the channel landed, or a
+ * channel's share of the counters below one pixel).  The channels' windows
+ * together hold at most the plan's window_words pixels.
  * Measurement aid: with the frame's histogram it gives the numbers of
  * shared-memory and global splats exactly.  Waits for the launch;
  * CFS_ERR_INVALID_ARG before the first launch. */
